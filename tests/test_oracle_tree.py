@@ -1,0 +1,178 @@
+"""Pins for the oracle's balanced tree (Sec. 2.1.2, eta = 1 median splits;
+Algorithm 2) and connectivity (Eq. 2.2 and the inheritance rule of Sec. 2.1.1):
+invariants, a second independent implementation, and brute force."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_04894_gb300 import inputs
+
+
+def naive_tree(x, levels):
+    """Second, independent implementation of the same reading: full sort of
+    each box on its longest cell axis, floor(n/2) smallest keys to the left."""
+    x = np.asarray(x, float) + 0.0
+    nb = (2 << levels) - 1
+    lo = np.zeros((nb, 3)); hi = np.zeros((nb, 3)); plane = np.zeros(nb)
+    members = [None] * nb
+    members[0] = np.arange(len(x))
+    lo[0], hi[0] = x.min(0), x.max(0)
+    for l in range(levels):
+        for j in range(1 << l):
+            g = (1 << l) - 1 + j
+            idx = members[g]
+            ext = hi[g] - lo[g]
+            ax = int(np.argmax(ext))           # first maximum: x before y before z
+            order = sorted(idx, key=lambda i: (x[i, ax], i))
+            k = len(idx) // 2
+            left = set(order[:k])
+            if len(idx) >= 2:
+                s = 0.5 * (x[order[k - 1], ax] + x[order[k], ax])
+            elif len(idx) == 1:
+                s = x[order[0], ax]
+            else:
+                s = 0.5 * (lo[g, ax] + hi[g, ax])
+            plane[g] = s
+            a, b = 2 * g + 1, 2 * g + 2
+            members[a] = np.array([i for i in idx if i in left], int)
+            members[b] = np.array([i for i in idx if i not in left], int)
+            lo[a], hi[a], lo[b], hi[b] = lo[g], hi[g].copy(), lo[g].copy(), hi[g]
+            hi[a, ax] = s
+            lo[b, ax] = s
+    first_leaf = (1 << levels) - 1
+    perm = np.concatenate([members[g] for g in range(first_leaf, nb)])
+    return perm, lo, hi, plane
+
+
+CASES = [("uniform", 1000, 5), ("uniform", 777, 6), ("plummer", 1500, 6), ("gmm", 1200, 7),
+         ("uniform", 20, 6), ("uniform", 1, 3), ("uniform", 2, 2)]
+
+
+@pytest.mark.parametrize("kind,n,levels", CASES)
+def test_tree_matches_independent_implementation(kind, n, levels):
+    x = inputs.points(kind, n, seed=n)
+    t = oracle.Tree(x, levels, 2, 0.5).tree()
+    perm, lo, hi, plane = naive_tree(x, levels)
+    np.testing.assert_array_equal(t["perm"], perm)
+    np.testing.assert_array_equal(t["lo"], lo)
+    np.testing.assert_array_equal(t["hi"], hi)
+    internal = (1 << levels) - 1
+    np.testing.assert_array_equal(t["plane"][:internal], plane[:internal])
+
+
+def test_tree_with_ties_and_negative_zero():
+    rng = np.random.default_rng(1)
+    x = rng.integers(0, 3, size=(300, 3)).astype(float) - 1.0
+    x[::7] *= -1.0                         # produces -0.0 entries
+    t = oracle.Tree(x, 5, 2, 0.5).tree()
+    perm, lo, hi, _ = naive_tree(x, 5)
+    np.testing.assert_array_equal(t["perm"], perm)
+    np.testing.assert_array_equal(t["lo"], lo)
+
+
+@pytest.mark.parametrize("kind,n,levels", CASES[:4])
+def test_tree_invariants(kind, n, levels):
+    x = inputs.points(kind, n, seed=3) + 0.0
+    t = oracle.Tree(x, levels, 2, 0.5).tree()
+    assert sorted(t["perm"]) == list(range(n))                    # bijection
+    for l in range(levels + 1):
+        for j in range(1 << l):
+            g = (1 << l) - 1 + j
+            cnt = t["count"][g]
+            assert cnt in (n >> l, -((-n) >> l))                  # balanced (Sec. 1)
+            pts = t["perm"][t["begin"][g]:t["begin"][g] + cnt]
+            if l == levels:
+                assert np.all(np.diff(pts) > 0)                   # stable: ascending index
+            assert np.all(x[pts] >= t["lo"][g]) and np.all(x[pts] <= t["hi"][g])
+            np.testing.assert_array_equal(t["centre"][g], 0.5 * (t["lo"][g] + t["hi"][g]))
+            if l < levels:
+                ax = t["axis"][g]
+                ext = t["hi"][g] - t["lo"][g]
+                assert ext[ax] == ext.max() and np.argmax(ext) == ax
+                a, b = 2 * g + 1, 2 * g + 2
+                assert t["count"][a] == cnt // 2
+                la = x[t["perm"][t["begin"][a]:t["begin"][a] + t["count"][a]], ax]
+                rb = x[t["perm"][t["begin"][b]:t["begin"][b] + t["count"][b]], ax]
+                if len(la) and len(rb):
+                    assert la.max() <= t["plane"][g] <= rb.min()
+
+
+def ancestors_weak(t, theta, l, a, b):
+    while l > 0:
+        l -= 1
+        a //= 2
+        b //= 2
+        ga, gb = (1 << l) - 1 + a, (1 << l) - 1 + b
+        if oracle.theta_weak(theta, t["centre"][ga], t["radius"][ga], t["centre"][gb], t["radius"][gb]):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.35, 0.5, 0.8])
+def test_lists_brute_force(theta):
+    x = inputs.points("plummer", 300, seed=4)
+    levels = 5
+    T = oracle.Tree(x, levels, 2, theta)
+    t = T.tree()
+    for l in range(1, levels + 1):
+        wp, ws = T.lists(l, "weak")
+        sp, ss = T.lists(l, "strong")
+        for a in range(1 << l):
+            want_w, want_s = [], []
+            for b in range(1 << l):
+                if ancestors_weak(t, theta, l, a, b):
+                    continue
+                ga, gb = (1 << l) - 1 + a, (1 << l) - 1 + b
+                if oracle.theta_weak(theta, t["centre"][ga], t["radius"][ga], t["centre"][gb], t["radius"][gb]):
+                    want_w.append(b)
+                else:
+                    want_s.append(b)
+            assert list(ws[wp[a]:wp[a + 1]]) == want_w
+            assert list(ss[sp[a]:sp[a + 1]]) == want_s
+
+
+def test_theta_criterion_formula_and_edges():
+    c0, c1 = np.zeros(3), np.array([3.0, 0, 0])
+    # R + theta r <= theta d at equality is weak: r = R = 1, theta = 0.5, d = 3
+    assert oracle.theta_weak(0.5, c0, 1.0, c1, 1.0)
+    assert not oracle.theta_weak(0.5, c0, 1.0, c1, 1.0 + 1e-12)
+    assert not oracle.theta_weak(0.0, c0, 0.0, c1, 0.0)          # theta = 0: never weak
+    assert not oracle.theta_weak(0.5, c0, 0.0, c0, 0.0)          # d = 0: never weak
+    assert oracle.theta_weak(0.5, c0, 0.0, c1, 0.0)
+
+
+@pytest.mark.parametrize("kind,theta", [("uniform", 0.5), ("plummer", 0.4), ("gmm", 0.6)])
+def test_every_source_counted_once(kind, theta):
+    """For every target leaf, sources reached through weak lists at all levels
+    (their whole subtrees) plus strong leaves cover all N points exactly once."""
+    n, levels = 800, 6
+    x = inputs.points(kind, n, seed=2)
+    T = oracle.Tree(x, levels, 2, theta)
+    t = T.tree()
+    lists = {l: T.lists(l, "weak") for l in range(1, levels + 1)}
+    sp, ss = T.lists(levels, "strong")
+    for leaf in range(1 << levels):
+        total = 0
+        for l in range(1, levels + 1):
+            a = leaf >> (levels - l)
+            wp, ws = lists[l]
+            total += sum(t["count"][(1 << l) - 1 + b] for b in ws[wp[a]:wp[a + 1]])
+        total += sum(t["count"][(1 << levels) - 1 + b] for b in ss[sp[leaf]:sp[leaf + 1]])
+        assert total == n
+
+
+def test_list_counts_follow_cost_model_directions():
+    """M2L work rises and P2P work falls with theta and with levels (Sec. 3.2)."""
+    x = inputs.points("uniform", 4000, seed=0)
+
+    def counts(levels, theta):
+        T = oracle.Tree(x, levels, 2, theta)
+        w = sum(len(T.lists(l, "weak")[1]) for l in range(1, levels + 1))
+        return w, len(T.lists(levels, "strong")[1])
+    w1, s1 = counts(7, 0.4)
+    w2, s2 = counts(7, 0.6)
+    assert w2 > w1 and s2 < s1
+    w3, s3 = counts(8, 0.5)
+    w4, s4 = counts(6, 0.5)
+    assert w3 > w4
+    assert s3 * (4000 / 256) ** 2 < s4 * (4000 / 64) ** 2
