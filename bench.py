@@ -1,0 +1,331 @@
+"""Benchmark: Mpoints/s of one balanced-tree FMM solve (fmm_plan + fmm_eval).
+
+Default workload (N=1): 2,000,000 points from a Plummer sphere (scale radius
+0.1, truncated at 10 radii), charges uniform in [-1, 1], 14 binary levels
+(~122 points per leaf), expansion order p = 10, theta = 0.5, FP64 throughout.
+A step is one whole solve: tree, lists, P2M, M2M, M2L, L2L, L2P, P2P. Inputs
+are resident on the device when a step starts; the L2 cache is flushed
+between steps (a 512 MB write, outside the timed events).
+
+Reported beside the throughput: fmm_eval-only throughput, relative L2 error
+of potential and field against the FP64 direct sum on 1000 sampled targets
+(GPU fmm_direct; cross-checked with the CPU oracle's direct sum on rank 0),
+per-stage device times, the end-to-end number through host buffers, the
+roofline of the dominant kernel, SM clocks sampled during the timed region,
+and the CPU oracle timed on a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--prec fp64|mixed] [--impl ours|reference]
+Multi-GPU (torchrun): every rank solves its own independent system (seed =
+rank), no collective on the data path: weak scaling, replicas only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2002_04894_gb300 import inputs  # noqa: E402
+
+WORKLOADS = {
+    # name: (distribution, N, levels, p, theta, point dtype, charges)
+    "plummer2m_l14_p10": ("plummer", 2_000_000, 14, 10, 0.5, "f64", "uniform"),
+    "uniform20k_l8_p8": ("uniform", 20_000, 8, 8, 0.5, "f64", "uniform"),
+    "gmm8m_l16_p12": ("gmm", 8_000_000, 16, 12, 0.5, "f32", "pm1"),
+}
+DEFAULT = "plummer2m_l14_p10"
+FLOPS_PER_INTERACTION = 20   # P2P convention (N-body): 20 flops per pair
+SM_COUNT = 152
+FP32_FLOPS_PER_CLK_SM = 256  # 128 FP32 lanes x FMA
+FP64_FLOPS_PER_CLK_SM = 4    # GB300 nominal 1.25 TFLOP/s FP64 at 2.07 GHz / 152 SMs
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_inputs(name, seed):
+    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name]
+    x = inputs.points(dist, n, seed)
+    q = inputs.charges_uniform(n, seed) if ch == "uniform" else inputs.charges_pm1(n, seed)
+    if pdt == "f32":
+        x, q = x.astype(np.float32), q.astype(np.float32)
+    return x, q, levels, p, theta
+
+
+def cpu_sample_config(name):
+    """The bounded CPU sample of a workload: same distribution, charges, p and
+    theta; N reduced and levels lowered so that points per leaf stay equal."""
+    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name]
+    ns = min(n, 1 << 17)
+    ls = max(0, levels - int(round(np.log2(n / ns))))
+    return dist, ns, ls, p, theta, ch
+
+
+def run_oracle_sample(name, seed=0):
+    import oracle
+    dist, ns, ls, p, theta, ch = cpu_sample_config(name)
+    x = inputs.points(dist, ns, seed)
+    q = inputs.charges_uniform(ns, seed) if ch == "uniform" else inputs.charges_pm1(ns, seed)
+    t0 = time.perf_counter()
+    T = oracle.Tree(x, ls, p, theta)
+    T.eval(q)
+    dt = time.perf_counter() - t0
+    return ns, ls, dt, oracle.num_threads()
+
+
+def bench_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, same metric and unit."""
+    if rank != 0:
+        return
+    name = args.workload
+    for _ in range(args.warmup):
+        run_oracle_sample(name)
+    times = []
+    for _ in range(args.steps):
+        ns, ls, dt, cores = run_oracle_sample(name)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    val = ns / (ms / 1e3) / 1e6
+    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name]
+    sample = f"{dist} N={ns} levels={ls} p={p} theta={theta} (same points/leaf as N={n}, {levels} levels)"
+    print(json.dumps({
+        "impl": "reference", "metric": "Mpoints/s per FMM solve (plan+eval)", "value": round(val, 6),
+        "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "sample": sample, "l2": "host"},
+        "cpu_baseline": {"value": round(val, 6), "unit": "Mpoints/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(val, 6), "unit": "Mpoints/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def bench_ours(args, rank, world, local):
+    import torch
+    import paper_2002_04894_gb300 as fmm
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fmm.load()
+    prec = fmm.FMM_PREC_MIXED if args.prec == "mixed" else fmm.FMM_PREC_FP64
+    x, q, levels, p, theta = make_inputs(args.workload, seed=rank)
+    n = x.shape[0]
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    pot = torch.empty(n, dtype=qd.dtype, device="cuda")
+    fld = torch.empty((n, 3), dtype=qd.dtype, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True)
+        fmm.fmm_eval(plan, qd, pot, fld)
+        return plan
+
+    for _ in range(args.warmup):
+        fmm.fmm_destroy(solve())
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_sum = {s: 0.0 for s in fmm.STAGES}
+    launches0 = fmm.fmm_kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1, e2 = ev[k]
+            e0.record(stream)
+            plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True)
+            e1.record(stream)
+            fmm.fmm_eval(plan, qd, pot, fld)
+            e2.record(stream)
+            st = fmm.fmm_stage_times(plan)          # synchronises
+            for s in st:
+                stage_sum[s] += st[s]
+            stats = fmm.fmm_plan_stats(plan)
+            fmm.fmm_destroy(plan)
+        torch.cuda.synchronize()
+    launches = fmm.fmm_kernel_launches() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    t_solve = sum(a.elapsed_time(c) for a, b, c in ev) / args.steps
+    t_eval = sum(b.elapsed_time(c) for a, b, c in ev) / args.steps
+    if world > 1:
+        tt = torch.tensor([t_solve, t_eval], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_solve, t_eval = tt.tolist()
+    stage_ms = {s: v / args.steps for s, v in stage_sum.items()}
+
+    # accuracy vs the FP64 direct sum on 1000 sampled targets (GPU)
+    tgt = inputs.sample_targets(n, 1000, seed=rank)
+    dp, dE = fmm.fmm_direct(xd, qd, torch.from_numpy(tgt).cuda())
+    dp, dE = dp.double().cpu().numpy(), dE.double().cpu().numpy()
+    gp, gE = pot.double().cpu().numpy()[tgt], fld.double().cpu().numpy()[tgt]
+    err_phi = float(np.linalg.norm(gp - dp) / np.linalg.norm(dp))
+    err_E = float(np.linalg.norm(gE - dE) / np.linalg.norm(dE))
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    xh = torch.from_numpy(x).pin_memory()
+    qh = torch.from_numpy(q).pin_memory()
+    poth = torch.empty(n, dtype=qh.dtype).pin_memory()
+    fldh = torch.empty((n, 3), dtype=qh.dtype).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    fmm.fmm_destroy(fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan = fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None)
+        fmm.fmm_eval(plan, qh, poth, fldh)
+        fmm.fmm_destroy(plan)
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    es = x.dtype.itemsize
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp = FP64_FLOPS_PER_CLK_SM if prec == fmm.FMM_PREC_FP64 else FP32_FLOPS_PER_CLK_SM
+    peak_tflops = SM_COUNT * fp * max_mhz * 1e6 / 1e12
+    p2p_flops = FLOPS_PER_INTERACTION * stats["p2p_interactions"]
+    achieved = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
+    value = world * n / (t_solve * 1e-3) / 1e6
+    out = {
+        "metric": "Mpoints/s per FMM solve (plan+eval) at rel err <= 1e-6 vs FP64 direct",
+        "value": round(value, 4), "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_solve, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == fmm.FMM_PREC_FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "levels": levels, "p": p, "theta": theta,
+                   "prec": args.prec, "points": WORKLOADS[args.workload][0],
+                   "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "eval_only": {"value": round(world * n / (t_eval * 1e-3) / 1e6, 4), "unit": "Mpoints/s",
+                      "ms": round(t_eval, 3)},
+        "accuracy": {"rel_l2_phi": err_phi, "rel_l2_field": err_E, "targets": len(tgt),
+                     "reference": "fmm_direct (FP64, GPU)"},
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "work": {"p2p_interactions": stats["p2p_interactions"], "weak_pairs": stats["weak_pairs"],
+                 "strong_leaf_pairs": stats["strong_leaf_pairs"]},
+        "roofline": {"kernel": "p2p", "bound": "alu", "achieved": round(achieved, 4),
+                     "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak_tflops, 4), "traffic": None,
+                     "peak_basis": (f"{SM_COUNT} SMs x {fp} flop/clk x {max_mhz:.0f} MHz "
+                                    f"({'FP64' if fp == FP64_FLOPS_PER_CLK_SM else 'FP32'} pipe)"),
+                     "flops_basis": f"{FLOPS_PER_INTERACTION} flop per pair x exact pair count"},
+        "e2e": {"value": round(world * n / (t_e2e * 1e-3) / 1e6, 4), "unit": "Mpoints/s",
+                "h2d_bytes_per_step": int(n * 3 * es + n * es),
+                "d2h_bytes_per_step": int(n * es + 3 * n * es)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        ns, ls, dt, cores = run_oracle_sample(args.workload)
+        dist, _, _, pp, th, ch = cpu_sample_config(args.workload)
+        out["cpu_baseline"] = {"value": round(ns / dt / 1e6, 6), "unit": "Mpoints/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{dist} N={ns} levels={ls} p={pp} theta={th}, tree+lists+eval"}
+        import oracle
+        op = oracle.direct(x.astype(np.float64), q.astype(np.float64), targets=tgt, field=False)
+        out["accuracy"]["rel_l2_phi_vs_oracle_direct"] = float(np.linalg.norm(gp - op) / np.linalg.norm(op))
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        bench_reference(args, rank, world)
+    else:
+        bench_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * fmm.h -- C ABI of the GB300 balanced-tree fast multipole method.
+ *
+ * The method is the balanced-tree adaptive FMM of Bull & Engblom,
+ * "Distributed and Adaptive Fast Multipole Method in Three Dimensions"
+ * (arXiv:2002.04894): a tree of a fixed number of levels whose boxes are split
+ * at median planes (Sec. 2.1.2, eta = 1), theta-criterion connectivity
+ * (Eq. 2.2), multipole/local expansions of order p (Sec. 2.1), and the stage
+ * order of Algorithm 1 (Tree; P2M; M2M; M2L and L2L, Algorithm 3; L2P and P2P,
+ * Algorithm 4). It evaluates, for N points x_i with real charges q_i,
+ *
+ *     phi_i = sum_{j != i} q_j / |x_i - x_j|                      (Eq. 2.1)
+ *     E_i   = -grad phi_i = sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3
+ *
+ * with no physical constant. Pairs at zero distance contribute nothing.
+ *
+ * Conventions shared by every entry point:
+ *  - A "level" is one binary median bisection: `levels` = B gives 2^B leaves
+ *    and boxes numbered in heap order, box g = 2^l - 1 + j for box j of
+ *    level l (children of g are 2g+1 and 2g+2).
+ *  - Pointers to point, charge and output arrays may be device pointers or
+ *    host pointers (pageable or pinned); the library detects which with
+ *    cudaPointerGetAttributes and stages host data through device buffers.
+ *    Host outputs are complete when the call returns; device work is
+ *    asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *  - All parity/inspection hooks (fmm_plan_tree, fmm_plan_list,
+ *    fmm_eval_expansions, fmm_plan_stats) write HOST memory and synchronise
+ *    the plan's stream.
+ *  - Status codes are returned, never thrown; the library never aborts,
+ *    traps or exits. Device-detected errors are reported by the call that
+ *    next synchronises (fmm_plan always does).
+ *  - Distinct plans may be used from distinct host threads concurrently; one
+ *    plan must not be used by two threads at once.
+ */
+#ifndef FMM_H
+#define FMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum fmm_status {
+    FMM_OK = 0,
+    FMM_EINVAL = -1,      /* bad argument: n < 1, levels or p out of range, theta not in [0,1),
+                             unknown precision or flag bits */
+    FMM_ENOMEM = -2,      /* the allocator returned NULL */
+    FMM_ENONFINITE = -3,  /* a point coordinate is NaN or infinite */
+    FMM_ECAPACITY = -4,   /* an interaction list exceeds 2^31 - 1 entries */
+    FMM_ETIMEDOUT = -5,   /* a bounded device wait gave up (reserved for persistent kernels) */
+    FMM_ECUDA = -6        /* a CUDA runtime call failed; fmm_last_cuda_error() has the code */
+};
+
+/* Element type of points, charges and outputs. */
+enum fmm_dtype { FMM_F64 = 0, FMM_F32 = 1 };
+
+/*
+ * Arithmetic of the evaluation stages.
+ *  FMM_PREC_FP64  every stage in double precision (the plain form).
+ *  FMM_PREC_MIXED box geometry, theta-test, M2M and L2L in double; P2M, M2L,
+ *                 L2P and P2P in single precision with leaf-centred
+ *                 coordinates and compensated per-target sums.
+ */
+enum fmm_prec { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
+
+#define FMM_MAX_LEVELS 24
+#define FMM_MAX_P 20
+
+/* fmm_opts.flags bits */
+#define FMM_FLAG_PROFILE 1  /* record per-stage device times (fmm_stage_times) */
+
+/* Stages of Algorithm 1 as timed by fmm_stage_times. */
+enum fmm_stage {
+    FMM_STAGE_TREE = 0,  /* fmm_plan: bounding box, median splits, cell geometry */
+    FMM_STAGE_LISTS,     /* fmm_plan: theta-criterion connectivity */
+    FMM_STAGE_P2M,       /* fmm_eval: charge gather + P2M */
+    FMM_STAGE_M2M,
+    FMM_STAGE_M2L,
+    FMM_STAGE_L2L,
+    FMM_STAGE_L2P,
+    FMM_STAGE_P2P,       /* includes the scatter to input order */
+    FMM_NSTAGES
+};
+
+typedef struct fmm_opts {
+    int levels;     /* B: number of binary bisections, 0 <= B <= FMM_MAX_LEVELS */
+    int p;          /* expansion order: degrees 0..p, 0 <= p <= FMM_MAX_P */
+    double theta;   /* theta-criterion parameter (Eq. 2.2), 0 <= theta < 1;
+                       theta = 0 gives no weak pairs (the FMM reduces to Eq. 2.1) */
+    int prec;       /* enum fmm_prec */
+    int flags;      /* FMM_FLAG_* bits; other bits must be 0 */
+} fmm_opts;
+
+/*
+ * Optional device allocator. alloc returns device memory of at least `bytes`
+ * usable in stream order on `stream` (or NULL on failure); free releases it.
+ * Without one the library uses cudaMallocAsync / cudaFreeAsync.
+ */
+typedef void *(*fmm_alloc_fn)(size_t bytes, void *ctx, void *stream);
+typedef void (*fmm_free_fn)(void *ptr, size_t bytes, void *ctx, void *stream);
+typedef struct fmm_allocator {
+    fmm_alloc_fn alloc;
+    fmm_free_fn free;
+    void *ctx;
+} fmm_allocator;
+
+typedef struct fmm_plan_s *fmm_plan_t;
+
+/*
+ * fmm_plan -- build the balanced tree and its connectivity (Algorithm 2 on one
+ * device; Sec. 2.1.1-2.1.2).
+ *   points  n x 3 row-major coordinates, dtype `dtype`, host or device.
+ *   n       number of points, 1 <= n <= 2^31 - 1.
+ *   opts    levels, p, theta, precision, flags (copied).
+ *   alloc   optional allocator (copied; must outlive the plan), or NULL.
+ *   stream  cudaStream_t for all of the plan's device work.
+ *   out     receives the plan handle (owned by the caller; fmm_destroy frees).
+ * The root cell is the tight bounding box; each box is split on the longest
+ * axis of its cell so that the left child holds the floor(n/2) smallest
+ * (coordinate, original index) keys, at the plane halfway between the two
+ * sides. The plan copies the points into leaf order and keeps no pointer to
+ * `points`. Synchronises `stream` (it reads the list sizes).
+ * Errors: FMM_EINVAL, FMM_ENONFINITE, FMM_ENOMEM, FMM_ECAPACITY, FMM_ECUDA;
+ * on error *out is NULL and nothing is leaked.
+ */
+int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
+             const fmm_allocator *alloc, void *stream, fmm_plan_t *out);
+
+/*
+ * fmm_eval -- one FMM evaluation for the plan's points (Algorithm 1 after
+ * Tree: P2M, M2M, M2L, L2L, L2P, P2P).
+ *   charges     n charges, plan's dtype, host or device.
+ *   potentials  n outputs phi_i, plan's dtype, input order, host or device.
+ *   fields      n x 3 row-major outputs E_i = -grad phi_i, or NULL to skip.
+ * Allocates nothing (all scratch belongs to the plan). Asynchronous on
+ * `stream` when every pointer is device memory; otherwise it returns after
+ * the host outputs are written.
+ * Errors: FMM_EINVAL (NULL plan/charges/potentials), FMM_ECUDA.
+ */
+int fmm_eval(fmm_plan_t plan, const void *charges, void *potentials, void *fields,
+             void *stream);
+
+/* fmm_destroy -- release the plan and its device memory (stream-ordered on
+ * the plan's stream). NULL is a no-op. */
+void fmm_destroy(fmm_plan_t plan);
+
+/*
+ * fmm_direct -- the exact sum of Eq. 2.1 at selected targets, in double
+ * precision on the device, for accuracy checks of fmm_eval.
+ *   points, charges  n x 3 and n values (dtype), host or device.
+ *   targets          ntargets int64 indices into [0, n), host or device.
+ *   potentials       ntargets outputs (dtype); fields: ntargets x 3 or NULL.
+ * Sources are summed in blocks with compensated (Neumaier) partial sums.
+ * Allocates device staging only for host arguments (cudaMallocAsync).
+ * Errors: FMM_EINVAL (n < 1, ntargets < 0, NULL pointers), FMM_ECUDA.
+ */
+int fmm_direct(const void *points, const void *charges, int64_t n, int dtype,
+               const int64_t *targets, int64_t ntargets, void *potentials,
+               void *fields, void *stream);
+
+/* Plan statistics (host). Counts are exact, from the plan's lists. */
+typedef struct fmm_stats {
+    int64_t n, nbox, nleaf;
+    int levels, p, prec, dtype;
+    double theta;
+    int64_t weak_pairs;          /* directed M2L pairs, all levels */
+    int64_t strong_leaf_pairs;   /* directed P2P leaf pairs, self pairs included */
+    int64_t p2p_interactions;    /* sum over strong leaf pairs of n_t * n_s */
+    int64_t weak_pairs_level[FMM_MAX_LEVELS + 1];
+} fmm_stats;
+
+/* fmm_plan_stats -- fill *out. Errors: FMM_EINVAL. */
+int fmm_plan_stats(fmm_plan_t plan, fmm_stats *out);
+
+/*
+ * fmm_plan_tree -- copy the tree to host arrays (any may be NULL):
+ *   perm    n     original index of the point in each leaf-order slot
+ *   begin   nbox  first slot of each box;  count nbox  points per box
+ *   lo, hi  nbox x 3 cell bounds;  centre nbox x 3;  radius nbox
+ *   axis    nbox  split axis (longest cell axis; leaves too)
+ *   plane   nbox  split coordinate (0 for leaves)
+ * Errors: FMM_EINVAL, FMM_ECUDA.
+ */
+int fmm_plan_tree(fmm_plan_t plan, int64_t *perm, int64_t *begin, int64_t *count,
+                  double *lo, double *hi, double *centre, double *radius,
+                  int32_t *axis, double *plane);
+
+/*
+ * fmm_plan_list -- copy one connectivity list to host memory (Eq. 2.2).
+ *   kind 0: weak (M2L) pairs of `level`;  kind 1: strong pairs of `level`
+ *   (at level == levels, the P2P list). CSR over the 2^level target boxes of
+ *   the level: ptr[2^level + 1] (int64), src[ptr[2^level]] (int32, box index
+ *   within the level, ascending per target). Both orientations are stored.
+ * If src is NULL only ptr is written (to size src). Errors: FMM_EINVAL, FMM_ECUDA.
+ */
+int fmm_plan_list(fmm_plan_t plan, int level, int kind, int64_t *ptr, int32_t *src);
+
+/*
+ * fmm_eval_expansions -- copy the multipole (which = 0) or local (which = 1)
+ * coefficients left by the last fmm_eval to host memory: nbox x ncoef complex
+ * values as (re, im) doubles, ncoef = (p+1)(p+2)/2, coefficient (n, m) with
+ * 0 <= m <= n at n(n+1)/2 + m. Normalisation: M_n^m = sum_j q_j
+ * conj(Y_n^m(x_j - c)), phi(c + s) = sum L_n^m conj(Y_n^m(s)), with
+ * Y_n^m = (-1)^m r^n P_n^m(cos t) e^{i m phi} / (n+m)! (no Condon-Shortley phase)
+ * and C_n^{-m} = (-1)^m conj(C_n^m). Errors: FMM_EINVAL, FMM_ECUDA.
+ */
+int fmm_eval_expansions(fmm_plan_t plan, int which, double *out);
+
+/*
+ * fmm_stage_times -- device milliseconds of each stage (enum fmm_stage) of
+ * the plan's construction (TREE, LISTS) and of its last fmm_eval (the rest),
+ * measured with CUDA events on the plan's stream. Needs FMM_FLAG_PROFILE in
+ * the plan's opts. Writes FMM_NSTAGES doubles to host memory; synchronises.
+ * Errors: FMM_EINVAL (NULL, or profiling off), FMM_ECUDA.
+ */
+int fmm_stage_times(fmm_plan_t plan, double *ms);
+
+/*
+ * fmm_kernel_launches -- number of CUDA kernels this library has launched in
+ * the process so far (all plans, all threads). For launch accounting.
+ */
+int64_t fmm_kernel_launches(void);
+
+/* fmm_strerror -- static text for a status code. */
+const char *fmm_strerror(int status);
+
+/* fmm_last_cuda_error -- the cudaError_t behind the calling thread's last FMM_ECUDA. */
+int fmm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H */

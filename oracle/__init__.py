@@ -81,6 +81,9 @@ def _lib():
     lib.orc_eval.argtypes = [C.c_void_p, _f64p, _f64p, C.c_void_p]
     lib.orc_get_expansions.argtypes = [C.c_void_p, C.c_int, _f64p]
     lib.orc_num_threads.restype = C.c_int
+    lib.orc_bisect_box.argtypes = [C.c_int64, _f64p, _f64p, _f64p,
+                                   np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS"), _f64p]
+    lib.orc_bisect_box.restype = C.c_int
     _LIB = lib
     return lib
 
@@ -161,6 +164,16 @@ def direct(x, q, targets=None, field: bool = True):
 
 def theta_weak(theta: float, ca, ra: float, cb, rb: float) -> bool:
     return bool(_lib().orc_theta_weak(theta, _vec3(ca), ra, _vec3(cb), rb))
+
+
+def bisect_box(x, lo, hi):
+    """One median bisection of a box given its points (ascending original
+    index) and cell: returns (axis, left mask, plane)."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    left = np.zeros(len(x), np.int8)
+    plane = np.zeros(1)
+    ax = _lib().orc_bisect_box(len(x), x, _vec3(lo), _vec3(hi), left, plane)
+    return int(ax), left.astype(bool), float(plane[0])
 
 
 class Tree:

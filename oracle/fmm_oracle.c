@@ -429,6 +429,40 @@ static void orc_build_tree(orc_fmm *F)
     free(left);
 }
 
+/*
+ * One median bisection of a single box (Sec. 2.1.2, eta = 1), for checking
+ * sampled boxes of a large tree one at a time: x holds the box's nn points
+ * (nn x 3) in ascending original index, [lo, hi] its cell. The split axis is
+ * the first longest cell extent; left[t] = 1 for the floor(nn/2) smallest
+ * (coordinate, position) keys; returns the axis and writes the plane.
+ */
+int orc_bisect_box(int64_t nn, const double *x, const double lo[3], const double hi[3],
+                   char *left, double *plane)
+{
+    double e[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    int ax = 0;
+    if (e[1] > e[ax]) ax = 1;
+    if (e[2] > e[ax]) ax = 2;
+    orc_key *keys = malloc(sizeof(orc_key) * (nn > 0 ? nn : 1));
+    for (int64_t t = 0; t < nn; t++) {
+        keys[t].key = x[3 * t + ax] + 0.0;
+        keys[t].idx = t;
+        left[t] = 0;
+    }
+    qsort(keys, nn, sizeof(orc_key), key_cmp);
+    int64_t k = nn / 2;
+    for (int64_t t = 0; t < k; t++)
+        left[keys[t].idx] = 1;
+    if (nn >= 2)
+        *plane = 0.5 * (keys[k - 1].key + keys[k].key);
+    else if (nn == 1)
+        *plane = keys[0].key;
+    else
+        *plane = 0.5 * (lo[ax] + hi[ax]);
+    free(keys);
+    return ax;
+}
+
 /* ------------------------------------------------------------------ */
 /* Connectivity (Eq. 2.2 and the inheritance rule of Sec. 2.1.1)        */
 /* ------------------------------------------------------------------ */

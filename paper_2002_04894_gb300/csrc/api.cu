@@ -1,0 +1,402 @@
+// C ABI of the GB300 FMM library: argument checking, memory ownership,
+// host/device staging and the stage order of Algorithm 1 (Tree in fmm_plan;
+// P2M, M2M, M2L, L2L, L2P, P2P in fmm_eval).
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+std::atomic<long long> g_launches{0};
+
+cudaError_t eval_expansions(Plan &P, const void *charges, int dtype);
+cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype);
+
+void *dalloc(Plan &P, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (P.has_alloc) return P.alloc.alloc(bytes, P.alloc.ctx, (void *)P.stream);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, P.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(Plan &P, void *ptr, size_t bytes) {
+    if (!ptr) return;
+    if (bytes == 0) bytes = 16;
+    if (P.has_alloc)
+        P.alloc.free(ptr, bytes, P.alloc.ctx, (void *)P.stream);
+    else
+        cudaFreeAsync(ptr, P.stream);
+}
+
+void *palloc(Plan &P, size_t bytes) {
+    void *p = dalloc(P, bytes);
+    if (p) P.owned.push_back({p, bytes ? bytes : 16});
+    return p;
+}
+
+}  // namespace fmm
+
+using fmm::Plan;
+
+struct fmm_plan_s {
+    Plan P;
+};
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FMM_OK;
+    g_last_cuda = (int)e;
+    if (e == cudaErrorMemoryAllocation) return FMM_ENOMEM;
+    return FMM_ECUDA;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void release(Plan &P) {
+    for (int s = 0; s < FMM_NSTAGES; s++)
+        for (int e = 0; e < 2; e++)
+            if (P.ev[s][e]) cudaEventDestroy(P.ev[s][e]);
+    for (auto it = P.owned.rbegin(); it != P.owned.rend(); ++it) fmm::dfree(P, it->first, it->second);
+    P.owned.clear();
+    cudaStreamSynchronize(P.stream);
+    cudaGetLastError();
+}
+
+size_t dsize(int dtype) { return dtype == FMM_F64 ? 8 : 4; }
+
+}  // namespace
+
+extern "C" {
+
+int fmm_stage_times(fmm_plan_t plan, double *ms) {
+    if (!plan || !ms || !plan->P.profile) return FMM_EINVAL;
+    Plan &P = plan->P;
+    cudaError_t e = cudaStreamSynchronize(P.stream);
+    for (int s = 0; s < FMM_NSTAGES && e == cudaSuccess; s++) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, P.ev[s][0], P.ev[s][1]);
+        ms[s] = t;
+    }
+    return cuda_status(e);
+}
+
+int64_t fmm_kernel_launches(void) { return (int64_t)fmm::g_launches.load(); }
+
+const char *fmm_strerror(int status) {
+    switch (status) {
+        case FMM_OK: return "success";
+        case FMM_EINVAL: return "invalid argument";
+        case FMM_ENOMEM: return "device allocation failed";
+        case FMM_ENONFINITE: return "non-finite point coordinate";
+        case FMM_ECAPACITY: return "interaction list exceeds 2^31-1 entries";
+        case FMM_ETIMEDOUT: return "bounded device wait timed out";
+        case FMM_ECUDA: return "CUDA runtime error";
+        default: return "unknown status";
+    }
+}
+
+int fmm_last_cuda_error(void) { return g_last_cuda; }
+
+int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
+             const fmm_allocator *alloc, void *stream, fmm_plan_t *out) {
+    if (out) *out = nullptr;
+    if (!out || !points || !opts) return FMM_EINVAL;
+    if (n < 1 || n > 0x7fffffffLL) return FMM_EINVAL;
+    if (dtype != FMM_F64 && dtype != FMM_F32) return FMM_EINVAL;
+    if (opts->levels < 0 || opts->levels > FMM_MAX_LEVELS) return FMM_EINVAL;
+    if (opts->p < 0 || opts->p > FMM_MAX_P) return FMM_EINVAL;
+    if (!(opts->theta >= 0.0 && opts->theta < 1.0)) return FMM_EINVAL;
+    if (opts->prec != FMM_PREC_FP64 && opts->prec != FMM_PREC_MIXED) return FMM_EINVAL;
+    if (opts->flags & ~FMM_FLAG_PROFILE) return FMM_EINVAL;
+    if (alloc && (!alloc->alloc || !alloc->free)) return FMM_EINVAL;
+
+    fmm_plan_s *H = new (std::nothrow) fmm_plan_s();
+    if (!H) return FMM_ENOMEM;
+    Plan &P = H->P;
+    P.n = n;
+    P.B = opts->levels;
+    P.p = opts->p;
+    P.nc = fmm::ncoef(P.p);
+    P.theta = opts->theta;
+    P.prec = opts->prec;
+    P.dtype = dtype;
+    P.nbox = ((int64_t)2 << P.B) - 1;
+    P.nleaf = (int64_t)1 << P.B;
+    P.stream = (cudaStream_t)stream;
+    if (alloc) {
+        P.alloc = *alloc;
+        P.has_alloc = true;
+    }
+    cudaGetDevice(&P.device);
+    P.profile = (opts->flags & FMM_FLAG_PROFILE) != 0;
+
+    auto fail = [&](int status) {
+        release(P);
+        delete H;
+        return status;
+    };
+
+    // box point ranges depend on n and the level only
+    std::vector<int32_t> hb(P.nbox), hc(P.nbox);
+    hb[0] = 0;
+    hc[0] = (int32_t)n;
+    for (int64_t g = 0; g < P.nbox - P.nleaf; g++) {
+        const int32_t k = hc[g] / 2;
+        hb[2 * g + 1] = hb[g];
+        hc[2 * g + 1] = k;
+        hb[2 * g + 2] = hb[g] + k;
+        hc[2 * g + 2] = hc[g] - k;
+    }
+    const size_t nb = (size_t)P.nbox;
+    P.x = (double *)fmm::palloc(P, n * 8);
+    P.y = (double *)fmm::palloc(P, n * 8);
+    P.z = (double *)fmm::palloc(P, n * 8);
+    P.perm = (int32_t *)fmm::palloc(P, n * 4);
+    P.begin = (int32_t *)fmm::palloc(P, nb * 4);
+    P.count = (int32_t *)fmm::palloc(P, nb * 4);
+    P.lo = (double *)fmm::palloc(P, nb * 24);
+    P.hi = (double *)fmm::palloc(P, nb * 24);
+    P.centre = (double *)fmm::palloc(P, nb * 24);
+    P.radius = (double *)fmm::palloc(P, nb * 8);
+    P.plane = (double *)fmm::palloc(P, nb * 8);
+    P.axis = (int32_t *)fmm::palloc(P, nb * 4);
+    P.d_err = (int *)fmm::palloc(P, 16);
+    if (!P.x || !P.y || !P.z || !P.perm || !P.begin || !P.count || !P.lo || !P.hi || !P.centre ||
+        !P.radius || !P.plane || !P.axis || !P.d_err)
+        return fail(FMM_ENOMEM);
+    if (P.profile)
+        for (int s = 0; s < FMM_NSTAGES; s++)
+            for (int k = 0; k < 2; k++)
+                if (cudaEventCreate(&P.ev[s][k]) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
+    cudaMemcpyAsync(P.begin, hb.data(), nb * 4, cudaMemcpyHostToDevice, P.stream);
+    cudaMemcpyAsync(P.count, hc.data(), nb * 4, cudaMemcpyHostToDevice, P.stream);
+    cudaMemsetAsync(P.plane, 0, nb * 8, P.stream);
+    cudaMemsetAsync(P.d_err, 0, 16, P.stream);
+
+    const void *pts = points;
+    void *staged = nullptr;
+    const size_t pbytes = (size_t)n * 3 * dsize(dtype);
+    if (!is_device_ptr(points)) {
+        staged = fmm::dalloc(P, pbytes);
+        if (!staged) return fail(FMM_ENOMEM);
+        cudaMemcpyAsync(staged, points, pbytes, cudaMemcpyHostToDevice, P.stream);
+        pts = staged;
+    }
+    fmm::stage_mark(P, FMM_STAGE_TREE, 0);
+    cudaError_t e = fmm::tree_build(P, pts, dtype);
+    fmm::stage_mark(P, FMM_STAGE_TREE, 1);
+    if (staged) fmm::dfree(P, staged, pbytes);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    int herr = 0;
+    cudaMemcpyAsync(&herr, P.d_err, 4, cudaMemcpyDeviceToHost, P.stream);
+    e = cudaStreamSynchronize(P.stream);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    if (herr & 1) return fail(FMM_ENONFINITE);
+    if (herr) return fail(FMM_ECUDA);  // internal consistency check of the partition failed
+
+    fmm::stage_mark(P, FMM_STAGE_LISTS, 0);
+    e = fmm::lists_build(P);
+    fmm::stage_mark(P, FMM_STAGE_LISTS, 1);
+    if (P.capacity_exceeded) return fail(FMM_ECAPACITY);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+
+    P.q = (double *)fmm::palloc(P, n * 8);
+    P.far_phi = (double *)fmm::palloc(P, n * 8);
+    P.far_E = (double *)fmm::palloc(P, n * 24);
+    P.M = (double2 *)fmm::palloc(P, nb * P.nc * sizeof(double2));
+    P.L = (double2 *)fmm::palloc(P, nb * P.nc * sizeof(double2));
+    if (!P.q || !P.far_phi || !P.far_E || !P.M || !P.L) return fail(FMM_ENOMEM);
+    e = cudaStreamSynchronize(P.stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    *out = H;
+    return FMM_OK;
+}
+
+int fmm_eval(fmm_plan_t plan, const void *charges, void *potentials, void *fields, void *stream) {
+    if (!plan || !charges || !potentials) return FMM_EINVAL;
+    Plan &P = plan->P;
+    P.stream = (cudaStream_t)stream;
+    const size_t es = dsize(P.dtype), n = (size_t)P.n;
+    const bool dq = is_device_ptr(charges), dp = is_device_ptr(potentials),
+               df = !fields || is_device_ptr(fields);
+    const size_t need = (dq ? 0 : n * es) + (dp ? 0 : n * es) + (df ? 0 : 3 * n * es);
+    if (need > P.stage_bytes) {
+        void *s = fmm::palloc(P, need);
+        if (!s) return FMM_ENOMEM;
+        P.stage = s;
+        P.stage_bytes = need;
+    }
+    char *sp = (char *)P.stage;
+    const void *q = charges;
+    void *pot = potentials, *fld = fields;
+    if (!dq) {
+        cudaMemcpyAsync(sp, charges, n * es, cudaMemcpyHostToDevice, P.stream);
+        q = sp;
+        sp += n * es;
+    }
+    if (!dp) {
+        pot = sp;
+        sp += n * es;
+    }
+    if (!df) fld = sp;
+    cudaError_t e = fmm::eval_expansions(P, q, P.dtype);
+    if (e == cudaSuccess) e = fmm::eval_p2p(P, pot, fld, P.dtype);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!dp) cudaMemcpyAsync(potentials, pot, n * es, cudaMemcpyDeviceToHost, P.stream);
+    if (!df) cudaMemcpyAsync(fields, fld, 3 * n * es, cudaMemcpyDeviceToHost, P.stream);
+    if (!dp || !df || !dq) {
+        e = cudaStreamSynchronize(P.stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+void fmm_destroy(fmm_plan_t plan) {
+    if (!plan) return;
+    release(plan->P);
+    delete plan;
+}
+
+int fmm_direct(const void *points, const void *charges, int64_t n, int dtype,
+               const int64_t *targets, int64_t ntargets, void *potentials, void *fields,
+               void *stream) {
+    if (!points || !charges || !targets || !potentials || n < 1 || ntargets < 0) return FMM_EINVAL;
+    if (dtype != FMM_F64 && dtype != FMM_F32) return FMM_EINVAL;
+    if (ntargets == 0) return FMM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = dsize(dtype);
+    const void *a[3] = {points, charges, targets};
+    const size_t bytes[3] = {(size_t)n * 3 * es, (size_t)n * es, (size_t)ntargets * 8};
+    const size_t obytes[2] = {(size_t)ntargets * es, (size_t)ntargets * 3 * es};
+    void *dev[3] = {nullptr, nullptr, nullptr}, *odev[2] = {nullptr, nullptr};
+    const void *use[3];
+    void *ouse[2] = {potentials, fields};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; i++) {
+        use[i] = a[i];
+        if (!is_device_ptr(a[i])) {
+            e = cudaMallocAsync(&dev[i], bytes[i], st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dev[i], a[i], bytes[i], cudaMemcpyHostToDevice, st);
+            use[i] = dev[i];
+        }
+    }
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+        if (ouse[i] && !is_device_ptr(ouse[i])) {
+            e = cudaMallocAsync(&odev[i], obytes[i], st);
+            ouse[i] = odev[i];
+        }
+    }
+    if (e == cudaSuccess)
+        e = fmm::direct_run(use[0], use[1], n, dtype, (const int64_t *)use[2], ntargets, ouse[0],
+                            ouse[1], st);
+    if (e == cudaSuccess && odev[0]) e = cudaMemcpyAsync(potentials, odev[0], obytes[0], cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && odev[1]) e = cudaMemcpyAsync(fields, odev[1], obytes[1], cudaMemcpyDeviceToHost, st);
+    for (int i = 0; i < 3; i++)
+        if (dev[i]) cudaFreeAsync(dev[i], st);
+    for (int i = 0; i < 2; i++)
+        if (odev[i]) cudaFreeAsync(odev[i], st);
+    if (odev[0] || odev[1]) {
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_status(e);
+}
+
+int fmm_plan_stats(fmm_plan_t plan, fmm_stats *out) {
+    if (!plan || !out) return FMM_EINVAL;
+    const Plan &P = plan->P;
+    std::memset(out, 0, sizeof(*out));
+    out->n = P.n;
+    out->nbox = P.nbox;
+    out->nleaf = P.nleaf;
+    out->levels = P.B;
+    out->p = P.p;
+    out->prec = P.prec;
+    out->dtype = P.dtype;
+    out->theta = P.theta;
+    for (int l = 0; l <= P.B; l++) {
+        out->weak_pairs_level[l] = P.nweak[l];
+        out->weak_pairs += P.nweak[l];
+    }
+    out->strong_leaf_pairs = P.nstrong[P.B];
+    out->p2p_interactions = P.p2p_interactions;
+    return FMM_OK;
+}
+
+int fmm_plan_tree(fmm_plan_t plan, int64_t *perm, int64_t *begin, int64_t *count, double *lo,
+                  double *hi, double *centre, double *radius, int32_t *axis, double *plane) {
+    if (!plan) return FMM_EINVAL;
+    Plan &P = plan->P;
+    cudaError_t e = cudaStreamSynchronize(P.stream);
+    const size_t nb = (size_t)P.nbox, n = (size_t)P.n;
+    if (e == cudaSuccess && perm) {
+        std::vector<int32_t> t(n);
+        e = cudaMemcpy(t.data(), P.perm, n * 4, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < n; i++) perm[i] = t[i];
+    }
+    if (e == cudaSuccess && (begin || count)) {
+        std::vector<int32_t> b(nb), c(nb);
+        e = cudaMemcpy(b.data(), P.begin, nb * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(c.data(), P.count, nb * 4, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < nb; i++) {
+            if (begin) begin[i] = b[i];
+            if (count) count[i] = c[i];
+        }
+    }
+    if (e == cudaSuccess && lo) e = cudaMemcpy(lo, P.lo, nb * 24, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && hi) e = cudaMemcpy(hi, P.hi, nb * 24, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && centre) e = cudaMemcpy(centre, P.centre, nb * 24, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && radius) e = cudaMemcpy(radius, P.radius, nb * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && axis) e = cudaMemcpy(axis, P.axis, nb * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && plane) e = cudaMemcpy(plane, P.plane, nb * 8, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+int fmm_plan_list(fmm_plan_t plan, int level, int kind, int64_t *ptr, int32_t *src) {
+    if (!plan || !ptr || (kind != 0 && kind != 1)) return FMM_EINVAL;
+    Plan &P = plan->P;
+    if (level < 0 || level > P.B) return FMM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(P.stream);
+    const int64_t nt = (int64_t)1 << level;
+    std::vector<int32_t> t(nt + 1);
+    const int32_t *dp = kind == 0 ? P.wptr[level] : P.sptr[level];
+    const int32_t *ds = kind == 0 ? P.wsrc[level] : P.ssrc[level];
+    if (e == cudaSuccess) e = cudaMemcpy(t.data(), dp, (nt + 1) * 4, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i <= nt; i++) ptr[i] = t[i];
+    if (e == cudaSuccess && src && t[nt] > 0)
+        e = cudaMemcpy(src, ds, (size_t)t[nt] * 4, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+int fmm_eval_expansions(fmm_plan_t plan, int which, double *out) {
+    if (!plan || !out || (which != 0 && which != 1)) return FMM_EINVAL;
+    Plan &P = plan->P;
+    cudaError_t e = cudaStreamSynchronize(P.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, which == 0 ? P.M : P.L, (size_t)P.nbox * P.nc * sizeof(double2),
+                       cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+}  // extern "C"

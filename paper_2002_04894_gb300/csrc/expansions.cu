@@ -1,0 +1,331 @@
+// Expansion stages of Algorithm 1 in double precision: P2M at the leaves,
+// M2M upward (Algorithm 1), M2L at every level with weak pairs and L2L
+// downward (Algorithm 3), and L2P at the leaves (Algorithm 4).
+//
+// Expansions are spherical-harmonic multipole and local series of order p
+// about the cell centres (Sec. 2.1). With Y_n^m = (-1)^m R_n^m (m >= 0),
+// Y_n^{-m} = conj(R_n^m), R_n^m = r^n P_n^m e^{im phi}/(n+m)! and the matching
+// irregular Th_n^m built from I_n^m = (n-m)! P_n^m e^{im phi}/r^{n+1}:
+//   M_n^m  = sum_j q_j conj(Y_n^m(x_j - c))                         (P2M)
+//   M'_n^m = sum_{k,l} conj(Y_k^l(c - c')) M_{n-k}^{m-l}             (M2M)
+//   L_k^l  = (-1)^k sum_{n,m} M_n^m Th_{n+k}^{m+l}(c_t - c_s)        (M2L)
+//   L'_j^i = sum_{k>=j,l} L_k^l conj(Y_{k-j}^{l-i}(c' - c))          (L2L)
+//   phi(c + s) = sum_{k,l} L_k^l conj(Y_k^l(s)), E = -grad phi        (L2P)
+// Only m >= 0 is stored: real charges give C_n^{-m} = (-1)^m conj(C_n^m).
+//
+// GPU mapping: P2M is one CTA per leaf with one point per lane, streaming the
+// harmonics through the Legendre recurrences and reducing each coefficient
+// over the warp; M2M/L2L are one CTA per parent with one thread per output
+// coefficient; M2L is one CTA per target box with one thread per output
+// coefficient and the irregular harmonics of each source offset built in
+// shared memory one column per thread; L2P is one thread per point with O(1)
+// registers (the series and its gradient accumulate as the recurrence runs).
+
+#include <algorithm>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kExpThreads = 128;
+
+// (n, m) from a packed triangle index
+__device__ __forceinline__ void untri(int c, int &n, int &m) {
+    n = (int)((sqrt(8.0 * c + 1.0) - 1.0) * 0.5);
+    while (tri(n + 1, 0) <= c) n++;
+    while (tri(n, 0) > c) n--;
+    m = c - tri(n, 0);
+}
+
+// signed-order view of a stored harmonic table H (R or I): (-1)^m H_n^m for
+// m >= 0 and conj(H_n^|m|) for m < 0
+__device__ __forceinline__ double2 sview(const double2 *H, int n, int m) {
+    if (n < 0 || m > n || -m > n) return make_double2(0.0, 0.0);
+    if (m >= 0) {
+        const double2 h = H[tri(n, m)];
+        return (m & 1) ? make_double2(-h.x, -h.y) : h;
+    }
+    return cconj(H[tri(n, -m)]);
+}
+
+template <typename T>
+__global__ void k_gather_q(const T *__restrict__ qin, const int32_t *__restrict__ perm,
+                           double *__restrict__ q, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = (double)qin[perm[i]];
+}
+
+__global__ void __launch_bounds__(kExpThreads)
+k_p2m(int B, int p, const double *__restrict__ x, const double *__restrict__ y,
+      const double *__restrict__ z, const double *__restrict__ q, const int32_t *__restrict__ begin,
+      const int32_t *__restrict__ count, const double *__restrict__ centre, double2 *__restrict__ M) {
+    extern __shared__ double2 acc[];  // [warps][nc]
+    const int nc = ncoef(p);
+    const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
+    const int b = begin[g], n = count[g];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double cx = centre[3 * g], cy = centre[3 * g + 1], cz = centre[3 * g + 2];
+    for (int c = threadIdx.x; c < nc * (kExpThreads / 32); c += kExpThreads)
+        acc[c] = make_double2(0.0, 0.0);
+    __syncthreads();
+    double2 *mine = acc + w * nc;
+    for (int base = w * 32; base < n; base += kExpThreads) {
+        const int i = base + lane;
+        const bool valid = i < n;
+        const double dx = valid ? x[b + i] - cx : 0.0;
+        const double dy = valid ? y[b + i] - cy : 0.0;
+        const double dz = valid ? z[b + i] - cz : 0.0;
+        const double qi = valid ? q[b + i] : 0.0;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        double2 mm = make_double2(1.0, 0.0);  // R_m^m
+        for (int m = 0; m <= p; m++) {
+            if (m > 0) mm = cscale(cmul(mm, make_double2(dx, dy)), 0.5 / m);
+            double2 cur = mm, prev = make_double2(0.0, 0.0);
+            const double sg = (m & 1) ? -qi : qi;
+            for (int nn = m; nn <= p; nn++) {
+                if (nn > m) {
+                    double2 nxt;
+                    if (nn == m + 1) {
+                        nxt = cscale(cur, dz);
+                    } else {
+                        const double s = 1.0 / ((double)(nn - m) * (double)(nn + m));
+                        nxt = make_double2(((2 * nn - 1) * dz * cur.x - r2 * prev.x) * s,
+                                           ((2 * nn - 1) * dz * cur.y - r2 * prev.y) * s);
+                    }
+                    prev = cur;
+                    cur = nxt;
+                }
+                // q conj(Y_n^m) = q (-1)^m conj(R_n^m)
+                double vr = sg * cur.x, vi = -sg * cur.y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vr += __shfl_xor_sync(0xffffffffu, vr, o);
+                    vi += __shfl_xor_sync(0xffffffffu, vi, o);
+                }
+                if (lane == 0) {
+                    double2 a = mine[tri(nn, m)];
+                    mine[tri(nn, m)] = make_double2(a.x + vr, a.y + vi);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += kExpThreads) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int j = 0; j < kExpThreads / 32; j++) s = cadd(s, acc[j * nc + c]);
+        M[g * nc + c] = s;
+    }
+}
+
+// M2M: parents of level `level - 1` from their two children at `level`
+__global__ void __launch_bounds__(kExpThreads)
+k_m2m(int level, int p, const double *__restrict__ centre, double2 *M) {
+    extern __shared__ double2 sm[];
+    const int nc = ncoef(p);
+    double2 *R = sm, *Mc = sm + 2 * nc;
+    const int64_t gp = ((int64_t)1 << (level - 1)) - 1 + blockIdx.x;
+    const int64_t gc0 = 2 * gp + 1;
+    if (threadIdx.x < 2) {
+        const int64_t gc = gc0 + threadIdx.x;
+        regular_serial(centre[3 * gc] - centre[3 * gp], centre[3 * gc + 1] - centre[3 * gp + 1],
+                       centre[3 * gc + 2] - centre[3 * gp + 2], p, R + threadIdx.x * nc);
+    }
+    for (int c = threadIdx.x; c < 2 * nc; c += kExpThreads) Mc[c] = M[gc0 * nc + c];
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += kExpThreads) {
+        int n, m;
+        untri(c, n, m);
+        double2 s = make_double2(0.0, 0.0);
+        for (int ch = 0; ch < 2; ch++) {
+            const double2 *Rc = R + ch * nc, *Mk = Mc + ch * nc;
+            for (int k = 0; k <= n; k++)
+                for (int l = -k; l <= k; l++) {
+                    if (m - l > n - k || l - m > n - k) continue;
+                    s = cadd(s, cmul(cconj(sview(Rc, k, l)), coef_at(Mk, n - k, m - l)));
+                }
+        }
+        M[gp * nc + c] = s;
+    }
+}
+
+// M2L at one level, basic O(p^4) form: one CTA per target box of the level
+__global__ void __launch_bounds__(256)
+k_m2l(int level, int p, const int32_t *__restrict__ wptr, const int32_t *__restrict__ wsrc,
+      const double *__restrict__ centre, const double2 *__restrict__ M, double2 *L) {
+    extern __shared__ double2 sm[];
+    const int nc = ncoef(p), p2 = 2 * p;
+    double2 *Ih = sm, *Ms = sm + ncoef(p2);
+    const int64_t off = ((int64_t)1 << level) - 1;
+    const int t = blockIdx.x;
+    const int64_t gt = off + t;
+    const int e0 = wptr[t], e1 = wptr[t + 1];
+    int kk = 0, ll = 0;
+    if (threadIdx.x < nc) untri(threadIdx.x, kk, ll);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int e = e0; e < e1; e++) {
+        const int64_t gs = off + wsrc[e];
+        const double dx = centre[3 * gt] - centre[3 * gs];
+        const double dy = centre[3 * gt + 1] - centre[3 * gs + 1];
+        const double dz = centre[3 * gt + 2] - centre[3 * gs + 2];
+        if (threadIdx.x <= p2) {
+            // column m of I_n^m(d), n = m..2p
+            const int m = threadIdx.x;
+            const double r2 = dx * dx + dy * dy + dz * dz, ir2 = 1.0 / r2;
+            double2 v = make_double2(1.0 / sqrt(r2), 0.0);
+            for (int j = 1; j <= m; j++) v = cscale(cmul(v, make_double2(dx, dy)), (2 * j - 1) * ir2);
+            double2 prev = make_double2(0.0, 0.0), cur = v;
+            Ih[tri(m, m)] = cur;
+            for (int n = m + 1; n <= p2; n++) {
+                const double a = (2 * n - 1) * dz, b = (double)(n - 1 + m) * (double)(n - 1 - m);
+                const double2 nxt = make_double2((a * cur.x - b * prev.x) * ir2,
+                                                 (a * cur.y - b * prev.y) * ir2);
+                prev = cur;
+                cur = nxt;
+                Ih[tri(n, m)] = cur;
+            }
+        }
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) Ms[c] = M[gs * nc + c];
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            for (int n = 0; n <= p; n++)
+                for (int m = -n; m <= n; m++)
+                    acc = cadd(acc, cmul(coef_at(Ms, n, m), sview(Ih, n + kk, m + ll)));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < nc) L[gt * nc + threadIdx.x] = (kk & 1) ? make_double2(-acc.x, -acc.y) : acc;
+}
+
+// L2L: children at `level` receive their parent's local expansion
+__global__ void __launch_bounds__(kExpThreads)
+k_l2l(int level, int p, const double *__restrict__ centre, double2 *L) {
+    extern __shared__ double2 sm[];
+    const int nc = ncoef(p);
+    double2 *R = sm, *Lp = sm + 2 * nc;
+    const int64_t gp = ((int64_t)1 << (level - 1)) - 1 + blockIdx.x;
+    const int64_t gc0 = 2 * gp + 1;
+    if (threadIdx.x < 2) {
+        const int64_t gc = gc0 + threadIdx.x;
+        regular_serial(centre[3 * gc] - centre[3 * gp], centre[3 * gc + 1] - centre[3 * gp + 1],
+                       centre[3 * gc + 2] - centre[3 * gp + 2], p, R + threadIdx.x * nc);
+    }
+    for (int c = threadIdx.x; c < nc; c += kExpThreads) Lp[c] = L[gp * nc + c];
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += kExpThreads) {
+        int j, i;
+        untri(c, j, i);
+        for (int ch = 0; ch < 2; ch++) {
+            const double2 *Rc = R + ch * nc;
+            double2 s = make_double2(0.0, 0.0);
+            for (int k = j; k <= p; k++)
+                for (int l = -k; l <= k; l++) {
+                    if (l - i > k - j || i - l > k - j) continue;
+                    s = cadd(s, cmul(coef_at(Lp, k, l), cconj(sview(Rc, k - j, l - i))));
+                }
+            L[(gc0 + ch) * nc + c] = cadd(L[(gc0 + ch) * nc + c], s);
+        }
+    }
+}
+
+// L2P: far-field potential and field at every leaf point (leaf order)
+__global__ void __launch_bounds__(kExpThreads)
+k_l2p(int B, int p, int64_t npts, const double *__restrict__ x, const double *__restrict__ y,
+      const double *__restrict__ z, const int32_t *__restrict__ begin,
+      const int32_t *__restrict__ count, const double *__restrict__ centre,
+      const double2 *__restrict__ L, double *__restrict__ far_phi, double *__restrict__ far_E) {
+    extern __shared__ double2 Ls[];
+    const int nc = ncoef(p);
+    const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
+    const int b = begin[g], n = count[g];
+    for (int c = threadIdx.x; c < nc; c += kExpThreads) Ls[c] = L[g * nc + c];
+    __syncthreads();
+    const double cx = centre[3 * g], cy = centre[3 * g + 1], cz = centre[3 * g + 2];
+    for (int i = threadIdx.x; i < n; i += kExpThreads) {
+        const double dx = x[b + i] - cx, dy = y[b + i] - cy, dz = z[b + i] - cz;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        double phi = 0.0, g0 = 0.0;          // phi and the degree-1, order-0 shifted coefficient
+        double2 g1 = make_double2(0.0, 0.0); // degree-1, order-1 shifted coefficient
+        double2 mm = make_double2(1.0, 0.0);
+        for (int m = 0; m <= p; m++) {
+            if (m > 0) mm = cscale(cmul(mm, make_double2(dx, dy)), 0.5 / m);
+            double2 cur = mm, prev = make_double2(0.0, 0.0);
+            const double w = m == 0 ? 1.0 : 2.0;
+            for (int nn = m; nn <= p; nn++) {
+                if (nn > m) {
+                    double2 nxt;
+                    if (nn == m + 1) {
+                        nxt = cscale(cur, dz);
+                    } else {
+                        const double s = 1.0 / ((double)(nn - m) * (double)(nn + m));
+                        nxt = make_double2(((2 * nn - 1) * dz * cur.x - r2 * prev.x) * s,
+                                           ((2 * nn - 1) * dz * cur.y - r2 * prev.y) * s);
+                    }
+                    prev = cur;
+                    cur = nxt;
+                }
+                // Y = (-1)^m R; Yc = conj(Y)
+                const double2 Y = (m & 1) ? make_double2(-cur.x, -cur.y) : cur;
+                const double2 Yc = cconj(Y);
+                phi += w * cmul(Ls[tri(nn, m)], Yc).x;
+                if (nn < p) {
+                    g0 += w * cmul(Ls[tri(nn + 1, m)], Yc).x;
+                    g1 = cadd(g1, cmul(Ls[tri(nn + 1, m + 1)], Yc));
+                    if (m >= 1) {
+                        const double2 t = cmul(cconj(Ls[tri(nn + 1, m - 1)]), Y);
+                        g1 = make_double2(g1.x - t.x, g1.y - t.y);
+                    }
+                }
+            }
+        }
+        far_phi[b + i] = phi;
+        far_E[b + i] = g1.x;
+        far_E[npts + b + i] = g1.y;
+        far_E[2 * npts + b + i] = -g0;
+    }
+}
+
+}  // namespace
+
+cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
+    cudaStream_t st = P.stream;
+    const int64_t n = P.n;
+    const int nc = P.nc;
+    const int gq = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    stage_mark(P, FMM_STAGE_P2M, 0);
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_gather_q<double>, gq, 256, 0, st, (const double *)charges, P.perm, P.q, n);
+    else
+        FMM_LAUNCH(k_gather_q<float>, gq, 256, 0, st, (const float *)charges, P.perm, P.q, n);
+    FMM_LAUNCH(k_p2m, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * nc * (kExpThreads / 32), st,
+               P.B, P.p, P.x, P.y, P.z, P.q, P.begin, P.count, P.centre, P.M);
+    stage_mark(P, FMM_STAGE_P2M, 1);
+    stage_mark(P, FMM_STAGE_M2M, 0);
+    for (int l = P.B; l >= 1; l--)
+        FMM_LAUNCH(k_m2m, 1u << (l - 1), kExpThreads, sizeof(double2) * 4 * nc, st, l, P.p, P.centre,
+                   P.M);
+    stage_mark(P, FMM_STAGE_M2M, 1);
+    // Algorithm 3: M2L at every level (each overwrites its level's L), then L2L downward
+    stage_mark(P, FMM_STAGE_M2L, 0);
+    cudaMemsetAsync(P.L, 0, sizeof(double2) * nc, st);  // root: no far field
+    const size_t m2l_smem = sizeof(double2) * (ncoef(2 * P.p) + nc);
+    const int m2l_threads = std::max(64, (std::max(nc, 2 * P.p + 1) + 31) / 32 * 32);
+    for (int l = 1; l <= P.B; l++)
+        FMM_LAUNCH(k_m2l, 1u << l, m2l_threads, m2l_smem, st, l, P.p, P.wptr[l], P.wsrc[l], P.centre,
+                   P.M, P.L);
+    stage_mark(P, FMM_STAGE_M2L, 1);
+    stage_mark(P, FMM_STAGE_L2L, 0);
+    for (int l = 1; l <= P.B; l++)
+        FMM_LAUNCH(k_l2l, 1u << (l - 1), kExpThreads, sizeof(double2) * 3 * nc, st, l, P.p, P.centre,
+                   P.L);
+    stage_mark(P, FMM_STAGE_L2L, 1);
+    stage_mark(P, FMM_STAGE_L2P, 0);
+    FMM_LAUNCH(k_l2p, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * nc, st, P.B, P.p, n, P.x, P.y,
+               P.z, P.begin, P.count, P.centre, P.L, P.far_phi, P.far_E);
+    stage_mark(P, FMM_STAGE_L2P, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace fmm

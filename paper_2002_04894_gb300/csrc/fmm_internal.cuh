@@ -1,0 +1,143 @@
+// Internal declarations of the GB300 FMM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <utility>
+#include <vector>
+
+#include "fmm.h"
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------
+// Plan: everything lives in device memory owned by the plan.
+// ---------------------------------------------------------------------------
+struct Plan {
+    int64_t n = 0;
+    int B = 0, p = 0, nc = 0, prec = 0, dtype = 0, device = 0;
+    double theta = 0.0;
+    int64_t nbox = 0, nleaf = 0;
+    cudaStream_t stream = nullptr;
+    fmm_allocator alloc{};
+    bool has_alloc = false;
+
+    // points in leaf order (structure of arrays) and slot -> original index
+    double *x = nullptr, *y = nullptr, *z = nullptr;
+    int32_t *perm = nullptr;
+    // boxes in heap order
+    int32_t *begin = nullptr;   // first leaf-order slot of each box
+    int32_t *count = nullptr;   // points per box
+    double *lo = nullptr, *hi = nullptr, *centre = nullptr;   // nbox x 3
+    double *radius = nullptr, *plane = nullptr;               // nbox
+    int32_t *axis = nullptr;                                  // nbox
+    // connectivity: CSR per level over the 2^l target boxes of level l
+    int32_t *wptr[FMM_MAX_LEVELS + 1] = {}, *wsrc[FMM_MAX_LEVELS + 1] = {};
+    int32_t *sptr[FMM_MAX_LEVELS + 1] = {}, *ssrc[FMM_MAX_LEVELS + 1] = {};
+    int64_t nweak[FMM_MAX_LEVELS + 1] = {}, nstrong[FMM_MAX_LEVELS + 1] = {};
+    int64_t p2p_interactions = 0;
+    bool capacity_exceeded = false;
+    // evaluation scratch
+    double *q = nullptr;                 // charges in leaf order
+    double2 *M = nullptr, *L = nullptr;  // nbox x nc
+    double *far_phi = nullptr;           // n, leaf order
+    double *far_E = nullptr;             // 3n, leaf order (SoA: x | y | z)
+    // staging for host arguments
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    int *d_err = nullptr;                // device error word
+    // per-stage device timing (FMM_FLAG_PROFILE)
+    bool profile = false;
+    cudaEvent_t ev[FMM_NSTAGES][2] = {};
+    // every plan-lifetime device buffer, released by fmm_destroy
+    std::vector<std::pair<void *, size_t>> owned;
+};
+
+// Allocation through the plan's allocator (or stream-ordered cudaMallocAsync).
+// dalloc/dfree: temporaries; palloc: owned by the plan until fmm_destroy.
+void *dalloc(Plan &P, size_t bytes);
+void dfree(Plan &P, void *ptr, size_t bytes);
+void *palloc(Plan &P, size_t bytes);
+
+// Kernel launches made by the library (fmm_kernel_launches).
+extern std::atomic<long long> g_launches;
+#define FMM_LAUNCH(kernel, grid, block, smem, stream, ...)          \
+    do {                                                            \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__); \
+        ::fmm::g_launches.fetch_add(1, std::memory_order_relaxed);  \
+    } while (0)
+
+// Stage timing marks (no-ops unless the plan profiles).
+inline void stage_mark(Plan &P, int stage, int edge) {
+    if (P.profile) cudaEventRecord(P.ev[stage][edge], P.stream);
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+__host__ __device__ inline int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
+
+// Order-preserving map from doubles to unsigned 64-bit keys (no NaN; -0 was
+// canonicalised to +0 on input).
+__device__ __forceinline__ uint64_t dkey(double v) {
+    uint64_t u = (uint64_t)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(uint64_t k) {
+    uint64_t u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) {
+    return make_double2(a.x * s, a.y * s);
+}
+
+// Coefficient C_n^m of a real-source expansion stored for m >= 0:
+// C_n^{-m} = (-1)^m conj(C_n^m); zero outside |m| <= n.
+__device__ __forceinline__ double2 coef_at(const double2 *C, int n, int m) {
+    if (n < 0 || m > n || -m > n) return make_double2(0.0, 0.0);
+    if (m >= 0) return C[tri(n, m)];
+    double2 c = C[tri(n, -m)];
+    return ((-m) & 1) ? make_double2(-c.x, c.y) : make_double2(c.x, -c.y);
+}
+
+// Regular solid harmonics R_n^m(d) = r^n P_n^m e^{im phi}/(n+m)!, 0 <= m <= n <= p,
+// by the Legendre recurrences (serial; used for translation vectors).
+__device__ inline void regular_serial(double dx, double dy, double dz, int p, double2 *R) {
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double2 mm = make_double2(1.0, 0.0);
+    for (int m = 0; m <= p; m++) {
+        if (m > 0) mm = cscale(cmul(mm, make_double2(dx, dy)), 0.5 / m);
+        R[tri(m, m)] = mm;
+        if (m + 1 <= p) R[tri(m + 1, m)] = cscale(mm, dz);
+        for (int n = m + 2; n <= p; n++) {
+            double2 a = R[tri(n - 1, m)], b = R[tri(n - 2, m)];
+            double s = 1.0 / ((double)(n - m) * (double)(n + m));
+            R[tri(n, m)] = make_double2(((2 * n - 1) * dz * a.x - r2 * b.x) * s,
+                                        ((2 * n - 1) * dz * a.y - r2 * b.y) * s);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (each in its own translation unit)
+// ---------------------------------------------------------------------------
+cudaError_t tree_build(Plan &P, const void *points_dev, int dtype);
+cudaError_t lists_build(Plan &P);
+cudaError_t direct_run(const void *points, const void *charges, int64_t n, int dtype,
+                       const int64_t *targets, int64_t nt, void *pot, void *field,
+                       cudaStream_t s);
+// device-wide exclusive scan of int32 counts (n + 1 outputs, last = total)
+cudaError_t scan_exclusive(Plan &P, const int32_t *in, int32_t *out, int64_t n);
+
+}  // namespace fmm

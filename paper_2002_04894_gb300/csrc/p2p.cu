@@ -1,0 +1,163 @@
+// Near field (P2P, Algorithm 4) and the exact sum of Eq. 2.1.
+//
+// P2P: for every target leaf, the direct interaction with the points of all
+// strongly connected leaves (itself included), pairs at zero distance
+// skipped. One CTA per target leaf, one target point per thread; source
+// leaves are staged through shared memory in tiles of (x, y, z, q). The
+// kernel adds the far field left by L2P and writes phi and E straight to the
+// caller's arrays in input order (the un-permute step).
+//
+// Direct: one CTA per target, threads stride over all sources with
+// Neumaier-compensated partial sums, then a block reduction.
+
+#include <algorithm>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kP2PThreads = 128;
+
+template <typename OutT>
+__global__ void __launch_bounds__(kP2PThreads)
+k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__restrict__ y,
+          const double *__restrict__ z, const double *__restrict__ q,
+          const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+          const int32_t *__restrict__ sptr, const int32_t *__restrict__ ssrc,
+          const int32_t *__restrict__ perm, const double *__restrict__ far_phi,
+          const double *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
+    __shared__ double4 tile[kP2PThreads];
+    const int64_t off = ((int64_t)1 << B) - 1;
+    const int t = blockIdx.x;
+    const int bt = begin[off + t], nt = count[off + t];
+    const int e0 = sptr[t], e1 = sptr[t + 1];
+    for (int tb = 0; tb < nt; tb += kP2PThreads) {
+        const int i = tb + threadIdx.x;
+        const bool active = i < nt;
+        const double xi = active ? x[bt + i] : 0.0;
+        const double yi = active ? y[bt + i] : 0.0;
+        const double zi = active ? z[bt + i] : 0.0;
+        double phi = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+        for (int e = e0; e < e1; e++) {
+            const int64_t gs = off + ssrc[e];
+            const int bs = begin[gs], ns = count[gs];
+            for (int sb = 0; sb < ns; sb += kP2PThreads) {
+                const int j = sb + threadIdx.x;
+                tile[threadIdx.x] = j < ns ? make_double4(x[bs + j], y[bs + j], z[bs + j], q[bs + j])
+                                           : make_double4(0.0, 0.0, 0.0, 0.0);
+                __syncthreads();
+                const int mcount = min(kP2PThreads, ns - sb);
+                for (int jj = 0; jj < mcount; jj++) {
+                    const double4 s = tile[jj];
+                    const double dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
+                    const double qr = s.w * rinv;
+                    const double qr3 = qr * rinv * rinv;
+                    phi += qr;
+                    ex += qr3 * dx;
+                    ey += qr3 * dy;
+                    ez += qr3 * dz;
+                }
+                __syncthreads();
+            }
+        }
+        if (active) {
+            const int64_t a = bt + i;
+            const int64_t o = perm[a];
+            pot[o] = (OutT)(far_phi[a] + phi);
+            if (field) {
+                field[3 * o] = (OutT)(far_E[a] + ex);
+                field[3 * o + 1] = (OutT)(far_E[npts + a] + ey);
+                field[3 * o + 2] = (OutT)(far_E[2 * npts + a] + ez);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void neumaier(double &s, double &c, double v) {
+    const double t = s + v;
+    if (fabs(s) >= fabs(v))
+        c += (s - t) + v;
+    else
+        c += (v - t) + s;
+    s = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_direct(const T *__restrict__ pts, const T *__restrict__ q, int64_t n,
+         const int64_t *__restrict__ targets, T *__restrict__ pot, T *__restrict__ field) {
+    __shared__ double red[4][256];
+    const int64_t i = targets[blockIdx.x];
+    if (i < 0 || i >= n) {  // out-of-range index: NaN outputs, no access
+        if (threadIdx.x < 4) {
+            const T nan = (T)__longlong_as_double(0x7ff8000000000000ll);
+            if (threadIdx.x == 0)
+                pot[blockIdx.x] = nan;
+            else if (field)
+                field[3 * blockIdx.x + threadIdx.x - 1] = nan;
+        }
+        return;
+    }
+    const double xi = (double)pts[3 * i], yi = (double)pts[3 * i + 1], zi = (double)pts[3 * i + 2];
+    double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    for (int64_t j = threadIdx.x; j < n; j += 256) {
+        const double dx = xi - (double)pts[3 * j], dy = yi - (double)pts[3 * j + 1],
+                     dz = zi - (double)pts[3 * j + 2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 == 0.0) continue;
+        const double r = sqrt(r2);
+        const double qj = (double)q[j];
+        const double qr3 = qj / (r2 * r);
+        neumaier(s[0], c[0], qj / r);
+        neumaier(s[1], c[1], qr3 * dx);
+        neumaier(s[2], c[2], qr3 * dy);
+        neumaier(s[3], c[3], qr3 * dz);
+    }
+    for (int a = 0; a < 4; a++) red[a][threadIdx.x] = s[a] + c[a];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double ss = 0.0, cc = 0.0;
+        for (int j = 0; j < 256; j++) neumaier(ss, cc, red[threadIdx.x][j]);
+        const double v = ss + cc;
+        if (threadIdx.x == 0)
+            pot[blockIdx.x] = (T)v;
+        else if (field)
+            field[3 * blockIdx.x + threadIdx.x - 1] = (T)v;
+    }
+}
+
+}  // namespace
+
+cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
+    const unsigned grid = (unsigned)P.nleaf;
+    stage_mark(P, FMM_STAGE_P2P, 0);
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_p2p_f64<double>, grid, kP2PThreads, 0, P.stream, 
+            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.perm,
+            P.far_phi, P.far_E, (double *)pot, (double *)field);
+    else
+        FMM_LAUNCH(k_p2p_f64<float>, grid, kP2PThreads, 0, P.stream, 
+            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.perm,
+            P.far_phi, P.far_E, (float *)pot, (float *)field);
+    stage_mark(P, FMM_STAGE_P2P, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t direct_run(const void *points, const void *charges, int64_t n, int dtype,
+                       const int64_t *targets, int64_t nt, void *pot, void *field,
+                       cudaStream_t s) {
+    if (nt == 0) return cudaSuccess;
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_direct<double>, (unsigned)nt, 256, 0, s, (const double *)points, (const double *)charges,
+                                                      n, targets, (double *)pot, (double *)field);
+    else
+        FMM_LAUNCH(k_direct<float>, (unsigned)nt, 256, 0, s, (const float *)points, (const float *)charges, n,
+                                                     targets, (float *)pot, (float *)field);
+    return cudaGetLastError();
+}
+
+}  // namespace fmm

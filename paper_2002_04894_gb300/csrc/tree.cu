@@ -1,0 +1,645 @@
+// Balanced-tree construction (Sec. 2.1.2 with eta = 1; Algorithm 2 on one
+// device): the root cell is the tight bounding box of the points; every box of
+// a level is split on the longest axis of its cell so that the left child
+// receives the floor(n/2) smallest (coordinate, original index) keys, both
+// children keeping ascending original-index order; the split plane lies
+// halfway between the largest left and the smallest right coordinate.
+//
+// GPU design. Points are kept in structure-of-arrays order (x | y | z | idx)
+// and ping-pong between two buffers, one level per pass. Because the tree is
+// balanced, every segment of a level holds floor or ceil(N / 2^l) points, so a
+// level is handled by one of two regimes:
+//   small  (<= 4096 points per box): one CTA per box, keys in shared memory,
+//          8-bit radix select of the rank-(k-1) key, then a warp-ballot stable
+//          partition;
+//   large: many CTAs per box (4096-point chunks); per-pass histograms are
+//          privatised in shared memory and merged with global atomics, a
+//          one-warp pick kernel chooses each digit, and the stable partition
+//          is a chunk-level count, a per-box scan of chunk counts and a
+//          warp-ballot scatter.
+// Keys are order-preserving 64-bit images of the coordinate. Since a box's
+// points are in ascending original index, the index tie-break of the key
+// (coordinate, index) equals the position order inside the box: among points
+// equal to the selected key v, the first (k - #{key < v}) in position go left.
+// All geometry uses explicitly rounded double operations (no contraction).
+
+#include <algorithm>
+#include <utility>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kSmallCap = 4096;
+constexpr int kChunk = 4096;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t < v ? t : v;
+    }
+    return v;
+}
+
+// Cell geometry of box g: centre = 0.5 (lo + hi); radius = 0.5 sqrt((ex^2 + ey^2) + ez^2);
+// split axis = first longest extent.
+__device__ void box_geometry(double *lo, double *hi, double *centre, double *radius,
+                             int32_t *axis, int64_t g) {
+    double e[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        e[a] = __dsub_rn(hi[3 * g + a], lo[3 * g + a]);
+        centre[3 * g + a] = __dmul_rn(0.5, __dadd_rn(lo[3 * g + a], hi[3 * g + a]));
+    }
+    double s = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])),
+                         __dmul_rn(e[2], e[2]));
+    radius[g] = __dmul_rn(0.5, __dsqrt_rn(s));
+    int ax = 0;
+    if (e[1] > e[ax]) ax = 1;
+    if (e[2] > e[ax]) ax = 2;
+    axis[g] = ax;
+}
+
+// --------------------------------------------------------------------------
+// Input: n x 3 row-major -> SoA doubles, -0.0 -> +0.0, finiteness, bounding box
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_prepare(const T *__restrict__ pts, int64_t n, double *__restrict__ x, double *__restrict__ y,
+          double *__restrict__ z, int32_t *__restrict__ idx, unsigned long long *bbox, int *err) {
+    uint64_t mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            v[a] = (double)pts[3 * i + a] + 0.0;
+            bad |= !isfinite(v[a]);
+            uint64_t k = dkey(v[a]);
+            mn[a] = k < mn[a] ? k : mn[a];
+            mx[a] = k > mx[a] ? k : mx[a];
+        }
+        x[i] = v[0];
+        y[i] = v[1];
+        z[i] = v[2];
+        idx[i] = (int32_t)i;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        mn[a] = warp_min_u64(mn[a]);
+        for (int o = 16; o > 0; o >>= 1) {
+            uint64_t t = __shfl_xor_sync(0xffffffffu, mx[a], o);
+            mx[a] = t > mx[a] ? t : mx[a];
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 1);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            atomicMin(&bbox[a], (unsigned long long)mn[a]);
+            atomicMax(&bbox[3 + a], (unsigned long long)mx[a]);
+        }
+    }
+}
+
+__global__ void k_root(const unsigned long long *bbox, double *lo, double *hi, double *centre,
+                       double *radius, int32_t *axis) {
+    if (threadIdx.x != 0) return;
+    for (int a = 0; a < 3; a++) {
+        lo[a] = dkey_inv(bbox[a]);
+        hi[a] = dkey_inv(bbox[3 + a]);
+    }
+    box_geometry(lo, hi, centre, radius, axis, 0);
+}
+
+// --------------------------------------------------------------------------
+// Shared pieces of the radix select
+// --------------------------------------------------------------------------
+
+// One warp: find the digit whose bucket holds rank *rrem among hist[0..255],
+// update the key prefix and the remaining rank.
+__device__ void pick_digit(const unsigned *hist, int shift, uint64_t *prefix, unsigned *rrem) {
+    const int lane = threadIdx.x & 31;
+    unsigned c[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        c[j] = hist[lane * 8 + j];
+        sum += c[j];
+    }
+    unsigned incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const unsigned excl = incl - sum;
+    const unsigned r = *rrem;
+    const uint64_t pre = *prefix;
+    __syncwarp();
+    if (excl <= r && r < incl) {
+        unsigned acc = excl;
+        for (int j = 0; j < 8; j++) {
+            if (r < acc + c[j]) {
+                *rrem = r - acc;
+                *prefix = pre | ((uint64_t)(lane * 8 + j) << shift);
+                break;
+            }
+            acc += c[j];
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool prefix_match(uint64_t key, uint64_t prefix, int shift) {
+    return shift >= 56 || (key >> (shift + 8)) == (prefix >> (shift + 8));
+}
+
+// --------------------------------------------------------------------------
+// Small regime: one CTA per box
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_split_small(int level, const double *__restrict__ xin, const double *__restrict__ yin,
+              const double *__restrict__ zin, const int32_t *__restrict__ iin,
+              double *__restrict__ xout, double *__restrict__ yout, double *__restrict__ zout,
+              int32_t *__restrict__ iout, const int32_t *__restrict__ begin,
+              const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
+              uint64_t *sel_v, unsigned long long *sel_minr, int *err) {
+    __shared__ uint64_t keys[kSmallCap];
+    __shared__ unsigned hist[256];
+    __shared__ unsigned flags[kSmallCap / 32];
+    __shared__ uint64_t s_prefix;
+    __shared__ unsigned s_rrem;
+    __shared__ unsigned long long s_minr;
+    __shared__ unsigned w_eq[kWarps], w_left[kWarps];
+
+    const int s = blockIdx.x;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    const int b = begin[g], n = count[g], ax = axis[g], k = n / 2;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const double *src = ax == 0 ? xin : (ax == 1 ? yin : zin);
+
+    if (n <= 1) {
+        if (n == 1 && tid == 0) {
+            xout[b] = xin[b];
+            yout[b] = yin[b];
+            zout[b] = zin[b];
+            iout[b] = iin[b];
+            sel_minr[s] = dkey(src[b]);
+        }
+        return;
+    }
+    for (int i = tid; i < n; i += kThreads) keys[i] = dkey(src[b + i]);
+    if (tid == 0) {
+        s_prefix = 0;
+        s_rrem = (unsigned)(k - 1);
+        s_minr = ~0ull;
+    }
+    __syncthreads();
+
+    for (int pass = 0; pass < 8; pass++) {
+        const int shift = 56 - 8 * pass;
+        hist[tid] = 0;  // kThreads == 256 bins
+        __syncthreads();
+        const uint64_t pre = s_prefix;
+        for (int i = tid; i < n; i += kThreads) {
+            uint64_t kk = keys[i];
+            if (prefix_match(kk, pre, shift)) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (w == 0) pick_digit(hist, shift, &s_prefix, &s_rrem);
+        __syncthreads();
+    }
+    const uint64_t v = s_prefix;
+    const unsigned need_eq = s_rrem + 1;  // equal keys that go left, in position order
+
+    // warp w owns positions [start, end)
+    const int per_warp = ((n + kWarps - 1) / kWarps + 31) & ~31;
+    const int start = w * per_warp;
+    const int end = min(n, start + per_warp);
+
+    unsigned eqc = 0;
+    uint64_t mr = ~0ull;
+    for (int base = start; base < end; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < end;
+        const uint64_t kk = valid ? keys[i] : 0;
+        eqc += __popc(__ballot_sync(0xffffffffu, valid && kk == v));
+        if (valid && kk > v && kk < mr) mr = kk;
+    }
+    mr = warp_min_u64(mr);
+    if (lane == 0) {
+        w_eq[w] = eqc;
+        atomicMin(&s_minr, (unsigned long long)mr);
+    }
+    __syncthreads();
+    unsigned eqrun = 0, eqtot = 0;
+    for (int j = 0; j < kWarps; j++) {
+        eqrun += j < w ? w_eq[j] : 0;
+        eqtot += w_eq[j];
+    }
+    unsigned leftc = 0;
+    for (int base = start; base < end; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < end;
+        const uint64_t kk = valid ? keys[i] : 0;
+        const bool eq = valid && kk == v;
+        const unsigned em = __ballot_sync(0xffffffffu, eq);
+        const unsigned rank = eqrun + __popc(em & lanemask_lt());
+        const bool f = valid && (kk < v || (eq && rank < need_eq));
+        const unsigned fm = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) flags[base >> 5] = fm;
+        leftc += __popc(fm);
+        eqrun += __popc(em);
+    }
+    if (lane == 0) w_left[w] = leftc;
+    __syncthreads();
+    unsigned lrun = 0;
+    for (int j = 0; j < w; j++) lrun += w_left[j];
+    for (int base = start; base < end; base += 32) {
+        const int i = base + lane;
+        const unsigned fm = flags[base >> 5];
+        const bool f = (fm >> lane) & 1u;
+        const unsigned lrank = lrun + __popc(fm & lanemask_lt());
+        if (i < end) {
+            const int rel = f ? (int)lrank : k + (i - (int)lrank);
+            if (rel >= 0 && rel < n) {
+                xout[b + rel] = xin[b + i];
+                yout[b + rel] = yin[b + i];
+                zout[b + rel] = zin[b + i];
+                iout[b + rel] = iin[b + i];
+            } else {
+                atomicOr(err, 2);  // inconsistent partition: report, never write outside the box
+            }
+        }
+        lrun += __popc(fm);
+    }
+    if (tid == 0) {
+        sel_v[s] = v;
+        sel_minr[s] = eqtot > need_eq ? (unsigned long long)v : s_minr;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Large regime: many CTAs per box
+// --------------------------------------------------------------------------
+__global__ void k_sel_init(int level, const int32_t *count, uint64_t *prefix, unsigned *rrem,
+                           unsigned long long *minr, unsigned *ghist) {
+    const int s = blockIdx.x;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    if (threadIdx.x == 0) {
+        const int n = count[g];
+        prefix[s] = 0;
+        rrem[s] = n >= 2 ? (unsigned)(n / 2 - 1) : 0u;
+        minr[s] = ~0ull;
+    }
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) ghist[(int64_t)s * 256 + i] = 0;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_sel_hist(int level, int pass, const double *__restrict__ xs, const double *__restrict__ ys,
+           const double *__restrict__ zs, const int32_t *__restrict__ begin,
+           const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
+           const uint64_t *__restrict__ prefix, unsigned *ghist) {
+    __shared__ unsigned h[256];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    const int b = begin[g], n = count[g], ax = axis[g];
+    const int start = c * kChunk;
+    if (start >= n) return;
+    const int end = min(n, start + kChunk);
+    const double *src = ax == 0 ? xs : (ax == 1 ? ys : zs);
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int shift = 56 - 8 * pass;
+    const uint64_t pre = prefix[s];
+    for (int i = start + threadIdx.x; i < end; i += kThreads) {
+        const uint64_t kk = dkey(src[b + i]);
+        if (prefix_match(kk, pre, shift)) atomicAdd(&h[(kk >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&ghist[(int64_t)s * 256 + threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_sel_pick(int pass, unsigned *ghist, uint64_t *prefix, unsigned *rrem) {
+    const int s = blockIdx.x;
+    __shared__ unsigned h[256];
+    __shared__ uint64_t pre;
+    __shared__ unsigned rr;
+    for (int i = threadIdx.x; i < 256; i += 32) {
+        h[i] = ghist[(int64_t)s * 256 + i];
+        ghist[(int64_t)s * 256 + i] = 0;
+    }
+    if (threadIdx.x == 0) {
+        pre = prefix[s];
+        rr = rrem[s];
+    }
+    __syncwarp();
+    pick_digit(h, 56 - 8 * pass, &pre, &rr);
+    if (threadIdx.x == 0) {
+        prefix[s] = pre;
+        rrem[s] = rr;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_sel_count(int level, int nch, const double *__restrict__ xs, const double *__restrict__ ys,
+            const double *__restrict__ zs, const int32_t *__restrict__ begin,
+            const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
+            const uint64_t *__restrict__ prefix, unsigned *chunk_lt, unsigned *chunk_eq,
+            unsigned long long *minr) {
+    __shared__ unsigned s_lt[kWarps], s_eq[kWarps];
+    __shared__ unsigned long long s_mr;
+    const int s = blockIdx.y, c = blockIdx.x;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    const int b = begin[g], n = count[g], ax = axis[g];
+    const int start = c * kChunk;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_mr = ~0ull;
+    __syncthreads();
+    const double *src = ax == 0 ? xs : (ax == 1 ? ys : zs);
+    const uint64_t v = prefix[s];
+    unsigned lt = 0, eq = 0;
+    uint64_t mr = ~0ull;
+    const int end = min(n, start + kChunk);
+    for (int i = start + threadIdx.x; i < end; i += kThreads) {
+        const uint64_t kk = dkey(src[b + i]);
+        lt += kk < v;
+        eq += kk == v;
+        if (kk > v && kk < mr) mr = kk;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lt += __shfl_xor_sync(0xffffffffu, lt, o);
+        eq += __shfl_xor_sync(0xffffffffu, eq, o);
+    }
+    mr = warp_min_u64(mr);
+    if (lane == 0) {
+        s_lt[w] = lt;
+        s_eq[w] = eq;
+        atomicMin(&s_mr, (unsigned long long)mr);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned a = 0, e = 0;
+        for (int j = 0; j < kWarps; j++) a += s_lt[j], e += s_eq[j];
+        chunk_lt[(int64_t)s * nch + c] = a;
+        chunk_eq[(int64_t)s * nch + c] = e;
+        if (s_mr != ~0ull) atomicMin(&minr[s], s_mr);
+    }
+}
+
+// Per box: exclusive scans over its chunks of the equal-key counts and of the
+// left counts; fixes the smallest right key when equal keys straddle.
+__global__ void k_sel_offsets(int level, int nch, const int32_t *count, const unsigned *chunk_lt,
+                              const unsigned *chunk_eq, const uint64_t *prefix,
+                              const unsigned *rrem, unsigned *eq_off, unsigned *left_off,
+                              unsigned long long *minr, uint64_t *sel_v) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (1 << level)) return;
+    const unsigned need_eq = rrem[s] + 1;
+    unsigned eo = 0, lo = 0;
+    for (int c = 0; c < nch; c++) {
+        const int64_t i = (int64_t)s * nch + c;
+        const unsigned e = chunk_eq[i], l = chunk_lt[i];
+        eq_off[i] = eo;
+        left_off[i] = lo;
+        const unsigned take = need_eq > eo ? min(need_eq - eo, e) : 0u;
+        lo += l + take;
+        eo += e;
+    }
+    sel_v[s] = prefix[s];
+    if (eo > need_eq) minr[s] = prefix[s];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_sel_scatter(int level, int nch, const double *__restrict__ xin, const double *__restrict__ yin,
+              const double *__restrict__ zin, const int32_t *__restrict__ iin,
+              double *__restrict__ xout, double *__restrict__ yout, double *__restrict__ zout,
+              int32_t *__restrict__ iout, const int32_t *__restrict__ begin,
+              const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
+              const uint64_t *__restrict__ prefix, const unsigned *__restrict__ rrem,
+              const unsigned *__restrict__ eq_off, const unsigned *__restrict__ left_off, int *err) {
+    __shared__ unsigned flags[kChunk / 32];
+    __shared__ unsigned w_eq[kWarps], w_left[kWarps];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    const int b = begin[g], n = count[g], ax = axis[g], k = n / 2;
+    const int cstart = c * kChunk;
+    if (cstart >= n) return;
+    const int cend = min(n, cstart + kChunk);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double *src = ax == 0 ? xin : (ax == 1 ? yin : zin);
+    const uint64_t v = prefix[s];
+    const unsigned need_eq = rrem[s] + 1;
+    constexpr int per_warp = kChunk / kWarps;
+    const int start = cstart + w * per_warp;
+    const int end = min(cend, start + per_warp);
+
+    unsigned eqc = 0;
+    for (int base = start; base < end; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < end;
+        const uint64_t kk = valid ? dkey(src[b + i]) : 0;
+        eqc += __popc(__ballot_sync(0xffffffffu, valid && kk == v));
+    }
+    if (lane == 0) w_eq[w] = eqc;
+    __syncthreads();
+    unsigned eqrun = eq_off[(int64_t)s * nch + c];
+    for (int j = 0; j < w; j++) eqrun += w_eq[j];
+    unsigned leftc = 0;
+    for (int base = start; base < end; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < end;
+        const uint64_t kk = valid ? dkey(src[b + i]) : 0;
+        const bool eq = valid && kk == v;
+        const unsigned em = __ballot_sync(0xffffffffu, eq);
+        const unsigned rank = eqrun + __popc(em & lanemask_lt());
+        const bool f = valid && (kk < v || (eq && rank < need_eq));
+        const unsigned fm = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) flags[(base - cstart) >> 5] = fm;
+        leftc += __popc(fm);
+        eqrun += __popc(em);
+    }
+    if (lane == 0) w_left[w] = leftc;
+    __syncthreads();
+    unsigned lrun = left_off[(int64_t)s * nch + c];
+    for (int j = 0; j < w; j++) lrun += w_left[j];
+    for (int base = start; base < end; base += 32) {
+        const int i = base + lane;
+        const unsigned fm = flags[(base - cstart) >> 5];
+        const bool f = (fm >> lane) & 1u;
+        const unsigned lrank = lrun + __popc(fm & lanemask_lt());
+        if (i < end) {
+            const int rel = f ? (int)lrank : k + (i - (int)lrank);
+            if (rel >= 0 && rel < n) {
+                xout[b + rel] = xin[b + i];
+                yout[b + rel] = yin[b + i];
+                zout[b + rel] = zin[b + i];
+                iout[b + rel] = iin[b + i];
+            } else {
+                atomicOr(err, 2);  // inconsistent partition: report, never write outside the box
+            }
+        }
+        lrun += __popc(fm);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Children's cells and geometry
+// --------------------------------------------------------------------------
+__global__ void k_children(int level, const int32_t *count, const uint64_t *sel_v,
+                           const unsigned long long *sel_minr, double *lo, double *hi, double *centre,
+                           double *radius, int32_t *axis, double *plane) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (1 << level)) return;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    const int n = count[g], ax = axis[g];
+    double sp;
+    if (n >= 2)
+        sp = __dmul_rn(0.5, __dadd_rn(dkey_inv(sel_v[s]), dkey_inv(sel_minr[s])));
+    else if (n == 1)
+        sp = dkey_inv(sel_minr[s]);
+    else
+        sp = __dmul_rn(0.5, __dadd_rn(lo[3 * g + ax], hi[3 * g + ax]));
+    plane[g] = sp;
+    const int64_t a = 2 * g + 1, c = 2 * g + 2;
+    for (int d = 0; d < 3; d++) {
+        lo[3 * a + d] = lo[3 * g + d];
+        hi[3 * a + d] = hi[3 * g + d];
+        lo[3 * c + d] = lo[3 * g + d];
+        hi[3 * c + d] = hi[3 * g + d];
+    }
+    hi[3 * a + ax] = sp;
+    lo[3 * c + ax] = sp;
+    box_geometry(lo, hi, centre, radius, axis, a);
+    box_geometry(lo, hi, centre, radius, axis, c);
+}
+
+}  // namespace
+
+// Builds the tree: points (device, n x 3, dtype) -> leaf-order SoA positions,
+// permutation, and all box cells/geometry. Box begin/count are host-computed
+// (they depend on n and the level only) and already on the device.
+cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
+    const int64_t n = P.n;
+    cudaStream_t st = P.stream;
+    const size_t nb = (size_t)n;
+    // ping-pong buffers
+    double *x2 = (double *)dalloc(P, nb * 8), *y2 = (double *)dalloc(P, nb * 8),
+           *z2 = (double *)dalloc(P, nb * 8);
+    int32_t *i2 = (int32_t *)dalloc(P, nb * 4);
+    const int maxseg = 1 << (P.B > 0 ? P.B - 1 : 0);
+    uint64_t *sel_v = (uint64_t *)dalloc(P, (size_t)maxseg * 8);
+    uint64_t *sel_prefix = (uint64_t *)dalloc(P, (size_t)maxseg * 8);
+    unsigned long long *sel_minr = (unsigned long long *)dalloc(P, (size_t)maxseg * 8);
+    unsigned *sel_rrem = (unsigned *)dalloc(P, (size_t)maxseg * 4);
+    unsigned long long *bbox = (unsigned long long *)dalloc(P, 64);
+    if (!x2 || !y2 || !z2 || !i2 || !sel_v || !sel_prefix || !sel_minr || !sel_rrem || !bbox)
+        return cudaErrorMemoryAllocation;
+
+    unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+    cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    const int pgrid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_prepare<double>, pgrid, kThreads, 0, st, (const double *)pts, n, P.x, P.y, P.z,
+                                                      P.perm, bbox, P.d_err);
+    else
+        FMM_LAUNCH(k_prepare<float>, pgrid, kThreads, 0, st, (const float *)pts, n, P.x, P.y, P.z,
+                                                     P.perm, bbox, P.d_err);
+    FMM_LAUNCH(k_root, 1, 32, 0, st, bbox, P.lo, P.hi, P.centre, P.radius, P.axis);
+
+    double *xa = P.x, *ya = P.y, *za = P.z, *xb = x2, *yb = y2, *zb = z2;
+    int32_t *ia = P.perm, *ib = i2;
+    unsigned *ghist = nullptr, *chunk_lt = nullptr, *chunk_eq = nullptr, *eq_off = nullptr,
+             *left_off = nullptr;
+    size_t chunk_alloc = 0, ghist_alloc = 0;
+    for (int l = 0; l < P.B; l++) {
+        const int S = 1 << l;
+        const int64_t maxn = (n + S - 1) / S;
+        if (maxn <= kSmallCap) {
+            FMM_LAUNCH(k_split_small, S, kThreads, 0, st, l, xa, ya, za, ia, xb, yb, zb, ib, P.begin,
+                                                  P.count, P.axis, sel_v, sel_minr, P.d_err);
+        } else {
+            const int nch = (int)((maxn + kChunk - 1) / kChunk);
+            const size_t need_c = (size_t)S * nch * 4, need_h = (size_t)S * 256 * 4;
+            if (need_c > chunk_alloc) {
+                if (chunk_alloc) {
+                    dfree(P, chunk_lt, chunk_alloc);
+                    dfree(P, chunk_eq, chunk_alloc);
+                    dfree(P, eq_off, chunk_alloc);
+                    dfree(P, left_off, chunk_alloc);
+                }
+                chunk_alloc = need_c;
+                chunk_lt = (unsigned *)dalloc(P, need_c);
+                chunk_eq = (unsigned *)dalloc(P, need_c);
+                eq_off = (unsigned *)dalloc(P, need_c);
+                left_off = (unsigned *)dalloc(P, need_c);
+                if (!chunk_lt || !chunk_eq || !eq_off || !left_off) return cudaErrorMemoryAllocation;
+            }
+            if (need_h > ghist_alloc) {
+                if (ghist_alloc) dfree(P, ghist, ghist_alloc);
+                ghist_alloc = need_h;
+                ghist = (unsigned *)dalloc(P, need_h);
+                if (!ghist) return cudaErrorMemoryAllocation;
+            }
+            FMM_LAUNCH(k_sel_init, S, 256, 0, st, l, P.count, sel_prefix, sel_rrem, sel_minr, ghist);
+            const dim3 grid(nch, S);
+            for (int pass = 0; pass < 8; pass++) {
+                FMM_LAUNCH(k_sel_hist, grid, kThreads, 0, st, l, pass, xa, ya, za, P.begin, P.count, P.axis,
+                                                      sel_prefix, ghist);
+                FMM_LAUNCH(k_sel_pick, S, 32, 0, st, pass, ghist, sel_prefix, sel_rrem);
+            }
+            FMM_LAUNCH(k_sel_count, grid, kThreads, 0, st, l, nch, xa, ya, za, P.begin, P.count, P.axis,
+                                                   sel_prefix, chunk_lt, chunk_eq, sel_minr);
+            FMM_LAUNCH(k_sel_offsets, (S + 127) / 128, 128, 0, st, l, nch, P.count, chunk_lt, chunk_eq,
+                                                           sel_prefix, sel_rrem, eq_off, left_off,
+                                                           sel_minr, sel_v);
+            FMM_LAUNCH(k_sel_scatter, grid, kThreads, 0, st, l, nch, xa, ya, za, ia, xb, yb, zb, ib, P.begin,
+                                                     P.count, P.axis, sel_prefix, sel_rrem, eq_off,
+                                                     left_off, P.d_err);
+        }
+        FMM_LAUNCH(k_children, (S + 127) / 128, 128, 0, st, l, P.count, sel_v, sel_minr,
+                                                    P.lo, P.hi, P.centre, P.radius, P.axis, P.plane);
+        std::swap(xa, xb);
+        std::swap(ya, yb);
+        std::swap(za, zb);
+        std::swap(ia, ib);
+    }
+    cudaError_t e = cudaGetLastError();
+    // leave the final order in the plan's primary buffers
+    if (xa != P.x) {
+        cudaMemcpyAsync(P.x, xa, nb * 8, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(P.y, ya, nb * 8, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(P.z, za, nb * 8, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(P.perm, ia, nb * 4, cudaMemcpyDeviceToDevice, st);
+    }
+    if (chunk_alloc) {
+        dfree(P, chunk_lt, chunk_alloc);
+        dfree(P, chunk_eq, chunk_alloc);
+        dfree(P, eq_off, chunk_alloc);
+        dfree(P, left_off, chunk_alloc);
+    }
+    if (ghist_alloc) dfree(P, ghist, ghist_alloc);
+    dfree(P, x2, nb * 8);
+    dfree(P, y2, nb * 8);
+    dfree(P, z2, nb * 8);
+    dfree(P, i2, nb * 4);
+    dfree(P, sel_v, (size_t)maxseg * 8);
+    dfree(P, sel_prefix, (size_t)maxseg * 8);
+    dfree(P, sel_minr, (size_t)maxseg * 8);
+    dfree(P, sel_rrem, (size_t)maxseg * 4);
+    dfree(P, bbox, 64);
+    return e;
+}
+
+}  // namespace fmm

@@ -176,3 +176,17 @@ def test_list_counts_follow_cost_model_directions():
     w4, s4 = counts(6, 0.5)
     assert w3 > w4
     assert s3 * (4000 / 256) ** 2 < s4 * (4000 / 64) ** 2
+
+
+@pytest.mark.parametrize("kind,n", [("uniform", 999), ("plummer", 1200), ("gmm", 64)])
+def test_single_box_bisection_matches_tree(kind, n):
+    """The one-box bisection agrees with the tree's own splits of every box."""
+    x = inputs.points(kind, n, seed=6) + 0.0
+    t = oracle.Tree(x, 4, 2, 0.5).tree()
+    for g in range(15):
+        pts = np.sort(t["perm"][t["begin"][g]:t["begin"][g] + t["count"][g]])
+        ax, left, plane = oracle.bisect_box(x[pts], t["lo"][g], t["hi"][g])
+        assert ax == t["axis"][g] and plane == t["plane"][g]
+        a = 2 * g + 1
+        want = set(t["perm"][t["begin"][a]:t["begin"][a] + t["count"][a]])
+        assert set(pts[left]) == want
