@@ -224,6 +224,40 @@ int fmm_stage_times(fmm_plan_t plan, double *ms);
  */
 int64_t fmm_kernel_launches(void);
 
+/*
+ * fmm_orb_order_noalloc -- the leaf order of the balanced tree (the `perm`
+ * that fmm_plan_tree reports for the same points and levels) for small point
+ * sets, computed without allocating any device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code that runs while a stream is being
+ * captured into a CUDA graph (an allocation call there breaks the capture),
+ * plug-ins inside a host application that owns every byte of device memory,
+ * and real-time loops that may not pay for an allocation. It runs the same
+ * median-split kernels as fmm_plan, with all of their scratch (both copies of
+ * the positions and indices, the box cells, the selection state) in one
+ * static device array of FMM_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   points  DEVICE pointer, n x 3 row-major, dtype FMM_F64 or FMM_F32.
+ *   n       1 <= n <= FMM_NOALLOC_MAX_POINTS.
+ *   levels  0 <= levels <= FMM_NOALLOC_MAX_LEVELS.
+ *   perm    DEVICE pointer, n int32: original index of each leaf-order slot.
+ *   stream  cudaStream_t for the work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins. Every call shares the one array and
+ * re-initialises what must start cleared, so calls that overlap on the GPU
+ * (other streams, other host threads) race and corrupt each other's results:
+ * serialise them. Synchronises `stream` to report non-finite points.
+ * Errors: FMM_EINVAL (NULL or host pointers, n or levels out of range, bad
+ * dtype), FMM_ENONFINITE, FMM_ECUDA. Calls no allocating routine.
+ */
+#define FMM_NOALLOC_MAX_POINTS 4096
+#define FMM_NOALLOC_MAX_LEVELS 12
+#define FMM_NOALLOC_SCRATCH_BYTES (1280u * 1024u)
+int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, int levels, int32_t *perm,
+                          void *stream);
+
 /* fmm_strerror -- static text for a status code. */
 const char *fmm_strerror(int status);
 

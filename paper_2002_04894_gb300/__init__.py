@@ -58,7 +58,9 @@ class fmm_stats(C.Structure):
 _LIB = None
 EXPORTS = ("fmm_plan", "fmm_eval", "fmm_destroy", "fmm_direct", "fmm_plan_stats",
            "fmm_plan_tree", "fmm_plan_list", "fmm_eval_expansions", "fmm_strerror",
-           "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches")
+           "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches",
+           "fmm_orb_order_noalloc")
+FMM_NOALLOC_MAX_POINTS, FMM_NOALLOC_MAX_LEVELS = 4096, 12
 
 
 def lib_path() -> str:
@@ -100,6 +102,8 @@ def load(build: bool = True) -> C.CDLL:
     lib.fmm_stage_times.restype = i32
     lib.fmm_kernel_launches.argtypes = []
     lib.fmm_kernel_launches.restype = i64
+    lib.fmm_orb_order_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
+    lib.fmm_orb_order_noalloc.restype = i32
     _LIB = lib
     return lib
 
@@ -324,3 +328,18 @@ def fmm_stage_times(plan: Plan) -> dict:
 def fmm_kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().fmm_kernel_launches())
+
+
+def fmm_orb_order_noalloc(points, levels: int, perm=None, stream=None):
+    """Leaf order of the balanced tree for <= 4096 points without any device
+    allocation inside the library (for callers that cannot allocate, e.g.
+    during stream capture). `points` and `perm` must be CUDA tensors; perm is
+    an int32 tensor of n entries (created here if not given)."""
+    import torch
+    n = int(points.shape[0])
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device=points.device)
+    _check(load().fmm_orb_order_noalloc(points.data_ptr(), n, _dtype_code(points), int(levels),
+                                        perm.data_ptr(), _stream(stream)),
+           "fmm_orb_order_noalloc")
+    return perm

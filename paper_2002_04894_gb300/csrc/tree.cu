@@ -642,4 +642,147 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
     return e;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free ORB leaf order for small point sets (fmm_orb_order_noalloc).
+//
+// For callers that cannot allocate device memory (stream capture, host
+// applications that own all device memory, real-time loops): the small-regime
+// split kernels above run with every scratch buffer carved out of one static
+// device array. Up to FMM_NOALLOC_MAX_POINTS points every level is in the
+// one-CTA regime, so no chunk counters or histograms are needed.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNaMaxN = FMM_NOALLOC_MAX_POINTS;
+constexpr int kNaMaxBoxes = (2 << FMM_NOALLOC_MAX_LEVELS) - 1;
+constexpr int kNaMaxSeg = 1 << (FMM_NOALLOC_MAX_LEVELS - 1);
+constexpr size_t na_round(size_t b) { return (b + 255) / 256 * 256; }
+// byte offsets of the scratch buffers inside the static array
+constexpr size_t kNaPos = 0;                                        // 6 x n doubles (2 copies of x|y|z)
+constexpr size_t kNaIdx = kNaPos + na_round(6ull * kNaMaxN * 8);    // 2 x n int32
+constexpr size_t kNaBox = kNaIdx + na_round(2ull * kNaMaxN * 4);    // begin|count|axis int32
+constexpr size_t kNaGeo = kNaBox + na_round(3ull * kNaMaxBoxes * 4);  // lo|hi|centre (x3) radius|plane
+constexpr size_t kNaSel = kNaGeo + na_round(11ull * kNaMaxBoxes * 8); // sel_v|sel_minr
+constexpr size_t kNaMisc = kNaSel + na_round(2ull * kNaMaxSeg * 8);  // bbox[6] u64, err
+constexpr size_t kNaEnd = kNaMisc + 256;
+static_assert(kNaEnd <= FMM_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
+
+}  // namespace
+
+// The scratch itself: file scope, one per device that loads the library.
+static __device__ __align__(256) unsigned char g_orb_scratch[FMM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Resets what must start cleared (bounding box, error word, plane values) and
+// writes the boxes' point ranges, which depend on n and the level only.
+__global__ void k_noalloc_init(int n, int levels, int32_t *begin, int32_t *count,
+                               unsigned long long *bbox, int *err, double *plane) {
+    const int nb = (2 << levels) - 1;
+    for (int g = threadIdx.x; g < nb; g += blockDim.x) plane[g] = 0.0;
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; a++) {
+            bbox[a] = ~0ull;
+            bbox[3 + a] = 0ull;
+        }
+        *err = 0;
+        begin[0] = 0;
+        count[0] = n;
+        for (int g = 0; g < nb - (1 << levels); g++) {
+            const int k = count[g] / 2;
+            begin[2 * g + 1] = begin[g];
+            count[2 * g + 1] = k;
+            begin[2 * g + 2] = begin[g] + k;
+            count[2 * g + 2] = count[g] - k;
+        }
+    }
+}
+
+unsigned char *g_na_addr[64] = {};
+std::atomic<int> g_na_lock{0};
+
+// Device address of g_orb_scratch on the current device (looked up once).
+cudaError_t noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    while (g_na_lock.exchange(1, std::memory_order_acquire)) {
+    }
+    if (!g_na_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_orb_scratch);
+        if (e == cudaSuccess) g_na_addr[dev] = (unsigned char *)p;
+    }
+    *out = g_na_addr[dev];
+    g_na_lock.store(0, std::memory_order_release);
+    return e;
+}
+
+bool na_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 }  // namespace fmm
+
+extern "C" int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, int levels,
+                                     int32_t *perm, void *stream) {
+    using namespace fmm;
+    if (!points || !perm || n < 1 || n > kNaMaxN || levels < 0 ||
+        levels > FMM_NOALLOC_MAX_LEVELS || (dtype != FMM_F64 && dtype != FMM_F32))
+        return FMM_EINVAL;
+    if (!na_device_ptr(points) || !na_device_ptr(perm)) return FMM_EINVAL;
+    unsigned char *s = nullptr;
+    cudaError_t e = noalloc_scratch(&s);
+    if (e != cudaSuccess) return FMM_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *pos = (double *)(s + kNaPos);
+    double *xa = pos, *ya = pos + kNaMaxN, *za = pos + 2 * kNaMaxN;
+    double *xb = pos + 3 * kNaMaxN, *yb = pos + 4 * kNaMaxN, *zb = pos + 5 * kNaMaxN;
+    int32_t *ia = (int32_t *)(s + kNaIdx), *ib = ia + kNaMaxN;
+    int32_t *begin = (int32_t *)(s + kNaBox), *count = begin + kNaMaxBoxes,
+            *axis = begin + 2 * kNaMaxBoxes;
+    double *geo = (double *)(s + kNaGeo);
+    double *lo = geo, *hi = geo + 3 * kNaMaxBoxes, *centre = geo + 6 * kNaMaxBoxes;
+    double *radius = geo + 9 * kNaMaxBoxes, *plane = geo + 10 * kNaMaxBoxes;
+    uint64_t *sel_v = (uint64_t *)(s + kNaSel);
+    unsigned long long *sel_minr = (unsigned long long *)(s + kNaSel) + kNaMaxSeg;
+    unsigned long long *bbox = (unsigned long long *)(s + kNaMisc);
+    int *err = (int *)(s + kNaMisc + 64);
+
+    FMM_LAUNCH(k_noalloc_init, 1, 256, 0, st, (int)n, levels, begin, count, bbox, err, plane);
+    const int pgrid = (int)((n + kThreads - 1) / kThreads);
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_prepare<double>, pgrid, kThreads, 0, st, (const double *)points, n, xa, ya, za, ia,
+                   bbox, err);
+    else
+        FMM_LAUNCH(k_prepare<float>, pgrid, kThreads, 0, st, (const float *)points, n, xa, ya, za, ia,
+                   bbox, err);
+    FMM_LAUNCH(k_root, 1, 32, 0, st, bbox, lo, hi, centre, radius, axis);
+    for (int l = 0; l < levels; l++) {
+        const int S = 1 << l;
+        FMM_LAUNCH(k_split_small, S, kThreads, 0, st, l, xa, ya, za, ia, xb, yb, zb, ib, begin, count,
+                   axis, sel_v, sel_minr, err);
+        FMM_LAUNCH(k_children, (S + 127) / 128, 128, 0, st, l, count, sel_v, sel_minr, lo, hi, centre,
+                   radius, axis, plane);
+        std::swap(xa, xb);
+        std::swap(ya, yb);
+        std::swap(za, zb);
+        std::swap(ia, ib);
+    }
+    e = cudaMemcpyAsync(perm, ia, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return FMM_ECUDA;
+    if (herr & 1) return FMM_ENONFINITE;
+    return herr ? FMM_ECUDA : FMM_OK;
+}
