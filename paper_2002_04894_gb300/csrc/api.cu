@@ -2,6 +2,7 @@
 // host/device staging and the stage order of Algorithm 1 (Tree in fmm_plan;
 // P2M, M2M, M2L, L2L, L2P, P2P in fmm_eval).
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -16,8 +17,9 @@ std::atomic<long long> g_launches{0};
 cudaError_t eval_expansions(Plan &P, const void *charges, int dtype);
 cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype);
 
-void *dalloc(Plan &P, size_t bytes) {
-    if (bytes == 0) bytes = 16;
+namespace {
+
+void *raw_alloc(Plan &P, size_t bytes) {
     if (P.has_alloc) return P.alloc.alloc(bytes, P.alloc.ctx, (void *)P.stream);
     void *p = nullptr;
     if (cudaMallocAsync(&p, bytes, P.stream) != cudaSuccess) {
@@ -27,20 +29,42 @@ void *dalloc(Plan &P, size_t bytes) {
     return p;
 }
 
-void dfree(Plan &P, void *ptr, size_t bytes) {
-    if (!ptr) return;
-    if (bytes == 0) bytes = 16;
+void raw_free(Plan &P, void *ptr, size_t bytes) {
     if (P.has_alloc)
         P.alloc.free(ptr, bytes, P.alloc.ctx, (void *)P.stream);
     else
         cudaFreeAsync(ptr, P.stream);
 }
 
-void *palloc(Plan &P, size_t bytes) {
-    void *p = dalloc(P, bytes);
-    if (p) P.owned.push_back({p, bytes ? bytes : 16});
-    return p;
+void *arena_alloc(Plan &P, Arena &A, size_t bytes) {
+    bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+    if (bytes > A.left) {
+        const size_t bs = std::max(bytes, std::max<size_t>(A.hint, 1 << 20));
+        void *p = raw_alloc(P, bs);
+        if (!p) return nullptr;
+        A.blocks.push_back({p, bs});
+        A.cur = (char *)p;
+        A.left = bs;
+        A.hint = std::max<size_t>(A.hint / 2, 1 << 20);  // later blocks: smaller
+    }
+    void *r = A.cur;
+    A.cur += bytes;
+    A.left -= bytes;
+    return r;
 }
+
+}  // namespace
+
+void arena_release(Plan &P, Arena &A) {
+    for (auto it = A.blocks.rbegin(); it != A.blocks.rend(); ++it) raw_free(P, it->first, it->second);
+    A.blocks.clear();
+    A.cur = nullptr;
+    A.left = 0;
+}
+
+void *dalloc(Plan &P, size_t bytes) { return arena_alloc(P, P.scratch, bytes); }
+void dfree(Plan &, void *, size_t) {}
+void *palloc(Plan &P, size_t bytes) { return arena_alloc(P, P.persist, bytes); }
 
 }  // namespace fmm
 
@@ -75,8 +99,8 @@ void release(Plan &P) {
     for (int s = 0; s < FMM_NSTAGES; s++)
         for (int e = 0; e < 2; e++)
             if (P.ev[s][e]) cudaEventDestroy(P.ev[s][e]);
-    for (auto it = P.owned.rbegin(); it != P.owned.rend(); ++it) fmm::dfree(P, it->first, it->second);
-    P.owned.clear();
+    fmm::arena_release(P, P.scratch);
+    fmm::arena_release(P, P.persist);
     cudaStreamSynchronize(P.stream);
     cudaGetLastError();
 }
@@ -155,6 +179,11 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
         return status;
     };
 
+    // arena sizes: points, boxes, expansions and a guess for the lists
+    P.persist.hint = (size_t)n * 96 + (size_t)P.nbox * (128 + 32 * (size_t)P.nc) +
+                     (size_t)P.nleaf * 2048 + (1 << 20);
+    P.scratch.hint = (size_t)n * 40 + (size_t)P.nbox * 64 + (1 << 20);
+
     // box point ranges depend on n and the level only
     std::vector<int32_t> hb(P.nbox), hc(P.nbox);
     hb[0] = 0;
@@ -219,6 +248,13 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     if (P.capacity_exceeded) return fail(FMM_ECAPACITY);
     if (e != cudaSuccess) return fail(cuda_status(e));
 
+    e = fmm::m2l_setup(P);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    if (P.prec == FMM_PREC_MIXED) {
+        e = fmm::mixed_setup(P);
+        if (e == cudaSuccess) e = fmm::m2l_f32_setup(P);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+    }
     P.q = (double *)fmm::palloc(P, n * 8);
     P.far_phi = (double *)fmm::palloc(P, n * 8);
     P.far_E = (double *)fmm::palloc(P, n * 24);
@@ -228,6 +264,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     e = cudaStreamSynchronize(P.stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(cuda_status(e));
+    fmm::arena_release(P, P.scratch);  // temporaries of the build, stream-ordered
     *out = H;
     return FMM_OK;
 }

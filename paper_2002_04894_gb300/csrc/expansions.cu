@@ -16,10 +16,9 @@
 // GPU mapping: P2M is one CTA per leaf with one point per lane, streaming the
 // harmonics through the Legendre recurrences and reducing each coefficient
 // over the warp; M2M/L2L are one CTA per parent with one thread per output
-// coefficient; M2L is one CTA per target box with one thread per output
-// coefficient and the irregular harmonics of each source offset built in
-// shared memory one column per thread; L2P is one thread per point with O(1)
-// registers (the series and its gradient accumulate as the recurrence runs).
+// coefficient; M2L (in m2l.cu) uses the rotational form, one weak pair per
+// thread; L2P is one thread per point with O(1) registers (the series and its
+// gradient accumulate as the recurrence runs).
 
 #include <algorithm>
 
@@ -151,54 +150,6 @@ k_m2m(int level, int p, const double *__restrict__ centre, double2 *M) {
     }
 }
 
-// M2L at one level, basic O(p^4) form: one CTA per target box of the level
-__global__ void __launch_bounds__(256)
-k_m2l(int level, int p, const int32_t *__restrict__ wptr, const int32_t *__restrict__ wsrc,
-      const double *__restrict__ centre, const double2 *__restrict__ M, double2 *L) {
-    extern __shared__ double2 sm[];
-    const int nc = ncoef(p), p2 = 2 * p;
-    double2 *Ih = sm, *Ms = sm + ncoef(p2);
-    const int64_t off = ((int64_t)1 << level) - 1;
-    const int t = blockIdx.x;
-    const int64_t gt = off + t;
-    const int e0 = wptr[t], e1 = wptr[t + 1];
-    int kk = 0, ll = 0;
-    if (threadIdx.x < nc) untri(threadIdx.x, kk, ll);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int e = e0; e < e1; e++) {
-        const int64_t gs = off + wsrc[e];
-        const double dx = centre[3 * gt] - centre[3 * gs];
-        const double dy = centre[3 * gt + 1] - centre[3 * gs + 1];
-        const double dz = centre[3 * gt + 2] - centre[3 * gs + 2];
-        if (threadIdx.x <= p2) {
-            // column m of I_n^m(d), n = m..2p
-            const int m = threadIdx.x;
-            const double r2 = dx * dx + dy * dy + dz * dz, ir2 = 1.0 / r2;
-            double2 v = make_double2(1.0 / sqrt(r2), 0.0);
-            for (int j = 1; j <= m; j++) v = cscale(cmul(v, make_double2(dx, dy)), (2 * j - 1) * ir2);
-            double2 prev = make_double2(0.0, 0.0), cur = v;
-            Ih[tri(m, m)] = cur;
-            for (int n = m + 1; n <= p2; n++) {
-                const double a = (2 * n - 1) * dz, b = (double)(n - 1 + m) * (double)(n - 1 - m);
-                const double2 nxt = make_double2((a * cur.x - b * prev.x) * ir2,
-                                                 (a * cur.y - b * prev.y) * ir2);
-                prev = cur;
-                cur = nxt;
-                Ih[tri(n, m)] = cur;
-            }
-        }
-        for (int c = threadIdx.x; c < nc; c += blockDim.x) Ms[c] = M[gs * nc + c];
-        __syncthreads();
-        if (threadIdx.x < nc) {
-            for (int n = 0; n <= p; n++)
-                for (int m = -n; m <= n; m++)
-                    acc = cadd(acc, cmul(coef_at(Ms, n, m), sview(Ih, n + kk, m + ll)));
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < nc) L[gt * nc + threadIdx.x] = (kk & 1) ? make_double2(-acc.x, -acc.y) : acc;
-}
-
 // L2L: children at `level` receive their parent's local expansion
 __global__ void __launch_bounds__(kExpThreads)
 k_l2l(int level, int p, const double *__restrict__ centre, double2 *L) {
@@ -293,14 +244,20 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     cudaStream_t st = P.stream;
     const int64_t n = P.n;
     const int nc = P.nc;
+    const bool mixed = P.prec == FMM_PREC_MIXED;
     const int gq = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
     stage_mark(P, FMM_STAGE_P2M, 0);
-    if (dtype == FMM_F64)
-        FMM_LAUNCH(k_gather_q<double>, gq, 256, 0, st, (const double *)charges, P.perm, P.q, n);
-    else
-        FMM_LAUNCH(k_gather_q<float>, gq, 256, 0, st, (const float *)charges, P.perm, P.q, n);
-    FMM_LAUNCH(k_p2m, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * nc * (kExpThreads / 32), st,
-               P.B, P.p, P.x, P.y, P.z, P.q, P.begin, P.count, P.centre, P.M);
+    if (mixed) {
+        cudaError_t e = mixed_p2m(P, charges, dtype);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (dtype == FMM_F64)
+            FMM_LAUNCH(k_gather_q<double>, gq, 256, 0, st, (const double *)charges, P.perm, P.q, n);
+        else
+            FMM_LAUNCH(k_gather_q<float>, gq, 256, 0, st, (const float *)charges, P.perm, P.q, n);
+        FMM_LAUNCH(k_p2m, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * nc * (kExpThreads / 32),
+                   st, P.B, P.p, P.x, P.y, P.z, P.q, P.begin, P.count, P.centre, P.M);
+    }
     stage_mark(P, FMM_STAGE_P2M, 1);
     stage_mark(P, FMM_STAGE_M2M, 0);
     for (int l = P.B; l >= 1; l--)
@@ -310,11 +267,14 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     // Algorithm 3: M2L at every level (each overwrites its level's L), then L2L downward
     stage_mark(P, FMM_STAGE_M2L, 0);
     cudaMemsetAsync(P.L, 0, sizeof(double2) * nc, st);  // root: no far field
-    const size_t m2l_smem = sizeof(double2) * (ncoef(2 * P.p) + nc);
-    const int m2l_threads = std::max(64, (std::max(nc, 2 * P.p + 1) + 31) / 32 * 32);
-    for (int l = 1; l <= P.B; l++)
-        FMM_LAUNCH(k_m2l, 1u << l, m2l_threads, m2l_smem, st, l, P.p, P.wptr[l], P.wsrc[l], P.centre,
-                   P.M, P.L);
+    for (int l = 1; l <= P.B; l++) {
+        if (mixed && P.Mf) {
+            cudaError_t e = m2l_f32_level(P, l);
+            if (e != cudaSuccess) return e;
+        } else {
+            m2l_level(P, l);
+        }
+    }
     stage_mark(P, FMM_STAGE_M2L, 1);
     stage_mark(P, FMM_STAGE_L2L, 0);
     for (int l = 1; l <= P.B; l++)
@@ -322,8 +282,13 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
                    P.L);
     stage_mark(P, FMM_STAGE_L2L, 1);
     stage_mark(P, FMM_STAGE_L2P, 0);
-    FMM_LAUNCH(k_l2p, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * nc, st, P.B, P.p, n, P.x, P.y,
-               P.z, P.begin, P.count, P.centre, P.L, P.far_phi, P.far_E);
+    if (mixed) {
+        cudaError_t e = mixed_l2p(P);
+        if (e != cudaSuccess) return e;
+    } else {
+        FMM_LAUNCH(k_l2p, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * nc, st, P.B, P.p, n, P.x,
+                   P.y, P.z, P.begin, P.count, P.centre, P.L, P.far_phi, P.far_E);
+    }
     stage_mark(P, FMM_STAGE_L2P, 1);
     return cudaGetLastError();
 }

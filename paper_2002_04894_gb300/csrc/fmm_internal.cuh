@@ -15,6 +15,14 @@ namespace fmm {
 // ---------------------------------------------------------------------------
 // Plan: everything lives in device memory owned by the plan.
 // ---------------------------------------------------------------------------
+// Bump allocator over a few large blocks from the caller's allocator: a plan
+// makes a handful of allocator calls instead of one per buffer.
+struct Arena {
+    std::vector<std::pair<void *, size_t>> blocks;
+    char *cur = nullptr;
+    size_t left = 0, hint = 0;
+};
+
 struct Plan {
     int64_t n = 0;
     int B = 0, p = 0, nc = 0, prec = 0, dtype = 0, device = 0;
@@ -39,6 +47,14 @@ struct Plan {
     int64_t nweak[FMM_MAX_LEVELS + 1] = {}, nstrong[FMM_MAX_LEVELS + 1] = {};
     int64_t p2p_interactions = 0;
     bool capacity_exceeded = false;
+    // M2L rotation tables (D = d(pi/2) quadrants, axial coefficients, F_nm)
+    double *m2l_tab = nullptr;
+    int m2l_ntab = 0, m2l_threads = 0;
+    size_t m2l_smem = 0;
+    // mixed precision: leaf offsets hi|lo (6n floats), float charges and far
+    // field, radius-scaled float multipoles for the single-precision M2L
+    float *hl = nullptr, *qf = nullptr, *far_phi_f = nullptr, *far_E_f = nullptr;
+    float2 *Mf = nullptr;
     // evaluation scratch
     double *q = nullptr;                 // charges in leaf order
     double2 *M = nullptr, *L = nullptr;  // nbox x nc
@@ -51,15 +67,18 @@ struct Plan {
     // per-stage device timing (FMM_FLAG_PROFILE)
     bool profile = false;
     cudaEvent_t ev[FMM_NSTAGES][2] = {};
-    // every plan-lifetime device buffer, released by fmm_destroy
-    std::vector<std::pair<void *, size_t>> owned;
+    // plan-lifetime buffers (released by fmm_destroy) and fmm_plan temporaries
+    // (released when fmm_plan returns)
+    Arena persist, scratch;
 };
 
 // Allocation through the plan's allocator (or stream-ordered cudaMallocAsync).
-// dalloc/dfree: temporaries; palloc: owned by the plan until fmm_destroy.
+// palloc: owned by the plan until fmm_destroy; dalloc: temporary of fmm_plan,
+// released in bulk when fmm_plan returns (dfree is then a no-op marker).
 void *dalloc(Plan &P, size_t bytes);
 void dfree(Plan &P, void *ptr, size_t bytes);
 void *palloc(Plan &P, size_t bytes);
+void arena_release(Plan &P, Arena &A);
 
 // Kernel launches made by the library (fmm_kernel_launches).
 extern std::atomic<long long> g_launches;
@@ -137,6 +156,15 @@ cudaError_t lists_build(Plan &P);
 cudaError_t direct_run(const void *points, const void *charges, int64_t n, int dtype,
                        const int64_t *targets, int64_t nt, void *pot, void *field,
                        cudaStream_t s);
+cudaError_t m2l_setup(Plan &P);
+void m2l_level(Plan &P, int level);
+bool m2l_f32_supported(int p);
+cudaError_t m2l_f32_setup(Plan &P);
+cudaError_t m2l_f32_level(Plan &P, int level);
+cudaError_t mixed_setup(Plan &P);
+cudaError_t mixed_p2m(Plan &P, const void *charges, int dtype);
+cudaError_t mixed_l2p(Plan &P);
+cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype);
 // device-wide exclusive scan of int32 counts (n + 1 outputs, last = total)
 cudaError_t scan_exclusive(Plan &P, const int32_t *in, int32_t *out, int64_t n);
 

@@ -1,0 +1,593 @@
+// M2L in the rotational form the paper uses (Sec. 2.1.3: rotate the z-axis of
+// the expansion onto the box-to-box vector, translate along it, rotate back;
+// O(p^3) per weak pair instead of O(p^4)).
+//
+// With d = c_t - c_s = rho (sin b cos a, sin b sin a, cos b) and the
+// normalisation F_nm = sqrt((n+|m|)! (n-|m|)!), a multipole M_n^m of the
+// source becomes a local expansion L_k^l of the target by
+//   1. u_m   = F_nm M_n^m e^{i m a}                    z-rotation (diagonal)
+//   2. Mr_n  = d^n(b)^T u                              y-rotation, per degree
+//   3. Lr_k^l = sum_n (-1)^(k+l) (n+k)!/(F_nl F_kl) rho^-(n+k+1) conj(Mr_n^l)
+//                                                     translation along z
+//   4. Lb_k  = d^k(b) Lr_k                             inverse y-rotation
+//   5. L_k^l += F_kl e^{i l a} Lb_k^l                  inverse z-rotation
+// and the y-rotation factors through the fixed matrix D = d^n(pi/2)
+// (Pinchon & Hoggan):  d_{m'm}(b) = sum_k i^{m-m'} D_{km'} D_{km} e^{ikb}.
+// Every vector has the real-source symmetry v_{-m} = (-1)^m conj(v_m), and
+// D_{k,-m} = (-1)^{n+k} D_{km}, so a product with D folds onto m, k >= 0:
+//   out_k = sum_{m = n+k mod 2} D_km Re v_m + i sum_{m != n+k mod 2} D_km Im v_m
+// with v_m doubled for m > 0: (n+1)^2 real multiply-adds per degree.
+//
+// GPU mapping (double precision): GB300's FP64 pipe retires about two
+// multiply-adds per clock per SM, so the kernel is organised to issue as few
+// FP64 instructions as possible and lets everything else be cheap: one CTA
+// per target box, one weak pair per thread, per-thread coefficient vectors
+// in shared memory (column per thread, conflict-free), D and the axial
+// coefficients in shared memory (every lane reads the same entry: broadcast),
+// and a warp shuffle reduction of the contributions into a per-warp
+// accumulator, so no atomics are needed.
+
+#include <algorithm>
+#include <cmath>
+#include <atomic>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+__device__ __forceinline__ double2 mul_ipow(int m, double2 v) {  // i^m v
+    switch (m & 3) {
+        case 0: return v;
+        case 1: return make_double2(-v.y, v.x);
+        case 2: return make_double2(-v.x, -v.y);
+        default: return make_double2(v.y, -v.x);
+    }
+}
+
+// out_k (k = 0..n) = fold(D^n) applied to v (m = 0..n); transpose: use D_mk.
+__device__ __forceinline__ void fold_apply(const double *__restrict__ D, int n, const double2 *v,
+                                           double2 *out, int stride, bool transpose) {
+    for (int k = 0; k <= n; k++) {
+        double re = 0.0, im = 0.0;
+        const int par = (n + k) & 1;
+        for (int m = par; m <= n; m += 2)
+            re = fma(transpose ? D[m * (n + 1) + k] : D[k * (n + 1) + m], v[m * stride].x, re);
+        for (int m = 1 - par; m <= n; m += 2)
+            im = fma(transpose ? D[m * (n + 1) + k] : D[k * (n + 1) + m], v[m * stride].y, im);
+        out[k * stride] = make_double2(re, im);
+    }
+}
+
+__global__ void k_m2l_rot_f64(int level, int p, const int32_t *__restrict__ wptr,
+                              const int32_t *__restrict__ wsrc, const double *__restrict__ centre,
+                              const double2 *__restrict__ M, double2 *__restrict__ L,
+                              const double *__restrict__ gtab, int ntab) {
+    extern __shared__ double2 sm2[];
+    const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, w = tid >> 5, nw = T >> 5;
+    // shared layout: [acc: nw*nc][V: nc*T][U: (p+1)*T][W: (p+1)*T][tables: ntab doubles]
+    double2 *acc = sm2;
+    double2 *V = acc + nw * nc;
+    double2 *U = V + nc * T;
+    double2 *W = U + (p + 1) * T;
+    double *tab = (double *)(W + (p + 1) * T);
+    for (int i = tid; i < ntab; i += T) tab[i] = gtab[i];
+    for (int i = tid; i < nw * nc; i += T) acc[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    // tables: D (sum (n+1)^2), axial A (sum_l (p+1-l)^2), G_nm = F_nm (nc), H = 2 F (m>0)
+    const double *Dt = tab;
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    const double *At = Dt + nD;
+    const double *Ft = At + nD;
+    double2 *v = V + tid, *u = U + tid, *x = W + tid;
+
+    const int64_t off = ((int64_t)1 << level) - 1;
+    const int t = blockIdx.x;
+    const int64_t gt = off + t;
+    const int e0 = wptr[t], e1 = wptr[t + 1];
+    const double ctx = centre[3 * gt], cty = centre[3 * gt + 1], ctz = centre[3 * gt + 2];
+
+    for (int eb = e0; eb < e1; eb += T) {
+        const int e = eb + tid;
+        const bool valid = e < e1;
+        int64_t gs = 0;
+        double dx = 1.0, dy = 0.0, dz = 0.0;
+        if (valid) {
+            gs = off + wsrc[e];
+            dx = ctx - centre[3 * gs];
+            dy = cty - centre[3 * gs + 1];
+            dz = ctz - centre[3 * gs + 2];
+        }
+        const double rxy = sqrt(dx * dx + dy * dy);
+        const double rho = sqrt(dx * dx + dy * dy + dz * dz);
+        const double rinv = 1.0 / rho;
+        const double2 ea = rxy > 0.0 ? make_double2(dx / rxy, dy / rxy) : make_double2(1.0, 0.0);
+        const double2 eb_ = make_double2(dz * rinv, rxy * rinv);
+        const double2 eai = make_double2(ea.y, -ea.x);  // -i e^{ia}
+
+        // ---- forward rotation, degree by degree -> v = Mr (tilde normalisation)
+        const double *Dn = Dt;
+        for (int n = 0; n <= p; n++) {
+            double2 ph = make_double2(1.0, 0.0);
+            for (int m = 0; m <= n; m++) {
+                const int c = tri(n, m);
+                const double2 mv = valid ? M[gs * nc + c] : make_double2(0.0, 0.0);
+                u[m * T] = cscale(cmul(mv, ph), Ft[c] * (m ? 2.0 : 1.0));
+                ph = cmul(ph, eai);
+            }
+            fold_apply(Dn, n, u, x, T, false);
+            double2 pb = make_double2(1.0, 0.0);
+            for (int k = 0; k <= n; k++) {
+                x[k * T] = cscale(cmul(x[k * T], pb), k ? 2.0 : 1.0);
+                pb = cmul(pb, eb_);
+            }
+            fold_apply(Dn, n, x, u, T, true);
+            for (int m = 0; m <= n; m++) v[tri(n, m) * T] = mul_ipow(m, u[m * T]);
+            Dn += (n + 1) * (n + 1);
+        }
+        // ---- translation along z, order by order (in place)
+        const double *Al = At;
+        double rl = 1.0;  // rho^-l
+        for (int l = 0; l <= p; l++) {
+            const int len = p + 1 - l;
+            double rp = rl;
+            for (int n = l; n <= p; n++) {
+                const double2 mr = v[tri(n, l) * T];
+                u[(n - l) * T] = make_double2(mr.x * rp, -mr.y * rp);
+                rp *= rinv;
+            }
+            double rk = rl * rinv;  // rho^-(k+1) at k = l
+            for (int k = l; k <= p; k++) {
+                double re = 0.0, im = 0.0;
+                const double *a = Al + (k - l) * len;
+                for (int j = 0; j < len; j++) {
+                    const double2 s = u[j * T];
+                    re = fma(a[j], s.x, re);
+                    im = fma(a[j], s.y, im);
+                }
+                v[tri(k, l) * T] = make_double2(re * rk, im * rk);
+                rk *= rinv;
+            }
+            Al += len * len;
+            rl *= rinv;
+        }
+        // ---- inverse rotation, degree by degree; reduce over the warp
+        Dn = Dt;
+        for (int k = 0; k <= p; k++) {
+            for (int m = 0; m <= k; m++)
+                u[m * T] = cscale(mul_ipow(m, v[tri(k, m) * T]), m ? 2.0 : 1.0);
+            fold_apply(Dn, k, u, x, T, false);
+            double2 pb = make_double2(1.0, 0.0);
+            for (int j = 0; j <= k; j++) {
+                x[j * T] = cscale(cmul(x[j * T], pb), j ? 2.0 : 1.0);
+                pb = cmul(pb, eb_);
+            }
+            fold_apply(Dn, k, x, u, T, true);
+            double2 ph = make_double2(1.0, 0.0);
+            for (int l = 0; l <= k; l++) {
+                const int c = tri(k, l);
+                double2 r = cscale(cmul(mul_ipow(4 - (l & 3), u[l * T]), ph), Ft[c]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+                    r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+                }
+                if (lane == (c & 31)) acc[w * nc + c] = cadd(acc[w * nc + c], r);
+                ph = cmul(ph, ea);
+            }
+            Dn += (k + 1) * (k + 1);
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < nc; c += T) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int j = 0; j < nw; j++) s = cadd(s, acc[j * nc + c]);
+        L[gt * nc + c] = s;
+    }
+}
+
+long double factl(int n) {
+    long double r = 1.0L;
+    for (int i = 2; i <= n; i++) r *= (long double)i;
+    return r;
+}
+
+// Wigner d^n_{k m}(pi/2) by the explicit sum, in long double (the sum
+// cancels; double loses ~5 digits by degree 20).
+long double wigner_half_pi(int n, int k, int m) {
+    long double tot = 0.0L;
+    const long double c2n = powl(0.5L, (long double)n);
+    for (int s = std::max(0, m - k); s <= std::min(n + m, n - k); s++) {
+        const long double term =
+            c2n / (factl(n + m - s) * factl(s) * factl(k - m + s) * factl(n - k - s));
+        tot += ((k - m + s) & 1) ? -term : term;
+    }
+    return sqrtl(factl(n + k) * factl(n - k) * factl(n + m) * factl(n - m)) * tot;
+}
+
+}  // namespace
+
+// Tables for order p: D_n quadrants, axial coefficients, F_nm.
+std::vector<double> m2l_tables(int p) {
+    std::vector<double> t;
+    for (int n = 0; n <= p; n++)
+        for (int k = 0; k <= n; k++)
+            for (int m = 0; m <= n; m++) t.push_back((double)wigner_half_pi(n, k, m));
+    auto F = [](int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); };
+    for (int l = 0; l <= p; l++)
+        for (int k = l; k <= p; k++)
+            for (int n = l; n <= p; n++) {
+                long double a = factl(n + k) / (F(n, l) * F(k, l));
+                t.push_back((double)(((k + l) & 1) ? -a : a));
+            }
+    for (int n = 0; n <= p; n++)
+        for (int m = 0; m <= n; m++) t.push_back((double)F(n, m));
+    return t;
+}
+
+cudaError_t m2l_setup(Plan &P) {
+    const std::vector<double> t = m2l_tables(P.p);
+    P.m2l_ntab = (int)t.size();
+    P.m2l_tab = (double *)palloc(P, t.size() * 8);
+    if (!P.m2l_tab) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemcpyAsync(P.m2l_tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, P.stream);
+    if (e != cudaSuccess) return e;
+    // stream-ordered copy from pageable memory completes before return
+    const int nc = P.nc;
+    int threads = 64;
+    auto smem = [&](int T) {
+        return (size_t)(T / 32) * nc * 16 + (size_t)T * (nc + 2 * (P.p + 1)) * 16 + t.size() * 8;
+    };
+    if (smem(threads) > 220 * 1024) threads = 32;
+    P.m2l_threads = threads;
+    P.m2l_smem = smem(threads);
+    return cudaFuncSetAttribute(k_m2l_rot_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)P.m2l_smem);
+}
+
+void m2l_level(Plan &P, int l) {
+    FMM_LAUNCH(k_m2l_rot_f64, 1u << l, P.m2l_threads, P.m2l_smem, P.stream, l, P.p, P.wptr[l],
+               P.wsrc[l], P.centre, P.M, P.L, P.m2l_tab, P.m2l_ntab);
+}
+
+
+// ---------------------------------------------------------------------------
+// Single-precision rotational M2L (FMM_PREC_MIXED).
+//
+// Same five steps, on scaled coefficients: the source multipole is read as
+// Mhat_n = M_n / r_s^n (float, prepared once per box) and the contribution is
+// formed as Lhat_k = r_t^k L_k, so the translation becomes
+//   Lhat r_k^l = (1/rho) (r_t/rho)^k sum_n A(k,n,l) (r_s/rho)^n conj(Mhat r_n^l)
+// with r_s/rho, r_t/rho < 1 for every weak pair: all float values stay O(1).
+// The order p is a template parameter, so every loop is unrolled, the per-
+// degree vectors live in registers and the fixed tables (D, A, F) are read as
+// constant-bank operands of the multiply-adds; the full coefficient vector
+// between the steps lives in shared memory, one column per thread. The
+// target's local expansion is accumulated in double.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPMax = FMM_MAX_P;
+constexpr int kTabN = (kPMax + 1) * (kPMax + 2) * (2 * kPMax + 3) / 6;  // sum (n+1)^2
+__constant__ float c_D[kTabN];     // D_n quadrant, offset n(n+1)(2n+1)/6, [k][m]
+__constant__ float c_A[kTabN];     // axial, per l a (kPMax+1-l)^2 block [k-l][n-l]
+__constant__ float c_F[(kPMax + 1) * (kPMax + 2) / 2];
+
+__host__ __device__ constexpr int dof(int n) { return n * (n + 1) * (2 * n + 1) / 6; }
+__host__ __device__ constexpr int aof(int l) {
+    // sum_{j<l} (kPMax+1-j)^2
+    return dof(kPMax + 1) - dof(kPMax + 1 - l);
+}
+
+__device__ __forceinline__ float2 fmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 fipow(int m, float2 v) {
+    switch (m & 3) {
+        case 0: return v;
+        case 1: return make_float2(-v.y, v.x);
+        case 2: return make_float2(-v.x, -v.y);
+        default: return make_float2(v.y, -v.x);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void ffold(const float2 (&v)[N + 1], float2 (&out)[N + 1], bool tr) {
+#pragma unroll
+    for (int k = 0; k <= N; k++) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int m = 0; m <= N; m++) {
+            const float d = tr ? c_D[dof(N) + m * (N + 1) + k] : c_D[dof(N) + k * (N + 1) + m];
+            if (((N + k + m) & 1) == 0)
+                re = fmaf(d, v[m].x, re);
+            else
+                im = fmaf(d, v[m].y, im);
+        }
+        out[k] = make_float2(re, im);
+    }
+}
+
+// forward rotation of degree N of the scaled source multipole into V
+template <int N>
+__device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, float2 *V, int T, float2 eai,
+                                     float2 ebv) {
+    float2 u[N + 1], w[N + 1];
+    float2 ph = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int m = 0; m <= N; m++) {
+        const float2 mv = Ms[tri(N, m)];
+        const float s = c_F[tri(N, m)] * (m ? 2.f : 1.f);
+        const float2 t = fmulc(mv, ph);
+        u[m] = make_float2(t.x * s, t.y * s);
+        ph = fmulc(ph, eai);
+    }
+    ffold<N>(u, w, false);
+    float2 pb = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int k = 0; k <= N; k++) {
+        const float2 t = fmulc(w[k], pb);
+        w[k] = k ? make_float2(2.f * t.x, 2.f * t.y) : t;
+        pb = fmulc(pb, ebv);
+    }
+    ffold<N>(w, u, true);
+#pragma unroll
+    for (int m = 0; m <= N; m++) V[tri(N, m) * T] = fipow(m, u[m]);
+}
+
+// inverse rotation of degree N; warp-reduce into the per-warp accumulator
+template <int N>
+__device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 ebv, double2 *acc,
+                                     int lane) {
+    float2 u[N + 1], w[N + 1];
+#pragma unroll
+    for (int m = 0; m <= N; m++) {
+        const float2 t = fipow(m, V[tri(N, m) * T]);
+        u[m] = m ? make_float2(2.f * t.x, 2.f * t.y) : t;
+    }
+    ffold<N>(u, w, false);
+    float2 pb = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int j = 0; j <= N; j++) {
+        const float2 t = fmulc(w[j], pb);
+        w[j] = j ? make_float2(2.f * t.x, 2.f * t.y) : t;
+        pb = fmulc(pb, ebv);
+    }
+    ffold<N>(w, u, true);
+    float2 ph = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int l = 0; l <= N; l++) {
+        const int c = tri(N, l);
+        const float2 t = fmulc(fipow(4 - (l & 3), u[l]), ph);
+        float rx = t.x * c_F[c], ry = t.y * c_F[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rx += __shfl_xor_sync(0xffffffffu, rx, o);
+            ry += __shfl_xor_sync(0xffffffffu, ry, o);
+        }
+        if (lane == (c & 31)) acc[c] = make_double2(acc[c].x + rx, acc[c].y + ry);
+        ph = fmulc(ph, ea);
+    }
+}
+
+// translation along z of order L (orders P+1-L coefficients), in place in V;
+// qs = r_s / rho, qt = r_t / rho
+template <int P, int L>
+__device__ __noinline__ void axial_ord(float2 *V, int T, float qs, float qt, float rinv) {
+    constexpr int len = P + 1 - L;
+    float2 s[len];
+    float sp = 1.f;
+#pragma unroll
+    for (int j = 0; j < L; j++) sp *= qs;
+#pragma unroll
+    for (int n = L; n <= P; n++) {
+        const float2 mr = V[tri(n, L) * T];
+        s[n - L] = make_float2(mr.x * sp, -mr.y * sp);
+        sp *= qs;
+    }
+    float tp = rinv;
+#pragma unroll
+    for (int j = 0; j < L; j++) tp *= qt;
+#pragma unroll
+    for (int k = L; k <= P; k++) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int n = L; n <= P; n++) {
+            const float a = c_A[aof(L) + (k - L) * (kPMax + 1 - L) + (n - L)];
+            re = fmaf(a, s[n - L].x, re);
+            im = fmaf(a, s[n - L].y, im);
+        }
+        V[tri(k, L) * T] = make_float2(re * tp, im * tp);
+        tp *= qt;
+    }
+}
+
+template <int P, int N>
+struct Seq {
+    __device__ static __forceinline__ void fwd(const float2 *Ms, float2 *V, int T, float2 eai,
+                                               float2 ebv) {
+        fwd_deg<N>(Ms, V, T, eai, ebv);
+        Seq<P, N + 1>::fwd(Ms, V, T, eai, ebv);
+    }
+    __device__ static __forceinline__ void axial(float2 *V, int T, float qs, float qt, float rinv) {
+        axial_ord<P, N>(V, T, qs, qt, rinv);
+        Seq<P, N + 1>::axial(V, T, qs, qt, rinv);
+    }
+    __device__ static __forceinline__ void bwd(const float2 *V, int T, float2 ea, float2 ebv,
+                                               double2 *acc, int lane) {
+        bwd_deg<N>(V, T, ea, ebv, acc, lane);
+        Seq<P, N + 1>::bwd(V, T, ea, ebv, acc, lane);
+    }
+};
+template <int P>
+struct Seq<P, P + 1> {
+    __device__ static __forceinline__ void fwd(const float2 *, float2 *, int, float2, float2) {}
+    __device__ static __forceinline__ void axial(float2 *, int, float, float, float) {}
+    __device__ static __forceinline__ void bwd(const float2 *, int, float2, float2, double2 *, int) {}
+};
+
+constexpr int kF32Threads = 128;
+
+template <int P>
+__global__ void __launch_bounds__(kF32Threads)
+k_m2l_rot_f32(int level, const int32_t *__restrict__ wptr, const int32_t *__restrict__ wsrc,
+              const double *__restrict__ centre, const double *__restrict__ radius,
+              const float2 *__restrict__ Mf, double2 *__restrict__ L) {
+    constexpr int NC = (P + 1) * (P + 2) / 2;
+    extern __shared__ double2 smd[];
+    double2 *acc = smd;                                   // [warps][NC]
+    float2 *V = (float2 *)(acc + (kF32Threads / 32) * NC);  // [NC][threads]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < (kF32Threads / 32) * NC; i += kF32Threads) acc[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const int64_t off = ((int64_t)1 << level) - 1;
+    const int t = blockIdx.x;
+    const int64_t gt = off + t;
+    const int e0 = wptr[t], e1 = wptr[t + 1];
+    const double ctx = centre[3 * gt], cty = centre[3 * gt + 1], ctz = centre[3 * gt + 2];
+    const double rt = radius[gt] > 0.0 ? radius[gt] : 1.0;
+    float2 *v = V + tid;
+    for (int eb = e0; eb < e1; eb += kF32Threads) {
+        const int e = eb + tid;
+        const bool valid = e < e1;
+        int64_t gs = 0;
+        double dx = 1.0, dy = 0.0, dz = 0.0, rs = 1.0;
+        if (valid) {
+            gs = off + wsrc[e];
+            dx = ctx - centre[3 * gs];
+            dy = cty - centre[3 * gs + 1];
+            dz = ctz - centre[3 * gs + 2];
+            rs = radius[gs] > 0.0 ? radius[gs] : 1.0;
+        }
+        const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
+        const float2 ea = rxy > 0.0 ? make_float2((float)(dx / rxy), (float)(dy / rxy))
+                                    : make_float2(1.f, 0.f);
+        const float2 ebv = make_float2((float)(dz / rho), (float)(rxy / rho));
+        const float2 eai = make_float2(ea.y, -ea.x);
+        const float rinv = (float)(1.0 / rho);
+        const float qs = (float)(rs / rho), qt = (float)(rt / rho);
+        if (valid) {
+            Seq<P, 0>::fwd(Mf + gs * NC, v, kF32Threads, eai, ebv);
+        } else {
+            for (int c = 0; c < NC; c++) v[c * kF32Threads] = make_float2(0.f, 0.f);
+        }
+        Seq<P, 0>::axial(v, kF32Threads, qs, qt, rinv);
+        Seq<P, 0>::bwd(v, kF32Threads, ea, ebv, acc + w * NC, lane);
+    }
+    __syncthreads();
+    // L_k = Lhat_k / r_t^k
+    for (int c = tid; c < NC; c += kF32Threads) {
+        int n = 0;
+        while (tri(n + 1, 0) <= c) n++;
+        double s = 1.0;
+        for (int j = 0; j < n; j++) s /= rt;
+        double2 a = make_double2(0.0, 0.0);
+        for (int j = 0; j < kF32Threads / 32; j++) a = cadd(a, acc[j * NC + c]);
+        L[gt * NC + c] = make_double2(a.x * s, a.y * s);
+    }
+}
+
+// Mhat = M / r^n in float, every box of one level
+__global__ void k_scale_multipoles(int level, int p, const double *__restrict__ radius,
+                                   const double2 *__restrict__ M, float2 *__restrict__ Mf) {
+    const int nc = ncoef(p);
+    const int64_t off = ((int64_t)1 << level) - 1;
+    const int64_t total = ((int64_t)1 << level) * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = off + i / nc;
+        const int c = (int)(i % nc);
+        int n = 0;
+        while (tri(n + 1, 0) <= c) n++;
+        const double r = radius[g] > 0.0 ? radius[g] : 1.0;
+        double s = 1.0;
+        for (int j = 0; j < n; j++) s /= r;
+        const double2 m = M[g * nc + c];
+        Mf[g * nc + c] = make_float2((float)(m.x * s), (float)(m.y * s));
+    }
+}
+
+bool g_ctab_ready[64] = {};
+std::atomic<int> g_ctab_lock{0};
+
+cudaError_t f32_tables_ready() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    while (g_ctab_lock.exchange(1, std::memory_order_acquire)) {
+    }
+    if (!g_ctab_ready[dev]) {
+        std::vector<float> D, A, F;
+        for (int n = 0; n <= kPMax; n++)
+            for (int k = 0; k <= n; k++)
+                for (int m = 0; m <= n; m++) D.push_back((float)wigner_half_pi(n, k, m));
+        auto Fl = [](int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); };
+        for (int l = 0; l <= kPMax; l++)
+            for (int k = l; k <= kPMax; k++)
+                for (int n = l; n <= kPMax; n++) {
+                    const long double a = factl(n + k) / (Fl(n, l) * Fl(k, l));
+                    A.push_back((float)(((k + l) & 1) ? -a : a));
+                }
+        for (int n = 0; n <= kPMax; n++)
+            for (int m = 0; m <= n; m++) F.push_back((float)Fl(n, m));
+        e = cudaMemcpyToSymbol(c_D, D.data(), D.size() * 4);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_A, A.data(), A.size() * 4);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_F, F.data(), F.size() * 4);
+        if (e == cudaSuccess) g_ctab_ready[dev] = true;
+    }
+    g_ctab_lock.store(0, std::memory_order_release);
+    return e;
+}
+
+template <int P>
+cudaError_t launch_f32(Plan &P_, int l) {
+    constexpr int NC = (P + 1) * (P + 2) / 2;
+    const size_t smem = (size_t)(kF32Threads / 32) * NC * 16 + (size_t)kF32Threads * NC * 8;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_m2l_rot_f32<P>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    FMM_LAUNCH(k_m2l_rot_f32<P>, 1u << l, kF32Threads, smem, P_.stream, l, P_.wptr[l], P_.wsrc[l],
+               P_.centre, P_.radius, P_.Mf, P_.L);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool m2l_f32_supported(int p) {
+    return p == 4 || p == 6 || p == 8 || p == 10 || p == 12 || p == 14 || p == 16;
+}
+
+cudaError_t m2l_f32_setup(Plan &P) {
+    if (!m2l_f32_supported(P.p)) return cudaSuccess;
+    P.Mf = (float2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(float2));
+    if (!P.Mf) return cudaErrorMemoryAllocation;
+    return f32_tables_ready();
+}
+
+cudaError_t m2l_f32_level(Plan &P, int l) {
+    const int64_t total = ((int64_t)1 << l) * P.nc;
+    FMM_LAUNCH(k_scale_multipoles, (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0,
+               P.stream, l, P.p, P.radius, P.M, P.Mf);
+    switch (P.p) {
+        case 4: return launch_f32<4>(P, l);
+        case 6: return launch_f32<6>(P, l);
+        case 8: return launch_f32<8>(P, l);
+        case 10: return launch_f32<10>(P, l);
+        case 12: return launch_f32<12>(P, l);
+        case 14: return launch_f32<14>(P, l);
+        case 16: return launch_f32<16>(P, l);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fmm

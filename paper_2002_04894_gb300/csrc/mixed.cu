@@ -1,0 +1,350 @@
+// Mixed-precision leaf stages (FMM_PREC_MIXED): P2M, L2P and P2P in single
+// precision, with the box geometry, the theta-test, M2M and L2L left in double
+// precision and the multipole/local coefficients stored in double as before.
+//
+// Conditioning. Every point is kept as its offset a = x - c from its leaf
+// centre, split into a float pair hi + lo (hi = float(a), lo = float(a - hi)).
+// In P2P the source offsets are re-expressed relative to the target leaf's
+// centre with an error-free float TwoSum, so the difference of a close pair is
+// taken between two nearly equal hi parts, which is exact (Sterbenz), and
+// close pairs keep full relative precision. Per-target sums are Kahan-
+// compensated. The expansions are evaluated on scaled offsets a / r (r the
+// box radius, so |a / r| <= 1) and with scaled coefficients M_n / r^n and
+// L_n r^n, which keeps every float value O(1) whatever the box size.
+
+#include <algorithm>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ float2 fcmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ double box_scale(double r) { return r > 0.0 ? r : 1.0; }
+
+// offsets from the leaf centre, split hi/lo
+__global__ void k_leaf_offsets(int B, int64_t n, const double *__restrict__ x,
+                               const double *__restrict__ y, const double *__restrict__ z,
+                               const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                               const double *__restrict__ centre, float *__restrict__ hl) {
+    const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
+    const int b = begin[g], cnt = count[g];
+    const double c[3] = {centre[3 * g], centre[3 * g + 1], centre[3 * g + 2]};
+    const double *src[3] = {x, y, z};
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        for (int a = 0; a < 3; a++) {
+            const double d = src[a][b + i] - c[a];
+            const float h = (float)d;
+            hl[a * n + b + i] = h;
+            hl[(3 + a) * n + b + i] = (float)(d - (double)h);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_gather_qf(const T *__restrict__ qin, const int32_t *__restrict__ perm,
+                            float *__restrict__ q, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = (float)qin[perm[i]];
+}
+
+// P2M on scaled offsets; the warp sums go to double accumulators, and the
+// leaf's multipole is stored unscaled in double (M_n^m = r^n Mhat_n^m).
+__global__ void __launch_bounds__(kThreads)
+k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__restrict__ q,
+          const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+          const double *__restrict__ radius, double2 *__restrict__ M) {
+    extern __shared__ double2 acc[];  // [warps][nc]
+    const int nc = ncoef(p);
+    const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
+    const int b = begin[g], cnt = count[g];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double rs = box_scale(radius[g]);
+    const float rinv = (float)(1.0 / rs);
+    for (int c = threadIdx.x; c < nc * (kThreads / 32); c += kThreads) acc[c] = make_double2(0.0, 0.0);
+    __syncthreads();
+    double2 *mine = acc + w * nc;
+    for (int base = w * 32; base < cnt; base += kThreads) {
+        const int i = base + lane;
+        const bool valid = i < cnt;
+        const float sx = valid ? (hl[b + i] + hl[3 * n + b + i]) * rinv : 0.f;
+        const float sy = valid ? (hl[n + b + i] + hl[4 * n + b + i]) * rinv : 0.f;
+        const float sz = valid ? (hl[2 * n + b + i] + hl[5 * n + b + i]) * rinv : 0.f;
+        const float qi = valid ? q[b + i] : 0.f;
+        const float r2 = sx * sx + sy * sy + sz * sz;
+        float2 mm = make_float2(1.f, 0.f);
+        for (int m = 0; m <= p; m++) {
+            if (m > 0) {
+                mm = fcmul(mm, make_float2(sx, sy));
+                const float s = 0.5f / m;
+                mm = make_float2(mm.x * s, mm.y * s);
+            }
+            float2 cur = mm, prev = make_float2(0.f, 0.f);
+            const float sg = (m & 1) ? -qi : qi;
+            for (int nn = m; nn <= p; nn++) {
+                if (nn > m) {
+                    float2 nxt;
+                    if (nn == m + 1) {
+                        nxt = make_float2(cur.x * sz, cur.y * sz);
+                    } else {
+                        const float s = 1.f / ((float)(nn - m) * (float)(nn + m));
+                        const float a = (2 * nn - 1) * sz;
+                        nxt = make_float2((a * cur.x - r2 * prev.x) * s, (a * cur.y - r2 * prev.y) * s);
+                    }
+                    prev = cur;
+                    cur = nxt;
+                }
+                float vr = sg * cur.x, vi = -sg * cur.y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vr += __shfl_xor_sync(0xffffffffu, vr, o);
+                    vi += __shfl_xor_sync(0xffffffffu, vi, o);
+                }
+                if (lane == 0) {
+                    double2 a = mine[tri(nn, m)];
+                    mine[tri(nn, m)] = make_double2(a.x + vr, a.y + vi);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += kThreads) {
+        int nn = 0;
+        while (tri(nn + 1, 0) <= c) nn++;
+        double s = 1.0;
+        for (int j = 0; j < nn; j++) s *= rs;
+        double2 v = make_double2(0.0, 0.0);
+        for (int j = 0; j < kThreads / 32; j++) v = cadd(v, acc[j * nc + c]);
+        M[g * nc + c] = make_double2(v.x * s, v.y * s);
+    }
+}
+
+// L2P on scaled offsets: Lhat_k^l = r^k L_k^l; phi = sum Lhat conj(Y(a/r));
+// E = -grad phi = (Re G1, Im G1, -G0) / r with the degree-1 shifted terms.
+__global__ void __launch_bounds__(kThreads)
+k_l2p_f32(int B, int p, int64_t n, const float *__restrict__ hl, const int32_t *__restrict__ begin,
+          const int32_t *__restrict__ count, const double *__restrict__ radius,
+          const double2 *__restrict__ L, float *__restrict__ far_phi, float *__restrict__ far_E) {
+    extern __shared__ float2 Ls[];
+    const int nc = ncoef(p);
+    const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
+    const int b = begin[g], cnt = count[g];
+    const double rs = box_scale(radius[g]);
+    for (int c = threadIdx.x; c < nc; c += kThreads) {
+        int nn = 0;
+        while (tri(nn + 1, 0) <= c) nn++;
+        double s = 1.0;
+        for (int j = 0; j < nn; j++) s *= rs;
+        const double2 v = L[g * nc + c];
+        Ls[c] = make_float2((float)(v.x * s), (float)(v.y * s));
+    }
+    __syncthreads();
+    const float rinv = (float)(1.0 / rs);
+    for (int i = threadIdx.x; i < cnt; i += kThreads) {
+        const float sx = (hl[b + i] + hl[3 * n + b + i]) * rinv;
+        const float sy = (hl[n + b + i] + hl[4 * n + b + i]) * rinv;
+        const float sz = (hl[2 * n + b + i] + hl[5 * n + b + i]) * rinv;
+        const float r2 = sx * sx + sy * sy + sz * sz;
+        float phi = 0.f, g0 = 0.f;
+        float2 g1 = make_float2(0.f, 0.f);
+        float2 mm = make_float2(1.f, 0.f);
+        for (int m = 0; m <= p; m++) {
+            if (m > 0) {
+                mm = fcmul(mm, make_float2(sx, sy));
+                const float s = 0.5f / m;
+                mm = make_float2(mm.x * s, mm.y * s);
+            }
+            float2 cur = mm, prev = make_float2(0.f, 0.f);
+            const float w = m == 0 ? 1.f : 2.f;
+            for (int nn = m; nn <= p; nn++) {
+                if (nn > m) {
+                    float2 nxt;
+                    if (nn == m + 1) {
+                        nxt = make_float2(cur.x * sz, cur.y * sz);
+                    } else {
+                        const float s = 1.f / ((float)(nn - m) * (float)(nn + m));
+                        const float a = (2 * nn - 1) * sz;
+                        nxt = make_float2((a * cur.x - r2 * prev.x) * s, (a * cur.y - r2 * prev.y) * s);
+                    }
+                    prev = cur;
+                    cur = nxt;
+                }
+                const float2 Y = (m & 1) ? make_float2(-cur.x, -cur.y) : cur;
+                const float2 Yc = make_float2(Y.x, -Y.y);
+                phi += w * fcmul(Ls[tri(nn, m)], Yc).x;
+                if (nn < p) {
+                    g0 += w * fcmul(Ls[tri(nn + 1, m)], Yc).x;
+                    const float2 a = fcmul(Ls[tri(nn + 1, m + 1)], Yc);
+                    g1.x += a.x;
+                    g1.y += a.y;
+                    if (m >= 1) {
+                        const float2 lc = Ls[tri(nn + 1, m - 1)];
+                        const float2 t = fcmul(make_float2(lc.x, -lc.y), Y);
+                        g1.x -= t.x;
+                        g1.y -= t.y;
+                    }
+                }
+            }
+        }
+        far_phi[b + i] = phi;
+        far_E[b + i] = g1.x * rinv;
+        far_E[n + b + i] = g1.y * rinv;
+        far_E[2 * n + b + i] = -g0 * rinv;
+    }
+}
+
+__device__ __forceinline__ void kahan(float &s, float &c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// exact float sum a + b = s + e (Knuth TwoSum)
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+struct __align__(16) SrcHi {
+    float x, y, z, q;
+};
+struct __align__(16) SrcLo {
+    float x, y, z, pad;
+};
+
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads)
+k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
+          const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+          const double *__restrict__ centre, const int32_t *__restrict__ sptr,
+          const int32_t *__restrict__ ssrc, const int32_t *__restrict__ perm,
+          const float *__restrict__ far_phi, const float *__restrict__ far_E, OutT *__restrict__ pot,
+          OutT *__restrict__ field) {
+    __shared__ SrcHi th[kThreads];
+    __shared__ SrcLo tl[kThreads];
+    __shared__ float dlt[6];
+    const int64_t off = ((int64_t)1 << B) - 1;
+    const int t = blockIdx.x;
+    const int64_t gt = off + t;
+    const int bt = begin[gt], nt = count[gt];
+    const int e0 = sptr[t], e1 = sptr[t + 1];
+    for (int tb = 0; tb < nt; tb += kThreads) {
+        const int i = tb + threadIdx.x;
+        const bool active = i < nt;
+        const float xh = active ? hl[bt + i] : 0.f, yh = active ? hl[n + bt + i] : 0.f,
+                    zh = active ? hl[2 * n + bt + i] : 0.f;
+        const float xl = active ? hl[3 * n + bt + i] : 0.f, yl = active ? hl[4 * n + bt + i] : 0.f,
+                    zl = active ? hl[5 * n + bt + i] : 0.f;
+        float phi = 0.f, cphi = 0.f, ex = 0.f, cex = 0.f, ey = 0.f, cey = 0.f, ez = 0.f, cez = 0.f;
+        for (int e = e0; e < e1; e++) {
+            const int64_t gs = off + ssrc[e];
+            const int bs = begin[gs], ns = count[gs];
+            __syncthreads();
+            if (threadIdx.x < 3) {  // source-to-target centre offset, split hi/lo
+                const double d = centre[3 * gs + threadIdx.x] - centre[3 * gt + threadIdx.x];
+                const float h = (float)d;
+                dlt[threadIdx.x] = h;
+                dlt[3 + threadIdx.x] = (float)(d - (double)h);
+            }
+            __syncthreads();
+            for (int sb = 0; sb < ns; sb += kThreads) {
+                const int j = sb + threadIdx.x;
+                if (j < ns) {
+                    // offset of the source from the target leaf centre, hi + lo
+                    float ex_, ey_, ez_;
+                    const float sx = two_sum(hl[bs + j], dlt[0], ex_);
+                    const float sy = two_sum(hl[n + bs + j], dlt[1], ey_);
+                    const float sz = two_sum(hl[2 * n + bs + j], dlt[2], ez_);
+                    th[threadIdx.x] = SrcHi{sx, sy, sz, qf[bs + j]};
+                    tl[threadIdx.x] = SrcLo{ex_ + (hl[3 * n + bs + j] + dlt[3]),
+                                            ey_ + (hl[4 * n + bs + j] + dlt[4]),
+                                            ez_ + (hl[5 * n + bs + j] + dlt[5]), 0.f};
+                }
+                __syncthreads();
+                const int mcount = min(kThreads, ns - sb);
+                for (int jj = 0; jj < mcount; jj++) {
+                    const SrcHi s = th[jj];
+                    const SrcLo sl = tl[jj];
+                    const float dx = (xh - s.x) + (xl - sl.x);
+                    const float dy = (yh - s.y) + (yl - sl.y);
+                    const float dz = (zh - s.z) + (zl - sl.z);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                    const float qr = s.q * rinv;
+                    const float qr3 = qr * rinv * rinv;
+                    kahan(phi, cphi, qr);
+                    kahan(ex, cex, qr3 * dx);
+                    kahan(ey, cey, qr3 * dy);
+                    kahan(ez, cez, qr3 * dz);
+                }
+                __syncthreads();
+            }
+        }
+        if (active) {
+            const int64_t a = bt + i;
+            const int64_t o = perm[a];
+            pot[o] = (OutT)((double)far_phi[a] + ((double)phi - (double)cphi));
+            if (field) {
+                field[3 * o] = (OutT)((double)far_E[a] + ((double)ex - (double)cex));
+                field[3 * o + 1] = (OutT)((double)far_E[n + a] + ((double)ey - (double)cey));
+                field[3 * o + 2] = (OutT)((double)far_E[2 * n + a] + ((double)ez - (double)cez));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t mixed_setup(Plan &P) {
+    const int64_t n = P.n;
+    P.hl = (float *)palloc(P, (size_t)n * 6 * 4);
+    P.qf = (float *)palloc(P, (size_t)n * 4);
+    P.far_phi_f = (float *)palloc(P, (size_t)n * 4);
+    P.far_E_f = (float *)palloc(P, (size_t)n * 12);
+    if (!P.hl || !P.qf || !P.far_phi_f || !P.far_E_f) return cudaErrorMemoryAllocation;
+    FMM_LAUNCH(k_leaf_offsets, (unsigned)P.nleaf, 128, 0, P.stream, P.B, n, P.x, P.y, P.z, P.begin,
+               P.count, P.centre, P.hl);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_p2m(Plan &P, const void *charges, int dtype) {
+    const int64_t n = P.n;
+    const int gq = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_gather_qf<double>, gq, 256, 0, P.stream, (const double *)charges, P.perm, P.qf, n);
+    else
+        FMM_LAUNCH(k_gather_qf<float>, gq, 256, 0, P.stream, (const float *)charges, P.perm, P.qf, n);
+    FMM_LAUNCH(k_p2m_f32, (unsigned)P.nleaf, kThreads, sizeof(double2) * P.nc * (kThreads / 32),
+               P.stream, P.B, P.p, n, P.hl, P.qf, P.begin, P.count, P.radius, P.M);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_l2p(Plan &P) {
+    FMM_LAUNCH(k_l2p_f32, (unsigned)P.nleaf, kThreads, sizeof(float2) * P.nc, P.stream, P.B, P.p,
+               P.n, P.hl, P.begin, P.count, P.radius, P.L, P.far_phi_f, P.far_E_f);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.nleaf, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
+                   P.begin, P.count, P.centre, P.sptr[P.B], P.ssrc[P.B], P.perm, P.far_phi_f,
+                   P.far_E_f, (double *)pot, (double *)field);
+    else
+        FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.nleaf, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
+                   P.begin, P.count, P.centre, P.sptr[P.B], P.ssrc[P.B], P.perm, P.far_phi_f,
+                   P.far_E_f, (float *)pot, (float *)field);
+    return cudaGetLastError();
+}
+
+}  // namespace fmm

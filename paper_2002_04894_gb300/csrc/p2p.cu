@@ -135,6 +135,11 @@ k_direct(const T *__restrict__ pts, const T *__restrict__ q, int64_t n,
 cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
     const unsigned grid = (unsigned)P.nleaf;
     stage_mark(P, FMM_STAGE_P2P, 0);
+    if (P.prec == FMM_PREC_MIXED) {
+        cudaError_t e = mixed_p2p(P, pot, field, dtype);
+        stage_mark(P, FMM_STAGE_P2P, 1);
+        return e;
+    }
     if (dtype == FMM_F64)
         FMM_LAUNCH(k_p2p_f64<double>, grid, kP2PThreads, 0, P.stream, 
             P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.perm,
