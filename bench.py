@@ -2,7 +2,10 @@
 
 Default workload (N=1): 2,000,000 points from a Plummer sphere (scale radius
 0.1, truncated at 10 radii), charges uniform in [-1, 1], 14 binary levels
-(~122 points per leaf), expansion order p = 10, theta = 0.5, FP64 throughout.
+(~122 points per leaf), theta = 0.5, expansion order p = 12 -- the smallest
+order that meets the 1e-6 potential error against the FP64 direct sum --
+in the mixed-precision form (float P2M/M2L/L2P/P2P, double geometry, lists,
+M2M and L2L). The plain FP64 form is timed on the same inputs beside it.
 A step is one whole solve: tree, lists, P2M, M2M, M2L, L2L, L2P, P2P. Inputs
 are resident on the device when a step starts; the L2 cache is flushed
 between steps (a 512 MB write, outside the timed events).
@@ -38,12 +41,16 @@ sys.path.insert(0, ROOT)
 from paper_2002_04894_gb300 import inputs  # noqa: E402
 
 WORKLOADS = {
-    # name: (distribution, N, levels, p, theta, point dtype, charges)
-    "plummer2m_l14_p10": ("plummer", 2_000_000, 14, 10, 0.5, "f64", "uniform"),
-    "uniform20k_l8_p8": ("uniform", 20_000, 8, 8, 0.5, "f64", "uniform"),
-    "gmm8m_l16_p12": ("gmm", 8_000_000, 16, 12, 0.5, "f32", "pm1"),
+    # name: (distribution, N, levels, p, theta, point dtype, charges, precision)
+    # 2M Plummer points: p = 12 is the smallest order whose potential error
+    # against the FP64 direct sum is below 1e-6 (p = 10 gives 3.5e-6).
+    "plummer2m_l14_p12": ("plummer", 2_000_000, 14, 12, 0.5, "f64", "uniform", "mixed"),
+    "plummer2m_l14_p10_fp64": ("plummer", 2_000_000, 14, 10, 0.5, "f64", "uniform", "fp64"),
+    "uniform20k_l8_p8": ("uniform", 20_000, 8, 8, 0.5, "f64", "uniform", "fp64"),
+    "gmm8m_l16_p12": ("gmm", 8_000_000, 16, 12, 0.5, "f32", "pm1", "mixed"),
 }
-DEFAULT = "plummer2m_l14_p10"
+DEFAULT = "plummer2m_l14_p12"
+METRIC = "Mpoints/s per FMM solve (plan+eval) at rel err <= 1e-6 vs FP64 direct"
 FLOPS_PER_INTERACTION = 20   # P2P convention (N-body): 20 flops per pair
 SM_COUNT = 152
 FP32_FLOPS_PER_CLK_SM = 256  # 128 FP32 lanes x FMA
@@ -116,7 +123,7 @@ def dist_env():
 
 
 def make_inputs(name, seed):
-    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name]
+    dist, n, levels, p, theta, pdt, ch, _ = WORKLOADS[name]
     x = inputs.points(dist, n, seed)
     q = inputs.charges_uniform(n, seed) if ch == "uniform" else inputs.charges_pm1(n, seed)
     if pdt == "f32":
@@ -127,7 +134,7 @@ def make_inputs(name, seed):
 def cpu_sample_config(name):
     """The bounded CPU sample of a workload: same distribution, charges, p and
     theta; N reduced and levels lowered so that points per leaf stay equal."""
-    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name]
+    dist, n, levels, p, theta, pdt, ch, _ = WORKLOADS[name]
     ns = min(n, 1 << 17)
     ls = max(0, levels - int(round(np.log2(n / ns))))
     return dist, ns, ls, p, theta, ch
@@ -158,10 +165,10 @@ def bench_reference(args, rank, world):
         times.append(dt)
     ms = 1e3 * sum(times) / len(times)
     val = ns / (ms / 1e3) / 1e6
-    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name]
+    dist, n, levels, p, theta, pdt, ch, _ = WORKLOADS[name]
     sample = f"{dist} N={ns} levels={ls} p={p} theta={theta} (same points/leaf as N={n}, {levels} levels)"
     print(json.dumps({
-        "impl": "reference", "metric": "Mpoints/s per FMM solve (plan+eval)", "value": round(val, 6),
+        "impl": "reference", "metric": METRIC, "value": round(val, 6),
         "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -182,6 +189,7 @@ def bench_ours(args, rank, world, local):
         import torch.distributed as tdist
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fmm.load()
+    args.prec = args.prec or WORKLOADS[args.workload][7]
     prec = fmm.FMM_PREC_MIXED if args.prec == "mixed" else fmm.FMM_PREC_FP64
     x, q, levels, p, theta = make_inputs(args.workload, seed=rank)
     n = x.shape[0]
@@ -258,6 +266,29 @@ def bench_ours(args, rank, world, local):
     t_e2e = (time.perf_counter() - t0) * 1e3 / e2e_steps
     es = x.dtype.itemsize
 
+    # the plain FP64 form on the same inputs, as the comparator
+    fp64 = None
+    if args.fp64_steps > 0 and prec != fmm.FMM_PREC_FP64:
+        pot64 = torch.empty_like(pot)
+        fld64 = torch.empty_like(fld)
+        fmm.fmm_destroy(fmm.fmm_plan(xd, levels, p, theta, prec=fmm.FMM_PREC_FP64))
+        times = []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pl = fmm.fmm_plan(xd, levels, p, theta, prec=fmm.FMM_PREC_FP64)
+            fmm.fmm_eval(pl, qd, pot64, fld64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+            fmm.fmm_destroy(pl)
+        g64 = pot64.double().cpu().numpy()[tgt]
+        t64 = sum(times) / len(times)
+        fp64 = {"value": round(world * n / (t64 * 1e-3) / 1e6, 4), "unit": "Mpoints/s",
+                "ms": round(t64, 3), "steps": len(times),
+                "rel_l2_phi": float(np.linalg.norm(g64 - dp) / np.linalg.norm(dp))}
+
     if rank != 0:
         return
     peaks = measured_peaks()
@@ -269,7 +300,7 @@ def bench_ours(args, rank, world, local):
     achieved = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
     value = world * n / (t_solve * 1e-3) / 1e6
     out = {
-        "metric": "Mpoints/s per FMM solve (plan+eval) at rel err <= 1e-6 vs FP64 direct",
+        "metric": METRIC,
         "value": round(value, 4), "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_solve, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
@@ -296,6 +327,8 @@ def bench_ours(args, rank, world, local):
                 "h2d_bytes_per_step": int(n * 3 * es + n * es),
                 "d2h_bytes_per_step": int(n * es + 3 * n * es)},
         "gpu_launches": int(launches),
+        "launches_per_step": int(launches // args.steps),
+        "fp64_form": fp64,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -316,7 +349,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--prec", default=None, choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="steps of the plain FP64 form timed as the comparator (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -266,14 +266,10 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     stage_mark(P, FMM_STAGE_M2M, 1);
     // Algorithm 3: M2L at every level (each overwrites its level's L), then L2L downward
     stage_mark(P, FMM_STAGE_M2L, 0);
-    cudaMemsetAsync(P.L, 0, sizeof(double2) * nc, st);  // root: no far field
-    for (int l = 1; l <= P.B; l++) {
-        if (mixed && P.Mf) {
-            cudaError_t e = m2l_f32_level(P, l);
-            if (e != cudaSuccess) return e;
-        } else {
-            m2l_level(P, l);
-        }
+    {
+        // all levels in one launch; every L is (re)written, the root's stays zero
+        cudaError_t e = (mixed && P.Mf) ? m2l_f32_all(P) : m2l_all(P);
+        if (e != cudaSuccess) return e;
     }
     stage_mark(P, FMM_STAGE_M2L, 1);
     stage_mark(P, FMM_STAGE_L2L, 0);

@@ -44,6 +44,7 @@ struct Plan {
     // connectivity: CSR per level over the 2^l target boxes of level l
     int32_t *wptr[FMM_MAX_LEVELS + 1] = {}, *wsrc[FMM_MAX_LEVELS + 1] = {};
     int32_t *sptr[FMM_MAX_LEVELS + 1] = {}, *ssrc[FMM_MAX_LEVELS + 1] = {};
+    int32_t *wrow[FMM_MAX_LEVELS + 1] = {};  // target of every weak pair (flat M2L)
     int64_t nweak[FMM_MAX_LEVELS + 1] = {}, nstrong[FMM_MAX_LEVELS + 1] = {};
     int64_t p2p_interactions = 0;
     bool capacity_exceeded = false;
@@ -55,6 +56,7 @@ struct Plan {
     // field, radius-scaled float multipoles for the single-precision M2L
     float *hl = nullptr, *qf = nullptr, *far_phi_f = nullptr, *far_E_f = nullptr;
     float2 *Mf = nullptr;
+    double2 *Lh = nullptr;  // r^k-scaled locals accumulated by the float M2L
     // evaluation scratch
     double *q = nullptr;                 // charges in leaf order
     double2 *M = nullptr, *L = nullptr;  // nbox x nc
@@ -157,10 +159,10 @@ cudaError_t direct_run(const void *points, const void *charges, int64_t n, int d
                        const int64_t *targets, int64_t nt, void *pot, void *field,
                        cudaStream_t s);
 cudaError_t m2l_setup(Plan &P);
-void m2l_level(Plan &P, int level);
+cudaError_t m2l_all(Plan &P);
 bool m2l_f32_supported(int p);
 cudaError_t m2l_f32_setup(Plan &P);
-cudaError_t m2l_f32_level(Plan &P, int level);
+cudaError_t m2l_f32_all(Plan &P);
 cudaError_t mixed_setup(Plan &P);
 cudaError_t mixed_p2m(Plan &P, const void *charges, int dtype);
 cudaError_t mixed_l2p(Plan &P);

@@ -7,10 +7,14 @@
 // P2P list. Both orientations of a pair are stored (the paper keeps only the
 // lower triangle; the set of interactions is the same).
 //
-// GPU design: one thread per target box of level l walks its parent's strong
-// list (ascending) and tests the two children of every source, so the output
-// lists come out sorted per target with no sort. Count pass, exclusive scan,
-// fill pass; the only host synchronisation per level is the total size.
+// GPU design: the work is flattened over the parent level's strong pairs, not
+// over target boxes: clustered point sets make some boxes (large, sparse
+// ones) strongly connected to a large share of their level, and a
+// thread-per-target loop would run as long as the longest list. One thread
+// per parent pair tests its four child pairs and writes the flags in
+// target-major, source-ascending order; one scan of the weak flags gives the
+// CSR slot of every weak and strong pair. The only host synchronisation per
+// level is the total size.
 // Degenerate pairs (theta = 0, or coincident centres) are always strong.
 
 #include <algorithm>
@@ -33,43 +37,73 @@ __device__ __forceinline__ bool theta_weak(double theta, const double *ca, doubl
     return theta > 0.0 && d > 0.0 && __dadd_rn(R, __dmul_rn(theta, r)) <= __dmul_rn(theta, d);
 }
 
-template <bool kFill>
-__global__ void k_lists(int level, double theta, const int32_t *__restrict__ pptr,
-                        const int32_t *__restrict__ psrc, const double *__restrict__ centre,
-                        const double *__restrict__ radius, int32_t *wcnt, int32_t *scnt,
-                        const int32_t *__restrict__ wptr, const int32_t *__restrict__ sptr,
-                        int32_t *wsrc, int32_t *ssrc) {
-    const int64_t nt = (int64_t)1 << level;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nt) return;
-    const int64_t off = nt - 1;
-    const int64_t gt = off + t;
-    const double ct[3] = {centre[3 * gt], centre[3 * gt + 1], centre[3 * gt + 2]};
-    const double rt = radius[gt];
-    const int64_t T = t >> 1;
-    int32_t nw = 0, ns = 0;
-    int32_t iw = kFill ? wptr[t] : 0, is = kFill ? sptr[t] : 0;
-    for (int32_t e = pptr[T]; e < pptr[T + 1]; e++) {
-        const int32_t S = psrc[e];
-        for (int c = 0; c < 2; c++) {
-            const int32_t s = 2 * S + c;
+// One thread per strongly connected pair (T, S) of the parent level: its four
+// child pairs (2T+a, 2S+b) are tested and their flags written at their
+// position in the target-major candidate order
+//   cpos = 4 sptr[T] + a * 2 len(T) + 2 (e - sptr[T]) + b,
+// i.e. grouped by target 2T+a and, inside a target, by ascending source (the
+// parent's sources are ascending). A scan of the weak flags then places every
+// weak and strong pair directly in its sorted CSR slot.
+__global__ void k_cand(int level, int64_t npar, double theta, const int32_t *__restrict__ pptr,
+                       const int32_t *__restrict__ psrc, const int32_t *__restrict__ prow,
+                       const double *__restrict__ centre, const double *__restrict__ radius,
+                       int32_t *__restrict__ flag, int32_t *__restrict__ csrc,
+                       int32_t *__restrict__ ctgt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= npar) return;
+    const int32_t T = prow[e], S = psrc[e];
+    const int32_t b0 = pptr[T], len = pptr[T + 1] - b0;
+    const int64_t off = ((int64_t)1 << level) - 1;
+    for (int a = 0; a < 2; a++) {
+        const int32_t t = 2 * T + a;
+        const int64_t gt = off + t;
+        const int64_t base = 4ll * b0 + (int64_t)a * 2 * len + 2ll * (e - b0);
+        for (int b = 0; b < 2; b++) {
+            const int32_t s = 2 * S + b;
             const int64_t gs = off + s;
-            const bool weak = theta_weak(theta, ct, rt, centre + 3 * gs, radius[gs]);
-            if (kFill) {
-                if (weak)
-                    wsrc[iw++] = s;
-                else
-                    ssrc[is++] = s;
-            } else {
-                nw += weak;
-                ns += !weak;
-            }
+            flag[base + b] = theta_weak(theta, centre + 3 * gt, radius[gt], centre + 3 * gs, radius[gs]);
+            csrc[base + b] = s;
+            ctgt[base + b] = t;
         }
     }
-    if (!kFill) {
-        wcnt[t] = nw;
-        scnt[t] = ns;
+}
+
+__global__ void k_cand_scatter(int64_t ncand, const int32_t *__restrict__ flag,
+                               const int32_t *__restrict__ wpos, const int32_t *__restrict__ csrc,
+                               const int32_t *__restrict__ ctgt, int32_t *__restrict__ wsrc,
+                               int32_t *__restrict__ wrow, int32_t *__restrict__ ssrc,
+                               int32_t *__restrict__ srow) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncand) return;
+    const int32_t w = wpos[c];
+    if (flag[c]) {
+        wsrc[w] = csrc[c];
+        wrow[w] = ctgt[c];
+    } else {
+        const int64_t sp = c - w;
+        ssrc[sp] = csrc[c];
+        srow[sp] = ctgt[c];
     }
+}
+
+// CSR row pointers of level `level` from the parent's: target t = 2T + a
+// starts at candidate 4 sptr[T] + a * 2 len(T).
+__global__ void k_cand_ptrs(int level, const int32_t *__restrict__ pptr,
+                            const int32_t *__restrict__ wpos, int64_t ncand,
+                            int32_t *__restrict__ wptr, int32_t *__restrict__ sptr) {
+    const int64_t nt = (int64_t)1 << level;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t > nt) return;
+    int64_t first;
+    if (t == nt) {
+        first = ncand;
+    } else {
+        const int64_t T = t >> 1, a = t & 1;
+        first = 4ll * pptr[T] + a * 2ll * (pptr[T + 1] - pptr[T]);
+    }
+    const int32_t w = wpos[first];
+    wptr[t] = w;
+    sptr[t] = (int32_t)(first - w);
 }
 
 // ---- exclusive scan of int32 counts: out[0..n], out[n] = total -------------
@@ -166,19 +200,27 @@ __global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, cons
 }  // namespace
 
 cudaError_t scan_exclusive(Plan &P, const int32_t *in, int32_t *out, int64_t n) {
-    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-    if (ntiles > kScanTile) return cudaErrorInvalidValue;
-    int32_t *sums = (int32_t *)dalloc(P, (size_t)std::max<int64_t>(ntiles, 1) * 4);
-    if (!sums) return cudaErrorMemoryAllocation;
-    if (n > 0) {
-        FMM_LAUNCH(k_scan_tiles, (unsigned)ntiles, kScanThreads, 0, P.stream, in, out, n, sums);
-        FMM_LAUNCH(k_scan_sums, 1, kScanThreads, 0, P.stream, sums, ntiles, out + n);
-        if (ntiles > 1)
-            FMM_LAUNCH(k_scan_add, (unsigned)((n + 255) / 256), 256, 0, P.stream, out, n, sums);
-    } else {
+    if (n <= 0) {
         cudaMemsetAsync(out, 0, 4, P.stream);
+        return cudaGetLastError();
     }
-    dfree(P, sums, (size_t)std::max<int64_t>(ntiles, 1) * 4);
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles == 1) {
+        int32_t *sums = (int32_t *)dalloc(P, 4);
+        if (!sums) return cudaErrorMemoryAllocation;
+        FMM_LAUNCH(k_scan_tiles, 1, kScanThreads, 0, P.stream, in, out, n, sums);
+        FMM_LAUNCH(k_scan_sums, 1, kScanThreads, 0, P.stream, sums, 1, out + n);
+        return cudaGetLastError();
+    }
+    // tile sums -> their exclusive scan (recursively) -> add back
+    int32_t *sums = (int32_t *)dalloc(P, (size_t)ntiles * 4);
+    int32_t *sscan = (int32_t *)dalloc(P, (size_t)(ntiles + 1) * 4);
+    if (!sums || !sscan) return cudaErrorMemoryAllocation;
+    FMM_LAUNCH(k_scan_tiles, (unsigned)ntiles, kScanThreads, 0, P.stream, in, out, n, sums);
+    cudaError_t e = scan_exclusive(P, sums, sscan, ntiles);
+    if (e != cudaSuccess) return e;
+    FMM_LAUNCH(k_scan_add, (unsigned)((n + 255) / 256), 256, 0, P.stream, out, n, sscan);
+    cudaMemcpyAsync(out + n, sscan + ntiles, 4, cudaMemcpyDeviceToDevice, P.stream);
     return cudaGetLastError();
 }
 
@@ -189,61 +231,80 @@ cudaError_t lists_build(Plan &P) {
     P.sptr[0] = (int32_t *)palloc(P, 8);
     P.ssrc[0] = (int32_t *)palloc(P, 4);
     P.wsrc[0] = nullptr;
-    if (!P.wptr[0] || !P.sptr[0] || !P.ssrc[0]) return cudaErrorMemoryAllocation;
-    const int32_t w0[2] = {0, 0}, s0[2] = {0, 1}, src0 = 0;
+    P.wrow[0] = nullptr;
+    int32_t *srow_prev = (int32_t *)dalloc(P, 4);
+    if (!P.wptr[0] || !P.sptr[0] || !P.ssrc[0] || !srow_prev) return cudaErrorMemoryAllocation;
+    const int32_t w0[2] = {0, 0}, s0[2] = {0, 1}, zero = 0;
     cudaMemcpyAsync(P.wptr[0], w0, 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(P.sptr[0], s0, 8, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(P.ssrc[0], &src0, 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(P.ssrc[0], &zero, 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(srow_prev, &zero, 4, cudaMemcpyHostToDevice, st);
     P.nweak[0] = 0;
     P.nstrong[0] = 1;
     int32_t *totals = nullptr;
-    cudaMallocHost(&totals, 8);
+    cudaError_t e = cudaMallocHost(&totals, 8);
+    if (e != cudaSuccess) return e;
     for (int l = 1; l <= P.B; l++) {
         const int64_t nt = (int64_t)1 << l;
-        // every child pair of a strong parent pair is a candidate: 4 per parent pair
-        if (4 * P.nstrong[l - 1] > 0x7fffffffLL) {
+        const int64_t npar = P.nstrong[l - 1], ncand = 4 * npar;
+        if (ncand > 0x7fffffffLL) {
             P.capacity_exceeded = true;
             cudaFreeHost(totals);
             return cudaSuccess;
         }
-        int32_t *wcnt = (int32_t *)dalloc(P, nt * 4), *scnt = (int32_t *)dalloc(P, nt * 4);
+        int32_t *flag = (int32_t *)dalloc(P, (size_t)ncand * 4);
+        int32_t *wpos = (int32_t *)dalloc(P, (size_t)(ncand + 1) * 4);
+        int32_t *csrc = (int32_t *)dalloc(P, (size_t)ncand * 4);
+        int32_t *ctgt = (int32_t *)dalloc(P, (size_t)ncand * 4);
         P.wptr[l] = (int32_t *)palloc(P, (nt + 1) * 4);
         P.sptr[l] = (int32_t *)palloc(P, (nt + 1) * 4);
-        if (!wcnt || !scnt || !P.wptr[l] || !P.sptr[l]) return cudaErrorMemoryAllocation;
-        const unsigned grid = (unsigned)((nt + 127) / 128);
-        FMM_LAUNCH(k_lists<false>, grid, 128, 0, st, l, P.theta, P.sptr[l - 1], P.ssrc[l - 1], P.centre,
-                                             P.radius, wcnt, scnt, nullptr, nullptr, nullptr,
-                                             nullptr);
-        cudaError_t e = scan_exclusive(P, wcnt, P.wptr[l], nt);
-        if (e == cudaSuccess) e = scan_exclusive(P, scnt, P.sptr[l], nt);
-        if (e != cudaSuccess) return e;
-        cudaMemcpyAsync(totals, P.wptr[l] + nt, 4, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(totals + 1, P.sptr[l] + nt, 4, cudaMemcpyDeviceToHost, st);
+        if (!flag || !wpos || !csrc || !ctgt || !P.wptr[l] || !P.sptr[l]) {
+            cudaFreeHost(totals);
+            return cudaErrorMemoryAllocation;
+        }
+        FMM_LAUNCH(k_cand, (unsigned)((npar + 127) / 128), 128, 0, st, l, npar, P.theta, P.sptr[l - 1],
+                   P.ssrc[l - 1], srow_prev, P.centre, P.radius, flag, csrc, ctgt);
+        e = scan_exclusive(P, flag, wpos, ncand);
+        if (e != cudaSuccess) {
+            cudaFreeHost(totals);
+            return e;
+        }
+        FMM_LAUNCH(k_cand_ptrs, (unsigned)((nt + 1 + 255) / 256), 256, 0, st, l, P.sptr[l - 1], wpos,
+                   ncand, P.wptr[l], P.sptr[l]);
+        cudaMemcpyAsync(totals, wpos + ncand, 4, cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+            cudaFreeHost(totals);
+            return e;
+        }
         P.nweak[l] = totals[0];
-        P.nstrong[l] = totals[1];
+        P.nstrong[l] = ncand - totals[0];
         P.wsrc[l] = (int32_t *)palloc(P, (size_t)std::max<int64_t>(P.nweak[l], 1) * 4);
+        P.wrow[l] = (int32_t *)palloc(P, (size_t)std::max<int64_t>(P.nweak[l], 1) * 4);
         P.ssrc[l] = (int32_t *)palloc(P, (size_t)std::max<int64_t>(P.nstrong[l], 1) * 4);
-        if (!P.wsrc[l] || !P.ssrc[l]) return cudaErrorMemoryAllocation;
-        FMM_LAUNCH(k_lists<true>, grid, 128, 0, st, l, P.theta, P.sptr[l - 1], P.ssrc[l - 1], P.centre,
-                                            P.radius, nullptr, nullptr, P.wptr[l], P.sptr[l],
-                                            P.wsrc[l], P.ssrc[l]);
-        dfree(P, wcnt, nt * 4);
-        dfree(P, scnt, nt * 4);
+        int32_t *srow = (int32_t *)dalloc(P, (size_t)std::max<int64_t>(P.nstrong[l], 1) * 4);
+        if (!P.wsrc[l] || !P.wrow[l] || !P.ssrc[l] || !srow) {
+            cudaFreeHost(totals);
+            return cudaErrorMemoryAllocation;
+        }
+        FMM_LAUNCH(k_cand_scatter, (unsigned)((ncand + 255) / 256), 256, 0, st, ncand, flag, wpos, csrc,
+                   ctgt, P.wsrc[l], P.wrow[l], P.ssrc[l], srow);
+        srow_prev = srow;
     }
     // exact P2P work (sum of n_t * n_s over strong leaf pairs)
     unsigned long long *acc = (unsigned long long *)dalloc(P, 8);
-    if (!acc) return cudaErrorMemoryAllocation;
+    if (!acc) {
+        cudaFreeHost(totals);
+        return cudaErrorMemoryAllocation;
+    }
     cudaMemsetAsync(acc, 0, 8, st);
     const int64_t nl = (int64_t)1 << P.B;
-    FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.sptr[P.B], P.ssrc[P.B], P.count,
-                                                           acc);
+    FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.sptr[P.B], P.ssrc[P.B],
+               P.count, acc);
     unsigned long long h = 0;
     cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
+    e = cudaStreamSynchronize(st);
     P.p2p_interactions = (int64_t)h;
-    dfree(P, acc, 8);
     cudaFreeHost(totals);
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -38,6 +38,14 @@ namespace fmm {
 
 namespace {
 
+// weak pairs of every level, concatenated (levels lmin..lmax); passed by value
+struct PairTable {
+    const int32_t *tgt[FMM_MAX_LEVELS + 1];
+    const int32_t *src[FMM_MAX_LEVELS + 1];
+    long long off[FMM_MAX_LEVELS + 2];
+    int lmin, lmax;
+};
+
 __device__ __forceinline__ double2 mul_ipow(int m, double2 v) {  // i^m v
     switch (m & 3) {
         case 0: return v;
@@ -61,131 +69,147 @@ __device__ __forceinline__ void fold_apply(const double *__restrict__ D, int n, 
     }
 }
 
-__global__ void k_m2l_rot_f64(int level, int p, const int32_t *__restrict__ wptr,
-                              const int32_t *__restrict__ wsrc, const double *__restrict__ centre,
+// Segmented sum over lanes of equal target (the pair list is sorted by
+// target): after the five steps the first lane of each run holds the run's
+// sum. same[j] says whether lane + 2^j belongs to this lane's run.
+template <typename R>
+__device__ __forceinline__ R seg_sum(R v, const bool (&same)[5]) {
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        const R o = __shfl_down_sync(0xffffffffu, v, 1 << j);
+        if (same[j]) v += o;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void seg_setup(int64_t tgt, bool (&same)[5], bool &head) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        const int64_t o = __shfl_down_sync(0xffffffffu, tgt, 1 << j);
+        same[j] = (lane + (1 << j) < 32) && o == tgt;
+    }
+    const int64_t up = __shfl_up_sync(0xffffffffu, tgt, 1);
+    head = tgt >= 0 && (lane == 0 || up != tgt);
+}
+
+__device__ __forceinline__ void pair_of(const PairTable &PT, int64_t g, int64_t &gt, int64_t &gs) {
+    int l = PT.lmin;
+    while (l < PT.lmax && g >= PT.off[l + 1]) l++;
+    const int64_t e = g - PT.off[l];
+    const int64_t boff = ((int64_t)1 << l) - 1;
+    gt = boff + PT.tgt[l][e];
+    gs = boff + PT.src[l][e];
+}
+
+__global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ centre,
                               const double2 *__restrict__ M, double2 *__restrict__ L,
                               const double *__restrict__ gtab, int ntab) {
     extern __shared__ double2 sm2[];
     const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
-    const int lane = tid & 31, w = tid >> 5, nw = T >> 5;
-    // shared layout: [acc: nw*nc][V: nc*T][U: (p+1)*T][W: (p+1)*T][tables: ntab doubles]
-    double2 *acc = sm2;
-    double2 *V = acc + nw * nc;
+    // shared layout: [V: nc*T][U: (p+1)*T][W: (p+1)*T][tables: ntab doubles]
+    double2 *V = sm2;
     double2 *U = V + nc * T;
     double2 *W = U + (p + 1) * T;
     double *tab = (double *)(W + (p + 1) * T);
     for (int i = tid; i < ntab; i += T) tab[i] = gtab[i];
-    for (int i = tid; i < nw * nc; i += T) acc[i] = make_double2(0.0, 0.0);
     __syncthreads();
-    // tables: D (sum (n+1)^2), axial A (sum_l (p+1-l)^2), G_nm = F_nm (nc), H = 2 F (m>0)
+    // tables: D (sum (n+1)^2), axial A (sum_l (p+1-l)^2), F_nm (nc)
     const double *Dt = tab;
     const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
     const double *At = Dt + nD;
     const double *Ft = At + nD;
     double2 *v = V + tid, *u = U + tid, *x = W + tid;
 
-    const int64_t off = ((int64_t)1 << level) - 1;
-    const int t = blockIdx.x;
-    const int64_t gt = off + t;
-    const int e0 = wptr[t], e1 = wptr[t + 1];
-    const double ctx = centre[3 * gt], cty = centre[3 * gt + 1], ctz = centre[3 * gt + 2];
-
-    for (int eb = e0; eb < e1; eb += T) {
-        const int e = eb + tid;
-        const bool valid = e < e1;
-        int64_t gs = 0;
-        double dx = 1.0, dy = 0.0, dz = 0.0;
-        if (valid) {
-            gs = off + wsrc[e];
-            dx = ctx - centre[3 * gs];
-            dy = cty - centre[3 * gs + 1];
-            dz = ctz - centre[3 * gs + 2];
-        }
-        const double rxy = sqrt(dx * dx + dy * dy);
-        const double rho = sqrt(dx * dx + dy * dy + dz * dz);
-        const double rinv = 1.0 / rho;
-        const double2 ea = rxy > 0.0 ? make_double2(dx / rxy, dy / rxy) : make_double2(1.0, 0.0);
-        const double2 eb_ = make_double2(dz * rinv, rxy * rinv);
-        const double2 eai = make_double2(ea.y, -ea.x);  // -i e^{ia}
-
-        // ---- forward rotation, degree by degree -> v = Mr (tilde normalisation)
-        const double *Dn = Dt;
-        for (int n = 0; n <= p; n++) {
-            double2 ph = make_double2(1.0, 0.0);
-            for (int m = 0; m <= n; m++) {
-                const int c = tri(n, m);
-                const double2 mv = valid ? M[gs * nc + c] : make_double2(0.0, 0.0);
-                u[m * T] = cscale(cmul(mv, ph), Ft[c] * (m ? 2.0 : 1.0));
-                ph = cmul(ph, eai);
-            }
-            fold_apply(Dn, n, u, x, T, false);
-            double2 pb = make_double2(1.0, 0.0);
-            for (int k = 0; k <= n; k++) {
-                x[k * T] = cscale(cmul(x[k * T], pb), k ? 2.0 : 1.0);
-                pb = cmul(pb, eb_);
-            }
-            fold_apply(Dn, n, x, u, T, true);
-            for (int m = 0; m <= n; m++) v[tri(n, m) * T] = mul_ipow(m, u[m * T]);
-            Dn += (n + 1) * (n + 1);
-        }
-        // ---- translation along z, order by order (in place)
-        const double *Al = At;
-        double rl = 1.0;  // rho^-l
-        for (int l = 0; l <= p; l++) {
-            const int len = p + 1 - l;
-            double rp = rl;
-            for (int n = l; n <= p; n++) {
-                const double2 mr = v[tri(n, l) * T];
-                u[(n - l) * T] = make_double2(mr.x * rp, -mr.y * rp);
-                rp *= rinv;
-            }
-            double rk = rl * rinv;  // rho^-(k+1) at k = l
-            for (int k = l; k <= p; k++) {
-                double re = 0.0, im = 0.0;
-                const double *a = Al + (k - l) * len;
-                for (int j = 0; j < len; j++) {
-                    const double2 s = u[j * T];
-                    re = fma(a[j], s.x, re);
-                    im = fma(a[j], s.y, im);
-                }
-                v[tri(k, l) * T] = make_double2(re * rk, im * rk);
-                rk *= rinv;
-            }
-            Al += len * len;
-            rl *= rinv;
-        }
-        // ---- inverse rotation, degree by degree; reduce over the warp
-        Dn = Dt;
-        for (int k = 0; k <= p; k++) {
-            for (int m = 0; m <= k; m++)
-                u[m * T] = cscale(mul_ipow(m, v[tri(k, m) * T]), m ? 2.0 : 1.0);
-            fold_apply(Dn, k, u, x, T, false);
-            double2 pb = make_double2(1.0, 0.0);
-            for (int j = 0; j <= k; j++) {
-                x[j * T] = cscale(cmul(x[j * T], pb), j ? 2.0 : 1.0);
-                pb = cmul(pb, eb_);
-            }
-            fold_apply(Dn, k, x, u, T, true);
-            double2 ph = make_double2(1.0, 0.0);
-            for (int l = 0; l <= k; l++) {
-                const int c = tri(k, l);
-                double2 r = cscale(cmul(mul_ipow(4 - (l & 3), u[l * T]), ph), Ft[c]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
-                    r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
-                }
-                if (lane == (c & 31)) acc[w * nc + c] = cadd(acc[w * nc + c], r);
-                ph = cmul(ph, ea);
-            }
-            Dn += (k + 1) * (k + 1);
-        }
+    const int64_t g = blockIdx.x * (int64_t)T + tid;
+    const bool valid = g < PT.off[PT.lmax + 1];
+    int64_t gt = -1, gs = 0;
+    double dx = 1.0, dy = 0.0, dz = 0.0;
+    if (valid) {
+        pair_of(PT, g, gt, gs);
+        dx = centre[3 * gt] - centre[3 * gs];
+        dy = centre[3 * gt + 1] - centre[3 * gs + 1];
+        dz = centre[3 * gt + 2] - centre[3 * gs + 2];
     }
-    __syncthreads();
-    for (int c = tid; c < nc; c += T) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int j = 0; j < nw; j++) s = cadd(s, acc[j * nc + c]);
-        L[gt * nc + c] = s;
+    bool same[5], head;
+    seg_setup(gt, same, head);
+    const double rxy = sqrt(dx * dx + dy * dy);
+    const double rho = sqrt(dx * dx + dy * dy + dz * dz);
+    const double rinv = 1.0 / rho;
+    const double2 ea = rxy > 0.0 ? make_double2(dx / rxy, dy / rxy) : make_double2(1.0, 0.0);
+    const double2 eb_ = make_double2(dz * rinv, rxy * rinv);
+    const double2 eai = make_double2(ea.y, -ea.x);  // -i e^{ia}
+
+    // ---- forward rotation, degree by degree -> v = Mr (F-normalised)
+    const double *Dn = Dt;
+    for (int n = 0; n <= p; n++) {
+        double2 ph = make_double2(1.0, 0.0);
+        for (int m = 0; m <= n; m++) {
+            const int c = tri(n, m);
+            const double2 mv = valid ? M[gs * nc + c] : make_double2(0.0, 0.0);
+            u[m * T] = cscale(cmul(mv, ph), Ft[c] * (m ? 2.0 : 1.0));
+            ph = cmul(ph, eai);
+        }
+        fold_apply(Dn, n, u, x, T, false);
+        double2 pb = make_double2(1.0, 0.0);
+        for (int k = 0; k <= n; k++) {
+            x[k * T] = cscale(cmul(x[k * T], pb), k ? 2.0 : 1.0);
+            pb = cmul(pb, eb_);
+        }
+        fold_apply(Dn, n, x, u, T, true);
+        for (int m = 0; m <= n; m++) v[tri(n, m) * T] = mul_ipow(m, u[m * T]);
+        Dn += (n + 1) * (n + 1);
+    }
+    // ---- translation along z, order by order (in place)
+    const double *Al = At;
+    double rl = 1.0;  // rho^-l
+    for (int l = 0; l <= p; l++) {
+        const int len = p + 1 - l;
+        double rp = rl;
+        for (int n = l; n <= p; n++) {
+            const double2 mr = v[tri(n, l) * T];
+            u[(n - l) * T] = make_double2(mr.x * rp, -mr.y * rp);
+            rp *= rinv;
+        }
+        double rk = rl * rinv;  // rho^-(k+1) at k = l
+        for (int k = l; k <= p; k++) {
+            double re = 0.0, im = 0.0;
+            const double *a = Al + (k - l) * len;
+            for (int j = 0; j < len; j++) {
+                const double2 s = u[j * T];
+                re = fma(a[j], s.x, re);
+                im = fma(a[j], s.y, im);
+            }
+            v[tri(k, l) * T] = make_double2(re * rk, im * rk);
+            rk *= rinv;
+        }
+        Al += len * len;
+        rl *= rinv;
+    }
+    // ---- inverse rotation, degree by degree; segmented reduction per target
+    Dn = Dt;
+    for (int k = 0; k <= p; k++) {
+        for (int m = 0; m <= k; m++)
+            u[m * T] = cscale(mul_ipow(m, v[tri(k, m) * T]), m ? 2.0 : 1.0);
+        fold_apply(Dn, k, u, x, T, false);
+        double2 pb = make_double2(1.0, 0.0);
+        for (int j = 0; j <= k; j++) {
+            x[j * T] = cscale(cmul(x[j * T], pb), j ? 2.0 : 1.0);
+            pb = cmul(pb, eb_);
+        }
+        fold_apply(Dn, k, x, u, T, true);
+        double2 ph = make_double2(1.0, 0.0);
+        for (int l = 0; l <= k; l++) {
+            const int c = tri(k, l);
+            const double2 r = cscale(cmul(mul_ipow(4 - (l & 3), u[l * T]), ph), Ft[c]);
+            const double rx = seg_sum(r.x, same), ry = seg_sum(r.y, same);
+            if (head) {
+                atomicAdd(&L[gt * nc + c].x, rx);
+                atomicAdd(&L[gt * nc + c].y, ry);
+            }
+            ph = cmul(ph, ea);
+        }
+        Dn += (k + 1) * (k + 1);
     }
 }
 
@@ -228,6 +252,28 @@ std::vector<double> m2l_tables(int p) {
     return t;
 }
 
+PairTable pair_table(const Plan &P) {
+    PairTable PT{};
+    PT.lmin = 1;
+    PT.lmax = std::max(P.B, 1);
+    long long o = 0;
+    for (int l = 0; l <= FMM_MAX_LEVELS + 1; l++) {
+        if (l <= FMM_MAX_LEVELS && l >= 1 && l <= P.B) {
+            PT.tgt[l] = P.wrow[l];
+            PT.src[l] = P.wsrc[l];
+        }
+        PT.off[l] = o;
+        if (l >= 1 && l <= P.B) o += P.nweak[l];
+    }
+    return PT;
+}
+
+int64_t total_weak(const Plan &P) {
+    int64_t t = 0;
+    for (int l = 1; l <= P.B; l++) t += P.nweak[l];
+    return t;
+}
+
 cudaError_t m2l_setup(Plan &P) {
     const std::vector<double> t = m2l_tables(P.p);
     P.m2l_ntab = (int)t.size();
@@ -238,9 +284,7 @@ cudaError_t m2l_setup(Plan &P) {
     // stream-ordered copy from pageable memory completes before return
     const int nc = P.nc;
     int threads = 64;
-    auto smem = [&](int T) {
-        return (size_t)(T / 32) * nc * 16 + (size_t)T * (nc + 2 * (P.p + 1)) * 16 + t.size() * 8;
-    };
+    auto smem = [&](int T) { return (size_t)T * (nc + 2 * (P.p + 1)) * 16 + t.size() * 8; };
     if (smem(threads) > 220 * 1024) threads = 32;
     P.m2l_threads = threads;
     P.m2l_smem = smem(threads);
@@ -248,11 +292,15 @@ cudaError_t m2l_setup(Plan &P) {
                                 (int)P.m2l_smem);
 }
 
-void m2l_level(Plan &P, int l) {
-    FMM_LAUNCH(k_m2l_rot_f64, 1u << l, P.m2l_threads, P.m2l_smem, P.stream, l, P.p, P.wptr[l],
-               P.wsrc[l], P.centre, P.M, P.L, P.m2l_tab, P.m2l_ntab);
+// FP64 M2L over all levels in one launch; accumulates into L (zeroed first)
+cudaError_t m2l_all(Plan &P) {
+    cudaMemsetAsync(P.L, 0, (size_t)P.nbox * P.nc * sizeof(double2), P.stream);
+    const int64_t tot = total_weak(P);
+    if (tot == 0) return cudaGetLastError();
+    FMM_LAUNCH(k_m2l_rot_f64, (unsigned)((tot + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads,
+               P.m2l_smem, P.stream, pair_table(P), P.p, P.centre, P.M, P.L, P.m2l_tab, P.m2l_ntab);
+    return cudaGetLastError();
 }
-
 
 // ---------------------------------------------------------------------------
 // Single-precision rotational M2L (FMM_PREC_MIXED).
@@ -338,10 +386,11 @@ __device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, float2 *V, i
     for (int m = 0; m <= N; m++) V[tri(N, m) * T] = fipow(m, u[m]);
 }
 
-// inverse rotation of degree N; warp-reduce into the per-warp accumulator
+// inverse rotation of degree N; segmented reduction over lanes of equal
+// target, then the run's first lane adds into the scaled local Lh (double)
 template <int N>
-__device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 ebv, double2 *acc,
-                                     int lane) {
+__device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 ebv,
+                                     double2 *__restrict__ Lh, unsigned same_mask, bool head) {
     float2 u[N + 1], w[N + 1];
 #pragma unroll
     for (int m = 0; m <= N; m++) {
@@ -364,11 +413,18 @@ __device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 e
         const float2 t = fmulc(fipow(4 - (l & 3), u[l]), ph);
         float rx = t.x * c_F[c], ry = t.y * c_F[c];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rx += __shfl_xor_sync(0xffffffffu, rx, o);
-            ry += __shfl_xor_sync(0xffffffffu, ry, o);
+        for (int j = 0; j < 5; j++) {
+            const float ox = __shfl_down_sync(0xffffffffu, rx, 1 << j);
+            const float oy = __shfl_down_sync(0xffffffffu, ry, 1 << j);
+            if ((same_mask >> j) & 1u) {
+                rx += ox;
+                ry += oy;
+            }
         }
-        if (lane == (c & 31)) acc[c] = make_double2(acc[c].x + rx, acc[c].y + ry);
+        if (head) {
+            atomicAdd(&Lh[c].x, (double)rx);
+            atomicAdd(&Lh[c].y, (double)ry);
+        }
         ph = fmulc(ph, ea);
     }
 }
@@ -417,96 +473,98 @@ struct Seq {
         Seq<P, N + 1>::axial(V, T, qs, qt, rinv);
     }
     __device__ static __forceinline__ void bwd(const float2 *V, int T, float2 ea, float2 ebv,
-                                               double2 *acc, int lane) {
-        bwd_deg<N>(V, T, ea, ebv, acc, lane);
-        Seq<P, N + 1>::bwd(V, T, ea, ebv, acc, lane);
+                                               double2 *Lh, unsigned same, bool head) {
+        bwd_deg<N>(V, T, ea, ebv, Lh, same, head);
+        Seq<P, N + 1>::bwd(V, T, ea, ebv, Lh, same, head);
     }
 };
 template <int P>
 struct Seq<P, P + 1> {
     __device__ static __forceinline__ void fwd(const float2 *, float2 *, int, float2, float2) {}
     __device__ static __forceinline__ void axial(float2 *, int, float, float, float) {}
-    __device__ static __forceinline__ void bwd(const float2 *, int, float2, float2, double2 *, int) {}
+    __device__ static __forceinline__ void bwd(const float2 *, int, float2, float2, double2 *,
+                                               unsigned, bool) {}
 };
 
 constexpr int kF32Threads = 128;
 
+// one weak pair per thread, all levels; accumulates r_t^k L_k into Lh
 template <int P>
 __global__ void __launch_bounds__(kF32Threads)
-k_m2l_rot_f32(int level, const int32_t *__restrict__ wptr, const int32_t *__restrict__ wsrc,
-              const double *__restrict__ centre, const double *__restrict__ radius,
-              const float2 *__restrict__ Mf, double2 *__restrict__ L) {
+k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__restrict__ radius,
+              const float2 *__restrict__ Mf, double2 *__restrict__ Lh) {
     constexpr int NC = (P + 1) * (P + 2) / 2;
-    extern __shared__ double2 smd[];
-    double2 *acc = smd;                                   // [warps][NC]
-    float2 *V = (float2 *)(acc + (kF32Threads / 32) * NC);  // [NC][threads]
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < (kF32Threads / 32) * NC; i += kF32Threads) acc[i] = make_double2(0.0, 0.0);
-    __syncthreads();
-    const int64_t off = ((int64_t)1 << level) - 1;
-    const int t = blockIdx.x;
-    const int64_t gt = off + t;
-    const int e0 = wptr[t], e1 = wptr[t + 1];
-    const double ctx = centre[3 * gt], cty = centre[3 * gt + 1], ctz = centre[3 * gt + 2];
-    const double rt = radius[gt] > 0.0 ? radius[gt] : 1.0;
-    float2 *v = V + tid;
-    for (int eb = e0; eb < e1; eb += kF32Threads) {
-        const int e = eb + tid;
-        const bool valid = e < e1;
-        int64_t gs = 0;
-        double dx = 1.0, dy = 0.0, dz = 0.0, rs = 1.0;
-        if (valid) {
-            gs = off + wsrc[e];
-            dx = ctx - centre[3 * gs];
-            dy = cty - centre[3 * gs + 1];
-            dz = ctz - centre[3 * gs + 2];
-            rs = radius[gs] > 0.0 ? radius[gs] : 1.0;
-        }
-        const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
-        const float2 ea = rxy > 0.0 ? make_float2((float)(dx / rxy), (float)(dy / rxy))
-                                    : make_float2(1.f, 0.f);
-        const float2 ebv = make_float2((float)(dz / rho), (float)(rxy / rho));
-        const float2 eai = make_float2(ea.y, -ea.x);
-        const float rinv = (float)(1.0 / rho);
-        const float qs = (float)(rs / rho), qt = (float)(rt / rho);
-        if (valid) {
-            Seq<P, 0>::fwd(Mf + gs * NC, v, kF32Threads, eai, ebv);
-        } else {
-            for (int c = 0; c < NC; c++) v[c * kF32Threads] = make_float2(0.f, 0.f);
-        }
-        Seq<P, 0>::axial(v, kF32Threads, qs, qt, rinv);
-        Seq<P, 0>::bwd(v, kF32Threads, ea, ebv, acc + w * NC, lane);
+    extern __shared__ float2 smf[];  // [NC][threads]
+    const int tid = threadIdx.x;
+    const int64_t g = blockIdx.x * (int64_t)kF32Threads + tid;
+    const bool valid = g < PT.off[PT.lmax + 1];
+    int64_t gt = -1, gs = 0;
+    double dx = 1.0, dy = 0.0, dz = 0.0, rs = 1.0, rt = 1.0;
+    if (valid) {
+        pair_of(PT, g, gt, gs);
+        dx = centre[3 * gt] - centre[3 * gs];
+        dy = centre[3 * gt + 1] - centre[3 * gs + 1];
+        dz = centre[3 * gt + 2] - centre[3 * gs + 2];
+        rs = radius[gs] > 0.0 ? radius[gs] : 1.0;
+        rt = radius[gt] > 0.0 ? radius[gt] : 1.0;
     }
-    __syncthreads();
-    // L_k = Lhat_k / r_t^k
-    for (int c = tid; c < NC; c += kF32Threads) {
-        int n = 0;
-        while (tri(n + 1, 0) <= c) n++;
-        double s = 1.0;
-        for (int j = 0; j < n; j++) s /= rt;
-        double2 a = make_double2(0.0, 0.0);
-        for (int j = 0; j < kF32Threads / 32; j++) a = cadd(a, acc[j * NC + c]);
-        L[gt * NC + c] = make_double2(a.x * s, a.y * s);
+    bool same[5], head;
+    seg_setup(gt, same, head);
+    unsigned same_mask = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) same_mask |= (unsigned)same[j] << j;
+    const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
+    const float2 ea = rxy > 0.0 ? make_float2((float)(dx / rxy), (float)(dy / rxy))
+                                : make_float2(1.f, 0.f);
+    const float2 ebv = make_float2((float)(dz / rho), (float)(rxy / rho));
+    const float2 eai = make_float2(ea.y, -ea.x);
+    const float rinv = (float)(1.0 / rho);
+    const float qs = (float)(rs / rho), qt = (float)(rt / rho);
+    float2 *v = smf + tid;
+    if (valid) {
+        Seq<P, 0>::fwd(Mf + gs * NC, v, kF32Threads, eai, ebv);
+    } else {
+        for (int c = 0; c < NC; c++) v[c * kF32Threads] = make_float2(0.f, 0.f);
     }
+    Seq<P, 0>::axial(v, kF32Threads, qs, qt, rinv);
+    Seq<P, 0>::bwd(v, kF32Threads, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head);
 }
 
-// Mhat = M / r^n in float, every box of one level
-__global__ void k_scale_multipoles(int level, int p, const double *__restrict__ radius,
+// Mhat = M / r^n in float, every box (levels >= 1)
+__global__ void k_scale_multipoles(int64_t nbox, int p, const double *__restrict__ radius,
                                    const double2 *__restrict__ M, float2 *__restrict__ Mf) {
     const int nc = ncoef(p);
-    const int64_t off = ((int64_t)1 << level) - 1;
-    const int64_t total = ((int64_t)1 << level) * nc;
+    const int64_t total = nbox * nc;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = off + i / nc;
+        const int64_t g = i / nc;
         const int c = (int)(i % nc);
         int n = 0;
         while (tri(n + 1, 0) <= c) n++;
         const double r = radius[g] > 0.0 ? radius[g] : 1.0;
         double s = 1.0;
         for (int j = 0; j < n; j++) s /= r;
-        const double2 m = M[g * nc + c];
-        Mf[g * nc + c] = make_float2((float)(m.x * s), (float)(m.y * s));
+        const double2 m = M[i];
+        Mf[i] = make_float2((float)(m.x * s), (float)(m.y * s));
+    }
+}
+
+// L = Lhat / r^n, every box
+__global__ void k_unscale_locals(int64_t nbox, int p, const double *__restrict__ radius,
+                                 const double2 *__restrict__ Lh, double2 *__restrict__ L) {
+    const int nc = ncoef(p);
+    const int64_t total = nbox * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = i / nc;
+        const int c = (int)(i % nc);
+        int n = 0;
+        while (tri(n + 1, 0) <= c) n++;
+        const double r = radius[g] > 0.0 ? radius[g] : 1.0;
+        double s = 1.0;
+        for (int j = 0; j < n; j++) s *= r;
+        const double2 h = Lh[i];
+        L[i] = make_double2(h.x / s, h.y / s);
     }
 }
 
@@ -544,9 +602,9 @@ cudaError_t f32_tables_ready() {
 }
 
 template <int P>
-cudaError_t launch_f32(Plan &P_, int l) {
+cudaError_t launch_f32(Plan &Pl, int64_t tot) {
     constexpr int NC = (P + 1) * (P + 2) / 2;
-    const size_t smem = (size_t)(kF32Threads / 32) * NC * 16 + (size_t)kF32Threads * NC * 8;
+    const size_t smem = (size_t)kF32Threads * NC * 8;
     static bool attr_done[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -556,8 +614,8 @@ cudaError_t launch_f32(Plan &P_, int l) {
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
-    FMM_LAUNCH(k_m2l_rot_f32<P>, 1u << l, kF32Threads, smem, P_.stream, l, P_.wptr[l], P_.wsrc[l],
-               P_.centre, P_.radius, P_.Mf, P_.L);
+    FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)((tot + kF32Threads - 1) / kF32Threads), kF32Threads, smem,
+               Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh);
     return cudaGetLastError();
 }
 
@@ -570,24 +628,34 @@ bool m2l_f32_supported(int p) {
 cudaError_t m2l_f32_setup(Plan &P) {
     if (!m2l_f32_supported(P.p)) return cudaSuccess;
     P.Mf = (float2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(float2));
-    if (!P.Mf) return cudaErrorMemoryAllocation;
+    P.Lh = (double2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(double2));
+    if (!P.Mf || !P.Lh) return cudaErrorMemoryAllocation;
     return f32_tables_ready();
 }
 
-cudaError_t m2l_f32_level(Plan &P, int l) {
-    const int64_t total = ((int64_t)1 << l) * P.nc;
-    FMM_LAUNCH(k_scale_multipoles, (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0,
-               P.stream, l, P.p, P.radius, P.M, P.Mf);
-    switch (P.p) {
-        case 4: return launch_f32<4>(P, l);
-        case 6: return launch_f32<6>(P, l);
-        case 8: return launch_f32<8>(P, l);
-        case 10: return launch_f32<10>(P, l);
-        case 12: return launch_f32<12>(P, l);
-        case 14: return launch_f32<14>(P, l);
-        case 16: return launch_f32<16>(P, l);
-        default: return cudaErrorInvalidValue;
+// single-precision M2L over all levels; leaves the unscaled result in L
+cudaError_t m2l_f32_all(Plan &P) {
+    const int64_t total = P.nbox * P.nc;
+    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    FMM_LAUNCH(k_scale_multipoles, grid, 256, 0, P.stream, P.nbox, P.p, P.radius, P.M, P.Mf);
+    cudaMemsetAsync(P.Lh, 0, (size_t)total * sizeof(double2), P.stream);
+    const int64_t tot = total_weak(P);
+    cudaError_t e = cudaSuccess;
+    if (tot > 0) {
+        switch (P.p) {
+            case 4: e = launch_f32<4>(P, tot); break;
+            case 6: e = launch_f32<6>(P, tot); break;
+            case 8: e = launch_f32<8>(P, tot); break;
+            case 10: e = launch_f32<10>(P, tot); break;
+            case 12: e = launch_f32<12>(P, tot); break;
+            case 14: e = launch_f32<14>(P, tot); break;
+            case 16: e = launch_f32<16>(P, tot); break;
+            default: return cudaErrorInvalidValue;
+        }
     }
+    if (e != cudaSuccess) return e;
+    FMM_LAUNCH(k_unscale_locals, grid, 256, 0, P.stream, P.nbox, P.p, P.radius, P.Lh, P.L);
+    return cudaGetLastError();
 }
 
 }  // namespace fmm
