@@ -15,10 +15,10 @@
 //
 // GPU mapping: P2M is one CTA per leaf with one point per lane, streaming the
 // harmonics through the Legendre recurrences and reducing each coefficient
-// over the warp; M2M/L2L are one CTA per parent with one thread per output
-// coefficient; M2L (in m2l.cu) uses the rotational form, one weak pair per
-// thread; L2P is one thread per point with O(1) registers (the series and its
-// gradient accumulate as the recurrence runs).
+// over the warp; M2M is one CTA per parent, one thread per coefficient; L2L
+// and M2L (in m2l.cu) use the rotational form, one translation per thread;
+// L2P is one thread per point with O(1) registers
+// (the series and its gradient accumulate as the recurrence runs).
 
 #include <algorithm>
 
@@ -119,7 +119,10 @@ k_p2m(int B, int p, const double *__restrict__ x, const double *__restrict__ y,
     }
 }
 
-// M2M: parents of level `level - 1` from their two children at `level`
+// M2M (basic form): parents of level `level - 1` from their two children at
+// `level`, one thread per output coefficient. The rotational form (m2l.cu)
+// does fewer operations but exposes one translation per thread, too little
+// parallelism for the few thousand parents of a level on an FP64-bound part.
 __global__ void __launch_bounds__(kExpThreads)
 k_m2m(int level, int p, const double *__restrict__ centre, double2 *M) {
     extern __shared__ double2 sm[];
@@ -147,37 +150,6 @@ k_m2m(int level, int p, const double *__restrict__ centre, double2 *M) {
                 }
         }
         M[gp * nc + c] = s;
-    }
-}
-
-// L2L: children at `level` receive their parent's local expansion
-__global__ void __launch_bounds__(kExpThreads)
-k_l2l(int level, int p, const double *__restrict__ centre, double2 *L) {
-    extern __shared__ double2 sm[];
-    const int nc = ncoef(p);
-    double2 *R = sm, *Lp = sm + 2 * nc;
-    const int64_t gp = ((int64_t)1 << (level - 1)) - 1 + blockIdx.x;
-    const int64_t gc0 = 2 * gp + 1;
-    if (threadIdx.x < 2) {
-        const int64_t gc = gc0 + threadIdx.x;
-        regular_serial(centre[3 * gc] - centre[3 * gp], centre[3 * gc + 1] - centre[3 * gp + 1],
-                       centre[3 * gc + 2] - centre[3 * gp + 2], p, R + threadIdx.x * nc);
-    }
-    for (int c = threadIdx.x; c < nc; c += kExpThreads) Lp[c] = L[gp * nc + c];
-    __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += kExpThreads) {
-        int j, i;
-        untri(c, j, i);
-        for (int ch = 0; ch < 2; ch++) {
-            const double2 *Rc = R + ch * nc;
-            double2 s = make_double2(0.0, 0.0);
-            for (int k = j; k <= p; k++)
-                for (int l = -k; l <= k; l++) {
-                    if (l - i > k - j || i - l > k - j) continue;
-                    s = cadd(s, cmul(coef_at(Lp, k, l), cconj(sview(Rc, k - j, l - i))));
-                }
-            L[(gc0 + ch) * nc + c] = cadd(L[(gc0 + ch) * nc + c], s);
-        }
     }
 }
 
@@ -273,9 +245,7 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     }
     stage_mark(P, FMM_STAGE_M2L, 1);
     stage_mark(P, FMM_STAGE_L2L, 0);
-    for (int l = 1; l <= P.B; l++)
-        FMM_LAUNCH(k_l2l, 1u << (l - 1), kExpThreads, sizeof(double2) * 3 * nc, st, l, P.p, P.centre,
-                   P.L);
+    for (int l = 1; l <= P.B; l++) l2l_level(P, l);
     stage_mark(P, FMM_STAGE_L2L, 1);
     stage_mark(P, FMM_STAGE_L2P, 0);
     if (mixed) {

@@ -160,6 +160,7 @@ cudaError_t direct_run(const void *points, const void *charges, int64_t n, int d
                        cudaStream_t s);
 cudaError_t m2l_setup(Plan &P);
 cudaError_t m2l_all(Plan &P);
+void l2l_level(Plan &P, int level);
 bool m2l_f32_supported(int p);
 cudaError_t m2l_f32_setup(Plan &P);
 cudaError_t m2l_f32_all(Plan &P);

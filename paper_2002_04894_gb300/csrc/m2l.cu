@@ -213,6 +213,89 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
     }
 }
 
+// ---------------------------------------------------------------------------
+// L2L in the rotational form (double precision): rotate the parent's local
+// expansion onto the child offset, translate along z, rotate back:
+//   local, rotated frame (Lt = L / F):    Lt'_j^i = sum_{k>=j} Lt_k^i F_ki rho^{k-j}/(k-j)! / F_ji
+// The forward rotation of a local expansion uses the two folds of the M2L
+// back rotation with conjugate phases. One child per thread.
+// ---------------------------------------------------------------------------
+
+__global__ void k_l2l_rot(int level, int p, const double *__restrict__ centre, double2 *L,
+                          const double *__restrict__ gtab, int ntab) {
+    extern __shared__ double2 sm2[];
+    const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
+    double2 *V = sm2, *U = V + nc * T, *W = U + (p + 1) * T;
+    double *tab = (double *)(W + (p + 1) * T);
+    for (int i = tid; i < ntab; i += T) tab[i] = gtab[i];
+    __syncthreads();
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    const double *Dt = tab, *Ft = tab + 2 * nD;
+    double2 *v = V + tid, *u = U + tid, *x = W + tid;
+    const int64_t j = blockIdx.x * (int64_t)T + tid;  // child index within level
+    if (j >= ((int64_t)1 << level)) return;
+    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = (gc - 1) / 2;
+    const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
+                 dz = centre[3 * gc + 2] - centre[3 * gp + 2];
+    const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
+    const double2 ea = rxy > 0.0 ? make_double2(dx / rxy, dy / rxy) : make_double2(1.0, 0.0);
+    const double2 eb = rho > 0.0 ? make_double2(dz / rho, rxy / rho) : make_double2(1.0, 0.0);
+    const double2 ebc = cconj(eb), eac = cconj(ea);
+    // forward rotation of the parent's local expansion: v = Lt (= L / F) in the rotated frame
+    const double *Dn = Dt;
+    for (int k = 0; k <= p; k++) {
+        double2 ph = make_double2(1.0, 0.0);
+        for (int l = 0; l <= k; l++) {
+            const int c = tri(k, l);
+            u[l * T] = cscale(cmul(mul_ipow(l, L[gp * nc + c]), ph), (l ? 2.0 : 1.0) / Ft[c]);
+            ph = cmul(ph, eac);
+        }
+        fold_apply(Dn, k, u, x, T, false);
+        double2 pb = make_double2(1.0, 0.0);
+        for (int jj = 0; jj <= k; jj++) {
+            x[jj * T] = cscale(cmul(x[jj * T], pb), jj ? 2.0 : 1.0);
+            pb = cmul(pb, ebc);
+        }
+        fold_apply(Dn, k, x, u, T, true);
+        for (int m = 0; m <= k; m++) v[tri(k, m) * T] = mul_ipow(4 - (m & 3), u[m * T]);
+        Dn += (k + 1) * (k + 1);
+    }
+    // axial shift, order by order: Lt'_j^i = sum_{k>=j} Lt_k^i F_ki rho^{k-j}/(k-j)! / F_ji
+    for (int i = 0; i <= p; i++) {
+        for (int k = i; k <= p; k++) u[(k - i) * T] = cscale(v[tri(k, i) * T], Ft[tri(k, i)]);
+        for (int jj = i; jj <= p; jj++) {
+            double re = 0.0, im = 0.0, f = 1.0;
+            for (int k = jj; k <= p; k++) {
+                const double2 t = u[(k - i) * T];
+                re = fma(f, t.x, re);
+                im = fma(f, t.y, im);
+                f = f * rho / (k - jj + 1);
+            }
+            v[tri(jj, i) * T] = cscale(make_double2(re, im), 1.0 / Ft[tri(jj, i)]);
+        }
+    }
+    // back rotation (as in M2L) and add to the child
+    Dn = Dt;
+    for (int k = 0; k <= p; k++) {
+        for (int m = 0; m <= k; m++) u[m * T] = cscale(mul_ipow(m, v[tri(k, m) * T]), m ? 2.0 : 1.0);
+        fold_apply(Dn, k, u, x, T, false);
+        double2 pb = make_double2(1.0, 0.0);
+        for (int jj = 0; jj <= k; jj++) {
+            x[jj * T] = cscale(cmul(x[jj * T], pb), jj ? 2.0 : 1.0);
+            pb = cmul(pb, eb);
+        }
+        fold_apply(Dn, k, x, u, T, true);
+        double2 ph = make_double2(1.0, 0.0);
+        for (int l = 0; l <= k; l++) {
+            const int c = tri(k, l);
+            const double2 r = cscale(cmul(mul_ipow(4 - (l & 3), u[l * T]), ph), Ft[c]);
+            L[gc * nc + c] = cadd(L[gc * nc + c], r);
+            ph = cmul(ph, ea);
+        }
+        Dn += (k + 1) * (k + 1);
+    }
+}
+
 long double factl(int n) {
     long double r = 1.0L;
     for (int i = 2; i <= n; i++) r *= (long double)i;
@@ -288,8 +371,17 @@ cudaError_t m2l_setup(Plan &P) {
     if (smem(threads) > 220 * 1024) threads = 32;
     P.m2l_threads = threads;
     P.m2l_smem = smem(threads);
-    return cudaFuncSetAttribute(k_m2l_rot_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)P.m2l_smem);
+    e = cudaFuncSetAttribute(k_m2l_rot_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)P.m2l_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_l2l_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.m2l_smem);
+    return e;
+}
+
+void l2l_level(Plan &P, int l) {
+    const int64_t nch = (int64_t)1 << l;
+    FMM_LAUNCH(k_l2l_rot, (unsigned)((nch + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads,
+               P.m2l_smem, P.stream, l, P.p, P.centre, P.L, P.m2l_tab, P.m2l_ntab);
 }
 
 // FP64 M2L over all levels in one launch; accumulates into L (zeroed first)
@@ -499,27 +591,29 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
     const int64_t g = blockIdx.x * (int64_t)kF32Threads + tid;
     const bool valid = g < PT.off[PT.lmax + 1];
     int64_t gt = -1, gs = 0;
-    double dx = 1.0, dy = 0.0, dz = 0.0, rs = 1.0, rt = 1.0;
+    float dx = 1.f, dy = 0.f, dz = 0.f, rs = 1.f, rt = 1.f;
     if (valid) {
         pair_of(PT, g, gt, gs);
-        dx = centre[3 * gt] - centre[3 * gs];
-        dy = centre[3 * gt + 1] - centre[3 * gs + 1];
-        dz = centre[3 * gt + 2] - centre[3 * gs + 2];
-        rs = radius[gs] > 0.0 ? radius[gs] : 1.0;
-        rt = radius[gt] > 0.0 ? radius[gt] : 1.0;
+        // centre offsets in double, everything after in float
+        dx = (float)(centre[3 * gt] - centre[3 * gs]);
+        dy = (float)(centre[3 * gt + 1] - centre[3 * gs + 1]);
+        dz = (float)(centre[3 * gt + 2] - centre[3 * gs + 2]);
+        const double rsd = radius[gs], rtd = radius[gt];
+        rs = rsd > 0.0 ? (float)rsd : 1.f;
+        rt = rtd > 0.0 ? (float)rtd : 1.f;
     }
     bool same[5], head;
     seg_setup(gt, same, head);
     unsigned same_mask = 0;
 #pragma unroll
     for (int j = 0; j < 5; j++) same_mask |= (unsigned)same[j] << j;
-    const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
-    const float2 ea = rxy > 0.0 ? make_float2((float)(dx / rxy), (float)(dy / rxy))
-                                : make_float2(1.f, 0.f);
-    const float2 ebv = make_float2((float)(dz / rho), (float)(rxy / rho));
+    const float rxy2 = fmaf(dx, dx, dy * dy);
+    const float rxy = sqrtf(rxy2), rinv = rsqrtf(fmaf(dz, dz, rxy2));
+    const float rxinv = rxy > 0.f ? 1.f / rxy : 0.f;
+    const float2 ea = rxy > 0.f ? make_float2(dx * rxinv, dy * rxinv) : make_float2(1.f, 0.f);
+    const float2 ebv = make_float2(dz * rinv, rxy * rinv);
     const float2 eai = make_float2(ea.y, -ea.x);
-    const float rinv = (float)(1.0 / rho);
-    const float qs = (float)(rs / rho), qt = (float)(rt / rho);
+    const float qs = rs * rinv, qt = rt * rinv;
     float2 *v = smf + tid;
     if (valid) {
         Seq<P, 0>::fwd(Mf + gs * NC, v, kF32Threads, eai, ebv);

@@ -7,8 +7,11 @@
 // In P2P the source offsets are re-expressed relative to the target leaf's
 // centre with an error-free float TwoSum, so the difference of a close pair is
 // taken between two nearly equal hi parts, which is exact (Sterbenz), and
-// close pairs keep full relative precision. Per-target sums are Kahan-
-// compensated. The expansions are evaluated on scaled offsets a / r (r the
+// close pairs keep full relative precision. Per-target sums are plain float
+// over runs of 32 sources and Kahan-compensated across runs (the rounding of
+// a 32-term sum stays near the float unit roundoff while the compensation
+// costs a fraction of an instruction per pair). The expansions are evaluated
+// on scaled offsets a / r (r the
 // box radius, so |a / r| <= 1) and with scaled coefficients M_n / r^n and
 // L_n r^n, which keeps every float value O(1) whatever the box size.
 
@@ -272,20 +275,30 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
                 }
                 __syncthreads();
                 const int mcount = min(kThreads, ns - sb);
-                for (int jj = 0; jj < mcount; jj++) {
-                    const SrcHi s = th[jj];
-                    const SrcLo sl = tl[jj];
-                    const float dx = (xh - s.x) + (xl - sl.x);
-                    const float dy = (yh - s.y) + (yl - sl.y);
-                    const float dz = (zh - s.z) + (zl - sl.z);
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                    const float qr = s.q * rinv;
-                    const float qr3 = qr * rinv * rinv;
-                    kahan(phi, cphi, qr);
-                    kahan(ex, cex, qr3 * dx);
-                    kahan(ey, cey, qr3 * dy);
-                    kahan(ez, cez, qr3 * dz);
+                // plain float sums over runs of 32 sources, compensated once per run
+                for (int j0 = 0; j0 < mcount; j0 += 32) {
+                    const int j1 = min(mcount, j0 + 32);
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+                    for (int jj = j0; jj < j1; jj++) {
+                        const SrcHi s = th[jj];
+                        const SrcLo sl = tl[jj];
+                        const float dx = (xh - s.x) + (xl - sl.x);
+                        const float dy = (yh - s.y) + (yl - sl.y);
+                        const float dz = (zh - s.z) + (zl - sl.z);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        const float qr = s.q * rinv;
+                        const float qr3 = qr * (rinv * rinv);
+                        a0 += qr;
+                        a1 = fmaf(qr3, dx, a1);
+                        a2 = fmaf(qr3, dy, a2);
+                        a3 = fmaf(qr3, dz, a3);
+                    }
+                    kahan(phi, cphi, a0);
+                    kahan(ex, cex, a1);
+                    kahan(ey, cey, a2);
+                    kahan(ez, cez, a3);
                 }
                 __syncthreads();
             }
