@@ -57,6 +57,28 @@ FP32_FLOPS_PER_CLK_SM = 256  # 128 FP32 lanes x FMA
 FP64_FLOPS_PER_CLK_SM = 4    # GB300 nominal 1.25 TFLOP/s FP64 at 2.07 GHz / 152 SMs
 
 
+# DRAM bytes per launch of the dominant kernel from one ncu capture
+# (profiles/k_p2p_f32_plummer2m_l14_p12.md), valid only while the kernel's
+# source is the one that was captured (checked by hash; otherwise null).
+MEASURED_TRAFFIC = {
+    ("plummer2m_l14_p12", "k_p2p_f32"): {"bytes": 244380416 + 122345216,
+                                         "source": "paper_2002_04894_gb300/csrc/mixed.cu",
+                                         "sha256_16": "b7ef59df8ce107e9"},
+}
+
+
+def measured_traffic(workload, kernel):
+    import hashlib
+    m = MEASURED_TRAFFIC.get((workload, kernel))
+    if not m:
+        return None
+    try:
+        h = hashlib.sha256(open(os.path.join(ROOT, m["source"]), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return m["bytes"] if h == m["sha256_16"] else None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -317,9 +339,12 @@ def bench_ours(args, rank, world, local):
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "work": {"p2p_interactions": stats["p2p_interactions"], "weak_pairs": stats["weak_pairs"],
                  "strong_leaf_pairs": stats["strong_leaf_pairs"]},
-        "roofline": {"kernel": "p2p", "bound": "alu", "achieved": round(achieved, 4),
+        "roofline": {"kernel": "k_p2p_f32" if prec == fmm.FMM_PREC_MIXED else "k_p2p_f64",
+                     "bound": "alu", "achieved": round(achieved, 4),
                      "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
-                     "frac": round(achieved / peak_tflops, 4), "traffic": None,
+                     "frac": round(achieved / peak_tflops, 4),
+                     "traffic": measured_traffic(args.workload,
+                                                 "k_p2p_f32" if prec == fmm.FMM_PREC_MIXED else "k_p2p_f64"),
                      "peak_basis": (f"{SM_COUNT} SMs x {fp} flop/clk x {max_mhz:.0f} MHz "
                                     f"({'FP64' if fp == FP64_FLOPS_PER_CLK_SM else 'FP32'} pipe)"),
                      "flops_basis": f"{FLOPS_PER_INTERACTION} flop per pair x exact pair count"},
