@@ -205,7 +205,10 @@ int fmm_plan_list(fmm_plan_t plan, int level, int kind, int64_t *ptr, int32_t *s
  * 0 <= m <= n at n(n+1)/2 + m. Normalisation: M_n^m = sum_j q_j
  * conj(Y_n^m(x_j - c)), phi(c + s) = sum L_n^m conj(Y_n^m(s)), with
  * Y_n^m = (-1)^m r^n P_n^m(cos t) e^{i m phi} / (n+m)! (no Condon-Shortley phase)
- * and C_n^{-m} = (-1)^m conj(C_n^m). Errors: FMM_EINVAL, FMM_ECUDA.
+ * and C_n^{-m} = (-1)^m conj(C_n^m). Multipoles of the levels above the first
+ * level that has weak pairs are not formed (no stage reads them) and read as
+ * zero; local expansions there are zero by definition.
+ * Errors: FMM_EINVAL, FMM_ECUDA.
  */
 int fmm_eval_expansions(fmm_plan_t plan, int which, double *out);
 

@@ -15,9 +15,8 @@
 //
 // GPU mapping: P2M is one CTA per leaf with one point per lane, streaming the
 // harmonics through the Legendre recurrences and reducing each coefficient
-// over the warp; M2M is one CTA per parent, one thread per coefficient; L2L
-// and M2L (in m2l.cu) use the rotational form, one translation per thread;
-// L2P is one thread per point with O(1) registers
+// over the warp; M2M, L2L and M2L (in m2l.cu) use the rotational form, one
+// translation per thread; L2P is one thread per point with O(1) registers
 // (the series and its gradient accumulate as the recurrence runs).
 
 #include <algorithm>
@@ -119,40 +118,6 @@ k_p2m(int B, int p, const double *__restrict__ x, const double *__restrict__ y,
     }
 }
 
-// M2M (basic form): parents of level `level - 1` from their two children at
-// `level`, one thread per output coefficient. The rotational form (m2l.cu)
-// does fewer operations but exposes one translation per thread, too little
-// parallelism for the few thousand parents of a level on an FP64-bound part.
-__global__ void __launch_bounds__(kExpThreads)
-k_m2m(int level, int p, const double *__restrict__ centre, double2 *M) {
-    extern __shared__ double2 sm[];
-    const int nc = ncoef(p);
-    double2 *R = sm, *Mc = sm + 2 * nc;
-    const int64_t gp = ((int64_t)1 << (level - 1)) - 1 + blockIdx.x;
-    const int64_t gc0 = 2 * gp + 1;
-    if (threadIdx.x < 2) {
-        const int64_t gc = gc0 + threadIdx.x;
-        regular_serial(centre[3 * gc] - centre[3 * gp], centre[3 * gc + 1] - centre[3 * gp + 1],
-                       centre[3 * gc + 2] - centre[3 * gp + 2], p, R + threadIdx.x * nc);
-    }
-    for (int c = threadIdx.x; c < 2 * nc; c += kExpThreads) Mc[c] = M[gc0 * nc + c];
-    __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += kExpThreads) {
-        int n, m;
-        untri(c, n, m);
-        double2 s = make_double2(0.0, 0.0);
-        for (int ch = 0; ch < 2; ch++) {
-            const double2 *Rc = R + ch * nc, *Mk = Mc + ch * nc;
-            for (int k = 0; k <= n; k++)
-                for (int l = -k; l <= k; l++) {
-                    if (m - l > n - k || l - m > n - k) continue;
-                    s = cadd(s, cmul(cconj(sview(Rc, k, l)), coef_at(Mk, n - k, m - l)));
-                }
-        }
-        M[gp * nc + c] = s;
-    }
-}
-
 // L2P: far-field potential and field at every leaf point (leaf order)
 __global__ void __launch_bounds__(kExpThreads)
 k_l2p(int B, int p, int64_t npts, const double *__restrict__ x, const double *__restrict__ y,
@@ -231,10 +196,20 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
                    st, P.B, P.p, P.x, P.y, P.z, P.q, P.begin, P.count, P.centre, P.M);
     }
     stage_mark(P, FMM_STAGE_P2M, 1);
-    stage_mark(P, FMM_STAGE_M2M, 0);
+    // the first level with weak pairs: multipoles above it are never read (no
+    // M2L there, and M2M into them would only feed unused levels), so they are
+    // left zero; local expansions above it are exactly zero
+    int lw = P.B + 1;
     for (int l = P.B; l >= 1; l--)
-        FMM_LAUNCH(k_m2m, 1u << (l - 1), kExpThreads, sizeof(double2) * 4 * nc, st, l, P.p, P.centre,
-                   P.M);
+        if (P.nweak[l] > 0) lw = l;
+    stage_mark(P, FMM_STAGE_M2M, 0);
+    for (int l = P.B; l >= 1; l--) {
+        if (l - 1 >= lw)
+            m2m_level(P, l);
+        else
+            cudaMemsetAsync(P.M + (((int64_t)1 << (l - 1)) - 1) * nc, 0,
+                            (size_t)((int64_t)1 << (l - 1)) * nc * sizeof(double2), st);
+    }
     stage_mark(P, FMM_STAGE_M2M, 1);
     // Algorithm 3: M2L at every level (each overwrites its level's L), then L2L downward
     stage_mark(P, FMM_STAGE_M2L, 0);
@@ -245,7 +220,8 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     }
     stage_mark(P, FMM_STAGE_M2L, 1);
     stage_mark(P, FMM_STAGE_L2L, 0);
-    for (int l = 1; l <= P.B; l++) l2l_level(P, l);
+    // L2L into a level whose parents hold nothing would only add zeros
+    for (int l = std::max(1, lw + 1); l <= P.B; l++) l2l_level(P, l);
     stage_mark(P, FMM_STAGE_L2L, 1);
     stage_mark(P, FMM_STAGE_L2P, 0);
     if (mixed) {

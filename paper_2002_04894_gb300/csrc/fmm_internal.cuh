@@ -47,6 +47,7 @@ struct Plan {
     int32_t *wrow[FMM_MAX_LEVELS + 1] = {};  // target of every weak pair (flat M2L)
     int64_t nweak[FMM_MAX_LEVELS + 1] = {}, nstrong[FMM_MAX_LEVELS + 1] = {};
     int64_t p2p_interactions = 0;
+    int32_t *p2p_order = nullptr;  // target leaves, heaviest near-field work first
     bool capacity_exceeded = false;
     // M2L rotation tables (D = d(pi/2) quadrants, axial coefficients, F_nm)
     double *m2l_tab = nullptr;
@@ -55,6 +56,7 @@ struct Plan {
     // mixed precision: leaf offsets hi|lo (6n floats), float charges and far
     // field, radius-scaled float multipoles for the single-precision M2L
     float *hl = nullptr, *qf = nullptr, *far_phi_f = nullptr, *far_E_f = nullptr;
+    float4 *lgeo = nullptr;  // per leaf: centre hi (xyz, radius) | centre lo | half extents
     float2 *Mf = nullptr;
     double2 *Lh = nullptr;  // r^k-scaled locals accumulated by the float M2L
     // evaluation scratch
@@ -132,24 +134,6 @@ __device__ __forceinline__ double2 coef_at(const double2 *C, int n, int m) {
     return ((-m) & 1) ? make_double2(-c.x, c.y) : make_double2(c.x, -c.y);
 }
 
-// Regular solid harmonics R_n^m(d) = r^n P_n^m e^{im phi}/(n+m)!, 0 <= m <= n <= p,
-// by the Legendre recurrences (serial; used for translation vectors).
-__device__ inline void regular_serial(double dx, double dy, double dz, int p, double2 *R) {
-    double r2 = dx * dx + dy * dy + dz * dz;
-    double2 mm = make_double2(1.0, 0.0);
-    for (int m = 0; m <= p; m++) {
-        if (m > 0) mm = cscale(cmul(mm, make_double2(dx, dy)), 0.5 / m);
-        R[tri(m, m)] = mm;
-        if (m + 1 <= p) R[tri(m + 1, m)] = cscale(mm, dz);
-        for (int n = m + 2; n <= p; n++) {
-            double2 a = R[tri(n - 1, m)], b = R[tri(n - 2, m)];
-            double s = 1.0 / ((double)(n - m) * (double)(n + m));
-            R[tri(n, m)] = make_double2(((2 * n - 1) * dz * a.x - r2 * b.x) * s,
-                                        ((2 * n - 1) * dz * a.y - r2 * b.y) * s);
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Host-side launchers (each in its own translation unit)
 // ---------------------------------------------------------------------------
@@ -160,6 +144,7 @@ cudaError_t direct_run(const void *points, const void *charges, int64_t n, int d
                        cudaStream_t s);
 cudaError_t m2l_setup(Plan &P);
 cudaError_t m2l_all(Plan &P);
+void m2m_level(Plan &P, int level);
 void l2l_level(Plan &P, int level);
 bool m2l_f32_supported(int p);
 cudaError_t m2l_f32_setup(Plan &P);

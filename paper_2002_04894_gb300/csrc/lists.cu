@@ -18,6 +18,7 @@
 // Degenerate pairs (theta = 0, or coincident centres) are always strong.
 
 #include <algorithm>
+#include <vector>
 
 #include "fmm_internal.cuh"
 
@@ -181,9 +182,9 @@ __global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *tile_sums) {
     if (i < n) out[i] += tile_sums[i / kScanTile];
 }
 
-// sum over strong leaf pairs (t, s) of n_t * n_s
+// per target leaf and in total: sum over strong leaf pairs (t, s) of n_t * n_s
 __global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, const int32_t *count,
-                           unsigned long long *acc) {
+                           unsigned long long *acc, long long *per_leaf) {
     const int64_t nt = (int64_t)1 << B;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long v = 0;
@@ -192,6 +193,7 @@ __global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, cons
         unsigned long long ns = 0;
         for (int32_t e = sptr[t]; e < sptr[t + 1]; e++) ns += (unsigned long long)count[off + ssrc[e]];
         v = ns * (unsigned long long)count[off + t];
+        per_leaf[t] = (long long)v;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
@@ -291,21 +293,34 @@ cudaError_t lists_build(Plan &P) {
                    ctgt, P.wsrc[l], P.wrow[l], P.ssrc[l], srow);
         srow_prev = srow;
     }
-    // exact P2P work (sum of n_t * n_s over strong leaf pairs)
+    // exact P2P work (sum of n_t * n_s over strong leaf pairs), per leaf and in
+    // total; the near-field kernels take the leaves heaviest first, so that the
+    // long ones start early instead of forming the tail of the launch
+    const int64_t nl = (int64_t)1 << P.B;
     unsigned long long *acc = (unsigned long long *)dalloc(P, 8);
-    if (!acc) {
+    long long *work = (long long *)dalloc(P, (size_t)nl * 8);
+    P.p2p_order = (int32_t *)palloc(P, (size_t)nl * 4);
+    if (!acc || !work || !P.p2p_order) {
         cudaFreeHost(totals);
         return cudaErrorMemoryAllocation;
     }
     cudaMemsetAsync(acc, 0, 8, st);
-    const int64_t nl = (int64_t)1 << P.B;
     FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.sptr[P.B], P.ssrc[P.B],
-               P.count, acc);
+               P.count, acc, work);
+    std::vector<long long> hw((size_t)nl);
     unsigned long long h = 0;
     cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hw.data(), work, (size_t)nl * 8, cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     P.p2p_interactions = (int64_t)h;
     cudaFreeHost(totals);
+    if (e != cudaSuccess) return e;
+    std::vector<int32_t> order((size_t)nl);
+    for (int64_t i = 0; i < nl; i++) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return hw[a] > hw[b]; });
+    e = cudaMemcpyAsync(P.p2p_order, order.data(), (size_t)nl * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -214,12 +214,93 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
 }
 
 // ---------------------------------------------------------------------------
-// L2L in the rotational form (double precision): rotate the parent's local
+// M2M and L2L in the rotational form (double precision). L2L: rotate the parent's local
 // expansion onto the child offset, translate along z, rotate back:
 //   local, rotated frame (Lt = L / F):    Lt'_j^i = sum_{k>=j} Lt_k^i F_ki rho^{k-j}/(k-j)! / F_ji
 // The forward rotation of a local expansion uses the two folds of the M2L
 // back rotation with conjugate phases. One child per thread.
 // ---------------------------------------------------------------------------
+
+// M2M in the rotational form, one child per thread; the parent's multipole
+// (zeroed beforehand) receives both children's shifted expansions atomically.
+//   multipole, rotated frame (Mt = F M):  Mt'_n^m = F_nm sum_k rho^k/k! Mt_{n-k}^m / F_{n-k,m}
+__global__ void k_m2m_rot(int level, int p, const double *__restrict__ centre, double2 *M,
+                          const double *__restrict__ gtab, int ntab) {
+    extern __shared__ double2 sm2[];
+    const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
+    double2 *V = sm2, *U = V + nc * T, *W = U + (p + 1) * T;
+    double *tab = (double *)(W + (p + 1) * T);
+    for (int i = tid; i < ntab; i += T) tab[i] = gtab[i];
+    __syncthreads();
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    const double *Dt = tab, *Ft = tab + 2 * nD, *iFt = Ft + nc, *ik = iFt + nc;
+    double2 *v = V + tid, *u = U + tid, *x = W + tid;
+    const int64_t j = blockIdx.x * (int64_t)T + tid;  // child index within level
+    if (j >= ((int64_t)1 << level)) return;
+    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = (gc - 1) / 2;
+    const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
+                 dz = centre[3 * gc + 2] - centre[3 * gp + 2];
+    const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
+    const double irxy = rxy > 0.0 ? 1.0 / rxy : 0.0, irho = rho > 0.0 ? 1.0 / rho : 0.0;
+    const double2 ea = rxy > 0.0 ? make_double2(dx * irxy, dy * irxy) : make_double2(1.0, 0.0);
+    const double2 eb = rho > 0.0 ? make_double2(dz * irho, rxy * irho) : make_double2(1.0, 0.0);
+    const double2 eai = make_double2(ea.y, -ea.x), ebc = cconj(eb), eac = cconj(ea);
+    // forward rotation of the child's multipole -> v (F-normalised, rotated frame)
+    const double *Dn = Dt;
+    for (int n = 0; n <= p; n++) {
+        double2 ph = make_double2(1.0, 0.0);
+        for (int m = 0; m <= n; m++) {
+            const int c = tri(n, m);
+            u[m * T] = cscale(cmul(M[gc * nc + c], ph), Ft[c] * (m ? 2.0 : 1.0));
+            ph = cmul(ph, eai);
+        }
+        fold_apply(Dn, n, u, x, T, false);
+        double2 pb = make_double2(1.0, 0.0);
+        for (int k = 0; k <= n; k++) {
+            x[k * T] = cscale(cmul(x[k * T], pb), k ? 2.0 : 1.0);
+            pb = cmul(pb, eb);
+        }
+        fold_apply(Dn, n, x, u, T, true);
+        for (int m = 0; m <= n; m++) v[tri(n, m) * T] = mul_ipow(m, u[m * T]);
+        Dn += (n + 1) * (n + 1);
+    }
+    // axial shift, order by order
+    for (int m = 0; m <= p; m++) {
+        for (int n = m; n <= p; n++) u[(n - m) * T] = cscale(v[tri(n, m) * T], iFt[tri(n, m)]);
+        for (int n = m; n <= p; n++) {
+            double re = 0.0, im = 0.0, f = 1.0;
+            for (int k = 0; k <= n - m; k++) {
+                const double2 t = u[(n - m - k) * T];
+                re = fma(f, t.x, re);
+                im = fma(f, t.y, im);
+                f = f * rho * ik[k + 1];
+            }
+            v[tri(n, m) * T] = cscale(make_double2(re, im), Ft[tri(n, m)]);
+        }
+    }
+    // inverse rotation; add into the parent
+    Dn = Dt;
+    for (int n = 0; n <= p; n++) {
+        for (int m = 0; m <= n; m++)
+            u[m * T] = cscale(mul_ipow(4 - (m & 3), v[tri(n, m) * T]), m ? 2.0 : 1.0);
+        fold_apply(Dn, n, u, x, T, false);
+        double2 pb = make_double2(1.0, 0.0);
+        for (int k = 0; k <= n; k++) {
+            x[k * T] = cscale(cmul(x[k * T], pb), k ? 2.0 : 1.0);
+            pb = cmul(pb, ebc);
+        }
+        fold_apply(Dn, n, x, u, T, true);
+        double2 ph = make_double2(1.0, 0.0);
+        for (int m = 0; m <= n; m++) {
+            const int c = tri(n, m);
+            const double2 r = cscale(cmul(mul_ipow(m, u[m * T]), ph), iFt[c]);
+            atomicAdd(&M[gp * nc + c].x, r.x);
+            atomicAdd(&M[gp * nc + c].y, r.y);
+            ph = cmul(ph, eac);
+        }
+        Dn += (n + 1) * (n + 1);
+    }
+}
 
 __global__ void k_l2l_rot(int level, int p, const double *__restrict__ centre, double2 *L,
                           const double *__restrict__ gtab, int ntab) {
@@ -230,7 +311,7 @@ __global__ void k_l2l_rot(int level, int p, const double *__restrict__ centre, d
     for (int i = tid; i < ntab; i += T) tab[i] = gtab[i];
     __syncthreads();
     const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
-    const double *Dt = tab, *Ft = tab + 2 * nD;
+    const double *Dt = tab, *Ft = tab + 2 * nD, *iFt = Ft + nc, *ik = iFt + nc;
     double2 *v = V + tid, *u = U + tid, *x = W + tid;
     const int64_t j = blockIdx.x * (int64_t)T + tid;  // child index within level
     if (j >= ((int64_t)1 << level)) return;
@@ -247,7 +328,7 @@ __global__ void k_l2l_rot(int level, int p, const double *__restrict__ centre, d
         double2 ph = make_double2(1.0, 0.0);
         for (int l = 0; l <= k; l++) {
             const int c = tri(k, l);
-            u[l * T] = cscale(cmul(mul_ipow(l, L[gp * nc + c]), ph), (l ? 2.0 : 1.0) / Ft[c]);
+            u[l * T] = cscale(cmul(mul_ipow(l, L[gp * nc + c]), ph), (l ? 2.0 : 1.0) * iFt[c]);
             ph = cmul(ph, eac);
         }
         fold_apply(Dn, k, u, x, T, false);
@@ -269,9 +350,9 @@ __global__ void k_l2l_rot(int level, int p, const double *__restrict__ centre, d
                 const double2 t = u[(k - i) * T];
                 re = fma(f, t.x, re);
                 im = fma(f, t.y, im);
-                f = f * rho / (k - jj + 1);
+                f = f * rho * ik[k - jj + 1];
             }
-            v[tri(jj, i) * T] = cscale(make_double2(re, im), 1.0 / Ft[tri(jj, i)]);
+            v[tri(jj, i) * T] = cscale(make_double2(re, im), iFt[tri(jj, i)]);
         }
     }
     // back rotation (as in M2L) and add to the child
@@ -317,7 +398,7 @@ long double wigner_half_pi(int n, int k, int m) {
 
 }  // namespace
 
-// Tables for order p: D_n quadrants, axial coefficients, F_nm.
+// Tables for order p: D_n quadrants, axial coefficients, F_nm, 1/F_nm, 1/k.
 std::vector<double> m2l_tables(int p) {
     std::vector<double> t;
     for (int n = 0; n <= p; n++)
@@ -332,6 +413,9 @@ std::vector<double> m2l_tables(int p) {
             }
     for (int n = 0; n <= p; n++)
         for (int m = 0; m <= n; m++) t.push_back((double)F(n, m));
+    for (int n = 0; n <= p; n++)
+        for (int m = 0; m <= n; m++) t.push_back((double)(1.0L / F(n, m)));
+    for (int k = 0; k <= p + 1; k++) t.push_back(k ? (double)(1.0L / k) : 0.0);  // 1/k
     return t;
 }
 
@@ -375,7 +459,17 @@ cudaError_t m2l_setup(Plan &P) {
                              (int)P.m2l_smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_l2l_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.m2l_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_m2m_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.m2l_smem);
     return e;
+}
+
+// parents of level l-1 from their children at level l (parents zeroed first)
+void m2m_level(Plan &P, int l) {
+    const int64_t np = (int64_t)1 << (l - 1), nch = (int64_t)1 << l;
+    cudaMemsetAsync(P.M + (np - 1) * P.nc, 0, (size_t)np * P.nc * sizeof(double2), P.stream);
+    FMM_LAUNCH(k_m2m_rot, (unsigned)((nch + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads,
+               P.m2l_smem, P.stream, l, P.p, P.centre, P.M, P.m2l_tab, P.m2l_ntab);
 }
 
 void l2l_level(Plan &P, int l) {

@@ -218,29 +218,57 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
     return s;
 }
 
-struct __align__(16) SrcHi {
-    float x, y, z, q;
-};
-struct __align__(16) SrcLo {
-    float x, y, z, pad;
-};
+// per leaf, in float: centre hi (xyz) + radius | centre lo | half extents
+__global__ void k_leaf_geo(int B, const double *__restrict__ lo, const double *__restrict__ hi,
+                           const double *__restrict__ centre, const double *__restrict__ radius,
+                           float4 *__restrict__ geo) {
+    const int64_t nl = (int64_t)1 << B;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nl) return;
+    const int64_t g = nl - 1 + j;
+    float h[3], l[3], e[3];
+    for (int a = 0; a < 3; a++) {
+        const double c = centre[3 * g + a];
+        h[a] = (float)c;
+        l[a] = (float)(c - (double)h[a]);
+        e[a] = (float)(0.5 * (hi[3 * g + a] - lo[3 * g + a]));
+    }
+    geo[3 * j] = make_float4(h[0], h[1], h[2], (float)radius[g]);
+    geo[3 * j + 1] = make_float4(l[0], l[1], l[2], 0.f);
+    geo[3 * j + 2] = make_float4(e[0], e[1], e[2], 0.f);
+}
 
+constexpr int kLeafChunk = 256;
+
+// Near field in float. One CTA per target leaf (heaviest leaves first), one
+// target point per thread. For every source leaf the offset between the two
+// leaf centres is formed once, error-free (float TwoSum on the centres' hi/lo
+// parts), together with a near/far flag: far when the gap g between the two
+// cells is at least half the sum of their radii. The float offsets then carry
+// an absolute error of about 2u (r_t + r_s + |offset|), and since strongly
+// connected leaves have |offset| < 3 max(r_t, r_s), every far pair's distance
+// (>= g) is known to ~11u relative: a single float per coordinate suffices,
+// and no two points can coincide. Near leaves (touching cells) keep the split
+// hi/lo offsets, whose difference is exact for close pairs.
 template <typename OutT>
 __global__ void __launch_bounds__(kThreads)
 k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
-          const double *__restrict__ centre, const int32_t *__restrict__ sptr,
-          const int32_t *__restrict__ ssrc, const int32_t *__restrict__ perm,
-          const float *__restrict__ far_phi, const float *__restrict__ far_E, OutT *__restrict__ pot,
-          OutT *__restrict__ field) {
-    __shared__ SrcHi th[kThreads];
-    __shared__ SrcLo tl[kThreads];
-    __shared__ float dlt[6];
+          const float4 *__restrict__ geo, const int32_t *__restrict__ sptr,
+          const int32_t *__restrict__ ssrc, const int32_t *__restrict__ order,
+          const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
+          const float *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
+    __shared__ float4 th[kThreads];     // source offset from the target centre (hi) and charge
+    __shared__ float4 tl[kThreads];     // lo parts (near leaves)
+    __shared__ float4 dh[kLeafChunk];   // per source leaf: centre offset hi, near flag
+    __shared__ float4 dl[kLeafChunk];   // centre offset lo
+    __shared__ int2 rng[kLeafChunk];    // begin, count
     const int64_t off = ((int64_t)1 << B) - 1;
-    const int t = blockIdx.x;
+    const int t = order[blockIdx.x];
     const int64_t gt = off + t;
     const int bt = begin[gt], nt = count[gt];
     const int e0 = sptr[t], e1 = sptr[t + 1];
+    const float4 tc_h = geo[3 * t], tc_l = geo[3 * t + 1], tc_e = geo[3 * t + 2];
     for (int tb = 0; tb < nt; tb += kThreads) {
         const int i = tb + threadIdx.x;
         const bool active = i < nt;
@@ -249,58 +277,97 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
         const float xl = active ? hl[3 * n + bt + i] : 0.f, yl = active ? hl[4 * n + bt + i] : 0.f,
                     zl = active ? hl[5 * n + bt + i] : 0.f;
         float phi = 0.f, cphi = 0.f, ex = 0.f, cex = 0.f, ey = 0.f, cey = 0.f, ez = 0.f, cez = 0.f;
-        for (int e = e0; e < e1; e++) {
-            const int64_t gs = off + ssrc[e];
-            const int bs = begin[gs], ns = count[gs];
+        for (int cb = e0; cb < e1; cb += kLeafChunk) {
+            const int clen = min(kLeafChunk, e1 - cb);
             __syncthreads();
-            if (threadIdx.x < 3) {  // source-to-target centre offset, split hi/lo
-                const double d = centre[3 * gs + threadIdx.x] - centre[3 * gt + threadIdx.x];
-                const float h = (float)d;
-                dlt[threadIdx.x] = h;
-                dlt[3 + threadIdx.x] = (float)(d - (double)h);
+            for (int k = threadIdx.x; k < clen; k += kThreads) {
+                const int s = ssrc[cb + k];
+                const float4 sh = geo[3 * s], sl = geo[3 * s + 1], se = geo[3 * s + 2];
+                float e_x, e_y, e_z;
+                const float dxh = two_sum(sh.x, -tc_h.x, e_x);
+                const float dyh = two_sum(sh.y, -tc_h.y, e_y);
+                const float dzh = two_sum(sh.z, -tc_h.z, e_z);
+                const float gx = fmaxf(0.f, fabsf(dxh) - (tc_e.x + se.x));
+                const float gy = fmaxf(0.f, fabsf(dyh) - (tc_e.y + se.y));
+                const float gz = fmaxf(0.f, fabsf(dzh) - (tc_e.z + se.z));
+                const float half = 0.5f * (tc_h.w + sh.w);
+                const bool far = gx * gx + gy * gy + gz * gz >= half * half && half > 0.f;
+                dh[k] = make_float4(dxh, dyh, dzh, far ? 1.f : 0.f);
+                dl[k] = make_float4(e_x + (sl.x - tc_l.x), e_y + (sl.y - tc_l.y), e_z + (sl.z - tc_l.z), 0.f);
+                rng[k] = make_int2(begin[off + s], count[off + s]);
             }
             __syncthreads();
-            for (int sb = 0; sb < ns; sb += kThreads) {
-                const int j = sb + threadIdx.x;
-                if (j < ns) {
-                    // offset of the source from the target leaf centre, hi + lo
-                    float ex_, ey_, ez_;
-                    const float sx = two_sum(hl[bs + j], dlt[0], ex_);
-                    const float sy = two_sum(hl[n + bs + j], dlt[1], ey_);
-                    const float sz = two_sum(hl[2 * n + bs + j], dlt[2], ez_);
-                    th[threadIdx.x] = SrcHi{sx, sy, sz, qf[bs + j]};
-                    tl[threadIdx.x] = SrcLo{ex_ + (hl[3 * n + bs + j] + dlt[3]),
-                                            ey_ + (hl[4 * n + bs + j] + dlt[4]),
-                                            ez_ + (hl[5 * n + bs + j] + dlt[5]), 0.f};
-                }
-                __syncthreads();
-                const int mcount = min(kThreads, ns - sb);
-                // plain float sums over runs of 32 sources, compensated once per run
-                for (int j0 = 0; j0 < mcount; j0 += 32) {
-                    const int j1 = min(mcount, j0 + 32);
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 4
-                    for (int jj = j0; jj < j1; jj++) {
-                        const SrcHi s = th[jj];
-                        const SrcLo sl = tl[jj];
-                        const float dx = (xh - s.x) + (xl - sl.x);
-                        const float dy = (yh - s.y) + (yl - sl.y);
-                        const float dz = (zh - s.z) + (zl - sl.z);
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                        const float qr = s.q * rinv;
-                        const float qr3 = qr * (rinv * rinv);
-                        a0 += qr;
-                        a1 = fmaf(qr3, dx, a1);
-                        a2 = fmaf(qr3, dy, a2);
-                        a3 = fmaf(qr3, dz, a3);
+            for (int k = 0; k < clen; k++) {
+                const float4 d = dh[k];
+                const float4 dlo = dl[k];
+                const int bs = rng[k].x, ns = rng[k].y;
+                const bool far = d.w != 0.f;
+                for (int sb = 0; sb < ns; sb += kThreads) {
+                    const int j = sb + threadIdx.x;
+                    __syncthreads();
+                    if (j < ns) {
+                        const float ahx = hl[bs + j], ahy = hl[n + bs + j], ahz = hl[2 * n + bs + j];
+                        const float alx = hl[3 * n + bs + j], aly = hl[4 * n + bs + j],
+                                    alz = hl[5 * n + bs + j];
+                        const float q = qf[bs + j];
+                        if (far) {
+                            th[threadIdx.x] = make_float4((ahx + d.x) + (alx + dlo.x),
+                                                          (ahy + d.y) + (aly + dlo.y),
+                                                          (ahz + d.z) + (alz + dlo.z), q);
+                        } else {
+                            float ux, uy, uz;
+                            const float sx = two_sum(ahx, d.x, ux);
+                            const float sy = two_sum(ahy, d.y, uy);
+                            const float sz = two_sum(ahz, d.z, uz);
+                            th[threadIdx.x] = make_float4(sx, sy, sz, q);
+                            tl[threadIdx.x] = make_float4(ux + (alx + dlo.x), uy + (aly + dlo.y),
+                                                          uz + (alz + dlo.z), 0.f);
+                        }
                     }
-                    kahan(phi, cphi, a0);
-                    kahan(ex, cex, a1);
-                    kahan(ey, cey, a2);
-                    kahan(ez, cez, a3);
+                    __syncthreads();
+                    const int mcount = min(kThreads, ns - sb);
+                    // plain float sums over runs of 32 sources, compensated once per run
+                    for (int j0 = 0; j0 < mcount; j0 += 32) {
+                        const int j1 = min(mcount, j0 + 32);
+                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                        if (far) {
+                            // cells apart: no coincident points, single-float offsets
+#pragma unroll 4
+                            for (int jj = j0; jj < j1; jj++) {
+                                const float4 s = th[jj];
+                                const float dx = xh - s.x, dy = yh - s.y, dz = zh - s.z;
+                                const float rinv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                                const float qr = s.w * rinv;
+                                const float qr3 = qr * (rinv * rinv);
+                                a0 += qr;
+                                a1 = fmaf(qr3, dx, a1);
+                                a2 = fmaf(qr3, dy, a2);
+                                a3 = fmaf(qr3, dz, a3);
+                            }
+                        } else {
+#pragma unroll 4
+                            for (int jj = j0; jj < j1; jj++) {
+                                const float4 s = th[jj];
+                                const float4 sl = tl[jj];
+                                const float dx = (xh - s.x) + (xl - sl.x);
+                                const float dy = (yh - s.y) + (yl - sl.y);
+                                const float dz = (zh - s.z) + (zl - sl.z);
+                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                                const float qr = s.w * rinv;
+                                const float qr3 = qr * (rinv * rinv);
+                                a0 += qr;
+                                a1 = fmaf(qr3, dx, a1);
+                                a2 = fmaf(qr3, dy, a2);
+                                a3 = fmaf(qr3, dz, a3);
+                            }
+                        }
+                        kahan(phi, cphi, a0);
+                        kahan(ex, cex, a1);
+                        kahan(ey, cey, a2);
+                        kahan(ez, cez, a3);
+                    }
                 }
-                __syncthreads();
             }
         }
         if (active) {
@@ -324,9 +391,12 @@ cudaError_t mixed_setup(Plan &P) {
     P.qf = (float *)palloc(P, (size_t)n * 4);
     P.far_phi_f = (float *)palloc(P, (size_t)n * 4);
     P.far_E_f = (float *)palloc(P, (size_t)n * 12);
-    if (!P.hl || !P.qf || !P.far_phi_f || !P.far_E_f) return cudaErrorMemoryAllocation;
+    P.lgeo = (float4 *)palloc(P, (size_t)P.nleaf * 3 * sizeof(float4));
+    if (!P.hl || !P.qf || !P.far_phi_f || !P.far_E_f || !P.lgeo) return cudaErrorMemoryAllocation;
     FMM_LAUNCH(k_leaf_offsets, (unsigned)P.nleaf, 128, 0, P.stream, P.B, n, P.x, P.y, P.z, P.begin,
                P.count, P.centre, P.hl);
+    FMM_LAUNCH(k_leaf_geo, (unsigned)((P.nleaf + 127) / 128), 128, 0, P.stream, P.B, P.lo, P.hi,
+               P.centre, P.radius, P.lgeo);
     return cudaGetLastError();
 }
 
@@ -351,12 +421,12 @@ cudaError_t mixed_l2p(Plan &P) {
 cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
     if (dtype == FMM_F64)
         FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.nleaf, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.centre, P.sptr[P.B], P.ssrc[P.B], P.perm, P.far_phi_f,
-                   P.far_E_f, (double *)pot, (double *)field);
+                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_order, P.perm,
+                   P.far_phi_f, P.far_E_f, (double *)pot, (double *)field);
     else
         FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.nleaf, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.centre, P.sptr[P.B], P.ssrc[P.B], P.perm, P.far_phi_f,
-                   P.far_E_f, (float *)pot, (float *)field);
+                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_order, P.perm,
+                   P.far_phi_f, P.far_E_f, (float *)pot, (float *)field);
     return cudaGetLastError();
 }
 
