@@ -261,6 +261,28 @@ int64_t fmm_kernel_launches(void);
 int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, int levels, int32_t *perm,
                           void *stream);
 
+/*
+ * Batched evaluation of many independent systems (one graph launch).
+ *
+ * fmm_batch_create -- record the evaluation (fmm_eval) of nplans plans into
+ * one CUDA graph. Plan i reads charges[i] and writes potentials[i] and
+ * fields[i] (NULL entry: no field); all of these must be DEVICE pointers and
+ * stay valid for the life of the batch. The evaluations are spread over
+ * nstreams (1..64; 0 = 16) forked branches of the graph, so that independent
+ * systems of different sizes run concurrently on the device. `stream` is the
+ * stream used for the capture (a private one is made if it is NULL). The plans
+ * must not be evaluated elsewhere while the batch runs, and must outlive it.
+ * Errors: FMM_EINVAL, FMM_ECUDA.
+ * fmm_batch_launch -- run the recorded evaluations on `stream` (asynchronous).
+ * fmm_batch_destroy -- release the graph and its streams (NULL: no-op).
+ */
+typedef struct fmm_batch_s *fmm_batch_t;
+int fmm_batch_create(const fmm_plan_t *plans, int nplans, const void *const *charges,
+                     void *const *potentials, void *const *fields, int nstreams, void *stream,
+                     fmm_batch_t *out);
+int fmm_batch_launch(fmm_batch_t batch, void *stream);
+void fmm_batch_destroy(fmm_batch_t batch);
+
 /* fmm_strerror -- static text for a status code. */
 const char *fmm_strerror(int status);
 

@@ -59,7 +59,7 @@ _LIB = None
 EXPORTS = ("fmm_plan", "fmm_eval", "fmm_destroy", "fmm_direct", "fmm_plan_stats",
            "fmm_plan_tree", "fmm_plan_list", "fmm_eval_expansions", "fmm_strerror",
            "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches",
-           "fmm_orb_order_noalloc")
+           "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy")
 FMM_NOALLOC_MAX_POINTS, FMM_NOALLOC_MAX_LEVELS = 4096, 12
 
 
@@ -104,6 +104,12 @@ def load(build: bool = True) -> C.CDLL:
     lib.fmm_kernel_launches.restype = i64
     lib.fmm_orb_order_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
     lib.fmm_orb_order_noalloc.restype = i32
+    lib.fmm_batch_create.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(vp)]
+    lib.fmm_batch_create.restype = i32
+    lib.fmm_batch_launch.argtypes = [vp, vp]
+    lib.fmm_batch_launch.restype = i32
+    lib.fmm_batch_destroy.argtypes = [vp]
+    lib.fmm_batch_destroy.restype = None
     _LIB = lib
     return lib
 
@@ -341,5 +347,40 @@ def fmm_orb_order_noalloc(points, levels: int, perm=None, stream=None):
         perm = torch.empty(n, dtype=torch.int32, device=points.device)
     _check(load().fmm_orb_order_noalloc(points.data_ptr(), n, _dtype_code(points), int(levels),
                                         perm.data_ptr(), _stream(stream)),
-           "fmm_orb_order_noalloc")
+           "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy")
     return perm
+
+
+class Batch:
+    """Owning handle of an fmm_batch_t (graph of many evaluations)."""
+
+    def __init__(self, handle, keep):
+        self.handle, self._keep = handle, keep
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.fmm_batch_destroy(self.handle)
+            self.handle = None
+
+
+def fmm_batch_create(plans, charges, potentials, fields=None, nstreams: int = 16, stream=None):
+    """Record the evaluations of many plans (device buffers) into one graph."""
+    lib = load()
+    n = len(plans)
+    arr = lambda xs: (C.c_void_p * n)(*[(x.data_ptr() if x is not None else None) for x in xs])
+    hp, hq, hpot = (C.c_void_p * n)(*[p.handle for p in plans]), arr(charges), arr(potentials)
+    hf = arr(fields) if fields is not None else None
+    h = C.c_void_p()
+    _check(lib.fmm_batch_create(hp, n, hq, hpot, hf, int(nstreams), _stream(stream), C.byref(h)),
+           "fmm_batch_create")
+    return Batch(h.value, (plans, charges, potentials, fields))
+
+
+def fmm_batch_launch(batch: Batch, stream=None) -> None:
+    _check(load().fmm_batch_launch(batch.handle, _stream(stream)), "fmm_batch_launch")
+
+
+def fmm_batch_destroy(batch: Batch) -> None:
+    if batch.handle:
+        load().fmm_batch_destroy(batch.handle)
+        batch.handle = None

@@ -74,6 +74,14 @@ struct fmm_plan_s {
     Plan P;
 };
 
+struct fmm_batch_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaStream_t own = nullptr;
+};
+
 namespace {
 
 thread_local int g_last_cuda = 0;
@@ -358,6 +366,83 @@ int fmm_direct(const void *points, const void *charges, int64_t n, int dtype,
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_status(e);
+}
+
+void fmm_batch_destroy(fmm_batch_t b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    if (b->own) cudaStreamDestroy(b->own);
+    cudaGetLastError();
+    delete b;
+}
+
+int fmm_batch_create(const fmm_plan_t *plans, int nplans, const void *const *charges,
+                     void *const *potentials, void *const *fields, int nstreams, void *stream,
+                     fmm_batch_t *out) {
+    if (out) *out = nullptr;
+    if (!out || !plans || !charges || !potentials || nplans < 1 || nstreams < 0 || nstreams > 64)
+        return FMM_EINVAL;
+    for (int i = 0; i < nplans; i++) {
+        if (!plans[i] || !is_device_ptr(charges[i]) || !is_device_ptr(potentials[i])) return FMM_EINVAL;
+        if (fields && fields[i] && !is_device_ptr(fields[i])) return FMM_EINVAL;
+    }
+    const int K = std::min(nstreams ? nstreams : 16, nplans);
+    fmm_batch_s *b = new (std::nothrow) fmm_batch_s();
+    if (!b) return FMM_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    cudaStream_t s0 = (cudaStream_t)stream;
+    if (!s0) e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), s0 = b->own;
+    for (int k = 0; k < K && e == cudaSuccess; k++) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->streams.push_back(s);
+    }
+    for (int k = 0; k <= K && e == cudaSuccess; k++) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->events.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        fmm_batch_destroy(b);
+        return cuda_status(e);
+    }
+    e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(b->events[K], s0);  // fork
+        for (int k = 0; k < K; k++) cudaStreamWaitEvent(b->streams[k], b->events[K], 0);
+        for (int i = 0; i < nplans && e == cudaSuccess; i++) {
+            Plan &P = plans[i]->P;
+            const cudaStream_t keep = P.stream;
+            const bool prof = P.profile;
+            P.stream = b->streams[i % K];
+            P.profile = false;
+            e = fmm::eval_expansions(P, charges[i], P.dtype);
+            if (e == cudaSuccess) e = fmm::eval_p2p(P, potentials[i], fields ? fields[i] : nullptr, P.dtype);
+            P.stream = keep;
+            P.profile = prof;
+        }
+        for (int k = 0; k < K; k++) {  // join
+            cudaEventRecord(b->events[k], b->streams[k]);
+            cudaStreamWaitEvent(s0, b->events[k], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(s0, &b->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        fmm_batch_destroy(b);
+        return cuda_status(e);
+    }
+    *out = b;
+    return FMM_OK;
+}
+
+int fmm_batch_launch(fmm_batch_t b, void *stream) {
+    if (!b || !b->exec) return FMM_EINVAL;
+    return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
 }
 
 int fmm_plan_stats(fmm_plan_t plan, fmm_stats *out) {

@@ -790,18 +790,16 @@ cudaError_t f32_tables_ready() {
 }
 
 template <int P>
+cudaError_t attr_f32() {
+    constexpr int NC = (P + 1) * (P + 2) / 2;
+    return cudaFuncSetAttribute(k_m2l_rot_f32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)kF32Threads * NC * 8));
+}
+
+template <int P>
 cudaError_t launch_f32(Plan &Pl, int64_t tot) {
     constexpr int NC = (P + 1) * (P + 2) / 2;
     const size_t smem = (size_t)kF32Threads * NC * 8;
-    static bool attr_done[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_m2l_rot_f32<P>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
     FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)((tot + kF32Threads - 1) / kF32Threads), kF32Threads, smem,
                Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh);
     return cudaGetLastError();
@@ -813,12 +811,24 @@ bool m2l_f32_supported(int p) {
     return p == 4 || p == 6 || p == 8 || p == 10 || p == 12 || p == 14 || p == 16;
 }
 
+// plan-time setup, so that evaluations are safe to capture into a graph
 cudaError_t m2l_f32_setup(Plan &P) {
     if (!m2l_f32_supported(P.p)) return cudaSuccess;
     P.Mf = (float2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(float2));
     P.Lh = (double2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(double2));
     if (!P.Mf || !P.Lh) return cudaErrorMemoryAllocation;
-    return f32_tables_ready();
+    cudaError_t e = f32_tables_ready();
+    if (e != cudaSuccess) return e;
+    switch (P.p) {
+        case 4: return attr_f32<4>();
+        case 6: return attr_f32<6>();
+        case 8: return attr_f32<8>();
+        case 10: return attr_f32<10>();
+        case 12: return attr_f32<12>();
+        case 14: return attr_f32<14>();
+        case 16: return attr_f32<16>();
+        default: return cudaSuccess;
+    }
 }
 
 // single-precision M2L over all levels; leaves the unscaled result in L

@@ -1,0 +1,211 @@
+"""Continuous-batching server for FMM solves.
+
+Requests (points, charges, parameters) arrive over time. The server admits a
+request as soon as it has arrived, a worker slot is free, and its estimated
+device memory fits in what the budget has left; it never waits to fill a
+batch. Each worker owns a CUDA stream, so solves admitted while others are
+still running overlap on the device: host-to-device copies, tree, lists,
+expansions and near field of different requests interleave. Memory is given
+back when a solve completes, which admits the next requests in arrival order.
+Latency is measured from arrival to the result on the host.
+
+The admission policy (`Admission`) is plain Python and is unit-tested on the
+CPU with a stand-in executor; `FmmServer` runs it against the CUDA library.
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    points: object            # host array (n x 3), float64 or float32
+    charges: object           # host array (n)
+    arrival: float = 0.0      # seconds after the start of the run
+    levels: int = -1          # -1: chosen from the leaf-size policy
+    p: int = 10
+    theta: float = 0.5
+    prec: int = 1             # FMM_PREC_MIXED
+    fields: bool = True
+
+
+@dataclass
+class Result:
+    rid: int
+    potentials: np.ndarray
+    fields: np.ndarray | None
+    arrival: float
+    admitted: float
+    done: float
+    levels: int
+    bytes_reserved: int
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def default_levels(n: int, leaf: float = 100.0) -> int:
+    return max(0, int(round(math.log2(max(n, 1) / leaf))))
+
+
+def plan_bytes(n: int, levels: int, p: int, mixed: bool = True) -> int:
+    """Upper estimate of a plan's device memory while it is built and used:
+    points, boxes, lists and expansions (persistent) plus the build's
+    temporaries, plus the caller's input and output copies."""
+    nbox = (2 << levels) - 1
+    nleaf = 1 << levels
+    nc = (p + 1) * (p + 2) // 2
+    persist = n * (96 + (60 if mixed else 0)) + nbox * (128 + 32 * nc + (24 * nc if mixed else 0))
+    lists = nleaf * 3000
+    scratch = n * 40 + nbox * 64 + nleaf * 2000
+    io = n * 8 * 8
+    return int(1.25 * (persist + lists + scratch + io)) + (4 << 20)
+
+
+class Admission:
+    """Arrival-ordered admission under a memory budget and a slot limit.
+    A request larger than the whole budget is admitted alone (when nothing
+    else is in flight), so it cannot starve."""
+
+    def __init__(self, budget: int, slots: int):
+        self.budget, self.slots = int(budget), int(slots)
+        self.in_use = 0
+        self.active = 0
+        self.peak = 0
+
+    def can_admit(self, need: int) -> bool:
+        if self.active >= self.slots:
+            return False
+        return self.in_use + need <= self.budget or self.active == 0
+
+    def admit(self, need: int) -> None:
+        self.in_use += need
+        self.active += 1
+        self.peak = max(self.peak, self.in_use)
+
+    def release(self, need: int) -> None:
+        self.in_use -= need
+        self.active -= 1
+
+
+def run_schedule(requests, execute, budget: int, slots: int, realtime: bool = True, clock=time.perf_counter):
+    """Admit requests in arrival order as slots and memory free up; `execute`
+    (request, t0) -> Result runs on a worker thread. Returns results in
+    request order and the admission record."""
+    adm = Admission(budget, slots)
+    pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+    results = {}
+    cv = threading.Condition()
+    t0 = clock()
+    threads = []
+    errors = []
+
+    def worker(req, need, admitted):
+        try:
+            res = execute(req, t0)
+            res.admitted = admitted
+            res.bytes_reserved = need
+            with cv:
+                results[req.rid] = res
+        except BaseException as e:  # reported after the run
+            errors.append(e)
+        finally:
+            with cv:
+                adm.release(need)
+                cv.notify_all()
+
+    i = 0
+    while i < len(pending):
+        req = pending[i]
+        lv = req.levels if req.levels >= 0 else default_levels(len(req.charges))
+        need = plan_bytes(len(req.charges), lv, req.p, req.prec == 1)
+        with cv:
+            while True:
+                now = clock() - t0
+                if realtime and now < req.arrival:
+                    cv.wait(timeout=req.arrival - now)
+                    continue
+                if adm.can_admit(need):
+                    adm.admit(need)
+                    break
+                cv.wait(timeout=0.05)
+        th = threading.Thread(target=worker, args=(req, need, clock() - t0), daemon=True)
+        th.start()
+        threads.append(th)
+        i += 1
+    for th in threads:
+        th.join()
+    if errors:
+        raise errors[0]
+    return [results[r.rid] for r in requests], adm
+
+
+class FmmServer:
+    """Runs requests through the CUDA library with `workers` concurrent
+    solves, each on its own stream, under a device memory budget (bytes)."""
+
+    def __init__(self, budget: int, workers: int = 8):
+        import torch
+
+        from . import load
+        load()
+        self.budget, self.workers = int(budget), int(workers)
+        self._streams = [torch.cuda.Stream() for _ in range(self.workers)]
+        self._free = list(range(self.workers))
+        self._lock = threading.Lock()
+
+    def _execute(self, req: Request, t0: float) -> Result:
+        import torch
+
+        from . import fmm_destroy, fmm_eval, fmm_plan
+        with self._lock:
+            k = self._free.pop()
+        try:
+            s = self._streams[k]
+            n = len(req.charges)
+            lv = req.levels if req.levels >= 0 else default_levels(n)
+            with torch.cuda.stream(s):
+                xh = torch.as_tensor(req.points).pin_memory()
+                qh = torch.as_tensor(req.charges).pin_memory()
+                xd = xh.to("cuda", non_blocking=True)
+                qd = qh.to("cuda", non_blocking=True)
+                plan = fmm_plan(xd, lv, req.p, req.theta, prec=req.prec, stream=s)
+                pot, fld = fmm_eval(plan, qd, stream=s, want_fields=req.fields)
+                ph = torch.empty(pot.shape, dtype=pot.dtype).pin_memory()
+                ph.copy_(pot, non_blocking=True)
+                fh = None
+                if fld is not None:
+                    fh = torch.empty(fld.shape, dtype=fld.dtype).pin_memory()
+                    fh.copy_(fld, non_blocking=True)
+                s.synchronize()
+                fmm_destroy(plan)
+            done = time.perf_counter() - t0
+            return Result(req.rid, ph.numpy(), None if fh is None else fh.numpy(), req.arrival,
+                          0.0, done, lv, 0)
+        finally:
+            with self._lock:
+                self._free.append(k)
+
+    def run(self, requests, realtime: bool = True):
+        """Serve `requests` (arrival times relative to now). Returns
+        (results in request order, admission record)."""
+        return run_schedule(requests, self._execute, self.budget, self.workers, realtime)
+
+
+def latency_stats(results) -> dict:
+    lat = np.array([r.latency for r in results])
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3)}
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream: exponential gaps of mean 1/rate."""
+    gaps = np.random.default_rng([seed, 3]).exponential(1.0 / rate, size=count)
+    return np.cumsum(gaps)

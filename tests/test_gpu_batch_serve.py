@@ -1,0 +1,95 @@
+"""Batched graph evaluation and the continuous-batching server on the GPU:
+every result equals the same solve done alone. The only difference allowed
+is the order of the double-precision atomic additions in M2L/M2M: 1e-12
+relative in the FP64 form; in the mixed form a last-bit change of a double
+local coefficient can flip the rounding of its float copy in L2P, so 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2002_04894_gb300 import inputs, serve, tune
+
+pytestmark = pytest.mark.gpu
+TOL = {0: 1e-12, 1: 1e-6}
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+SYSTEMS = [("uniform", 3000), ("plummer", 12000), ("gmm", 800), ("uniform", 45000),
+           ("plummer", 1500), ("shell", 7000), ("helix", 20000), ("uniform", 64)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_graph_equals_individual_evals(gpu_lib, prec):
+    fmm = gpu_lib
+    plans, qs, pots, flds, alone = [], [], [], [], []
+    for i, (kind, n) in enumerate(SYSTEMS):
+        x = torch.from_numpy(inputs.points(kind, n, seed=i)).cuda()
+        q = torch.from_numpy(inputs.charges_uniform(n, seed=i)).cuda()
+        plan = fmm.fmm_plan(x, serve.default_levels(n), 8, 0.5, prec=prec)
+        a, b = fmm.fmm_eval(plan, q)
+        alone.append((a.cpu().numpy(), b.cpu().numpy()))
+        plans.append(plan)
+        qs.append(q)
+        pots.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
+        flds.append(torch.zeros((n, 3), dtype=torch.float64, device="cuda"))
+    batch = fmm.fmm_batch_create(plans, qs, pots, flds, nstreams=4)
+    for rep in range(2):                                   # replay: same graph, same buffers
+        for p_ in pots:
+            p_.zero_()
+        fmm.fmm_batch_launch(batch)
+        torch.cuda.synchronize()
+        for (a, b), p_, f_ in zip(alone, pots, flds):
+            assert rel(p_.cpu().numpy(), a) <= TOL[prec]
+            assert rel(f_.cpu().numpy(), b) <= TOL[prec]
+    # new charges in the same buffers are picked up by the next launch
+    qs[1].mul_(-2.0)
+    fmm.fmm_batch_launch(batch)
+    torch.cuda.synchronize()
+    assert rel(pots[1].cpu().numpy(), -2.0 * alone[1][0]) <= TOL[prec]
+    fmm.fmm_batch_destroy(batch)
+
+
+def test_server_mix_equals_alone(gpu_lib):
+    fmm = gpu_lib
+    reqs = []
+    for i, (kind, n) in enumerate(SYSTEMS * 2):
+        x = inputs.points(kind, n, seed=100 + i)
+        q = inputs.charges_uniform(n, seed=100 + i)
+        reqs.append(serve.Request(i, x, q, arrival=0.002 * i, p=8 + 2 * (i % 2), prec=i % 2))
+    alone = []
+    for r in reqs:
+        plan = fmm.fmm_plan(r.points, serve.default_levels(len(r.charges)), r.p, r.theta,
+                            prec=r.prec, allocator=None)
+        a, b = fmm.fmm_eval(plan, r.charges)
+        alone.append((a, b, fmm.fmm_plan_tree(plan)["perm"]))
+    srv = serve.FmmServer(budget=1 << 30, workers=4)
+    res, adm = srv.run(reqs, realtime=True)
+    assert adm.in_use == 0
+    for r, (a, b, perm) in zip(res, alone):
+        tol = TOL[reqs[r.rid].prec]
+        assert rel(r.potentials, a) <= tol, r.rid
+        assert rel(r.fields, b) <= tol, r.rid
+        assert r.done >= r.admitted >= r.arrival - 1e-3
+    st = serve.latency_stats(res)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_server_tight_budget_serialises_but_completes(gpu_lib):
+    reqs = [serve.Request(i, inputs.points("plummer", 20000, i), inputs.charges_uniform(20000, i),
+                          arrival=0.0, p=8) for i in range(5)]
+    need = serve.plan_bytes(20000, serve.default_levels(20000), 8)
+    srv = serve.FmmServer(budget=need + 1, workers=4)
+    res, adm = srv.run(reqs, realtime=False)
+    assert len(res) == 5 and adm.peak <= need + 1
+
+
+def test_tuner_meets_target(gpu_lib):
+    x = torch.from_numpy(inputs.points("plummer", 60000, 3)).cuda()
+    q = torch.from_numpy(inputs.charges_uniform(60000, 3)).cuda()
+    r = tune.tune(x, q, tol=1e-5, ps=(6, 8, 10, 12))
+    assert r.error <= 1e-5
+    assert 32 <= 60000 / 2 ** r.config.levels <= 256
+    assert r.config.theta in (0.4, 0.5, 0.6)
