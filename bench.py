@@ -178,7 +178,7 @@ def bench_reference(args, rank, world):
     """The oracle as it stands, on the host cores, same metric and unit."""
     if rank != 0:
         return
-    name = args.workload
+    name = args.workload if args.workload in WORKLOADS else DEFAULT
     for _ in range(args.warmup):
         run_oracle_sample(name)
     times = []
@@ -368,21 +368,187 @@ def bench_ours(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def bench_batch(args, rank, world, local):
+    """Batched form: many independent systems (N log-uniform in [1e3, 2e5],
+    even ones uniform, odd ones Plummer, float32 points and charges), their
+    parameters chosen by the autotuner per size class, all evaluations in one
+    graph launch per step; compared with the plain one-solve-per-launch FP64
+    form on the same systems."""
+    import torch
+    import paper_2002_04894_gb300 as fmm
+    from paper_2002_04894_gb300 import tune
+
+    torch.cuda.set_device(local)
+    fmm.load()
+    rng = np.random.default_rng([rank, 7])
+    ns = np.floor(10 ** rng.uniform(3.0, np.log10(2e5), size=args.systems)).astype(int)
+    xs, qs = [], []
+    for i, n in enumerate(ns):
+        kind = "uniform" if i % 2 == 0 else "plummer"
+        xs.append(torch.from_numpy(inputs.points(kind, int(n), 1000 * rank + i).astype(np.float32)).cuda())
+        qs.append(torch.from_numpy(inputs.charges_uniform(int(n), 1000 * rank + i).astype(np.float32)).cuda())
+    total = int(ns.sum())
+    # autotune one representative per size class (log2 N) and kind, target 1e-6
+    t_tune = time.perf_counter()
+    table = {}
+    for i, n in enumerate(ns):
+        key = (int(np.log2(n)), i % 2)
+        if key not in table:
+            r = tune.tune(xs[i], qs[i], tol=1e-6, ps=(6, 8, 10, 12, 14))
+            table[key] = r.config
+    t_tune = time.perf_counter() - t_tune
+    cfgs = [table[(int(np.log2(n)), i % 2)] for i, n in enumerate(ns)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plans = [fmm.fmm_plan(x, c.levels, c.p, c.theta, prec=fmm.FMM_PREC_MIXED) for x, c in zip(xs, cfgs)]
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t0
+    pots = [torch.empty(int(n), dtype=torch.float32, device="cuda") for n in ns]
+    flds = [torch.empty((int(n), 3), dtype=torch.float32, device="cuda") for n in ns]
+    k0 = fmm.fmm_kernel_launches()
+    batch = fmm.fmm_batch_create(plans, qs, pots, flds, nstreams=32)
+    graph_kernels = fmm.fmm_kernel_launches() - k0  # kernels recorded in the graph
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        fmm.fmm_batch_launch(batch)
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fmm.fmm_batch_launch(batch)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+    launches = graph_kernels * args.steps
+    t_eval = sum(times) / len(times)
+    # accuracy on a sample of systems (FP64 direct, 200 targets each)
+    errs = []
+    for i in range(0, len(ns), max(1, len(ns) // 16)):
+        tg = torch.from_numpy(inputs.sample_targets(int(ns[i]), 200, i)).cuda()
+        dp = fmm.fmm_direct(xs[i].double(), qs[i].double(), tg)[0]
+        g = pots[i].double()[tg]
+        errs.append(float(torch.linalg.norm(g - dp) / torch.linalg.norm(dp)))
+    # plain FP64 form, one solve per launch sequence, same systems and parameters
+    t0 = time.perf_counter()
+    for x, q, c in zip(xs, qs, cfgs):
+        pl = fmm.fmm_plan(x.double(), c.levels, c.p, c.theta, prec=fmm.FMM_PREC_FP64)
+        fmm.fmm_eval(pl, q.double())
+        fmm.fmm_destroy(pl)
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC + " (batched evaluation)", "value": round(total / (t_eval * 1e-3) / 1e6, 4),
+        "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_eval, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batch", "systems": int(len(ns)), "points": total,
+                   "n_range": [int(ns.min()), int(ns.max())], "kinds": "uniform/plummer alternating",
+                   "step": "one graph launch evaluating every system",
+                   "l2": "flushed between steps (512 MB write)"},
+        "plan_all_s": round(t_plan, 3),
+        "plan_plus_eval_mpts": round(total / (t_plan + t_eval * 1e-3) / 1e6, 4),
+        "fp64_one_solve_per_launch": {"value": round(total / t_fp64 / 1e6, 4), "unit": "Mpoints/s",
+                                      "s": round(t_fp64, 3)},
+        "tuner": {"s": round(t_tune, 2), "classes": {f"2^{k[0]}/{'uniform' if k[1] == 0 else 'plummer'}":
+                                                     [c.levels, c.p, c.theta] for k, c in table.items()}},
+        "accuracy": {"max_rel_l2_phi": max(errs), "systems_checked": len(errs)},
+        "gpu_launches": int(launches), "kernels_per_graph_launch": int(graph_kernels),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
+def bench_serve(args, rank, world, local):
+    """Serving: a Poisson stream of requests (200/s), N log-uniform in
+    [1e3, 1e6], uniform / Plummer / Gaussian-mixture points (1/3 each),
+    target error 1e-5 (p = args.serve_p, theta = 0.5, ~100 points per leaf,
+    mixed form), admitted under a device-memory budget by the continuous-batching
+    server; throughput and p50/p99 latency."""
+    import torch
+    import paper_2002_04894_gb300 as fmm
+    from paper_2002_04894_gb300 import serve
+
+    torch.cuda.set_device(local)
+    fmm.load()
+    kinds = ["uniform", "plummer", "gmm"]
+    pool = {(k, s): (inputs.points(k, 1_000_000, 50 + s), inputs.charges_uniform(1_000_000, 50 + s))
+            for k in kinds for s in range(2)}
+    rng = np.random.default_rng([rank, 11])
+    arr = serve.poisson_arrivals(args.requests, args.rate, seed=rank)
+    reqs = []
+    for i in range(args.requests):
+        n = int(10 ** rng.uniform(3.0, 6.0))
+        k = kinds[rng.integers(0, 3)]
+        x, q = pool[(k, int(rng.integers(0, 2)))]
+        o = int(rng.integers(0, 1_000_000 - n + 1))
+        reqs.append(serve.Request(i, x[o:o + n], q[o:o + n], arrival=float(arr[i]), p=args.serve_p,
+                                  theta=0.5, prec=fmm.FMM_PREC_MIXED))
+    srv = serve.FmmServer(budget=int(args.budget_gb * (1 << 30)), workers=args.workers)
+    warm = [serve.Request(-1 - j, reqs[j].points, reqs[j].charges, 0.0, p=args.serve_p) for j in range(4)]
+    srv.run(warm, realtime=False)
+    launches0 = fmm.fmm_kernel_launches()
+    t0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        res, adm = srv.run(reqs, realtime=True)
+    makespan = time.perf_counter() - t0
+    launches = fmm.fmm_kernel_launches() - launches0
+    pts = sum(len(r.charges) for r in reqs)
+    errs = []
+    for r, rr in list(zip(reqs, res))[:: max(1, len(reqs) // 20)]:
+        n = len(r.charges)
+        tg = inputs.sample_targets(n, 100, r.rid)
+        dp = fmm.fmm_direct(np.ascontiguousarray(r.points), np.ascontiguousarray(r.charges), tg)[0]
+        errs.append(float(np.linalg.norm(rr.potentials[tg] - dp) / np.linalg.norm(dp)))
+    if rank != 0:
+        return
+    lat = serve.latency_stats(res)
+    out = {
+        "metric": "served Mpoints/s and p50/p99 latency", "value": round(pts / makespan / 1e6, 4),
+        "unit": "Mpoints/s", "n_gpus": world, "steps": 1, "warmup": 1,
+        "ms_per_step": round(makespan * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serve", "requests": args.requests, "rate_per_s": args.rate,
+                   "n_range": [1000, 1000000], "budget_gb": args.budget_gb, "workers": args.workers,
+                   "p": args.serve_p, "theta": 0.5, "leaf": 100},
+        "latency_ms": lat, "requests_per_s": round(args.requests / makespan, 2),
+        "admission_peak_gb": round(adm.peak / (1 << 30), 3),
+        "accuracy": {"max_rel_l2_phi": max(errs), "requests_checked": len(errs), "target": 1e-5},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--prec", default=None, choices=["fp64", "mixed"])
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="steps of the plain FP64 form timed as the comparator (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--systems", type=int, default=512, help="batch mode: number of systems")
+    ap.add_argument("--requests", type=int, default=2000, help="serve mode: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve mode: arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve mode: device memory budget")
+    ap.add_argument("--workers", type=int, default=8, help="serve mode: concurrent solves")
+    ap.add_argument("--serve-p", type=int, default=8, help="serve mode: expansion order (target 1e-5)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         bench_reference(args, rank, world)
+    elif args.workload == "batch":
+        bench_batch(args, rank, world, local)
+    elif args.workload == "serve":
+        bench_serve(args, rank, world, local)
     else:
         bench_ours(args, rank, world, local)
 
