@@ -30,7 +30,9 @@
  *    gets the floor(n/2) smallest keys; both children keep ascending
  *    original-index order;
  *  - split plane s = 0.5*(max_left + min_right); one point: s = its
- *    coordinate; no point: s = cell midpoint;
+ *    coordinate; no point: s = cell midpoint; for eta < 1 the plane is
+ *    eta*s + (1-eta)*midpoint and the left child takes the points strictly
+ *    below it (Sec. 2.1.2's adaptivity parameter);
  *  - root cell = tight bounding box; box centre = cell midpoint; radius =
  *    half the cell diagonal;
  *  - weak iff theta > 0, d > 0 and R + theta*r <= theta*d;
@@ -315,6 +317,7 @@ typedef struct {
     int64_t n;
     int levels, p;
     double theta;
+    double eta;         /* adaptivity parameter of Sec. 2.1.2, [0, 1] */
     double *x;          /* n x 3 canonical positions (-0.0 -> +0.0), input order */
     int64_t *perm;      /* slot -> original index, leaf order */
     int64_t *begin;     /* per box (heap order), first slot; nbox + 1 entries by level */
@@ -395,6 +398,18 @@ static void orc_build_tree(orc_fmm *F)
                 s = keys[0].key;
             else
                 s = 0.5 * (F->lo[3 * g + ax] + F->hi[3 * g + ax]);
+            if (F->eta < 1.0) {
+                /* eta in [0, 1): the plane is the weighted average of the median
+                 * plane and the geometric midpoint (Sec. 2.1.2); the left child
+                 * takes the points strictly below it */
+                double mid = 0.5 * (F->lo[3 * g + ax] + F->hi[3 * g + ax]);
+                s = F->eta * s + (1.0 - F->eta) * mid;
+                k = 0;
+                for (int64_t t = 0; t < nn; t++) {
+                    left[lists[b + t]] = F->x[3 * lists[b + t] + ax] < s;
+                    k += left[lists[b + t]];
+                }
+            }
             F->plane[g] = s;
             /* stable partition of the ascending-index list */
             int64_t nl = 0, nr = 0;
@@ -545,10 +560,11 @@ static void orc_build_lists(orc_fmm *F)
 /* Public handle                                                        */
 /* ------------------------------------------------------------------ */
 
-orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta)
+orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, double eta)
 {
     orc_fmm *F = calloc(1, sizeof(orc_fmm));
     int64_t nb = nbox_of(levels);
+    F->eta = eta;
     F->n = n;
     F->levels = levels;
     F->p = p;

@@ -8,9 +8,11 @@ import oracle
 from paper_2002_04894_gb300 import inputs
 
 
-def naive_tree(x, levels):
+def naive_tree(x, levels, eta=1.0):
     """Second, independent implementation of the same reading: full sort of
-    each box on its longest cell axis, floor(n/2) smallest keys to the left."""
+    each box on its longest cell axis, floor(n/2) smallest keys to the left;
+    for eta < 1 the plane moves to eta*median + (1-eta)*midpoint and the left
+    child takes the points strictly below it."""
     x = np.asarray(x, float) + 0.0
     nb = (2 << levels) - 1
     lo = np.zeros((nb, 3)); hi = np.zeros((nb, 3)); plane = np.zeros(nb)
@@ -32,6 +34,9 @@ def naive_tree(x, levels):
                 s = x[order[0], ax]
             else:
                 s = 0.5 * (lo[g, ax] + hi[g, ax])
+            if eta < 1.0:
+                s = eta * s + (1.0 - eta) * (0.5 * (lo[g, ax] + hi[g, ax]))
+                left = {i for i in idx if x[i, ax] < s}
             plane[g] = s
             a, b = 2 * g + 1, 2 * g + 2
             members[a] = np.array([i for i in idx if i in left], int)
@@ -190,3 +195,44 @@ def test_single_box_bisection_matches_tree(kind, n):
         a = 2 * g + 1
         want = set(t["perm"][t["begin"][a]:t["begin"][a] + t["count"][a]])
         assert set(pts[left]) == want
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.25, 0.5, 0.75])
+@pytest.mark.parametrize("kind,n,levels", [("plummer", 900, 6), ("gmm", 700, 7), ("uniform", 50, 5)])
+def test_eta_tree_matches_independent_implementation(kind, n, levels, eta):
+    x = inputs.points(kind, n, seed=n + 1)
+    t = oracle.Tree(x, levels, 2, 0.5, eta=eta).tree()
+    perm, lo, hi, plane = naive_tree(x, levels, eta)
+    np.testing.assert_array_equal(t["perm"], perm)
+    np.testing.assert_array_equal(t["lo"], lo)
+    np.testing.assert_array_equal(t["hi"], hi)
+
+
+def test_eta_zero_is_the_fixed_geometric_tree():
+    """eta = 0: every split at the cell midpoint, so at level l each cell is
+    the root cell halved along its longest axes -- sizes independent of the
+    points (Sec. 2.1.2)."""
+    x = inputs.points("plummer", 2000, 5)
+    t = oracle.Tree(x, 6, 2, 0.5, eta=0.0).tree()
+    for g in range(63):
+        ax = t["axis"][g]
+        assert t["plane"][g] == 0.5 * (t["lo"][g, ax] + t["hi"][g, ax])
+    ext = t["hi"][63:] - t["lo"][63:]
+    assert np.allclose(ext, ext[0])                 # all leaves the same shape
+
+
+def test_eta_one_keeps_median_balance():
+    x = inputs.points("gmm", 3000, 2)
+    a = oracle.Tree(x, 6, 2, 0.5, eta=1.0).tree()
+    b = oracle.Tree(x, 6, 2, 0.5).tree()
+    np.testing.assert_array_equal(a["perm"], b["perm"])
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.5])
+def test_eta_fmm_accuracy(eta):
+    """The expansions do not depend on how boxes were split: accuracy holds."""
+    x = inputs.points("plummer", 4000, 9)
+    q = inputs.charges_uniform(4000, 9)
+    phi = oracle.Tree(x, 6, 10, 0.5, eta=eta).eval(q, field=False)
+    p0 = oracle.direct(x, q, field=False)
+    assert np.linalg.norm(phi - p0) / np.linalg.norm(p0) < 1e-5
