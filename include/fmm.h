@@ -4,7 +4,7 @@
  * The method is the balanced-tree adaptive FMM of Bull & Engblom,
  * "Distributed and Adaptive Fast Multipole Method in Three Dimensions"
  * (arXiv:2002.04894): a tree of a fixed number of levels whose boxes are split
- * at median planes (Sec. 2.1.2, eta = 1), theta-criterion connectivity
+ * at median planes (Sec. 2.1.2, eta = 1; eta < 1 by option), theta-criterion connectivity
  * (Eq. 2.2), multipole/local expansions of order p (Sec. 2.1), and the stage
  * order of Algorithm 1 (Tree; P2M; M2M; M2L and L2L, Algorithm 3; L2P and P2P,
  * Algorithm 4). It evaluates, for N points x_i with real charges q_i,
@@ -15,7 +15,8 @@
  * with no physical constant. Pairs at zero distance contribute nothing.
  *
  * Conventions shared by every entry point:
- *  - A "level" is one binary median bisection: `levels` = B gives 2^B leaves
+ *  - A "level" is one binary bisection (median by default, see fmm_opts.eta):
+ *    `levels` = B gives 2^B leaves
  *    and boxes numbered in heap order, box g = 2^l - 1 + j for box j of
  *    level l (children of g are 2g+1 and 2g+2).
  *  - Pointers to point, charge and output arrays may be device pointers or
@@ -71,6 +72,7 @@ enum fmm_prec { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
 
 /* fmm_opts.flags bits */
 #define FMM_FLAG_PROFILE 1  /* record per-stage device times (fmm_stage_times) */
+#define FMM_FLAG_ETA 2      /* use fmm_opts.eta; without it eta = 1 (median splits) */
 
 /* Stages of Algorithm 1 as timed by fmm_stage_times. */
 enum fmm_stage {
@@ -92,6 +94,14 @@ typedef struct fmm_opts {
                        theta = 0 gives no weak pairs (the FMM reduces to Eq. 2.1) */
     int prec;       /* enum fmm_prec */
     int flags;      /* FMM_FLAG_* bits; other bits must be 0 */
+    double eta;     /* adaptivity of the splits (Sec. 2.1.2), 0 <= eta <= 1, read
+                       only with FMM_FLAG_ETA. A box's cut plane is
+                       eta * (median plane) + (1 - eta) * (cell midpoint) and the
+                       lower child takes the points strictly below it: eta = 1 is
+                       the balanced median split (equal halves), eta = 0 the
+                       geometric bisection (children may be empty). For eta < 1
+                       the build reads the largest child size back to the host
+                       once per level. */
 } fmm_opts;
 
 /*

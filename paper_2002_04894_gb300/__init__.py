@@ -22,6 +22,7 @@ FMM_F64, FMM_F32 = 0, 1
 FMM_PREC_FP64, FMM_PREC_MIXED = 0, 1
 FMM_MAX_LEVELS, FMM_MAX_P = 24, 20
 FMM_FLAG_PROFILE = 1
+FMM_FLAG_ETA = 2
 STAGES = ("tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p")
 STATUS = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ENONFINITE",
           -4: "FMM_ECAPACITY", -5: "FMM_ETIMEDOUT", -6: "FMM_ECUDA"}
@@ -36,7 +37,7 @@ class FmmError(RuntimeError):
 
 class fmm_opts(C.Structure):
     _fields_ = [("levels", C.c_int), ("p", C.c_int), ("theta", C.c_double),
-                ("prec", C.c_int), ("flags", C.c_int)]
+                ("prec", C.c_int), ("flags", C.c_int), ("eta", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -205,13 +206,15 @@ class Plan:
 # the C ABI, one function each
 # ---------------------------------------------------------------------------
 def fmm_plan(points, levels: int, p: int, theta: float, prec: int = FMM_PREC_FP64,
-             stream=None, allocator="torch", profile: bool = False) -> Plan:
-    """Build the balanced tree and connectivity for n x 3 `points`."""
+             stream=None, allocator="torch", profile: bool = False, eta: float = 1.0) -> Plan:
+    """Build the tree and connectivity for n x 3 `points`; eta in [0, 1] is
+    the split adaptivity (1: balanced median splits, 0: cell bisection)."""
     lib = load()
     ptr, keep = _ptr(points)
     n = int(points.shape[0])
     dt = _dtype_code(points)
-    opts = fmm_opts(int(levels), int(p), float(theta), int(prec), FMM_FLAG_PROFILE if profile else 0)
+    flags = (FMM_FLAG_PROFILE if profile else 0) | (FMM_FLAG_ETA if float(eta) != 1.0 else 0)
+    opts = fmm_opts(int(levels), int(p), float(theta), int(prec), flags, float(eta))
     alloc, cbs = (None, None)
     if allocator == "torch":
         alloc, cbs = _torch_allocator()
@@ -347,7 +350,7 @@ def fmm_orb_order_noalloc(points, levels: int, perm=None, stream=None):
         perm = torch.empty(n, dtype=torch.int32, device=points.device)
     _check(load().fmm_orb_order_noalloc(points.data_ptr(), n, _dtype_code(points), int(levels),
                                         perm.data_ptr(), _stream(stream)),
-           "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy")
+           "fmm_orb_order_noalloc")
     return perm
 
 

@@ -174,7 +174,10 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
               double *__restrict__ xout, double *__restrict__ yout, double *__restrict__ zout,
               int32_t *__restrict__ iout, const int32_t *__restrict__ begin,
               const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
-              uint64_t *sel_v, unsigned long long *sel_minr, int *err) {
+              uint64_t *sel_v, unsigned long long *sel_minr, int *err,
+              const unsigned long long *__restrict__ thr, int32_t *__restrict__ ksplit) {
+    // thr == nullptr: median split (left = floor(n/2) smallest keys);
+    // otherwise threshold split (left = keys below thr[s], count to ksplit[s])
     __shared__ uint64_t keys[kSmallCap];
     __shared__ unsigned hist[256];
     __shared__ unsigned flags[kSmallCap / 32];
@@ -185,7 +188,8 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
 
     const int s = blockIdx.x;
     const int64_t g = ((int64_t)1 << level) - 1 + s;
-    const int b = begin[g], n = count[g], ax = axis[g], k = n / 2;
+    const int b = begin[g], n = count[g], ax = axis[g];
+    int k = n / 2;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const double *src = ax == 0 ? xin : (ax == 1 ? yin : zin);
 
@@ -195,8 +199,14 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
             yout[b] = yin[b];
             zout[b] = zin[b];
             iout[b] = iin[b];
-            sel_minr[s] = dkey(src[b]);
+            if (thr) {
+                ksplit[s] = dkey(src[b]) < thr[s] ? 1 : 0;
+            } else {
+                sel_v[s] = dkey(src[b]);
+                sel_minr[s] = dkey(src[b]);
+            }
         }
+        if (n == 0 && thr && tid == 0) ksplit[s] = 0;
         return;
     }
     for (int i = tid; i < n; i += kThreads) keys[i] = dkey(src[b + i]);
@@ -207,7 +217,7 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
     }
     __syncthreads();
 
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = 0; pass < 8 && !thr; pass++) {
         const int shift = 56 - 8 * pass;
         hist[tid] = 0;  // kThreads == 256 bins
         __syncthreads();
@@ -220,8 +230,8 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
         if (w == 0) pick_digit(hist, shift, &s_prefix, &s_rrem);
         __syncthreads();
     }
-    const uint64_t v = s_prefix;
-    const unsigned need_eq = s_rrem + 1;  // equal keys that go left, in position order
+    const uint64_t v = thr ? (uint64_t)thr[s] : s_prefix;
+    const unsigned need_eq = thr ? 0u : s_rrem + 1;  // equal keys that go left, in position order
 
     // warp w owns positions [start, end)
     const int per_warp = ((n + kWarps - 1) / kWarps + 31) & ~31;
@@ -266,6 +276,11 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
     __syncthreads();
     unsigned lrun = 0;
     for (int j = 0; j < w; j++) lrun += w_left[j];
+    if (thr) {
+        k = 0;
+        for (int j = 0; j < kWarps; j++) k += w_left[j];
+        if (tid == 0) ksplit[s] = k;
+    }
     for (int base = start; base < end; base += 32) {
         const int i = base + lane;
         const unsigned fm = flags[base >> 5];
@@ -284,7 +299,7 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
         }
         lrun += __popc(fm);
     }
-    if (tid == 0) {
+    if (tid == 0 && !thr) {
         sel_v[s] = v;
         sel_minr[s] = eqtot > need_eq ? (unsigned long long)v : s_minr;
     }
@@ -312,7 +327,7 @@ k_sel_hist(int level, int pass, const double *__restrict__ xs, const double *__r
            const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
            const uint64_t *__restrict__ prefix, unsigned *ghist) {
     __shared__ unsigned h[256];
-    const int s = blockIdx.y, c = blockIdx.x;
+    const int s = blockIdx.x, c = blockIdx.y;
     const int64_t g = ((int64_t)1 << level) - 1 + s;
     const int b = begin[g], n = count[g], ax = axis[g];
     const int start = c * kChunk;
@@ -357,10 +372,10 @@ k_sel_count(int level, int nch, const double *__restrict__ xs, const double *__r
             const double *__restrict__ zs, const int32_t *__restrict__ begin,
             const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
             const uint64_t *__restrict__ prefix, unsigned *chunk_lt, unsigned *chunk_eq,
-            unsigned long long *minr) {
+            unsigned long long *minr, const unsigned long long *__restrict__ thr) {
     __shared__ unsigned s_lt[kWarps], s_eq[kWarps];
     __shared__ unsigned long long s_mr;
-    const int s = blockIdx.y, c = blockIdx.x;
+    const int s = blockIdx.x, c = blockIdx.y;
     const int64_t g = ((int64_t)1 << level) - 1 + s;
     const int b = begin[g], n = count[g], ax = axis[g];
     const int start = c * kChunk;
@@ -368,7 +383,7 @@ k_sel_count(int level, int nch, const double *__restrict__ xs, const double *__r
     if (threadIdx.x == 0) s_mr = ~0ull;
     __syncthreads();
     const double *src = ax == 0 ? xs : (ax == 1 ? ys : zs);
-    const uint64_t v = prefix[s];
+    const uint64_t v = thr ? (uint64_t)thr[s] : prefix[s];
     unsigned lt = 0, eq = 0;
     uint64_t mr = ~0ull;
     const int end = min(n, start + kChunk);
@@ -403,10 +418,11 @@ k_sel_count(int level, int nch, const double *__restrict__ xs, const double *__r
 __global__ void k_sel_offsets(int level, int nch, const int32_t *count, const unsigned *chunk_lt,
                               const unsigned *chunk_eq, const uint64_t *prefix,
                               const unsigned *rrem, unsigned *eq_off, unsigned *left_off,
-                              unsigned long long *minr, uint64_t *sel_v) {
+                              unsigned long long *minr, uint64_t *sel_v,
+                              const unsigned long long *thr, int32_t *ksplit) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= (1 << level)) return;
-    const unsigned need_eq = rrem[s] + 1;
+    const unsigned need_eq = thr ? 0u : rrem[s] + 1;
     unsigned eo = 0, lo = 0;
     for (int c = 0; c < nch; c++) {
         const int64_t i = (int64_t)s * nch + c;
@@ -416,6 +432,10 @@ __global__ void k_sel_offsets(int level, int nch, const int32_t *count, const un
         const unsigned take = need_eq > eo ? min(need_eq - eo, e) : 0u;
         lo += l + take;
         eo += e;
+    }
+    if (thr) {
+        ksplit[s] = (int32_t)lo;
+        return;
     }
     sel_v[s] = prefix[s];
     if (eo > need_eq) minr[s] = prefix[s];
@@ -428,19 +448,21 @@ k_sel_scatter(int level, int nch, const double *__restrict__ xin, const double *
               int32_t *__restrict__ iout, const int32_t *__restrict__ begin,
               const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
               const uint64_t *__restrict__ prefix, const unsigned *__restrict__ rrem,
-              const unsigned *__restrict__ eq_off, const unsigned *__restrict__ left_off, int *err) {
+              const unsigned *__restrict__ eq_off, const unsigned *__restrict__ left_off, int *err,
+              const unsigned long long *__restrict__ thr, const int32_t *__restrict__ ksplit) {
     __shared__ unsigned flags[kChunk / 32];
     __shared__ unsigned w_eq[kWarps], w_left[kWarps];
-    const int s = blockIdx.y, c = blockIdx.x;
+    const int s = blockIdx.x, c = blockIdx.y;
     const int64_t g = ((int64_t)1 << level) - 1 + s;
-    const int b = begin[g], n = count[g], ax = axis[g], k = n / 2;
+    const int b = begin[g], n = count[g], ax = axis[g];
+    const int k = thr ? ksplit[s] : n / 2;
     const int cstart = c * kChunk;
     if (cstart >= n) return;
     const int cend = min(n, cstart + kChunk);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const double *src = ax == 0 ? xin : (ax == 1 ? yin : zin);
-    const uint64_t v = prefix[s];
-    const unsigned need_eq = rrem[s] + 1;
+    const uint64_t v = thr ? (uint64_t)thr[s] : prefix[s];
+    const unsigned need_eq = thr ? 0u : rrem[s] + 1;
     constexpr int per_warp = kChunk / kWarps;
     const int start = cstart + w * per_warp;
     const int end = min(cend, start + per_warp);
@@ -525,6 +547,58 @@ __global__ void k_children(int level, const int32_t *count, const uint64_t *sel_
     box_geometry(lo, hi, centre, radius, axis, c);
 }
 
+// eta in [0,1): the plane s = eta * median plane + (1 - eta) * cell midpoint
+// (Sec. 2.1.2); the left child takes the points strictly below it.
+__global__ void k_eta_plane(int level, double eta, const int32_t *count, const int32_t *axis,
+                            const double *lo, const double *hi, const uint64_t *sel_v,
+                            const unsigned long long *sel_minr, unsigned long long *thr,
+                            double *splane) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (1 << level)) return;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    const int n = count[g], ax = axis[g];
+    const double mid = __dmul_rn(0.5, __dadd_rn(lo[3 * g + ax], hi[3 * g + ax]));
+    double sm = mid;
+    if (eta > 0.0) {
+        if (n >= 2)
+            sm = __dmul_rn(0.5, __dadd_rn(dkey_inv(sel_v[s]), dkey_inv(sel_minr[s])));
+        else if (n == 1)
+            sm = dkey_inv(sel_v[s]);
+    }
+    const double sp = __dadd_rn(__dmul_rn(eta, sm), __dmul_rn(__dsub_rn(1.0, eta), mid));
+    splane[s] = sp;
+    thr[s] = dkey(sp);
+}
+
+// children of level `level` for the threshold split: cells cut at the plane,
+// point ranges from the left counts; the largest child count for the host
+__global__ void k_children_eta(int level, int32_t *begin, int32_t *count, const int32_t *ksplit,
+                               const double *splane, double *lo, double *hi, double *centre,
+                               double *radius, int32_t *axis, double *plane, int *maxcount) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (1 << level)) return;
+    const int64_t g = ((int64_t)1 << level) - 1 + s;
+    const int n = count[g], ax = axis[g], k = ksplit[s], b = begin[g];
+    const double sp = splane[s];
+    plane[g] = sp;
+    const int64_t a = 2 * g + 1, c = 2 * g + 2;
+    begin[a] = b;
+    count[a] = k;
+    begin[c] = b + k;
+    count[c] = n - k;
+    for (int d = 0; d < 3; d++) {
+        lo[3 * a + d] = lo[3 * g + d];
+        hi[3 * a + d] = hi[3 * g + d];
+        lo[3 * c + d] = lo[3 * g + d];
+        hi[3 * c + d] = hi[3 * g + d];
+    }
+    hi[3 * a + ax] = sp;
+    lo[3 * c + ax] = sp;
+    box_geometry(lo, hi, centre, radius, axis, a);
+    box_geometry(lo, hi, centre, radius, axis, c);
+    atomicMax(maxcount, max(k, n - k));
+}
+
 }  // namespace
 
 // Builds the tree: points (device, n x 3, dtype) -> leaf-order SoA positions,
@@ -563,12 +637,38 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
     unsigned *ghist = nullptr, *chunk_lt = nullptr, *chunk_eq = nullptr, *eq_off = nullptr,
              *left_off = nullptr;
     size_t chunk_alloc = 0, ghist_alloc = 0;
+    // eta < 1: data-dependent child sizes; the plane, the left counts and the
+    // largest child count (read back per level to pick the regime) live here
+    const bool eta_mode = P.eta < 1.0;
+    const bool need_median = !eta_mode || P.eta > 0.0;
+    unsigned long long *thr = nullptr;
+    double *splane = nullptr;
+    int32_t *ksplit = nullptr;
+    int *dmax = nullptr;
+    if (eta_mode) {
+        thr = (unsigned long long *)dalloc(P, (size_t)maxseg * 8);
+        splane = (double *)dalloc(P, (size_t)maxseg * 8);
+        ksplit = (int32_t *)dalloc(P, (size_t)maxseg * 4);
+        dmax = (int *)dalloc(P, 16);
+        if (!thr || !splane || !ksplit || !dmax) return cudaErrorMemoryAllocation;
+    }
+    int64_t maxn = n;
     for (int l = 0; l < P.B; l++) {
         const int S = 1 << l;
-        const int64_t maxn = (n + S - 1) / S;
+        const unsigned sg = (unsigned)((S + 127) / 128);
+        if (!eta_mode) maxn = (n + S - 1) / S;
         if (maxn <= kSmallCap) {
-            FMM_LAUNCH(k_split_small, S, kThreads, 0, st, l, xa, ya, za, ia, xb, yb, zb, ib, P.begin,
-                                                  P.count, P.axis, sel_v, sel_minr, P.d_err);
+            if (need_median)
+                FMM_LAUNCH(k_split_small, S, kThreads, 0, st, l, xa, ya, za, ia, xb, yb, zb, ib, P.begin,
+                                                      P.count, P.axis, sel_v, sel_minr, P.d_err,
+                                                      (const unsigned long long *)nullptr, (int32_t *)nullptr);
+            if (eta_mode) {
+                FMM_LAUNCH(k_eta_plane, sg, 128, 0, st, l, P.eta, P.count, P.axis, P.lo, P.hi, sel_v,
+                                                       sel_minr, thr, splane);
+                FMM_LAUNCH(k_split_small, S, kThreads, 0, st, l, xa, ya, za, ia, xb, yb, zb, ib, P.begin,
+                                                      P.count, P.axis, sel_v, sel_minr, P.d_err,
+                                                      (const unsigned long long *)thr, ksplit);
+            }
         } else {
             const int nch = (int)((maxn + kChunk - 1) / kChunk);
             const size_t need_c = (size_t)S * nch * 4, need_h = (size_t)S * 256 * 4;
@@ -592,24 +692,54 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
                 ghist = (unsigned *)dalloc(P, need_h);
                 if (!ghist) return cudaErrorMemoryAllocation;
             }
-            FMM_LAUNCH(k_sel_init, S, 256, 0, st, l, P.count, sel_prefix, sel_rrem, sel_minr, ghist);
-            const dim3 grid(nch, S);
-            for (int pass = 0; pass < 8; pass++) {
-                FMM_LAUNCH(k_sel_hist, grid, kThreads, 0, st, l, pass, xa, ya, za, P.begin, P.count, P.axis,
-                                                      sel_prefix, ghist);
-                FMM_LAUNCH(k_sel_pick, S, 32, 0, st, pass, ghist, sel_prefix, sel_rrem);
+            const dim3 grid(S, nch);  // boxes on x (up to 2^31 - 1), chunks on y
+            if (need_median) {
+                FMM_LAUNCH(k_sel_init, S, 256, 0, st, l, P.count, sel_prefix, sel_rrem, sel_minr, ghist);
+                for (int pass = 0; pass < 8; pass++) {
+                    FMM_LAUNCH(k_sel_hist, grid, kThreads, 0, st, l, pass, xa, ya, za, P.begin, P.count,
+                                                          P.axis, sel_prefix, ghist);
+                    FMM_LAUNCH(k_sel_pick, S, 32, 0, st, pass, ghist, sel_prefix, sel_rrem);
+                }
+                FMM_LAUNCH(k_sel_count, grid, kThreads, 0, st, l, nch, xa, ya, za, P.begin, P.count, P.axis,
+                                                       sel_prefix, chunk_lt, chunk_eq, sel_minr,
+                                                       (const unsigned long long *)nullptr);
+                FMM_LAUNCH(k_sel_offsets, sg, 128, 0, st, l, nch, P.count, chunk_lt, chunk_eq, sel_prefix,
+                                                       sel_rrem, eq_off, left_off, sel_minr, sel_v,
+                                                       (const unsigned long long *)nullptr, (int32_t *)nullptr);
             }
-            FMM_LAUNCH(k_sel_count, grid, kThreads, 0, st, l, nch, xa, ya, za, P.begin, P.count, P.axis,
-                                                   sel_prefix, chunk_lt, chunk_eq, sel_minr);
-            FMM_LAUNCH(k_sel_offsets, (S + 127) / 128, 128, 0, st, l, nch, P.count, chunk_lt, chunk_eq,
-                                                           sel_prefix, sel_rrem, eq_off, left_off,
-                                                           sel_minr, sel_v);
-            FMM_LAUNCH(k_sel_scatter, grid, kThreads, 0, st, l, nch, xa, ya, za, ia, xb, yb, zb, ib, P.begin,
-                                                     P.count, P.axis, sel_prefix, sel_rrem, eq_off,
-                                                     left_off, P.d_err);
+            if (!eta_mode) {
+                FMM_LAUNCH(k_sel_scatter, grid, kThreads, 0, st, l, nch, xa, ya, za, ia, xb, yb, zb, ib,
+                                                         P.begin, P.count, P.axis, sel_prefix, sel_rrem, eq_off,
+                                                         left_off, P.d_err, (const unsigned long long *)nullptr,
+                                                         (const int32_t *)nullptr);
+            } else {
+                FMM_LAUNCH(k_eta_plane, sg, 128, 0, st, l, P.eta, P.count, P.axis, P.lo, P.hi, sel_v,
+                                                       sel_minr, thr, splane);
+                FMM_LAUNCH(k_sel_count, grid, kThreads, 0, st, l, nch, xa, ya, za, P.begin, P.count, P.axis,
+                                                       sel_prefix, chunk_lt, chunk_eq, sel_minr,
+                                                       (const unsigned long long *)thr);
+                FMM_LAUNCH(k_sel_offsets, sg, 128, 0, st, l, nch, P.count, chunk_lt, chunk_eq, sel_prefix,
+                                                       sel_rrem, eq_off, left_off, sel_minr, sel_v,
+                                                       (const unsigned long long *)thr, ksplit);
+                FMM_LAUNCH(k_sel_scatter, grid, kThreads, 0, st, l, nch, xa, ya, za, ia, xb, yb, zb, ib,
+                                                         P.begin, P.count, P.axis, sel_prefix, sel_rrem, eq_off,
+                                                         left_off, P.d_err, (const unsigned long long *)thr,
+                                                         (const int32_t *)ksplit);
+            }
         }
-        FMM_LAUNCH(k_children, (S + 127) / 128, 128, 0, st, l, P.count, sel_v, sel_minr,
-                                                    P.lo, P.hi, P.centre, P.radius, P.axis, P.plane);
+        if (!eta_mode) {
+            FMM_LAUNCH(k_children, sg, 128, 0, st, l, P.count, sel_v, sel_minr, P.lo, P.hi, P.centre,
+                                                        P.radius, P.axis, P.plane);
+        } else {
+            cudaMemsetAsync(dmax, 0, 4, st);
+            FMM_LAUNCH(k_children_eta, sg, 128, 0, st, l, P.begin, P.count, ksplit, splane, P.lo, P.hi,
+                                                            P.centre, P.radius, P.axis, P.plane, dmax);
+            int hmax = 0;
+            cudaMemcpyAsync(&hmax, dmax, 4, cudaMemcpyDeviceToHost, st);
+            const cudaError_t es = cudaStreamSynchronize(st);
+            if (es != cudaSuccess) return es;
+            maxn = hmax;
+        }
         std::swap(xa, xb);
         std::swap(ya, yb);
         std::swap(za, zb);
@@ -639,6 +769,12 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
     dfree(P, sel_minr, (size_t)maxseg * 8);
     dfree(P, sel_rrem, (size_t)maxseg * 4);
     dfree(P, bbox, 64);
+    if (eta_mode) {
+        dfree(P, thr, (size_t)maxseg * 8);
+        dfree(P, splane, (size_t)maxseg * 8);
+        dfree(P, ksplit, (size_t)maxseg * 4);
+        dfree(P, dmax, 16);
+    }
     return e;
 }
 
@@ -769,7 +905,7 @@ extern "C" int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, i
     for (int l = 0; l < levels; l++) {
         const int S = 1 << l;
         FMM_LAUNCH(k_split_small, S, kThreads, 0, st, l, xa, ya, za, ia, xb, yb, zb, ib, begin, count,
-                   axis, sel_v, sel_minr, err);
+                   axis, sel_v, sel_minr, err, (const unsigned long long *)nullptr, (int32_t *)nullptr);
         FMM_LAUNCH(k_children, (S + 127) / 128, 128, 0, st, l, count, sel_v, sel_minr, lo, hi, centre,
                    radius, axis, plane);
         std::swap(xa, xb);
