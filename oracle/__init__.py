@@ -68,7 +68,7 @@ def _lib():
     lib.orc_direct.argtypes = [C.c_int64, _f64p, _f64p, C.c_int64, _i64p, _f64p, C.c_void_p]
     lib.orc_theta_weak.argtypes = [C.c_double, _f64p, C.c_double, _f64p, C.c_double]
     lib.orc_theta_weak.restype = C.c_int
-    lib.orc_build.argtypes = [C.c_int64, _f64p, C.c_int, C.c_int, C.c_double, C.c_double]
+    lib.orc_build.argtypes = [C.c_int64, _f64p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int]
     lib.orc_build.restype = C.c_void_p
     lib.orc_free.argtypes = [C.c_void_p]
     lib.orc_nbox.argtypes = [C.c_void_p]
@@ -179,10 +179,14 @@ def bisect_box(x, lo, hi):
 class Tree:
     """Balanced tree, connectivity and expansions of one point set."""
 
-    def __init__(self, x, levels: int, p: int, theta: float, eta: float = 1.0):
+    def __init__(self, x, levels: int, p: int, theta: float, eta: float = 1.0, step: int = 1):
+        """`levels` bisections; `step` bisections per FMM level (3: octree
+        levels of 8 children), `levels` a multiple of it."""
         x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
-        self.n, self.levels, self.p, self.theta, self.eta = len(x), levels, p, theta, eta
-        self._h = _lib().orc_build(self.n, x, levels, p, theta, eta)
+        if step < 1 or levels % step:
+            raise ValueError("levels must be a multiple of step >= 1")
+        self.n, self.levels, self.p, self.theta, self.eta, self.step = len(x), levels, p, theta, eta, step
+        self._h = _lib().orc_build(self.n, x, levels, p, theta, eta, step)
         if not self._h:
             raise MemoryError("oracle build failed")
 

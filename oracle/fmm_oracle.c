@@ -37,6 +37,9 @@
  *    half the cell diagonal;
  *  - weak iff theta > 0, d > 0 and R + theta*r <= theta*d;
  *  - M2L at every level that has weak pairs (leaf level included);
+ *  - the paper's octree levels (8 children per box) are `step` = 3
+ *    successive bisections per FMM level; connectivity, M2M, M2L and L2L
+ *    then act only on every step-th bisection level (step 1: every level);
  *  - coincident points (r^2 == 0) are skipped in every pairwise sum.
  */
 #include <complex.h>
@@ -318,6 +321,7 @@ typedef struct {
     int levels, p;
     double theta;
     double eta;         /* adaptivity parameter of Sec. 2.1.2, [0, 1] */
+    int step;           /* bisections per FMM level (1 binary, 3 octree) */
     double *x;          /* n x 3 canonical positions (-0.0 -> +0.0), input order */
     int64_t *perm;      /* slot -> original index, leaf order */
     int64_t *begin;     /* per box (heap order), first slot; nbox + 1 entries by level */
@@ -500,7 +504,8 @@ int orc_theta_weak(double theta, const double ca[3], double ra, const double cb[
  */
 static void orc_build_lists(orc_fmm *F)
 {
-    int B = F->levels;
+    int B = F->levels, st = F->step;
+    int64_t C = (int64_t)1 << st; /* children per box per FMM level */
     F->wptr = calloc(B + 1, sizeof(int64_t *));
     F->sptr = calloc(B + 1, sizeof(int64_t *));
     F->wsrc = calloc(B + 1, sizeof(int32_t *));
@@ -514,13 +519,22 @@ static void orc_build_lists(orc_fmm *F)
     for (int l = 1; l <= B; l++) {
         int64_t nt = (int64_t)1 << l;
         int64_t *pw = calloc(nt + 1, sizeof(int64_t)), *ps = calloc(nt + 1, sizeof(int64_t));
+        if (l % st != 0) {
+            /* a bisection level inside an FMM level: no connectivity */
+            F->wptr[l] = pw;
+            F->sptr[l] = ps;
+            F->wsrc[l] = malloc(sizeof(int32_t));
+            F->ssrc[l] = malloc(sizeof(int32_t));
+            continue;
+        }
+        int lp = l - st; /* parent FMM level */
         /* count */
         for (int64_t t = 0; t < nt; t++) {
-            int64_t T = t / 2, gt = gid(l, t);
-            for (int64_t e = F->sptr[l - 1][T]; e < F->sptr[l - 1][T + 1]; e++) {
-                int64_t S = F->ssrc[l - 1][e];
-                for (int c = 0; c < 2; c++) {
-                    int64_t gs = gid(l, 2 * S + c);
+            int64_t T = t / C, gt = gid(l, t);
+            for (int64_t e = F->sptr[lp][T]; e < F->sptr[lp][T + 1]; e++) {
+                int64_t S = F->ssrc[lp][e];
+                for (int64_t c = 0; c < C; c++) {
+                    int64_t gs = gid(l, C * S + c);
                     if (orc_theta_weak(F->theta, F->centre + 3 * gt, F->radius[gt],
                                        F->centre + 3 * gs, F->radius[gs]))
                         pw[t + 1]++;
@@ -536,11 +550,11 @@ static void orc_build_lists(orc_fmm *F)
         int32_t *sw = malloc(sizeof(int32_t) * (pw[nt] + 1));
         int32_t *ss = malloc(sizeof(int32_t) * (ps[nt] + 1));
         for (int64_t t = 0; t < nt; t++) {
-            int64_t T = t / 2, gt = gid(l, t), iw = pw[t], is = ps[t];
-            for (int64_t e = F->sptr[l - 1][T]; e < F->sptr[l - 1][T + 1]; e++) {
-                int64_t S = F->ssrc[l - 1][e];
-                for (int c = 0; c < 2; c++) {
-                    int64_t s = 2 * S + c, gs = gid(l, s);
+            int64_t T = t / C, gt = gid(l, t), iw = pw[t], is = ps[t];
+            for (int64_t e = F->sptr[lp][T]; e < F->sptr[lp][T + 1]; e++) {
+                int64_t S = F->ssrc[lp][e];
+                for (int64_t c = 0; c < C; c++) {
+                    int64_t s = C * S + c, gs = gid(l, s);
                     if (orc_theta_weak(F->theta, F->centre + 3 * gt, F->radius[gt],
                                        F->centre + 3 * gs, F->radius[gs]))
                         sw[iw++] = (int32_t)s;
@@ -560,11 +574,15 @@ static void orc_build_lists(orc_fmm *F)
 /* Public handle                                                        */
 /* ------------------------------------------------------------------ */
 
-orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, double eta)
+orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, double eta,
+                   int step)
 {
+    if (step < 1 || levels % step != 0)
+        return NULL;
     orc_fmm *F = calloc(1, sizeof(orc_fmm));
     int64_t nb = nbox_of(levels);
     F->eta = eta;
+    F->step = step;
     F->n = n;
     F->levels = levels;
     F->p = p;
@@ -666,13 +684,15 @@ void orc_eval(orc_fmm *F, const double *q, double *phi, double *E)
         orc_p2m(F->count[g], xl + 3 * F->begin[g], ql + F->begin[g],
                 F->centre + 3 * g, p, F->M + g * nc);
     }
-    /* M2M, leaves to root */
-    for (int l = B; l >= 1; l--)
+    /* M2M, leaves to root, over FMM levels (each box from its C children) */
+    int st = F->step;
+    int64_t C = (int64_t)1 << st;
+    for (int l = B; l >= st; l -= st)
 #pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t j = 0; j < ((int64_t)1 << (l - 1)); j++) {
-            int64_t gp = gid(l - 1, j);
-            for (int c = 0; c < 2; c++) {
-                int64_t gc = gid(l, 2 * j + c);
+        for (int64_t j = 0; j < ((int64_t)1 << (l - st)); j++) {
+            int64_t gp = gid(l - st, j);
+            for (int64_t c = 0; c < C; c++) {
+                int64_t gc = gid(l, C * j + c);
                 orc_m2m(F->M + gc * nc, F->centre + 3 * gc, F->centre + 3 * gp, p,
                         F->M + gp * nc);
             }
@@ -688,11 +708,11 @@ void orc_eval(orc_fmm *F, const double *q, double *phi, double *E)
                         F->L + gt * nc);
             }
         }
-    /* L2L, root to leaves */
-    for (int l = 1; l <= B; l++)
+    /* L2L, root to leaves, over FMM levels */
+    for (int l = st; l <= B; l += st)
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t j = 0; j < ((int64_t)1 << l); j++) {
-            int64_t gc = gid(l, j), gp = gid(l - 1, j / 2);
+            int64_t gc = gid(l, j), gp = gid(l - st, j / C);
             orc_l2l(F->L + gp * nc, F->centre + 3 * gp, F->centre + 3 * gc, p,
                     F->L + gc * nc);
         }

@@ -236,3 +236,101 @@ def test_eta_fmm_accuracy(eta):
     phi = oracle.Tree(x, 6, 10, 0.5, eta=eta).eval(q, field=False)
     p0 = oracle.direct(x, q, field=False)
     assert np.linalg.norm(phi - p0) / np.linalg.norm(p0) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Octree levels: 3 bisections per FMM level (8 children per box)
+# ---------------------------------------------------------------------------
+def ancestors_weak_step(t, theta, l, a, b, step):
+    while l > step:
+        l -= step
+        a >>= step
+        b >>= step
+        ga, gb = (1 << l) - 1 + a, (1 << l) - 1 + b
+        if oracle.theta_weak(theta, t["centre"][ga], t["radius"][ga], t["centre"][gb], t["radius"][gb]):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("step,levels", [(3, 6), (2, 6), (3, 3)])
+@pytest.mark.parametrize("theta", [0.35, 0.5, 0.8])
+def test_octree_lists_brute_force(step, levels, theta):
+    """Pairs of FMM level l are weak iff the theta-test holds at l and fails
+    at every coarser FMM level; bisection levels between FMM levels carry no
+    pairs at all."""
+    x = inputs.points("plummer", 400, seed=6)
+    T = oracle.Tree(x, levels, 2, theta, step=step)
+    t = T.tree()
+    for l in range(1, levels + 1):
+        wp, ws = T.lists(l, "weak")
+        sp, ss = T.lists(l, "strong")
+        if l % step:
+            assert wp[-1] == 0 and sp[-1] == 0
+            continue
+        for a in range(1 << l):
+            want_w, want_s = [], []
+            for b in range(1 << l):
+                if ancestors_weak_step(t, theta, l, a, b, step):
+                    continue
+                ga, gb = (1 << l) - 1 + a, (1 << l) - 1 + b
+                if oracle.theta_weak(theta, t["centre"][ga], t["radius"][ga], t["centre"][gb], t["radius"][gb]):
+                    want_w.append(b)
+                else:
+                    want_s.append(b)
+            assert list(ws[wp[a]:wp[a + 1]]) == want_w
+            assert list(ss[sp[a]:sp[a + 1]]) == want_s
+
+
+def test_octree_candidates_are_64_per_strong_parent_pair():
+    x = inputs.points("gmm", 3000, seed=8)
+    T = oracle.Tree(x, 9, 2, 0.5, step=3)
+    for l in (3, 6, 9):
+        nstrong_parent = T.lists(l - 3, "strong")[0][-1]
+        assert T.lists(l, "weak")[0][-1] + T.lists(l, "strong")[0][-1] == 64 * nstrong_parent
+
+
+@pytest.mark.parametrize("kind,theta", [("uniform", 0.5), ("plummer", 0.4)])
+def test_octree_every_source_counted_once(kind, theta):
+    n, levels, step = 900, 6, 3
+    x = inputs.points(kind, n, seed=3)
+    T = oracle.Tree(x, levels, 2, theta, step=step)
+    t = T.tree()
+    lists = {l: T.lists(l, "weak") for l in range(step, levels + 1, step)}
+    sp, ss = T.lists(levels, "strong")
+    for leaf in range(1 << levels):
+        total = 0
+        for l, (wp, ws) in lists.items():
+            a = leaf >> (levels - l)
+            total += sum(t["count"][(1 << l) - 1 + b] for b in ws[wp[a]:wp[a + 1]])
+        total += sum(t["count"][(1 << levels) - 1 + b] for b in ss[sp[leaf]:sp[leaf + 1]])
+        assert total == n
+
+
+def test_octree_tree_is_the_binary_tree():
+    """The step only changes which bisection levels carry expansions: the
+    boxes themselves are the same."""
+    x = inputs.points("plummer", 2000, seed=1)
+    a = oracle.Tree(x, 6, 2, 0.5).tree()
+    b = oracle.Tree(x, 6, 2, 0.5, step=3).tree()
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    with pytest.raises(ValueError):
+        oracle.Tree(x, 7, 2, 0.5, step=3)
+
+
+@pytest.mark.parametrize("kind", ["plummer", "uniform"])
+@pytest.mark.parametrize("theta,p,tol", [(0.0, 4, 1e-13), (0.5, 6, 1e-4), (0.5, 10, 2e-6),
+                                         (0.4, 12, 2e-8)])
+def test_octree_fmm_accuracy(kind, theta, p, tol):
+    """theta = 0: no weak pairs, so the FMM is the direct sum; otherwise the
+    octree FMM (tens of thousands of M2L pairs here) meets the accuracy of
+    the binary one (Sec. 3.1 bound)."""
+    n = 4000
+    x = inputs.points(kind, n, seed=12)
+    q = inputs.charges_uniform(n, seed=12)
+    T = oracle.Tree(x, 9, p, theta, step=3)
+    assert (sum(T.lists(l, "weak")[0][-1] for l in (3, 6, 9)) > 0) == (theta > 0)
+    phi, E = T.eval(q)
+    d_phi, d_E = oracle.direct(x, q)
+    assert np.linalg.norm(phi - d_phi) / np.linalg.norm(d_phi) <= tol
+    assert np.linalg.norm(E - d_E) / np.linalg.norm(d_E) <= 3 * tol
