@@ -102,6 +102,14 @@ typedef struct fmm_opts {
                        geometric bisection (children may be empty). For eta < 1
                        the build reads the largest child size back to the host
                        once per level. */
+    int bisections_per_level;
+                    /* bisections that make one expansion level: 0 or 1 (binary
+                       levels, the default), 2, or 3 (the paper's octree levels,
+                       8 children per box). `levels` counts bisections and must
+                       be a multiple of it; connectivity (a parent pair yields
+                       4^s candidate pairs), M2M, M2L and L2L then act only on
+                       every s-th bisection level, and the levels between carry
+                       empty lists and zero expansions. */
 } fmm_opts;
 
 /*
@@ -217,7 +225,9 @@ int fmm_plan_list(fmm_plan_t plan, int level, int kind, int64_t *ptr, int32_t *s
  * Y_n^m = (-1)^m r^n P_n^m(cos t) e^{i m phi} / (n+m)! (no Condon-Shortley phase)
  * and C_n^{-m} = (-1)^m conj(C_n^m). Multipoles of the levels above the first
  * level that has weak pairs are not formed (no stage reads them) and read as
- * zero; local expansions there are zero by definition.
+ * zero; local expansions there are zero by definition. With
+ * bisections_per_level = s > 1 the bisection levels that are not multiples of
+ * s hold no expansions and read as zero too.
  * Errors: FMM_EINVAL, FMM_ECUDA.
  */
 int fmm_eval_expansions(fmm_plan_t plan, int which, double *out);

@@ -37,7 +37,8 @@ class FmmError(RuntimeError):
 
 class fmm_opts(C.Structure):
     _fields_ = [("levels", C.c_int), ("p", C.c_int), ("theta", C.c_double),
-                ("prec", C.c_int), ("flags", C.c_int), ("eta", C.c_double)]
+                ("prec", C.c_int), ("flags", C.c_int), ("eta", C.c_double),
+                ("bisections_per_level", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -206,15 +207,18 @@ class Plan:
 # the C ABI, one function each
 # ---------------------------------------------------------------------------
 def fmm_plan(points, levels: int, p: int, theta: float, prec: int = FMM_PREC_FP64,
-             stream=None, allocator="torch", profile: bool = False, eta: float = 1.0) -> Plan:
+             stream=None, allocator="torch", profile: bool = False, eta: float = 1.0,
+             bisections_per_level: int = 1) -> Plan:
     """Build the tree and connectivity for n x 3 `points`; eta in [0, 1] is
-    the split adaptivity (1: balanced median splits, 0: cell bisection)."""
+    the split adaptivity (1: balanced median splits, 0: cell bisection);
+    bisections_per_level = 3 makes octree levels (`levels` counts bisections)."""
     lib = load()
     ptr, keep = _ptr(points)
     n = int(points.shape[0])
     dt = _dtype_code(points)
     flags = (FMM_FLAG_PROFILE if profile else 0) | (FMM_FLAG_ETA if float(eta) != 1.0 else 0)
-    opts = fmm_opts(int(levels), int(p), float(theta), int(prec), flags, float(eta))
+    opts = fmm_opts(int(levels), int(p), float(theta), int(prec), flags, float(eta),
+                    int(bisections_per_level))
     alloc, cbs = (None, None)
     if allocator == "torch":
         alloc, cbs = _torch_allocator()

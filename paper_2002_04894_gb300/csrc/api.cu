@@ -160,6 +160,8 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     if (opts->prec != FMM_PREC_FP64 && opts->prec != FMM_PREC_MIXED) return FMM_EINVAL;
     if (opts->flags & ~(FMM_FLAG_PROFILE | FMM_FLAG_ETA)) return FMM_EINVAL;
     if ((opts->flags & FMM_FLAG_ETA) && !(opts->eta >= 0.0 && opts->eta <= 1.0)) return FMM_EINVAL;
+    const int step = opts->bisections_per_level == 0 ? 1 : opts->bisections_per_level;
+    if (step < 1 || step > 3 || opts->levels % step != 0) return FMM_EINVAL;
     if (alloc && (!alloc->alloc || !alloc->free)) return FMM_EINVAL;
 
     fmm_plan_s *H = new (std::nothrow) fmm_plan_s();
@@ -171,6 +173,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     P.nc = fmm::ncoef(P.p);
     P.theta = opts->theta;
     P.eta = (opts->flags & FMM_FLAG_ETA) ? opts->eta : 1.0;
+    P.step = step;
     P.prec = opts->prec;
     P.dtype = dtype;
     P.nbox = ((int64_t)2 << P.B) - 1;

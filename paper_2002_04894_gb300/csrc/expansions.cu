@@ -202,13 +202,16 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     int lw = P.B + 1;
     for (int l = P.B; l >= 1; l--)
         if (P.nweak[l] > 0) lw = l;
+    // with 2^step children per box only every step-th bisection level holds
+    // expansions; the levels in between stay zero
+    const int sp = P.step;
     stage_mark(P, FMM_STAGE_M2M, 0);
-    for (int l = P.B; l >= 1; l--) {
-        if (l - 1 >= lw)
-            m2m_level(P, l);
+    for (int pl = P.B - 1; pl >= 0; pl--) {
+        if (pl % sp == 0 && pl >= lw)
+            m2m_level(P, pl + sp);
         else
-            cudaMemsetAsync(P.M + (((int64_t)1 << (l - 1)) - 1) * nc, 0,
-                            (size_t)((int64_t)1 << (l - 1)) * nc * sizeof(double2), st);
+            cudaMemsetAsync(P.M + (((int64_t)1 << pl) - 1) * nc, 0,
+                            (size_t)((int64_t)1 << pl) * nc * sizeof(double2), st);
     }
     stage_mark(P, FMM_STAGE_M2M, 1);
     // Algorithm 3: M2L at every level (each overwrites its level's L), then L2L downward
@@ -221,7 +224,8 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     stage_mark(P, FMM_STAGE_M2L, 1);
     stage_mark(P, FMM_STAGE_L2L, 0);
     // L2L into a level whose parents hold nothing would only add zeros
-    for (int l = std::max(1, lw + 1); l <= P.B; l++) l2l_level(P, l);
+    for (int l = sp; l <= P.B; l += sp)
+        if (l - sp >= lw) l2l_level(P, l);
     stage_mark(P, FMM_STAGE_L2L, 1);
     stage_mark(P, FMM_STAGE_L2P, 0);
     if (mixed) {

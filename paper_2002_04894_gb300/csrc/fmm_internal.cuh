@@ -28,6 +28,7 @@ struct Plan {
     int B = 0, p = 0, nc = 0, prec = 0, dtype = 0, device = 0;
     double theta = 0.0;
     double eta = 1.0;  // adaptivity of the splits (Sec. 2.1.2); 1: median splits
+    int step = 1;      // bisections per expansion level (3: octree levels)
     int64_t nbox = 0, nleaf = 0;
     cudaStream_t stream = nullptr;
     fmm_allocator alloc{};

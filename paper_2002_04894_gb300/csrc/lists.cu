@@ -1,6 +1,7 @@
 // Connectivity (Eq. 2.2 and the inheritance rule of Sec. 2.1.1; the
 // connectivity part of Algorithm 2): starting from the root's connection to
-// itself, the children of every strongly connected pair of level l-1 are
+// itself, the children of every strongly connected pair of level l-1 (or of
+// level l-step for levels of 2^step children, step = 3 being the octree) are
 // tested with the theta-criterion R + theta r <= theta d (R, r the larger and
 // smaller radius, d the centre distance). Weak pairs become the M2L list of
 // level l, strong pairs are refined further and at the leaf level form the
@@ -38,29 +39,31 @@ __device__ __forceinline__ bool theta_weak(double theta, const double *ca, doubl
     return theta > 0.0 && d > 0.0 && __dadd_rn(R, __dmul_rn(theta, r)) <= __dmul_rn(theta, d);
 }
 
-// One thread per strongly connected pair (T, S) of the parent level: its four
-// child pairs (2T+a, 2S+b) are tested and their flags written at their
-// position in the target-major candidate order
-//   cpos = 4 sptr[T] + a * 2 len(T) + 2 (e - sptr[T]) + b,
-// i.e. grouped by target 2T+a and, inside a target, by ascending source (the
-// parent's sources are ascending). A scan of the weak flags then places every
-// weak and strong pair directly in its sorted CSR slot.
-__global__ void k_cand(int level, int64_t npar, double theta, const int32_t *__restrict__ pptr,
+// One thread per strongly connected pair (T, S) of the parent level: its
+// C x C child pairs (C T + a, C S + b), C = 2^step children per box (step
+// bisections per level; 3 for octree levels), are tested and their flags
+// written at their position in the target-major candidate order
+//   cpos = C^2 sptr[T] + a * C len(T) + C (e - sptr[T]) + b,
+// i.e. grouped by target C T + a and, inside a target, by ascending source
+// (the parent's sources are ascending). A scan of the weak flags then places
+// every weak and strong pair directly in its sorted CSR slot.
+__global__ void k_cand(int level, int step, int64_t npar, double theta, const int32_t *__restrict__ pptr,
                        const int32_t *__restrict__ psrc, const int32_t *__restrict__ prow,
                        const double *__restrict__ centre, const double *__restrict__ radius,
                        int32_t *__restrict__ flag, int32_t *__restrict__ csrc,
                        int32_t *__restrict__ ctgt) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= npar) return;
+    const int C = 1 << step;
     const int32_t T = prow[e], S = psrc[e];
     const int32_t b0 = pptr[T], len = pptr[T + 1] - b0;
     const int64_t off = ((int64_t)1 << level) - 1;
-    for (int a = 0; a < 2; a++) {
-        const int32_t t = 2 * T + a;
+    for (int a = 0; a < C; a++) {
+        const int32_t t = C * T + a;
         const int64_t gt = off + t;
-        const int64_t base = 4ll * b0 + (int64_t)a * 2 * len + 2ll * (e - b0);
-        for (int b = 0; b < 2; b++) {
-            const int32_t s = 2 * S + b;
+        const int64_t base = (int64_t)C * C * b0 + (int64_t)a * C * len + (int64_t)C * (e - b0);
+        for (int b = 0; b < C; b++) {
+            const int32_t s = C * S + b;
             const int64_t gs = off + s;
             flag[base + b] = theta_weak(theta, centre + 3 * gt, radius[gt], centre + 3 * gs, radius[gs]);
             csrc[base + b] = s;
@@ -87,20 +90,21 @@ __global__ void k_cand_scatter(int64_t ncand, const int32_t *__restrict__ flag,
     }
 }
 
-// CSR row pointers of level `level` from the parent's: target t = 2T + a
-// starts at candidate 4 sptr[T] + a * 2 len(T).
-__global__ void k_cand_ptrs(int level, const int32_t *__restrict__ pptr,
+// CSR row pointers of level `level` from the parent level's: target
+// t = C T + a starts at candidate C^2 sptr[T] + a * C len(T).
+__global__ void k_cand_ptrs(int level, int step, const int32_t *__restrict__ pptr,
                             const int32_t *__restrict__ wpos, int64_t ncand,
                             int32_t *__restrict__ wptr, int32_t *__restrict__ sptr) {
     const int64_t nt = (int64_t)1 << level;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t > nt) return;
+    const int64_t C = (int64_t)1 << step;
     int64_t first;
     if (t == nt) {
         first = ncand;
     } else {
-        const int64_t T = t >> 1, a = t & 1;
-        first = 4ll * pptr[T] + a * 2ll * (pptr[T + 1] - pptr[T]);
+        const int64_t T = t >> step, a = t & (C - 1);
+        first = C * C * pptr[T] + a * C * (pptr[T + 1] - pptr[T]);
     }
     const int32_t w = wpos[first];
     wptr[t] = w;
@@ -246,9 +250,28 @@ cudaError_t lists_build(Plan &P) {
     int32_t *totals = nullptr;
     cudaError_t e = cudaMallocHost(&totals, 8);
     if (e != cudaSuccess) return e;
+    const int step = P.step, C = 1 << step;
     for (int l = 1; l <= P.B; l++) {
         const int64_t nt = (int64_t)1 << l;
-        const int64_t npar = P.nstrong[l - 1], ncand = 4 * npar;
+        if (l % step) {
+            // a bisection level inside a level of 2^step children: no pairs
+            P.wptr[l] = (int32_t *)palloc(P, (nt + 1) * 4);
+            P.sptr[l] = (int32_t *)palloc(P, (nt + 1) * 4);
+            P.wsrc[l] = (int32_t *)palloc(P, 4);
+            P.wrow[l] = (int32_t *)palloc(P, 4);
+            P.ssrc[l] = (int32_t *)palloc(P, 4);
+            if (!P.wptr[l] || !P.sptr[l] || !P.wsrc[l] || !P.wrow[l] || !P.ssrc[l]) {
+                cudaFreeHost(totals);
+                return cudaErrorMemoryAllocation;
+            }
+            cudaMemsetAsync(P.wptr[l], 0, (nt + 1) * 4, st);
+            cudaMemsetAsync(P.sptr[l], 0, (nt + 1) * 4, st);
+            P.nweak[l] = 0;
+            P.nstrong[l] = 0;
+            continue;
+        }
+        const int lp = l - step;
+        const int64_t npar = P.nstrong[lp], ncand = (int64_t)C * C * npar;
         if (ncand > 0x7fffffffLL) {
             P.capacity_exceeded = true;
             cudaFreeHost(totals);
@@ -264,14 +287,14 @@ cudaError_t lists_build(Plan &P) {
             cudaFreeHost(totals);
             return cudaErrorMemoryAllocation;
         }
-        FMM_LAUNCH(k_cand, (unsigned)((npar + 127) / 128), 128, 0, st, l, npar, P.theta, P.sptr[l - 1],
-                   P.ssrc[l - 1], srow_prev, P.centre, P.radius, flag, csrc, ctgt);
+        FMM_LAUNCH(k_cand, (unsigned)((npar + 127) / 128), 128, 0, st, l, step, npar, P.theta, P.sptr[lp],
+                   P.ssrc[lp], srow_prev, P.centre, P.radius, flag, csrc, ctgt);
         e = scan_exclusive(P, flag, wpos, ncand);
         if (e != cudaSuccess) {
             cudaFreeHost(totals);
             return e;
         }
-        FMM_LAUNCH(k_cand_ptrs, (unsigned)((nt + 1 + 255) / 256), 256, 0, st, l, P.sptr[l - 1], wpos,
+        FMM_LAUNCH(k_cand_ptrs, (unsigned)((nt + 1 + 255) / 256), 256, 0, st, l, step, P.sptr[lp], wpos,
                    ncand, P.wptr[l], P.sptr[l]);
         cudaMemcpyAsync(totals, wpos + ncand, 4, cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);

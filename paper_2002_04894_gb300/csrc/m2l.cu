@@ -224,7 +224,7 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
 // M2M in the rotational form, one child per thread; the parent's multipole
 // (zeroed beforehand) receives both children's shifted expansions atomically.
 //   multipole, rotated frame (Mt = F M):  Mt'_n^m = F_nm sum_k rho^k/k! Mt_{n-k}^m / F_{n-k,m}
-__global__ void k_m2m_rot(int level, int p, const double *__restrict__ centre, double2 *M,
+__global__ void k_m2m_rot(int level, int step, int p, const double *__restrict__ centre, double2 *M,
                           const double *__restrict__ gtab, int ntab) {
     extern __shared__ double2 sm2[];
     const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
@@ -237,7 +237,7 @@ __global__ void k_m2m_rot(int level, int p, const double *__restrict__ centre, d
     double2 *v = V + tid, *u = U + tid, *x = W + tid;
     const int64_t j = blockIdx.x * (int64_t)T + tid;  // child index within level
     if (j >= ((int64_t)1 << level)) return;
-    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = (gc - 1) / 2;
+    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = ((gc + 1) >> step) - 1;  // ancestor step levels up
     const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
                  dz = centre[3 * gc + 2] - centre[3 * gp + 2];
     const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
@@ -302,7 +302,7 @@ __global__ void k_m2m_rot(int level, int p, const double *__restrict__ centre, d
     }
 }
 
-__global__ void k_l2l_rot(int level, int p, const double *__restrict__ centre, double2 *L,
+__global__ void k_l2l_rot(int level, int step, int p, const double *__restrict__ centre, double2 *L,
                           const double *__restrict__ gtab, int ntab) {
     extern __shared__ double2 sm2[];
     const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
@@ -315,7 +315,7 @@ __global__ void k_l2l_rot(int level, int p, const double *__restrict__ centre, d
     double2 *v = V + tid, *u = U + tid, *x = W + tid;
     const int64_t j = blockIdx.x * (int64_t)T + tid;  // child index within level
     if (j >= ((int64_t)1 << level)) return;
-    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = (gc - 1) / 2;
+    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = ((gc + 1) >> step) - 1;  // ancestor step levels up
     const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
                  dz = centre[3 * gc + 2] - centre[3 * gp + 2];
     const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
@@ -464,18 +464,19 @@ cudaError_t m2l_setup(Plan &P) {
     return e;
 }
 
-// parents of level l-1 from their children at level l (parents zeroed first)
+// parents of level l-step from their descendants at level l (parents zeroed first)
 void m2m_level(Plan &P, int l) {
-    const int64_t np = (int64_t)1 << (l - 1), nch = (int64_t)1 << l;
+    const int64_t np = (int64_t)1 << (l - P.step), nch = (int64_t)1 << l;
     cudaMemsetAsync(P.M + (np - 1) * P.nc, 0, (size_t)np * P.nc * sizeof(double2), P.stream);
     FMM_LAUNCH(k_m2m_rot, (unsigned)((nch + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads,
-               P.m2l_smem, P.stream, l, P.p, P.centre, P.M, P.m2l_tab, P.m2l_ntab);
+               P.m2l_smem, P.stream, l, P.step, P.p, P.centre, P.M, P.m2l_tab, P.m2l_ntab);
 }
 
+// level l from its ancestors at level l-step
 void l2l_level(Plan &P, int l) {
     const int64_t nch = (int64_t)1 << l;
     FMM_LAUNCH(k_l2l_rot, (unsigned)((nch + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads,
-               P.m2l_smem, P.stream, l, P.p, P.centre, P.L, P.m2l_tab, P.m2l_ntab);
+               P.m2l_smem, P.stream, l, P.step, P.p, P.centre, P.L, P.m2l_tab, P.m2l_ntab);
 }
 
 // FP64 M2L over all levels in one launch; accumulates into L (zeroed first)

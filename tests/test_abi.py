@@ -48,7 +48,9 @@ def test_invalid_arguments_rejected_before_any_device_work():
                 fmm.fmm_opts(3, 4, 0.5, 7, 0), fmm.fmm_opts(3, 4, 0.5, 0, 4),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, 1.5),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, -0.25),
-                fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, float("nan"))):
+                fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, float("nan")),
+                fmm.fmm_opts(4, 4, 0.5, 0, 0, 1.0, 3), fmm.fmm_opts(4, 4, 0.5, 0, 0, 1.0, 4),
+                fmm.fmm_opts(4, 4, 0.5, 0, 0, 1.0, -1)):
         assert lib.fmm_plan(pts.ctypes.data, 4, 0, ctypes.byref(bad), None, None, ctypes.byref(h)) == -1
         assert h.value is None
     assert lib.fmm_plan(pts.ctypes.data, 0, 0, ctypes.byref(opts), None, None, ctypes.byref(h)) == -1
