@@ -524,12 +524,180 @@ def bench_serve(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def _timed_solves(fmm, torch, xd, qd, reps, flush, levels, p, theta, eta=1.0, step=1,
+                  prec=1, tgt=None, ref=None):
+    """One warm-up and `reps` timed solves (plan + eval, L2 flushed before
+    each); returns (ms list, mean stage ms, potential error on `tgt` vs `ref`,
+    the last plan's stats)."""
+    stream = torch.cuda.current_stream()
+    n = xd.shape[0]
+    pot = torch.empty(n, dtype=qd.dtype, device="cuda")
+    fld = torch.empty((n, 3), dtype=qd.dtype, device="cuda")
+    times, stages, stats = [], {s: 0.0 for s in fmm.STAGES}, None
+    for r in range(reps + 1):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True, eta=eta,
+                            bisections_per_level=step)
+        fmm.fmm_eval(plan, qd, pot, fld)
+        b.record(stream)
+        st = fmm.fmm_stage_times(plan)
+        if r > 0:
+            times.append(a.elapsed_time(b))
+            for k in st:
+                stages[k] += st[k] / reps
+        stats = fmm.fmm_plan_stats(plan)
+        fmm.fmm_destroy(plan)
+    err = None
+    if tgt is not None:
+        got = pot.double().cpu().numpy()[tgt]
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return times, stages, err, stats
+
+
+def bench_params(args, rank, world, local):
+    """Parameter response of Sec. 3.2: 100,000 points of four distributions
+    (uniform, spherical Gaussian, shell, helix), solve time against theta,
+    eta and the number of octree levels L (3 bisections each), one parameter
+    at a time around theta = 0.5, eta = 0.5, L = 3; each point 4 timed runs
+    after a warm-up; for each theta the smallest even p whose potential error
+    at the default eta and L is below 1e-6 (the fixed TOL of the study)."""
+    import torch
+    import paper_2002_04894_gb300 as fmm
+
+    torch.cuda.set_device(local)
+    fmm.load()
+    n, reps, tol = 100_000, 4, 1e-6
+    thetas = [0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8]
+    etas = [0.0, 0.25, 0.5, 0.75, 1.0]
+    Ls = [1, 2, 3, 4]
+    d_theta, d_eta, d_L = 0.5, 0.5, 3
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    launches0 = fmm.fmm_kernel_launches()
+    out_d = {}
+    best_rates = []
+    with ClockSampler(local) as clk:
+        for kind in ("uniform", "gaussian", "shell", "helix"):
+            x = inputs.points(kind, n, seed=rank)
+            q = inputs.charges_uniform(n, seed=rank)
+            xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+            tgt = inputs.sample_targets(n, 1000, seed=rank)
+            ref = fmm.fmm_direct(xd, qd, torch.from_numpy(tgt).cuda())[0].double().cpu().numpy()
+            p_of = {}
+            for th in thetas:
+                p_of[th] = 16
+                for pp in (4, 6, 8, 10, 12, 14, 16):
+                    _, _, e, _ = _timed_solves(fmm, torch, xd, qd, 0, flush, 3 * d_L, pp, th, d_eta, 3,
+                                               tgt=tgt, ref=ref)
+                    if e <= tol:
+                        p_of[th] = pp
+                        break
+
+            def point(th, eta, L):
+                t, st, e, stats = _timed_solves(fmm, torch, xd, qd, reps, flush, 3 * L, p_of[th], th, eta, 3,
+                                                tgt=tgt, ref=ref)
+                return {"mean_ms": round(statistics.mean(t), 3), "min_ms": round(min(t), 3),
+                        "max_ms": round(max(t), 3), "p": p_of[th], "rel_err_phi": e,
+                        "m2l_ms": round(st["m2l"], 3), "p2p_ms": round(st["p2p"], 3),
+                        "weak_pairs": stats["weak_pairs"], "p2p_interactions": stats["p2p_interactions"]}
+
+            curves = {"theta": {th: point(th, d_eta, d_L) for th in thetas},
+                      "eta": {e: point(d_theta, e, d_L) for e in etas},
+                      "L": {L: point(d_theta, d_eta, L) for L in Ls}}
+            norm = {"theta": curves["theta"][0.5]["mean_ms"], "eta": curves["eta"][0.0]["mean_ms"],
+                    "L": curves["L"][1]["mean_ms"]}
+            for c, pts in curves.items():
+                for v in pts.values():
+                    v["normalised"] = round(v["mean_ms"] / norm[c], 4)
+            opt = {c: min(pts, key=lambda k: pts[k]["mean_ms"]) for c, pts in curves.items()}
+            best = min(v["mean_ms"] for pts in curves.values() for v in pts.values())
+            best_rates.append(n / best / 1e3)
+            out_d[kind] = {"p_by_theta": p_of, "optimum": opt,
+                           **{c: {str(k): v for k, v in pts.items()} for c, pts in curves.items()}}
+    launches = fmm.fmm_kernel_launches() - launches0
+    if rank != 0:
+        return
+    value = float(np.exp(np.mean(np.log(best_rates))))
+    out = {
+        "metric": "solve time vs theta, eta and octree levels L (parameter response of Sec. 3.2)",
+        "value": round(value, 4), "unit": "Mpoints/s (geometric mean over the four distributions at "
+                                          "the fastest probed parameters)",
+        "n_gpus": world, "steps": reps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "params", "n": n, "tol": tol, "levels": "octree (3 bisections per level)",
+                   "defaults": {"theta": d_theta, "eta": d_eta, "L": d_L}, "prec": "mixed",
+                   "l2": "flushed between runs (512 MB write)",
+                   "normalised_by": "mean time at theta = 0.5, eta = 0, L = 1 respectively"},
+        "distributions": out_d, "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
+def bench_galaxy(args, rank, world, local):
+    """Adaptivity sweep standing in for the galaxy test of Sec. 3.5: a
+    2,000,000-point synthetic multiscale galaxy, 5 octree levels (15
+    bisections, ~61 points per leaf), p = 12, theta = 0.5, mixed form; solve
+    time, stage times, accuracy and near-field load balance for eta from 0
+    (cell bisection) to 1 (median splits)."""
+    import torch
+    import paper_2002_04894_gb300 as fmm
+
+    torch.cuda.set_device(local)
+    fmm.load()
+    n, levels, p, theta = 2_000_000, 15, 12, 0.5
+    reps = max(1, args.steps)
+    x = inputs.points("galaxy", n, seed=rank)
+    q = inputs.charges_uniform(n, seed=rank)
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    tgt = inputs.sample_targets(n, 1000, seed=rank)
+    ref = fmm.fmm_direct(xd, qd, torch.from_numpy(tgt).cuda())[0].double().cpu().numpy()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    etas = [0.0, 0.125, 0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 1.0]
+    rows = {}
+    launches0 = fmm.fmm_kernel_launches()
+    with ClockSampler(local) as clk:
+        for eta in etas:
+            t, st, e, stats = _timed_solves(fmm, torch, xd, qd, reps, flush, levels, p, theta, eta, 3,
+                                            tgt=tgt, ref=ref)
+            plan = fmm.fmm_plan(xd, levels, p, theta, prec=fmm.FMM_PREC_MIXED, eta=eta,
+                                bisections_per_level=3)
+            cnt = fmm.fmm_plan_tree(plan)["count"][(1 << levels) - 1:].astype(np.float64)
+            sp, ss = fmm.fmm_plan_list(plan, levels, "strong")
+            fmm.fmm_destroy(plan)
+            rows_of = np.repeat(np.arange(len(cnt)), np.diff(sp))
+            work = cnt * np.bincount(rows_of, weights=cnt[ss], minlength=len(cnt))
+            rows[str(eta)] = {"mean_ms": round(statistics.mean(t), 3), "min_ms": round(min(t), 3),
+                              "stage_ms": {k: round(v, 3) for k, v in st.items()}, "rel_err_phi": e,
+                              "weak_pairs": stats["weak_pairs"], "p2p_interactions": stats["p2p_interactions"],
+                              "leaf_points_max": int(cnt.max()), "empty_leaves": int((cnt == 0).sum()),
+                              "leaf_work_max_over_mean": round(float(work.max() / work.mean()), 3)}
+    launches = fmm.fmm_kernel_launches() - launches0
+    if rank != 0:
+        return
+    best = min(rows, key=lambda k: rows[k]["mean_ms"])
+    out = {
+        "metric": "solve time vs adaptivity eta on a synthetic galaxy (Sec. 3.5 stand-in)",
+        "value": round(n / rows[best]["mean_ms"] / 1e3, 4), "unit": "Mpoints/s at the fastest eta",
+        "n_gpus": world, "steps": reps, "warmup": 1, "ms_per_step": rows[best]["mean_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "galaxy_eta", "n": n, "levels": levels, "bisections_per_level": 3, "p": p,
+                   "theta": theta, "prec": "mixed", "points": "galaxy", "l2": "flushed between runs (512 MB write)"},
+        "best_eta": float(best),
+        "speedup_vs_eta1": round(rows["1.0"]["mean_ms"] / rows[best]["mean_ms"], 3),
+        "speedup_vs_eta0": round(rows["0.0"]["mean_ms"] / rows[best]["mean_ms"], 3),
+        "sweep": rows, "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["batch", "serve", "params", "galaxy_eta"])
     ap.add_argument("--prec", default=None, choices=["fp64", "mixed"])
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="steps of the plain FP64 form timed as the comparator (0: skip)")
@@ -549,6 +717,10 @@ def main():
         bench_batch(args, rank, world, local)
     elif args.workload == "serve":
         bench_serve(args, rank, world, local)
+    elif args.workload == "params":
+        bench_params(args, rank, world, local)
+    elif args.workload == "galaxy_eta":
+        bench_galaxy(args, rank, world, local)
     else:
         bench_ours(args, rank, world, local)
 

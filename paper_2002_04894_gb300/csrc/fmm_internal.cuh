@@ -12,6 +12,9 @@
 
 namespace fmm {
 
+// targets per near-field work unit (one CTA, one target per thread)
+constexpr int kP2PTile = 128;
+
 // ---------------------------------------------------------------------------
 // Plan: everything lives in device memory owned by the plan.
 // ---------------------------------------------------------------------------
@@ -49,7 +52,10 @@ struct Plan {
     int32_t *wrow[FMM_MAX_LEVELS + 1] = {};  // target of every weak pair (flat M2L)
     int64_t nweak[FMM_MAX_LEVELS + 1] = {}, nstrong[FMM_MAX_LEVELS + 1] = {};
     int64_t p2p_interactions = 0;
-    int32_t *p2p_order = nullptr;  // target leaves, heaviest near-field work first
+    // near-field work units (target leaf, first target of a kP2PTile tile),
+    // heaviest first
+    int2 *p2p_units = nullptr;
+    int64_t p2p_nunits = 0;
     bool capacity_exceeded = false;
     // M2L rotation tables (D = d(pi/2) quadrants, axial coefficients, F_nm)
     double *m2l_tab = nullptr;

@@ -186,7 +186,8 @@ __global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *tile_sums) {
     if (i < n) out[i] += tile_sums[i / kScanTile];
 }
 
-// per target leaf and in total: sum over strong leaf pairs (t, s) of n_t * n_s
+// per target leaf the near source points (sum of n_s over its strong leaf
+// pairs), and in total the sum over strong leaf pairs (t, s) of n_t * n_s
 __global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, const int32_t *count,
                            unsigned long long *acc, long long *per_leaf) {
     const int64_t nt = (int64_t)1 << B;
@@ -197,7 +198,7 @@ __global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, cons
         unsigned long long ns = 0;
         for (int32_t e = sptr[t]; e < sptr[t + 1]; e++) ns += (unsigned long long)count[off + ssrc[e]];
         v = ns * (unsigned long long)count[off + t];
-        per_leaf[t] = (long long)v;
+        per_leaf[t] = (long long)ns;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
@@ -316,33 +317,50 @@ cudaError_t lists_build(Plan &P) {
                    ctgt, P.wsrc[l], P.wrow[l], P.ssrc[l], srow);
         srow_prev = srow;
     }
-    // exact P2P work (sum of n_t * n_s over strong leaf pairs), per leaf and in
-    // total; the near-field kernels take the leaves heaviest first, so that the
-    // long ones start early instead of forming the tail of the launch
+    // exact P2P work (sum of n_t * n_s over strong leaf pairs). The near
+    // field runs as work units of up to kP2PTile targets of one leaf, so that
+    // a few large leaves still fill the GPU; units go heaviest first, so that
+    // the long ones start early instead of forming the tail of the launch.
     const int64_t nl = (int64_t)1 << P.B;
     unsigned long long *acc = (unsigned long long *)dalloc(P, 8);
-    long long *work = (long long *)dalloc(P, (size_t)nl * 8);
-    P.p2p_order = (int32_t *)palloc(P, (size_t)nl * 4);
-    if (!acc || !work || !P.p2p_order) {
+    long long *nsrc = (long long *)dalloc(P, (size_t)nl * 8);
+    if (!acc || !nsrc) {
         cudaFreeHost(totals);
         return cudaErrorMemoryAllocation;
     }
     cudaMemsetAsync(acc, 0, 8, st);
     FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.sptr[P.B], P.ssrc[P.B],
-               P.count, acc, work);
-    std::vector<long long> hw((size_t)nl);
+               P.count, acc, nsrc);
+    std::vector<long long> hns((size_t)nl);
+    std::vector<int32_t> hcnt((size_t)nl);
     unsigned long long h = 0;
     cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hw.data(), work, (size_t)nl * 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hns.data(), nsrc, (size_t)nl * 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hcnt.data(), P.count + (nl - 1), (size_t)nl * 4, cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     P.p2p_interactions = (int64_t)h;
     cudaFreeHost(totals);
     if (e != cudaSuccess) return e;
-    std::vector<int32_t> order((size_t)nl);
-    for (int64_t i = 0; i < nl; i++) order[i] = (int32_t)i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return hw[a] > hw[b]; });
-    e = cudaMemcpyAsync(P.p2p_order, order.data(), (size_t)nl * 4, cudaMemcpyHostToDevice, st);
+    std::vector<int2> units;
+    std::vector<long long> uw;
+    units.reserve((size_t)nl);
+    uw.reserve((size_t)nl);
+    for (int64_t t = 0; t < nl; t++)
+        for (int32_t tb = 0; tb < hcnt[t]; tb += kP2PTile) {
+            units.push_back(make_int2((int)t, tb));
+            uw.push_back((long long)std::min(kP2PTile, hcnt[t] - tb) * hns[t]);
+        }
+    std::vector<int32_t> idx(units.size());
+    for (size_t i = 0; i < idx.size(); i++) idx[i] = (int32_t)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return uw[a] > uw[b]; });
+    std::vector<int2> sorted(units.size());
+    for (size_t i = 0; i < idx.size(); i++) sorted[i] = units[idx[i]];
+    P.p2p_nunits = (int64_t)sorted.size();
+    P.p2p_units = (int2 *)palloc(P, std::max<size_t>(sorted.size(), 1) * sizeof(int2));
+    if (!P.p2p_units) return cudaErrorMemoryAllocation;
+    if (!sorted.empty())
+        e = cudaMemcpyAsync(P.p2p_units, sorted.data(), sorted.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e != cudaSuccess ? e : cudaGetLastError();
 }

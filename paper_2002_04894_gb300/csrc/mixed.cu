@@ -240,8 +240,8 @@ __global__ void k_leaf_geo(int B, const double *__restrict__ lo, const double *_
 
 constexpr int kLeafChunk = 256;
 
-// Near field in float. One CTA per target leaf (heaviest leaves first), one
-// target point per thread. For every source leaf the offset between the two
+// Near field in float. One CTA per work unit (a tile of up to 128 targets of
+// one leaf; heaviest units first), one target point per thread. For every source leaf the offset between the two
 // leaf centres is formed once, error-free (float TwoSum on the centres' hi/lo
 // parts), together with a near/far flag: far when the gap g between the two
 // cells is at least half the sum of their radii. The float offsets then carry
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kThreads)
 k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const float4 *__restrict__ geo, const int32_t *__restrict__ sptr,
-          const int32_t *__restrict__ ssrc, const int32_t *__restrict__ order,
+          const int32_t *__restrict__ ssrc, const int2 *__restrict__ units,
           const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
           const float *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
     __shared__ float4 th[kThreads];     // source offset from the target centre (hi) and charge
@@ -264,12 +264,15 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
     __shared__ float4 dl[kLeafChunk];   // centre offset lo
     __shared__ int2 rng[kLeafChunk];    // begin, count
     const int64_t off = ((int64_t)1 << B) - 1;
-    const int t = order[blockIdx.x];
+    static_assert(kThreads == kP2PTile, "one target per thread");
+    const int2 unit = units[blockIdx.x];
+    const int t = unit.x;
     const int64_t gt = off + t;
     const int bt = begin[gt], nt = count[gt];
     const int e0 = sptr[t], e1 = sptr[t + 1];
     const float4 tc_h = geo[3 * t], tc_l = geo[3 * t + 1], tc_e = geo[3 * t + 2];
-    for (int tb = 0; tb < nt; tb += kThreads) {
+    {
+        const int tb = unit.y;
         const int i = tb + threadIdx.x;
         const bool active = i < nt;
         const float xh = active ? hl[bt + i] : 0.f, yh = active ? hl[n + bt + i] : 0.f,
@@ -420,12 +423,12 @@ cudaError_t mixed_l2p(Plan &P) {
 
 cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
     if (dtype == FMM_F64)
-        FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.nleaf, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_order, P.perm,
+        FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.p2p_nunits, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
+                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.perm,
                    P.far_phi_f, P.far_E_f, (double *)pot, (double *)field);
     else
-        FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.nleaf, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_order, P.perm,
+        FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.p2p_nunits, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
+                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.perm,
                    P.far_phi_f, P.far_E_f, (float *)pot, (float *)field);
     return cudaGetLastError();
 }

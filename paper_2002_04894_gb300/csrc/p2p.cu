@@ -26,15 +26,18 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
           const double *__restrict__ z, const double *__restrict__ q,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const int32_t *__restrict__ sptr, const int32_t *__restrict__ ssrc,
-          const int32_t *__restrict__ order, const int32_t *__restrict__ perm,
+          const int2 *__restrict__ units, const int32_t *__restrict__ perm,
           const double *__restrict__ far_phi,
           const double *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
     __shared__ double4 tile[kP2PThreads];
     const int64_t off = ((int64_t)1 << B) - 1;
-    const int t = order[blockIdx.x];
+    static_assert(kP2PThreads == kP2PTile, "one target per thread");
+    const int2 unit = units[blockIdx.x];
+    const int t = unit.x;
     const int bt = begin[off + t], nt = count[off + t];
     const int e0 = sptr[t], e1 = sptr[t + 1];
-    for (int tb = 0; tb < nt; tb += kP2PThreads) {
+    {
+        const int tb = unit.y;
         const int i = tb + threadIdx.x;
         const bool active = i < nt;
         const double xi = active ? x[bt + i] : 0.0;
@@ -134,7 +137,7 @@ k_direct(const T *__restrict__ pts, const T *__restrict__ q, int64_t n,
 }  // namespace
 
 cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
-    const unsigned grid = (unsigned)P.nleaf;
+    const unsigned grid = (unsigned)P.p2p_nunits;
     stage_mark(P, FMM_STAGE_P2P, 0);
     if (P.prec == FMM_PREC_MIXED) {
         cudaError_t e = mixed_p2p(P, pot, field, dtype);
@@ -143,11 +146,11 @@ cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
     }
     if (dtype == FMM_F64)
         FMM_LAUNCH(k_p2p_f64<double>, grid, kP2PThreads, 0, P.stream, 
-            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_order,
+            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units,
             P.perm, P.far_phi, P.far_E, (double *)pot, (double *)field);
     else
         FMM_LAUNCH(k_p2p_f64<float>, grid, kP2PThreads, 0, P.stream, 
-            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_order,
+            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units,
             P.perm, P.far_phi, P.far_E, (float *)pot, (float *)field);
     stage_mark(P, FMM_STAGE_P2P, 1);
     return cudaGetLastError();

@@ -12,6 +12,11 @@ beyond their names; the stand-ins below are stated in the design notes):
   gaussian  one spherical Gaussian (sigma 0.1) centred at 0.5
   shell     spherical shell (radius 0.4, thickness 0.01) centred at 0.5
   helix     3-turn helix of radius 0.3 with 0.01 jitter
+  galaxy    multiscale disc after the recipe of Sec. 3.5: a seed ring of
+            10,000 points (radii 6000-18000 pc, two logarithmic arms), then
+            generations that replace every point by 10 points uniform in an
+            oblate spheroid around it (semi-axes R_k, R_k, R_k / 10 with
+            R_0 = 18000 / 20 pc, R_{k+1} = 2/3 R_k), scaled into the unit cube
 """
 from __future__ import annotations
 
@@ -70,8 +75,36 @@ def helix(n: int, seed: int = 0, turns: float = 3.0, radius: float = 0.3, jitter
     return pts + jitter * rng.normal(size=(n, 3))
 
 
+def _in_unit_ball(rng: np.random.Generator, n: int) -> np.ndarray:
+    return _isotropic(rng, n) * rng.random(n)[:, None] ** (1.0 / 3.0)
+
+
+def galaxy(n: int, seed: int = 0, seeds: int = 10_000, r_inner: float = 6000.0,
+           r_outer: float = 18000.0, children: int = 10) -> np.ndarray:
+    """Spiral-galaxy stand-in: seed ring with two logarithmic arms (pitch
+    15 degrees, 0.1 rad azimuthal scatter, 300 pc thickness), refined by
+    generations of `children` points per parent in shrinking oblate
+    spheroids; the last generation refines a random subset of parents."""
+    rng = np.random.default_rng([seed, 7])
+    m0 = min(seeds, n)
+    r = r_inner + (r_outer - r_inner) * rng.random(m0)
+    arm = rng.integers(0, 2, size=m0)
+    phi = np.log(r / r_inner) / np.tan(np.radians(15.0)) + np.pi * arm + 0.1 * rng.normal(size=m0)
+    pts = np.stack([r * np.cos(phi), r * np.sin(phi), 300.0 * rng.normal(size=m0)], axis=1)
+    big = r_outer / 20.0
+    while len(pts) < n:
+        need = min(n, len(pts) * children)
+        parents = pts[rng.permutation(len(pts))][: -(-need // children)]
+        kids = np.repeat(parents, children, axis=0)[:need]
+        off = _in_unit_ball(rng, need) * np.array([big, big, big / 10.0])
+        pts = kids + off
+        big *= 2.0 / 3.0
+    scale = 1.0 / (2.2 * r_outer)
+    return np.ascontiguousarray(0.5 + scale * pts[:n])
+
+
 DISTRIBUTIONS = dict(uniform=uniform, plummer=plummer, gmm=gmm, gaussian=gaussian,
-                     shell=shell, helix=helix)
+                     shell=shell, helix=helix, galaxy=galaxy)
 
 
 def points(kind: str, n: int, seed: int = 0) -> np.ndarray:
