@@ -73,6 +73,10 @@ enum fmm_prec { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
 /* fmm_opts.flags bits */
 #define FMM_FLAG_PROFILE 1  /* record per-stage device times (fmm_stage_times) */
 #define FMM_FLAG_ETA 2      /* use fmm_opts.eta; without it eta = 1 (median splits) */
+#define FMM_FLAG_TC_M2L 4   /* mixed form, p <= 12: M2L contractions on the tensor
+                               cores (tcgen05, split TF32) instead of the CUDA cores;
+                               same accuracy, slower at the orders measured (the
+                               fixed matrices are at most 13 x 13) */
 
 /* Stages of Algorithm 1 as timed by fmm_stage_times. */
 enum fmm_stage {
@@ -231,6 +235,14 @@ int fmm_plan_list(fmm_plan_t plan, int level, int kind, int64_t *ptr, int32_t *s
  * Errors: FMM_EINVAL, FMM_ECUDA.
  */
 int fmm_eval_expansions(fmm_plan_t plan, int which, double *out);
+
+/*
+ * fmm_eval_check -- synchronise the plan's stream and report device-side
+ * failures of the evaluations since the plan was built: FMM_ETIMEDOUT if a
+ * bounded wait inside a kernel ran out (its results are then invalid),
+ * FMM_OK otherwise. Errors: FMM_EINVAL, FMM_ECUDA.
+ */
+int fmm_eval_check(fmm_plan_t plan);
 
 /*
  * fmm_stage_times -- device milliseconds of each stage (enum fmm_stage) of

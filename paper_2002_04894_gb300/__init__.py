@@ -23,6 +23,7 @@ FMM_PREC_FP64, FMM_PREC_MIXED = 0, 1
 FMM_MAX_LEVELS, FMM_MAX_P = 24, 20
 FMM_FLAG_PROFILE = 1
 FMM_FLAG_ETA = 2
+FMM_FLAG_TC_M2L = 4
 STAGES = ("tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p")
 STATUS = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ENONFINITE",
           -4: "FMM_ECAPACITY", -5: "FMM_ETIMEDOUT", -6: "FMM_ECUDA"}
@@ -61,7 +62,8 @@ _LIB = None
 EXPORTS = ("fmm_plan", "fmm_eval", "fmm_destroy", "fmm_direct", "fmm_plan_stats",
            "fmm_plan_tree", "fmm_plan_list", "fmm_eval_expansions", "fmm_strerror",
            "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches",
-           "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy")
+           "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy",
+           "fmm_eval_check")
 FMM_NOALLOC_MAX_POINTS, FMM_NOALLOC_MAX_LEVELS = 4096, 12
 
 
@@ -97,6 +99,8 @@ def load(build: bool = True) -> C.CDLL:
     lib.fmm_plan_list.restype = i32
     lib.fmm_eval_expansions.argtypes = [vp, i32, vp]
     lib.fmm_eval_expansions.restype = i32
+    lib.fmm_eval_check.argtypes = [vp]
+    lib.fmm_eval_check.restype = i32
     lib.fmm_strerror.argtypes = [i32]
     lib.fmm_strerror.restype = C.c_char_p
     lib.fmm_last_cuda_error.restype = i32
@@ -208,7 +212,7 @@ class Plan:
 # ---------------------------------------------------------------------------
 def fmm_plan(points, levels: int, p: int, theta: float, prec: int = FMM_PREC_FP64,
              stream=None, allocator="torch", profile: bool = False, eta: float = 1.0,
-             bisections_per_level: int = 1) -> Plan:
+             bisections_per_level: int = 1, tc_m2l: bool = False) -> Plan:
     """Build the tree and connectivity for n x 3 `points`; eta in [0, 1] is
     the split adaptivity (1: balanced median splits, 0: cell bisection);
     bisections_per_level = 3 makes octree levels (`levels` counts bisections)."""
@@ -216,7 +220,8 @@ def fmm_plan(points, levels: int, p: int, theta: float, prec: int = FMM_PREC_FP6
     ptr, keep = _ptr(points)
     n = int(points.shape[0])
     dt = _dtype_code(points)
-    flags = (FMM_FLAG_PROFILE if profile else 0) | (FMM_FLAG_ETA if float(eta) != 1.0 else 0)
+    flags = ((FMM_FLAG_PROFILE if profile else 0) | (FMM_FLAG_ETA if float(eta) != 1.0 else 0)
+             | (FMM_FLAG_TC_M2L if tc_m2l else 0))
     opts = fmm_opts(int(levels), int(p), float(theta), int(prec), flags, float(eta),
                     int(bisections_per_level))
     alloc, cbs = (None, None)
@@ -314,6 +319,11 @@ def fmm_plan_list(plan: Plan, level: int, kind: str):
     _check(lib.fmm_plan_list(plan.handle, level, k, ptr.ctypes.data, src.ctypes.data),
            "fmm_plan_list")
     return ptr, src[: int(ptr[-1])]
+
+
+def fmm_eval_check(plan: Plan) -> None:
+    """Synchronise and raise if a device-side wait of an evaluation ran out."""
+    _check(load().fmm_eval_check(plan.handle), "fmm_eval_check")
 
 
 def fmm_eval_expansions(plan: Plan, which: str) -> np.ndarray:

@@ -158,7 +158,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     if (opts->p < 0 || opts->p > FMM_MAX_P) return FMM_EINVAL;
     if (!(opts->theta >= 0.0 && opts->theta < 1.0)) return FMM_EINVAL;
     if (opts->prec != FMM_PREC_FP64 && opts->prec != FMM_PREC_MIXED) return FMM_EINVAL;
-    if (opts->flags & ~(FMM_FLAG_PROFILE | FMM_FLAG_ETA)) return FMM_EINVAL;
+    if (opts->flags & ~(FMM_FLAG_PROFILE | FMM_FLAG_ETA | FMM_FLAG_TC_M2L)) return FMM_EINVAL;
     if ((opts->flags & FMM_FLAG_ETA) && !(opts->eta >= 0.0 && opts->eta <= 1.0)) return FMM_EINVAL;
     const int step = opts->bisections_per_level == 0 ? 1 : opts->bisections_per_level;
     if (step < 1 || step > 3 || opts->levels % step != 0) return FMM_EINVAL;
@@ -185,6 +185,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     }
     cudaGetDevice(&P.device);
     P.profile = (opts->flags & FMM_FLAG_PROFILE) != 0;
+    P.tc_m2l_opt = (opts->flags & FMM_FLAG_TC_M2L) != 0;
 
     auto fail = [&](int status) {
         release(P);
@@ -319,6 +320,16 @@ int fmm_eval(fmm_plan_t plan, const void *charges, void *potentials, void *field
         if (e != cudaSuccess) return cuda_status(e);
     }
     return cuda_status(cudaGetLastError());
+}
+
+int fmm_eval_check(fmm_plan_t plan) {
+    if (!plan) return FMM_EINVAL;
+    Plan &P = plan->P;
+    int herr[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(herr, P.d_err, 8, cudaMemcpyDeviceToHost, P.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return herr[1] & 16 ? FMM_ETIMEDOUT : FMM_OK;
 }
 
 void fmm_destroy(fmm_plan_t plan) {

@@ -65,6 +65,10 @@ struct Plan {
     // field, radius-scaled float multipoles for the single-precision M2L
     float *hl = nullptr, *qf = nullptr, *far_phi_f = nullptr, *far_E_f = nullptr;
     float4 *lgeo = nullptr;  // per leaf: centre hi (xyz, radius) | centre lo | half extents
+    bool m2l_tc = false;     // mixed form: M2L on the tensor cores (else the SIMT float kernel)
+    bool tc_m2l_opt = false; // FMM_FLAG_TC_M2L requested
+    void *tc_tab = nullptr;  // tensor-core M2L tables (per device and order, not owned)
+    int tc_ctas = 0;
     float2 *Mf = nullptr;
     double2 *Lh = nullptr;  // r^k-scaled locals accumulated by the float M2L
     // evaluation scratch
@@ -155,6 +159,9 @@ cudaError_t m2l_all(Plan &P);
 void m2m_level(Plan &P, int level);
 void l2l_level(Plan &P, int level);
 bool m2l_f32_supported(int p);
+bool m2l_tc_supported(int p);
+cudaError_t m2l_tc_setup(Plan &P);
+cudaError_t m2l_tc_launch(Plan &P);
 cudaError_t m2l_f32_setup(Plan &P);
 cudaError_t m2l_f32_all(Plan &P);
 cudaError_t mixed_setup(Plan &P);

@@ -33,18 +33,11 @@
 #include <vector>
 
 #include "fmm_internal.cuh"
+#include "m2l_common.cuh"
 
 namespace fmm {
 
 namespace {
-
-// weak pairs of every level, concatenated (levels lmin..lmax); passed by value
-struct PairTable {
-    const int32_t *tgt[FMM_MAX_LEVELS + 1];
-    const int32_t *src[FMM_MAX_LEVELS + 1];
-    long long off[FMM_MAX_LEVELS + 2];
-    int lmin, lmax;
-};
 
 __device__ __forceinline__ double2 mul_ipow(int m, double2 v) {  // i^m v
     switch (m & 3) {
@@ -67,39 +60,6 @@ __device__ __forceinline__ void fold_apply(const double *__restrict__ D, int n, 
             im = fma(transpose ? D[m * (n + 1) + k] : D[k * (n + 1) + m], v[m * stride].y, im);
         out[k * stride] = make_double2(re, im);
     }
-}
-
-// Segmented sum over lanes of equal target (the pair list is sorted by
-// target): after the five steps the first lane of each run holds the run's
-// sum. same[j] says whether lane + 2^j belongs to this lane's run.
-template <typename R>
-__device__ __forceinline__ R seg_sum(R v, const bool (&same)[5]) {
-#pragma unroll
-    for (int j = 0; j < 5; j++) {
-        const R o = __shfl_down_sync(0xffffffffu, v, 1 << j);
-        if (same[j]) v += o;
-    }
-    return v;
-}
-
-__device__ __forceinline__ void seg_setup(int64_t tgt, bool (&same)[5], bool &head) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int j = 0; j < 5; j++) {
-        const int64_t o = __shfl_down_sync(0xffffffffu, tgt, 1 << j);
-        same[j] = (lane + (1 << j) < 32) && o == tgt;
-    }
-    const int64_t up = __shfl_up_sync(0xffffffffu, tgt, 1);
-    head = tgt >= 0 && (lane == 0 || up != tgt);
-}
-
-__device__ __forceinline__ void pair_of(const PairTable &PT, int64_t g, int64_t &gt, int64_t &gs) {
-    int l = PT.lmin;
-    while (l < PT.lmax && g >= PT.off[l + 1]) l++;
-    const int64_t e = g - PT.off[l];
-    const int64_t boff = ((int64_t)1 << l) - 1;
-    gt = boff + PT.tgt[l][e];
-    gs = boff + PT.src[l][e];
 }
 
 __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ centre,
@@ -377,6 +337,8 @@ __global__ void k_l2l_rot(int level, int step, int p, const double *__restrict__
     }
 }
 
+}  // namespace
+
 long double factl(int n) {
     long double r = 1.0L;
     for (int i = 2; i <= n; i++) r *= (long double)i;
@@ -396,7 +358,6 @@ long double wigner_half_pi(int n, int k, int m) {
     return sqrtl(factl(n + k) * factl(n - k) * factl(n + m) * factl(n - m)) * tot;
 }
 
-}  // namespace
 
 // Tables for order p: D_n quadrants, axial coefficients, F_nm, 1/F_nm, 1/k.
 std::vector<double> m2l_tables(int p) {
@@ -814,10 +775,17 @@ bool m2l_f32_supported(int p) {
 
 // plan-time setup, so that evaluations are safe to capture into a graph
 cudaError_t m2l_f32_setup(Plan &P) {
-    if (!m2l_f32_supported(P.p)) return cudaSuccess;
+    // the SIMT float kernel by default; the tensor-core kernel on request, and
+    // for orders without a SIMT instance
+    const bool tc = m2l_tc_supported(P.p) && (P.tc_m2l_opt || !m2l_f32_supported(P.p));
+    if (!tc && !m2l_f32_supported(P.p)) return cudaSuccess;  // FP64 M2L
     P.Mf = (float2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(float2));
     P.Lh = (double2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(double2));
     if (!P.Mf || !P.Lh) return cudaErrorMemoryAllocation;
+    if (tc) {
+        P.m2l_tc = true;
+        return m2l_tc_setup(P);
+    }
     cudaError_t e = f32_tables_ready();
     if (e != cudaSuccess) return e;
     switch (P.p) {
@@ -840,7 +808,9 @@ cudaError_t m2l_f32_all(Plan &P) {
     cudaMemsetAsync(P.Lh, 0, (size_t)total * sizeof(double2), P.stream);
     const int64_t tot = total_weak(P);
     cudaError_t e = cudaSuccess;
-    if (tot > 0) {
+    if (tot > 0 && P.m2l_tc) {
+        e = m2l_tc_launch(P);
+    } else if (tot > 0) {
         switch (P.p) {
             case 4: e = launch_f32<4>(P, tot); break;
             case 6: e = launch_f32<6>(P, tot); break;
