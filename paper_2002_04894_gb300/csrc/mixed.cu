@@ -239,149 +239,163 @@ __global__ void k_leaf_geo(int B, const double *__restrict__ lo, const double *_
 }
 
 constexpr int kLeafChunk = 256;
+constexpr int kP2PThreads = 128;  // threads per work unit; one target each
+constexpr int kSrcTile = 128;     // sources staged per pass
 
-// Near field in float. One CTA per work unit (a tile of up to 128 targets of
-// one leaf; heaviest units first), one target point per thread. For every source leaf the offset between the two
-// leaf centres is formed once, error-free (float TwoSum on the centres' hi/lo
-// parts), together with a near/far flag: far when the gap g between the two
-// cells is at least half the sum of their radii. The float offsets then carry
-// an absolute error of about 2u (r_t + r_s + |offset|), and since strongly
-// connected leaves have |offset| < 3 max(r_t, r_s), every far pair's distance
-// (>= g) is known to ~11u relative: a single float per coordinate suffices,
-// and no two points can coincide. Near leaves (touching cells) keep the split
-// hi/lo offsets, whose difference is exact for close pairs.
+__device__ __forceinline__ void far_pair(float xh, float yh, float zh, const float4 s, float *a) {
+    const float dx = xh - s.x, dy = yh - s.y, dz = zh - s.z;
+    const float rinv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float qr = s.w * rinv;
+    const float qr3 = qr * (rinv * rinv);
+    a[0] += qr;
+    a[1] = fmaf(qr3, dx, a[1]);
+    a[2] = fmaf(qr3, dy, a[2]);
+    a[3] = fmaf(qr3, dz, a[3]);
+}
+
+// near (touching cells): split hi/lo offsets, coincident points skipped
+__device__ __forceinline__ void near_pair(float xh, float yh, float zh, float xl, float yl, float zl,
+                                          const float4 s, const float4 sl, float *a) {
+    const float dx = (xh - s.x) + (xl - sl.x);
+    const float dy = (yh - s.y) + (yl - sl.y);
+    const float dz = (zh - s.z) + (zl - sl.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float qr = s.w * rinv;
+    const float qr3 = qr * (rinv * rinv);
+    a[0] += qr;
+    a[1] = fmaf(qr3, dx, a[1]);
+    a[2] = fmaf(qr3, dy, a[2]);
+    a[3] = fmaf(qr3, dz, a[3]);
+}
+
+// Near field in float. One CTA per work unit (a tile of up to 128 targets
+// of one leaf; heaviest units first), one target point per thread. For every
+// source leaf the offset between the two leaf centres is formed once,
+// error-free (float TwoSum on the centres' hi/lo parts), together with a
+// near/far flag: far when the gap g between the two cells is at least half
+// the sum of their radii. The float offsets then carry an absolute error of
+// about 2u (r_t + r_s + |offset|), and since strongly connected leaves have
+// |offset| < 3 max(r_t, r_s), every far pair's distance (>= g) is known to
+// ~11u relative: a single float per coordinate suffices, and no two points
+// can coincide. Near leaves (touching cells) keep the split hi/lo offsets,
+// whose difference is exact for close pairs. Per target the sources are
+// summed in plain float over runs of 32 (full runs with a fixed trip count)
+// and the runs compensated (Kahan).
 template <typename OutT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kP2PThreads)
 k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const float4 *__restrict__ geo, const int32_t *__restrict__ sptr,
           const int32_t *__restrict__ ssrc, const int2 *__restrict__ units,
           const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
           const float *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
-    __shared__ float4 th[kThreads];     // source offset from the target centre (hi) and charge
-    __shared__ float4 tl[kThreads];     // lo parts (near leaves)
+    __shared__ float4 th[kSrcTile];     // source offset from the target centre (hi) and charge
+    __shared__ float4 tl[kSrcTile];     // lo parts (near leaves)
     __shared__ float4 dh[kLeafChunk];   // per source leaf: centre offset hi, near flag
     __shared__ float4 dl[kLeafChunk];   // centre offset lo
     __shared__ int2 rng[kLeafChunk];    // begin, count
+    static_assert(kP2PThreads == kP2PTile, "one target per thread");
     const int64_t off = ((int64_t)1 << B) - 1;
-    static_assert(kThreads == kP2PTile, "one target per thread");
     const int2 unit = units[blockIdx.x];
     const int t = unit.x;
     const int64_t gt = off + t;
     const int bt = begin[gt], nt = count[gt];
     const int e0 = sptr[t], e1 = sptr[t + 1];
     const float4 tc_h = geo[3 * t], tc_l = geo[3 * t + 1], tc_e = geo[3 * t + 2];
-    {
-        const int tb = unit.y;
-        const int i = tb + threadIdx.x;
-        const bool active = i < nt;
-        const float xh = active ? hl[bt + i] : 0.f, yh = active ? hl[n + bt + i] : 0.f,
-                    zh = active ? hl[2 * n + bt + i] : 0.f;
-        const float xl = active ? hl[3 * n + bt + i] : 0.f, yl = active ? hl[4 * n + bt + i] : 0.f,
-                    zl = active ? hl[5 * n + bt + i] : 0.f;
-        float phi = 0.f, cphi = 0.f, ex = 0.f, cex = 0.f, ey = 0.f, cey = 0.f, ez = 0.f, cez = 0.f;
-        for (int cb = e0; cb < e1; cb += kLeafChunk) {
-            const int clen = min(kLeafChunk, e1 - cb);
-            __syncthreads();
-            for (int k = threadIdx.x; k < clen; k += kThreads) {
-                const int s = ssrc[cb + k];
-                const float4 sh = geo[3 * s], sl = geo[3 * s + 1], se = geo[3 * s + 2];
-                float e_x, e_y, e_z;
-                const float dxh = two_sum(sh.x, -tc_h.x, e_x);
-                const float dyh = two_sum(sh.y, -tc_h.y, e_y);
-                const float dzh = two_sum(sh.z, -tc_h.z, e_z);
-                const float gx = fmaxf(0.f, fabsf(dxh) - (tc_e.x + se.x));
-                const float gy = fmaxf(0.f, fabsf(dyh) - (tc_e.y + se.y));
-                const float gz = fmaxf(0.f, fabsf(dzh) - (tc_e.z + se.z));
-                const float half = 0.5f * (tc_h.w + sh.w);
-                const bool far = gx * gx + gy * gy + gz * gz >= half * half && half > 0.f;
-                dh[k] = make_float4(dxh, dyh, dzh, far ? 1.f : 0.f);
-                dl[k] = make_float4(e_x + (sl.x - tc_l.x), e_y + (sl.y - tc_l.y), e_z + (sl.z - tc_l.z), 0.f);
-                rng[k] = make_int2(begin[off + s], count[off + s]);
-            }
-            __syncthreads();
-            for (int k = 0; k < clen; k++) {
-                const float4 d = dh[k];
-                const float4 dlo = dl[k];
-                const int bs = rng[k].x, ns = rng[k].y;
-                const bool far = d.w != 0.f;
-                for (int sb = 0; sb < ns; sb += kThreads) {
-                    const int j = sb + threadIdx.x;
-                    __syncthreads();
-                    if (j < ns) {
-                        const float ahx = hl[bs + j], ahy = hl[n + bs + j], ahz = hl[2 * n + bs + j];
-                        const float alx = hl[3 * n + bs + j], aly = hl[4 * n + bs + j],
-                                    alz = hl[5 * n + bs + j];
-                        const float q = qf[bs + j];
-                        if (far) {
-                            th[threadIdx.x] = make_float4((ahx + d.x) + (alx + dlo.x),
-                                                          (ahy + d.y) + (aly + dlo.y),
-                                                          (ahz + d.z) + (alz + dlo.z), q);
-                        } else {
-                            float ux, uy, uz;
-                            const float sx = two_sum(ahx, d.x, ux);
-                            const float sy = two_sum(ahy, d.y, uy);
-                            const float sz = two_sum(ahz, d.z, uz);
-                            th[threadIdx.x] = make_float4(sx, sy, sz, q);
-                            tl[threadIdx.x] = make_float4(ux + (alx + dlo.x), uy + (aly + dlo.y),
-                                                          uz + (alz + dlo.z), 0.f);
-                        }
+    const int tid = threadIdx.x;
+    const int i = unit.y + tid;
+    const bool active = i < nt;
+    float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
+    if (active) {
+        xh = hl[bt + i], yh = hl[n + bt + i], zh = hl[2 * n + bt + i];
+        xl = hl[3 * n + bt + i], yl = hl[4 * n + bt + i], zl = hl[5 * n + bt + i];
+    }
+    float sum[4], comp[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) sum[j] = comp[j] = 0.f;
+    for (int cb = e0; cb < e1; cb += kLeafChunk) {
+        const int clen = min(kLeafChunk, e1 - cb);
+        __syncthreads();
+        for (int k = tid; k < clen; k += kP2PThreads) {
+            const int s = ssrc[cb + k];
+            const float4 sh = geo[3 * s], sl = geo[3 * s + 1], se = geo[3 * s + 2];
+            float e_x, e_y, e_z;
+            const float dxh = two_sum(sh.x, -tc_h.x, e_x);
+            const float dyh = two_sum(sh.y, -tc_h.y, e_y);
+            const float dzh = two_sum(sh.z, -tc_h.z, e_z);
+            const float gx = fmaxf(0.f, fabsf(dxh) - (tc_e.x + se.x));
+            const float gy = fmaxf(0.f, fabsf(dyh) - (tc_e.y + se.y));
+            const float gz = fmaxf(0.f, fabsf(dzh) - (tc_e.z + se.z));
+            const float half = 0.5f * (tc_h.w + sh.w);
+            const bool far = gx * gx + gy * gy + gz * gz >= half * half && half > 0.f;
+            dh[k] = make_float4(dxh, dyh, dzh, far ? 1.f : 0.f);
+            dl[k] = make_float4(e_x + (sl.x - tc_l.x), e_y + (sl.y - tc_l.y), e_z + (sl.z - tc_l.z), 0.f);
+            rng[k] = make_int2(begin[off + s], count[off + s]);
+        }
+        __syncthreads();
+        for (int k = 0; k < clen; k++) {
+            const float4 d = dh[k];
+            const float4 dlo = dl[k];
+            const int bs = rng[k].x, ns = rng[k].y;
+            const bool far = d.w != 0.f;
+            for (int sb = 0; sb < ns; sb += kSrcTile) {
+                __syncthreads();
+                const int j = sb + tid;
+                if (j < ns) {
+                    const float ahx = hl[bs + j], ahy = hl[n + bs + j], ahz = hl[2 * n + bs + j];
+                    const float alx = hl[3 * n + bs + j], aly = hl[4 * n + bs + j], alz = hl[5 * n + bs + j];
+                    const float q = qf[bs + j];
+                    if (far) {
+                        th[tid] = make_float4((ahx + d.x) + (alx + dlo.x), (ahy + d.y) + (aly + dlo.y),
+                                              (ahz + d.z) + (alz + dlo.z), q);
+                    } else {
+                        float ux, uy, uz;
+                        const float sx = two_sum(ahx, d.x, ux);
+                        const float sy = two_sum(ahy, d.y, uy);
+                        const float sz = two_sum(ahz, d.z, uz);
+                        th[tid] = make_float4(sx, sy, sz, q);
+                        tl[tid] = make_float4(ux + (alx + dlo.x), uy + (aly + dlo.y), uz + (alz + dlo.z), 0.f);
                     }
-                    __syncthreads();
-                    const int mcount = min(kThreads, ns - sb);
-                    // plain float sums over runs of 32 sources, compensated once per run
-                    for (int j0 = 0; j0 < mcount; j0 += 32) {
-                        const int j1 = min(mcount, j0 + 32);
-                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                        if (far) {
-                            // cells apart: no coincident points, single-float offsets
-#pragma unroll 4
-                            for (int jj = j0; jj < j1; jj++) {
-                                const float4 s = th[jj];
-                                const float dx = xh - s.x, dy = yh - s.y, dz = zh - s.z;
-                                const float rinv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                                const float qr = s.w * rinv;
-                                const float qr3 = qr * (rinv * rinv);
-                                a0 += qr;
-                                a1 = fmaf(qr3, dx, a1);
-                                a2 = fmaf(qr3, dy, a2);
-                                a3 = fmaf(qr3, dz, a3);
-                            }
+                }
+                __syncthreads();
+                const int mcount = min(kSrcTile, ns - sb);
+                for (int j0 = 0; j0 < mcount; j0 += 32) {
+                    const int cnt = min(32, mcount - j0);
+                    float a[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (far) {
+                        if (cnt == 32) {
+#pragma unroll 8
+                            for (int jj = 0; jj < 32; jj++) far_pair(xh, yh, zh, th[j0 + jj], a);
                         } else {
 #pragma unroll 4
-                            for (int jj = j0; jj < j1; jj++) {
-                                const float4 s = th[jj];
-                                const float4 sl = tl[jj];
-                                const float dx = (xh - s.x) + (xl - sl.x);
-                                const float dy = (yh - s.y) + (yl - sl.y);
-                                const float dz = (zh - s.z) + (zl - sl.z);
-                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                                const float qr = s.w * rinv;
-                                const float qr3 = qr * (rinv * rinv);
-                                a0 += qr;
-                                a1 = fmaf(qr3, dx, a1);
-                                a2 = fmaf(qr3, dy, a2);
-                                a3 = fmaf(qr3, dz, a3);
-                            }
+                            for (int jj = 0; jj < cnt; jj++) far_pair(xh, yh, zh, th[j0 + jj], a);
                         }
-                        kahan(phi, cphi, a0);
-                        kahan(ex, cex, a1);
-                        kahan(ey, cey, a2);
-                        kahan(ez, cez, a3);
+                    } else {
+                        if (cnt == 32) {
+#pragma unroll 8
+                            for (int jj = 0; jj < 32; jj++)
+                                near_pair(xh, yh, zh, xl, yl, zl, th[j0 + jj], tl[j0 + jj], a);
+                        } else {
+#pragma unroll 4
+                            for (int jj = 0; jj < cnt; jj++)
+                                near_pair(xh, yh, zh, xl, yl, zl, th[j0 + jj], tl[j0 + jj], a);
+                        }
                     }
+#pragma unroll
+                    for (int q = 0; q < 4; q++) kahan(sum[q], comp[q], a[q]);
                 }
             }
         }
-        if (active) {
-            const int64_t a = bt + i;
-            const int64_t o = perm[a];
-            pot[o] = (OutT)((double)far_phi[a] + ((double)phi - (double)cphi));
-            if (field) {
-                field[3 * o] = (OutT)((double)far_E[a] + ((double)ex - (double)cex));
-                field[3 * o + 1] = (OutT)((double)far_E[n + a] + ((double)ey - (double)cey));
-                field[3 * o + 2] = (OutT)((double)far_E[2 * n + a] + ((double)ez - (double)cez));
-            }
+    }
+    if (active) {
+        const int64_t a = bt + i;
+        const int64_t o = perm[a];
+        pot[o] = (OutT)((double)far_phi[a] + ((double)sum[0] - (double)comp[0]));
+        if (field) {
+            field[3 * o] = (OutT)((double)far_E[a] + ((double)sum[1] - (double)comp[1]));
+            field[3 * o + 1] = (OutT)((double)far_E[n + a] + ((double)sum[2] - (double)comp[2]));
+            field[3 * o + 2] = (OutT)((double)far_E[2 * n + a] + ((double)sum[3] - (double)comp[3]));
         }
     }
 }
@@ -423,11 +437,11 @@ cudaError_t mixed_l2p(Plan &P) {
 
 cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
     if (dtype == FMM_F64)
-        FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.p2p_nunits, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
+        FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.p2p_nunits, kP2PThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
                    P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.perm,
                    P.far_phi_f, P.far_E_f, (double *)pot, (double *)field);
     else
-        FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.p2p_nunits, kThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
+        FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.p2p_nunits, kP2PThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
                    P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.perm,
                    P.far_phi_f, P.far_E_f, (float *)pot, (float *)field);
     return cudaGetLastError();
