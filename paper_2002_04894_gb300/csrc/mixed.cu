@@ -240,38 +240,56 @@ __global__ void k_leaf_geo(int B, const double *__restrict__ lo, const double *_
 
 constexpr int kLeafChunk = 256;
 constexpr int kP2PThreads = 128;  // threads per work unit; one target each
-constexpr int kSrcTile = 128;     // sources staged per pass
+constexpr int kSrcTile = 128;     // sources staged per pass (64 pairs)
+constexpr float kPadFar = 1.0e18f;  // padding source: zero charge, far away
 
-__device__ __forceinline__ void far_pair(float xh, float yh, float zh, const float4 s, float *a) {
-    const float dx = xh - s.x, dy = yh - s.y, dz = zh - s.z;
-    const float rinv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    const float qr = s.w * rinv;
-    const float qr3 = qr * (rinv * rinv);
-    a[0] += qr;
-    a[1] = fmaf(qr3, dx, a[1]);
-    a[2] = fmaf(qr3, dy, a[2]);
-    a[3] = fmaf(qr3, dz, a[3]);
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// One target against two sources at once, in packed float2 arithmetic. The
+// sources of a pair are staged as A = (-x0, -x1, -y0, -y1) and
+// B = (-z0, -z1, q0, q1), offsets from the target leaf's centre; the sums run
+// separately over even and odd sources.
+// far (cells apart): single-float offsets
+__device__ __forceinline__ void far_pair2(float2 X, float2 Y, float2 Z, const float4 A, const float4 B,
+                                          float2 *a) {
+    const float2 dx = add2(X, make_float2(A.x, A.y));
+    const float2 dy = add2(Y, make_float2(A.z, A.w));
+    const float2 dz = add2(Z, make_float2(B.x, B.y));
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 qr = mul2(make_float2(B.z, B.w), rinv);
+    const float2 qr3 = mul2(qr, mul2(rinv, rinv));
+    a[0] = add2(a[0], qr);
+    a[1] = fma2(qr3, dx, a[1]);
+    a[2] = fma2(qr3, dy, a[2]);
+    a[3] = fma2(qr3, dz, a[3]);
 }
 
-// near (touching cells): split hi/lo offsets, coincident points skipped
-__device__ __forceinline__ void near_pair(float xh, float yh, float zh, float xl, float yl, float zl,
-                                          const float4 s, const float4 sl, float *a) {
-    const float dx = (xh - s.x) + (xl - sl.x);
-    const float dy = (yh - s.y) + (yl - sl.y);
-    const float dz = (zh - s.z) + (zl - sl.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-    const float qr = s.w * rinv;
-    const float qr3 = qr * (rinv * rinv);
-    a[0] += qr;
-    a[1] = fmaf(qr3, dx, a[1]);
-    a[2] = fmaf(qr3, dy, a[2]);
-    a[3] = fmaf(qr3, dz, a[3]);
+// near (touching cells): split hi/lo offsets (lo parts staged as
+// C = (-xl0, -xl1, -yl0, -yl1), D = (-zl0, -zl1, ., .)), coincident points
+// skipped
+__device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 XL, float2 YL, float2 ZL,
+                                           const float4 A, const float4 B, const float4 C, const float4 D,
+                                           float2 *a) {
+    const float2 dx = add2(add2(X, make_float2(A.x, A.y)), add2(XL, make_float2(C.x, C.y)));
+    const float2 dy = add2(add2(Y, make_float2(A.z, A.w)), add2(YL, make_float2(C.z, C.w)));
+    const float2 dz = add2(add2(Z, make_float2(B.x, B.y)), add2(ZL, make_float2(D.x, D.y)));
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    const float2 rinv = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+    const float2 qr = mul2(make_float2(B.z, B.w), rinv);
+    const float2 qr3 = mul2(qr, mul2(rinv, rinv));
+    a[0] = add2(a[0], qr);
+    a[1] = fma2(qr3, dx, a[1]);
+    a[2] = fma2(qr3, dy, a[2]);
+    a[3] = fma2(qr3, dz, a[3]);
 }
 
 // Near field in float. One CTA per work unit (a tile of up to 128 targets
-// of one leaf; heaviest units first), one target point per thread. For every
-// source leaf the offset between the two leaf centres is formed once,
+// of one leaf; heaviest units first), one target point per thread, two
+// sources per step in packed float2 arithmetic (FFMA2/FADD2/FMUL2). For
+// every source leaf the offset between the two leaf centres is formed once,
 // error-free (float TwoSum on the centres' hi/lo parts), together with a
 // near/far flag: far when the gap g between the two cells is at least half
 // the sum of their radii. The float offsets then carry an absolute error of
@@ -290,8 +308,8 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
           const int32_t *__restrict__ ssrc, const int2 *__restrict__ units,
           const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
           const float *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
-    __shared__ float4 th[kSrcTile];     // source offset from the target centre (hi) and charge
-    __shared__ float4 tl[kSrcTile];     // lo parts (near leaves)
+    __shared__ float4 sA[kSrcTile / 2], sB[kSrcTile / 2];  // hi parts and charges, per source pair
+    __shared__ float4 sC[kSrcTile / 2], sD[kSrcTile / 2];  // lo parts (near leaves)
     __shared__ float4 dh[kLeafChunk];   // per source leaf: centre offset hi, near flag
     __shared__ float4 dl[kLeafChunk];   // centre offset lo
     __shared__ int2 rng[kLeafChunk];    // begin, count
@@ -311,9 +329,14 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
         xh = hl[bt + i], yh = hl[n + bt + i], zh = hl[2 * n + bt + i];
         xl = hl[3 * n + bt + i], yl = hl[4 * n + bt + i], zl = hl[5 * n + bt + i];
     }
+    const float2 X = make_float2(xh, xh), Y = make_float2(yh, yh), Z = make_float2(zh, zh);
+    const float2 XL = make_float2(xl, xl), YL = make_float2(yl, yl), ZL = make_float2(zl, zl);
     float sum[4], comp[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) sum[j] = comp[j] = 0.f;
+    float *fA = (float *)sA, *fB = (float *)sB, *fC = (float *)sC, *fD = (float *)sD;
+    // slot of this thread's staged source: pair tid/2, component tid&1
+    const int sp = (tid >> 1) * 4 + (tid & 1);
     for (int cb = e0; cb < e1; cb += kLeafChunk) {
         const int clen = min(kLeafChunk, e1 - cb);
         __syncthreads();
@@ -342,48 +365,63 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
             for (int sb = 0; sb < ns; sb += kSrcTile) {
                 __syncthreads();
                 const int j = sb + tid;
+                float sx = kPadFar, sy = kPadFar, sz = kPadFar, q = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
                 if (j < ns) {
                     const float ahx = hl[bs + j], ahy = hl[n + bs + j], ahz = hl[2 * n + bs + j];
                     const float alx = hl[3 * n + bs + j], aly = hl[4 * n + bs + j], alz = hl[5 * n + bs + j];
-                    const float q = qf[bs + j];
+                    q = qf[bs + j];
                     if (far) {
-                        th[tid] = make_float4((ahx + d.x) + (alx + dlo.x), (ahy + d.y) + (aly + dlo.y),
-                                              (ahz + d.z) + (alz + dlo.z), q);
+                        sx = (ahx + d.x) + (alx + dlo.x);
+                        sy = (ahy + d.y) + (aly + dlo.y);
+                        sz = (ahz + d.z) + (alz + dlo.z);
                     } else {
-                        float ux, uy, uz;
-                        const float sx = two_sum(ahx, d.x, ux);
-                        const float sy = two_sum(ahy, d.y, uy);
-                        const float sz = two_sum(ahz, d.z, uz);
-                        th[tid] = make_float4(sx, sy, sz, q);
-                        tl[tid] = make_float4(ux + (alx + dlo.x), uy + (aly + dlo.y), uz + (alz + dlo.z), 0.f);
+                        float ex, ey, ez;
+                        sx = two_sum(ahx, d.x, ex);
+                        sy = two_sum(ahy, d.y, ey);
+                        sz = two_sum(ahz, d.z, ez);
+                        ux = ex + (alx + dlo.x);
+                        uy = ey + (aly + dlo.y);
+                        uz = ez + (alz + dlo.z);
                     }
+                }
+                fA[sp] = -sx;
+                fA[sp + 2] = -sy;
+                fB[sp] = -sz;
+                fB[sp + 2] = q;
+                if (!far) {
+                    fC[sp] = -ux;
+                    fC[sp + 2] = -uy;
+                    fD[sp] = -uz;
                 }
                 __syncthreads();
                 const int mcount = min(kSrcTile, ns - sb);
                 for (int j0 = 0; j0 < mcount; j0 += 32) {
-                    const int cnt = min(32, mcount - j0);
-                    float a[4] = {0.f, 0.f, 0.f, 0.f};
+                    const int npair = (min(32, mcount - j0) + 1) >> 1;
+                    const int p0 = j0 >> 1;
+                    float2 a[4];
+#pragma unroll
+                    for (int c = 0; c < 4; c++) a[c] = make_float2(0.f, 0.f);
                     if (far) {
-                        if (cnt == 32) {
+                        if (npair == 16) {
 #pragma unroll 8
-                            for (int jj = 0; jj < 32; jj++) far_pair(xh, yh, zh, th[j0 + jj], a);
+                            for (int pp = 0; pp < 16; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
                         } else {
 #pragma unroll 4
-                            for (int jj = 0; jj < cnt; jj++) far_pair(xh, yh, zh, th[j0 + jj], a);
+                            for (int pp = 0; pp < npair; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
                         }
                     } else {
-                        if (cnt == 32) {
+                        if (npair == 16) {
 #pragma unroll 8
-                            for (int jj = 0; jj < 32; jj++)
-                                near_pair(xh, yh, zh, xl, yl, zl, th[j0 + jj], tl[j0 + jj], a);
+                            for (int pp = 0; pp < 16; pp++)
+                                near_pair2(X, Y, Z, XL, YL, ZL, sA[p0 + pp], sB[p0 + pp], sC[p0 + pp], sD[p0 + pp], a);
                         } else {
 #pragma unroll 4
-                            for (int jj = 0; jj < cnt; jj++)
-                                near_pair(xh, yh, zh, xl, yl, zl, th[j0 + jj], tl[j0 + jj], a);
+                            for (int pp = 0; pp < npair; pp++)
+                                near_pair2(X, Y, Z, XL, YL, ZL, sA[p0 + pp], sB[p0 + pp], sC[p0 + pp], sD[p0 + pp], a);
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; q++) kahan(sum[q], comp[q], a[q]);
+                    for (int c = 0; c < 4; c++) kahan(sum[c], comp[c], a[c].x + a[c].y);
                 }
             }
         }
