@@ -534,11 +534,17 @@ __device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, float2 *V, i
     for (int m = 0; m <= N; m++) V[tri(N, m) * T] = fipow(m, u[m]);
 }
 
-// inverse rotation of degree N; segmented reduction over lanes of equal
-// target, then the run's first lane adds into the scaled local Lh (double)
+constexpr int kRedStride = 36;  // floats per lane row of the per-warp transpose buffer
+
+// inverse rotation of degree N, then the sum over the warp's pairs into the
+// scaled local Lh (double) of their target: a warp whose valid lanes share
+// one target (the common case: the pair list is sorted by target) transposes
+// its 2 (N+1) values per lane through shared memory and adds each column with
+// one atomic; otherwise a segmented shuffle sum over runs of equal target
 template <int N>
 __device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 ebv,
-                                     double2 *__restrict__ Lh, unsigned same_mask, bool head) {
+                                     double2 *__restrict__ Lh, unsigned same_mask, bool head,
+                                     int uniform_tgt, double2 *__restrict__ Lbase, int nc, float *red) {
     float2 u[N + 1], w[N + 1];
 #pragma unroll
     for (int m = 0; m <= N; m++) {
@@ -559,7 +565,33 @@ __device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 e
     for (int l = 0; l <= N; l++) {
         const int c = tri(N, l);
         const float2 t = fmulc(fipow(4 - (l & 3), u[l]), ph);
-        float rx = t.x * c_F[c], ry = t.y * c_F[c];
+        u[l] = make_float2(t.x * c_F[c], t.y * c_F[c]);
+        ph = fmulc(ph, ea);
+    }
+    if (N <= 15 && uniform_tgt >= 0) {  // 2 (N+1) <= 32 columns, one per lane
+        const int lane = threadIdx.x & 31;
+        float *row = red + lane * kRedStride;
+#pragma unroll
+        for (int l = 0; l <= N; l++) {
+            row[l] = u[l].x;
+            row[16 + l] = u[l].y;
+        }
+        __syncwarp();
+        const int col = lane <= N ? lane : (lane < 2 * (N + 1) ? 16 + lane - (N + 1) : -1);
+        if (col >= 0) {
+            float s = 0.f;
+#pragma unroll 8
+            for (int i = 0; i < 32; i++) s += red[i * kRedStride + col];
+            double *dst = (double *)&Lbase[(int64_t)uniform_tgt * nc + tri(N, col & 15)];
+            atomicAdd(dst + (col >= 16 ? 1 : 0), (double)s);
+        }
+        __syncwarp();
+        return;
+    }
+#pragma unroll
+    for (int l = 0; l <= N; l++) {
+        const int c = tri(N, l);
+        float rx = u[l].x, ry = u[l].y;
 #pragma unroll
         for (int j = 0; j < 5; j++) {
             const float ox = __shfl_down_sync(0xffffffffu, rx, 1 << j);
@@ -573,7 +605,6 @@ __device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 e
             atomicAdd(&Lh[c].x, (double)rx);
             atomicAdd(&Lh[c].y, (double)ry);
         }
-        ph = fmulc(ph, ea);
     }
 }
 
@@ -621,9 +652,10 @@ struct Seq {
         Seq<P, N + 1>::axial(V, T, qs, qt, rinv);
     }
     __device__ static __forceinline__ void bwd(const float2 *V, int T, float2 ea, float2 ebv,
-                                               double2 *Lh, unsigned same, bool head) {
-        bwd_deg<N>(V, T, ea, ebv, Lh, same, head);
-        Seq<P, N + 1>::bwd(V, T, ea, ebv, Lh, same, head);
+                                               double2 *Lh, unsigned same, bool head, int ut,
+                                               double2 *Lbase, int nc, float *red) {
+        bwd_deg<N>(V, T, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
+        Seq<P, N + 1>::bwd(V, T, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
     }
 };
 template <int P>
@@ -631,7 +663,7 @@ struct Seq<P, P + 1> {
     __device__ static __forceinline__ void fwd(const float2 *, float2 *, int, float2, float2) {}
     __device__ static __forceinline__ void axial(float2 *, int, float, float, float) {}
     __device__ static __forceinline__ void bwd(const float2 *, int, float2, float2, double2 *,
-                                               unsigned, bool) {}
+                                               unsigned, bool, int, double2 *, int, float *) {}
 };
 
 constexpr int kF32Threads = 128;
@@ -677,7 +709,13 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
         for (int c = 0; c < NC; c++) v[c * kF32Threads] = make_float2(0.f, 0.f);
     }
     Seq<P, 0>::axial(v, kF32Threads, qs, qt, rinv);
-    Seq<P, 0>::bwd(v, kF32Threads, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head);
+    // the warp's pairs share one target (invalid lanes add zeros): transpose path
+    const int t32 = gt >= 0 ? (int)gt : -1;
+    const int tmax = __reduce_max_sync(0xffffffffu, t32);
+    const bool uniform = __all_sync(0xffffffffu, t32 == tmax || t32 < 0);
+    float *red = (float *)(smf + NC * kF32Threads) + (tid >> 5) * 32 * kRedStride;
+    Seq<P, 0>::bwd(v, kF32Threads, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head,
+                   uniform ? tmax : -1, Lh, NC, red);
 }
 
 // Mhat = M / r^n in float, every box (levels >= 1)
@@ -755,13 +793,13 @@ template <int P>
 cudaError_t attr_f32() {
     constexpr int NC = (P + 1) * (P + 2) / 2;
     return cudaFuncSetAttribute(k_m2l_rot_f32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((size_t)kF32Threads * NC * 8));
+                                (int)((size_t)kF32Threads * NC * 8 + kF32Threads * kRedStride * 4));
 }
 
 template <int P>
 cudaError_t launch_f32(Plan &Pl, int64_t tot) {
     constexpr int NC = (P + 1) * (P + 2) / 2;
-    const size_t smem = (size_t)kF32Threads * NC * 8;
+    const size_t smem = (size_t)kF32Threads * NC * 8 + kF32Threads * kRedStride * 4;
     FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)((tot + kF32Threads - 1) / kF32Threads), kF32Threads, smem,
                Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh);
     return cudaGetLastError();
