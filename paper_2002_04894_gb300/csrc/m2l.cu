@@ -181,23 +181,65 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
 // back rotation with conjugate phases. One child per thread.
 // ---------------------------------------------------------------------------
 
-// M2M in the rotational form, one child per thread; the parent's multipole
-// (zeroed beforehand) receives both children's shifted expansions atomically.
+// M2M and L2L in the rotational form, a group of kGrp = 4 threads per child
+// box: the child's coefficient vectors live in shared memory (interleaved
+// over the block's children with a padded stride, so that the group's
+// threads and neighbouring groups fall on different banks), and each thread
+// of the group computes every fourth output of the folds and of the axial
+// shift. This splits each child's serial multiply-add chains four ways and
+// packs four times as many threads into the shared memory a child needs.
 //   multipole, rotated frame (Mt = F M):  Mt'_n^m = F_nm sum_k rho^k/k! Mt_{n-k}^m / F_{n-k,m}
+//   local, rotated frame (Lt = L / F):   Lt'_j^i = sum_{k>=j} Lt_k^i F_ki rho^{k-j}/(k-j)! / F_ji
+constexpr int kGrp = 4;
+constexpr int kGrpThreads = 128;  // 32 children per block
+
+struct GrpCtx {
+    int lane, stride;  // lane within the group, element stride of the interleaved arrays
+};
+
+__device__ __forceinline__ double2 cpow(double2 z, int e) {
+    double2 r = make_double2(1.0, 0.0);
+    for (int i = 0; i < e; i++) r = cmul(r, z);
+    return r;
+}
+
+// out_k (k = lane, lane + 4, ...; k <= n) = fold(D^n) of in, times
+// (k ? 2 : 1) * post^k when post is given
+__device__ __forceinline__ void fold_grp(const double *__restrict__ D, int n, const double2 *in,
+                                         double2 *out, const GrpCtx &g, bool transpose, bool scale,
+                                         double2 post) {
+    const double2 step = cpow(post, kGrp);
+    double2 pk = cpow(post, g.lane);
+    for (int k = g.lane; k <= n; k += kGrp) {
+        double re = 0.0, im = 0.0;
+        const int par = (n + k) & 1;
+        for (int m = par; m <= n; m += 2)
+            re = fma(transpose ? D[m * (n + 1) + k] : D[k * (n + 1) + m], in[m * g.stride].x, re);
+        for (int m = 1 - par; m <= n; m += 2)
+            im = fma(transpose ? D[m * (n + 1) + k] : D[k * (n + 1) + m], in[m * g.stride].y, im);
+        double2 r = make_double2(re, im);
+        if (scale) r = cscale(cmul(r, pk), k ? 2.0 : 1.0);
+        out[k * g.stride] = r;
+        pk = cmul(pk, step);
+    }
+}
+
 __global__ void k_m2m_rot(int level, int step, int p, const double *__restrict__ centre, double2 *M,
                           const double *__restrict__ gtab, int ntab) {
     extern __shared__ double2 sm2[];
-    const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
-    double2 *V = sm2, *U = V + nc * T, *W = U + (p + 1) * T;
-    double *tab = (double *)(W + (p + 1) * T);
-    for (int i = tid; i < ntab; i += T) tab[i] = gtab[i];
+    const int nc = ncoef(p), C = blockDim.x / kGrp, S = C + 1, tid = threadIdx.x;
+    double2 *V = sm2, *U = V + nc * S, *W = U + (p + 1) * S;
+    double *tab = (double *)(W + (p + 1) * S);
+    for (int i = tid; i < ntab; i += blockDim.x) tab[i] = gtab[i];
     __syncthreads();
     const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
     const double *Dt = tab, *Ft = tab + 2 * nD, *iFt = Ft + nc, *ik = iFt + nc;
-    double2 *v = V + tid, *u = U + tid, *x = W + tid;
-    const int64_t j = blockIdx.x * (int64_t)T + tid;  // child index within level
-    if (j >= ((int64_t)1 << level)) return;
-    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = ((gc + 1) >> step) - 1;  // ancestor step levels up
+    const int grp = tid / kGrp;
+    const GrpCtx g{tid % kGrp, S};
+    double2 *v = V + grp, *u = U + grp, *x = W + grp;
+    const int64_t j = blockIdx.x * (int64_t)C + grp;  // child index within level
+    const bool valid = j < ((int64_t)1 << level);
+    const int64_t gc = ((int64_t)1 << level) - 1 + (valid ? j : 0), gp = ((gc + 1) >> step) - 1;
     const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
                  dz = centre[3 * gc + 2] - centre[3 * gp + 2];
     const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
@@ -205,59 +247,67 @@ __global__ void k_m2m_rot(int level, int step, int p, const double *__restrict__
     const double2 ea = rxy > 0.0 ? make_double2(dx * irxy, dy * irxy) : make_double2(1.0, 0.0);
     const double2 eb = rho > 0.0 ? make_double2(dz * irho, rxy * irho) : make_double2(1.0, 0.0);
     const double2 eai = make_double2(ea.y, -ea.x), ebc = cconj(eb), eac = cconj(ea);
+    const double2 one = make_double2(1.0, 0.0);
     // forward rotation of the child's multipole -> v (F-normalised, rotated frame)
     const double *Dn = Dt;
     for (int n = 0; n <= p; n++) {
-        double2 ph = make_double2(1.0, 0.0);
-        for (int m = 0; m <= n; m++) {
-            const int c = tri(n, m);
-            u[m * T] = cscale(cmul(M[gc * nc + c], ph), Ft[c] * (m ? 2.0 : 1.0));
-            ph = cmul(ph, eai);
+        {
+            const double2 st = cpow(eai, kGrp);
+            double2 ph = cpow(eai, g.lane);
+            for (int m = g.lane; m <= n; m += kGrp) {
+                const int c = tri(n, m);
+                const double2 mv = valid ? M[gc * nc + c] : make_double2(0.0, 0.0);
+                u[m * S] = cscale(cmul(mv, ph), Ft[c] * (m ? 2.0 : 1.0));
+                ph = cmul(ph, st);
+            }
         }
-        fold_apply(Dn, n, u, x, T, false);
-        double2 pb = make_double2(1.0, 0.0);
-        for (int k = 0; k <= n; k++) {
-            x[k * T] = cscale(cmul(x[k * T], pb), k ? 2.0 : 1.0);
-            pb = cmul(pb, eb);
-        }
-        fold_apply(Dn, n, x, u, T, true);
-        for (int m = 0; m <= n; m++) v[tri(n, m) * T] = mul_ipow(m, u[m * T]);
+        __syncwarp();
+        fold_grp(Dn, n, u, x, g, false, true, eb);
+        __syncwarp();
+        fold_grp(Dn, n, x, u, g, true, false, one);
+        __syncwarp();
+        for (int m = g.lane; m <= n; m += kGrp) v[tri(n, m) * S] = mul_ipow(m, u[m * S]);
         Dn += (n + 1) * (n + 1);
     }
+    __syncwarp();
     // axial shift, order by order
     for (int m = 0; m <= p; m++) {
-        for (int n = m; n <= p; n++) u[(n - m) * T] = cscale(v[tri(n, m) * T], iFt[tri(n, m)]);
-        for (int n = m; n <= p; n++) {
+        for (int n = m + g.lane; n <= p; n += kGrp) u[(n - m) * S] = cscale(v[tri(n, m) * S], iFt[tri(n, m)]);
+        __syncwarp();
+        for (int n = m + g.lane; n <= p; n += kGrp) {
             double re = 0.0, im = 0.0, f = 1.0;
             for (int k = 0; k <= n - m; k++) {
-                const double2 t = u[(n - m - k) * T];
+                const double2 t = u[(n - m - k) * S];
                 re = fma(f, t.x, re);
                 im = fma(f, t.y, im);
                 f = f * rho * ik[k + 1];
             }
-            v[tri(n, m) * T] = cscale(make_double2(re, im), Ft[tri(n, m)]);
+            v[tri(n, m) * S] = cscale(make_double2(re, im), Ft[tri(n, m)]);
         }
+        __syncwarp();
     }
     // inverse rotation; add into the parent
     Dn = Dt;
     for (int n = 0; n <= p; n++) {
-        for (int m = 0; m <= n; m++)
-            u[m * T] = cscale(mul_ipow(4 - (m & 3), v[tri(n, m) * T]), m ? 2.0 : 1.0);
-        fold_apply(Dn, n, u, x, T, false);
-        double2 pb = make_double2(1.0, 0.0);
-        for (int k = 0; k <= n; k++) {
-            x[k * T] = cscale(cmul(x[k * T], pb), k ? 2.0 : 1.0);
-            pb = cmul(pb, ebc);
+        for (int m = g.lane; m <= n; m += kGrp)
+            u[m * S] = cscale(mul_ipow(4 - (m & 3), v[tri(n, m) * S]), m ? 2.0 : 1.0);
+        __syncwarp();
+        fold_grp(Dn, n, u, x, g, false, true, ebc);
+        __syncwarp();
+        fold_grp(Dn, n, x, u, g, true, false, one);
+        __syncwarp();
+        if (valid) {
+            const double2 st = cpow(eac, kGrp);
+            double2 ph = cpow(eac, g.lane);
+            for (int m = g.lane; m <= n; m += kGrp) {
+                const int c = tri(n, m);
+                const double2 r = cscale(cmul(mul_ipow(m, u[m * S]), ph), iFt[c]);
+                atomicAdd(&M[gp * nc + c].x, r.x);
+                atomicAdd(&M[gp * nc + c].y, r.y);
+                ph = cmul(ph, st);
+            }
         }
-        fold_apply(Dn, n, x, u, T, true);
-        double2 ph = make_double2(1.0, 0.0);
-        for (int m = 0; m <= n; m++) {
-            const int c = tri(n, m);
-            const double2 r = cscale(cmul(mul_ipow(m, u[m * T]), ph), iFt[c]);
-            atomicAdd(&M[gp * nc + c].x, r.x);
-            atomicAdd(&M[gp * nc + c].y, r.y);
-            ph = cmul(ph, eac);
-        }
+        __syncwarp();
         Dn += (n + 1) * (n + 1);
     }
 }
@@ -265,74 +315,84 @@ __global__ void k_m2m_rot(int level, int step, int p, const double *__restrict__
 __global__ void k_l2l_rot(int level, int step, int p, const double *__restrict__ centre, double2 *L,
                           const double *__restrict__ gtab, int ntab) {
     extern __shared__ double2 sm2[];
-    const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
-    double2 *V = sm2, *U = V + nc * T, *W = U + (p + 1) * T;
-    double *tab = (double *)(W + (p + 1) * T);
-    for (int i = tid; i < ntab; i += T) tab[i] = gtab[i];
+    const int nc = ncoef(p), C = blockDim.x / kGrp, S = C + 1, tid = threadIdx.x;
+    double2 *V = sm2, *U = V + nc * S, *W = U + (p + 1) * S;
+    double *tab = (double *)(W + (p + 1) * S);
+    for (int i = tid; i < ntab; i += blockDim.x) tab[i] = gtab[i];
     __syncthreads();
     const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
     const double *Dt = tab, *Ft = tab + 2 * nD, *iFt = Ft + nc, *ik = iFt + nc;
-    double2 *v = V + tid, *u = U + tid, *x = W + tid;
-    const int64_t j = blockIdx.x * (int64_t)T + tid;  // child index within level
-    if (j >= ((int64_t)1 << level)) return;
-    const int64_t gc = ((int64_t)1 << level) - 1 + j, gp = ((gc + 1) >> step) - 1;  // ancestor step levels up
+    const int grp = tid / kGrp;
+    const GrpCtx g{tid % kGrp, S};
+    double2 *v = V + grp, *u = U + grp, *x = W + grp;
+    const int64_t j = blockIdx.x * (int64_t)C + grp;  // child index within level
+    const bool valid = j < ((int64_t)1 << level);
+    const int64_t gc = ((int64_t)1 << level) - 1 + (valid ? j : 0), gp = ((gc + 1) >> step) - 1;
     const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
                  dz = centre[3 * gc + 2] - centre[3 * gp + 2];
     const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
-    const double2 ea = rxy > 0.0 ? make_double2(dx / rxy, dy / rxy) : make_double2(1.0, 0.0);
-    const double2 eb = rho > 0.0 ? make_double2(dz / rho, rxy / rho) : make_double2(1.0, 0.0);
+    const double irxy = rxy > 0.0 ? 1.0 / rxy : 0.0, irho = rho > 0.0 ? 1.0 / rho : 0.0;
+    const double2 ea = rxy > 0.0 ? make_double2(dx * irxy, dy * irxy) : make_double2(1.0, 0.0);
+    const double2 eb = rho > 0.0 ? make_double2(dz * irho, rxy * irho) : make_double2(1.0, 0.0);
     const double2 ebc = cconj(eb), eac = cconj(ea);
+    const double2 one = make_double2(1.0, 0.0);
     // forward rotation of the parent's local expansion: v = Lt (= L / F) in the rotated frame
     const double *Dn = Dt;
     for (int k = 0; k <= p; k++) {
-        double2 ph = make_double2(1.0, 0.0);
-        for (int l = 0; l <= k; l++) {
-            const int c = tri(k, l);
-            u[l * T] = cscale(cmul(mul_ipow(l, L[gp * nc + c]), ph), (l ? 2.0 : 1.0) * iFt[c]);
-            ph = cmul(ph, eac);
+        {
+            const double2 st = cpow(eac, kGrp);
+            double2 ph = cpow(eac, g.lane);
+            for (int l = g.lane; l <= k; l += kGrp) {
+                const int c = tri(k, l);
+                u[l * S] = cscale(cmul(mul_ipow(l, L[gp * nc + c]), ph), (l ? 2.0 : 1.0) * iFt[c]);
+                ph = cmul(ph, st);
+            }
         }
-        fold_apply(Dn, k, u, x, T, false);
-        double2 pb = make_double2(1.0, 0.0);
-        for (int jj = 0; jj <= k; jj++) {
-            x[jj * T] = cscale(cmul(x[jj * T], pb), jj ? 2.0 : 1.0);
-            pb = cmul(pb, ebc);
-        }
-        fold_apply(Dn, k, x, u, T, true);
-        for (int m = 0; m <= k; m++) v[tri(k, m) * T] = mul_ipow(4 - (m & 3), u[m * T]);
+        __syncwarp();
+        fold_grp(Dn, k, u, x, g, false, true, ebc);
+        __syncwarp();
+        fold_grp(Dn, k, x, u, g, true, false, one);
+        __syncwarp();
+        for (int m = g.lane; m <= k; m += kGrp) v[tri(k, m) * S] = mul_ipow(4 - (m & 3), u[m * S]);
         Dn += (k + 1) * (k + 1);
     }
-    // axial shift, order by order: Lt'_j^i = sum_{k>=j} Lt_k^i F_ki rho^{k-j}/(k-j)! / F_ji
+    __syncwarp();
+    // axial shift, order by order
     for (int i = 0; i <= p; i++) {
-        for (int k = i; k <= p; k++) u[(k - i) * T] = cscale(v[tri(k, i) * T], Ft[tri(k, i)]);
-        for (int jj = i; jj <= p; jj++) {
+        for (int k = i + g.lane; k <= p; k += kGrp) u[(k - i) * S] = cscale(v[tri(k, i) * S], Ft[tri(k, i)]);
+        __syncwarp();
+        for (int jj = i + g.lane; jj <= p; jj += kGrp) {
             double re = 0.0, im = 0.0, f = 1.0;
             for (int k = jj; k <= p; k++) {
-                const double2 t = u[(k - i) * T];
+                const double2 t = u[(k - i) * S];
                 re = fma(f, t.x, re);
                 im = fma(f, t.y, im);
                 f = f * rho * ik[k - jj + 1];
             }
-            v[tri(jj, i) * T] = cscale(make_double2(re, im), iFt[tri(jj, i)]);
+            v[tri(jj, i) * S] = cscale(make_double2(re, im), iFt[tri(jj, i)]);
         }
+        __syncwarp();
     }
     // back rotation (as in M2L) and add to the child
     Dn = Dt;
     for (int k = 0; k <= p; k++) {
-        for (int m = 0; m <= k; m++) u[m * T] = cscale(mul_ipow(m, v[tri(k, m) * T]), m ? 2.0 : 1.0);
-        fold_apply(Dn, k, u, x, T, false);
-        double2 pb = make_double2(1.0, 0.0);
-        for (int jj = 0; jj <= k; jj++) {
-            x[jj * T] = cscale(cmul(x[jj * T], pb), jj ? 2.0 : 1.0);
-            pb = cmul(pb, eb);
+        for (int m = g.lane; m <= k; m += kGrp) u[m * S] = cscale(mul_ipow(m, v[tri(k, m) * S]), m ? 2.0 : 1.0);
+        __syncwarp();
+        fold_grp(Dn, k, u, x, g, false, true, eb);
+        __syncwarp();
+        fold_grp(Dn, k, x, u, g, true, false, one);
+        __syncwarp();
+        if (valid) {
+            const double2 st = cpow(ea, kGrp);
+            double2 ph = cpow(ea, g.lane);
+            for (int l = g.lane; l <= k; l += kGrp) {
+                const int c = tri(k, l);
+                const double2 r = cscale(cmul(mul_ipow(4 - (l & 3), u[l * S]), ph), Ft[c]);
+                L[gc * nc + c] = cadd(L[gc * nc + c], r);
+                ph = cmul(ph, st);
+            }
         }
-        fold_apply(Dn, k, x, u, T, true);
-        double2 ph = make_double2(1.0, 0.0);
-        for (int l = 0; l <= k; l++) {
-            const int c = tri(k, l);
-            const double2 r = cscale(cmul(mul_ipow(4 - (l & 3), u[l * T]), ph), Ft[c]);
-            L[gc * nc + c] = cadd(L[gc * nc + c], r);
-            ph = cmul(ph, ea);
-        }
+        __syncwarp();
         Dn += (k + 1) * (k + 1);
     }
 }
@@ -418,10 +478,11 @@ cudaError_t m2l_setup(Plan &P) {
     P.m2l_smem = smem(threads);
     e = cudaFuncSetAttribute(k_m2l_rot_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)P.m2l_smem);
+    P.grp_smem = (size_t)(nc + 2 * (P.p + 1)) * (kGrpThreads / kGrp + 1) * 16 + t.size() * 8;
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_l2l_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.m2l_smem);
+        e = cudaFuncSetAttribute(k_l2l_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grp_smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_m2m_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.m2l_smem);
+        e = cudaFuncSetAttribute(k_m2m_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grp_smem);
     return e;
 }
 
@@ -429,15 +490,17 @@ cudaError_t m2l_setup(Plan &P) {
 void m2m_level(Plan &P, int l) {
     const int64_t np = (int64_t)1 << (l - P.step), nch = (int64_t)1 << l;
     cudaMemsetAsync(P.M + (np - 1) * P.nc, 0, (size_t)np * P.nc * sizeof(double2), P.stream);
-    FMM_LAUNCH(k_m2m_rot, (unsigned)((nch + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads,
-               P.m2l_smem, P.stream, l, P.step, P.p, P.centre, P.M, P.m2l_tab, P.m2l_ntab);
+    const int per = kGrpThreads / kGrp;
+    FMM_LAUNCH(k_m2m_rot, (unsigned)((nch + per - 1) / per), kGrpThreads, P.grp_smem, P.stream, l, P.step,
+               P.p, P.centre, P.M, P.m2l_tab, P.m2l_ntab);
 }
 
 // level l from its ancestors at level l-step
 void l2l_level(Plan &P, int l) {
     const int64_t nch = (int64_t)1 << l;
-    FMM_LAUNCH(k_l2l_rot, (unsigned)((nch + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads,
-               P.m2l_smem, P.stream, l, P.step, P.p, P.centre, P.L, P.m2l_tab, P.m2l_ntab);
+    const int per = kGrpThreads / kGrp;
+    FMM_LAUNCH(k_l2l_rot, (unsigned)((nch + per - 1) / per), kGrpThreads, P.grp_smem, P.stream, l, P.step,
+               P.p, P.centre, P.L, P.m2l_tab, P.m2l_ntab);
 }
 
 // FP64 M2L over all levels in one launch; accumulates into L (zeroed first)
