@@ -61,9 +61,9 @@ FP64_FLOPS_PER_CLK_SM = 4    # GB300 nominal 1.25 TFLOP/s FP64 at 2.07 GHz / 152
 # (profiles/k_p2p_f32_plummer2m_l14_p12.md), valid only while the kernel's
 # source is the one that was captured (checked by hash; otherwise null).
 MEASURED_TRAFFIC = {
-    ("plummer2m_l14_p12", "k_p2p_f32"): {"bytes": 278594560 + 132710144,
+    ("plummer2m_l14_p12", "k_p2p_f32"): {"bytes": 272156928 + 135209984,
                                          "source": "paper_2002_04894_gb300/csrc/mixed.cu",
-                                         "sha256_16": "eb0a0f474e8cd1e0"},
+                                         "sha256_16": "f87c61298c72b7f3"},
 }
 
 
@@ -388,13 +388,14 @@ def bench_batch(args, rank, world, local):
         xs.append(torch.from_numpy(inputs.points(kind, int(n), 1000 * rank + i).astype(np.float32)).cuda())
         qs.append(torch.from_numpy(inputs.charges_uniform(int(n), 1000 * rank + i).astype(np.float32)).cuda())
     total = int(ns.sum())
-    # autotune one representative per size class (log2 N) and kind, target 1e-6
+    # autotune one representative per size class (log2 N) and kind; tuned to
+    # half the 1e-6 target, so that the class's other systems stay below it
     t_tune = time.perf_counter()
     table = {}
     for i, n in enumerate(ns):
         key = (int(np.log2(n)), i % 2)
         if key not in table:
-            r = tune.tune(xs[i], qs[i], tol=1e-6, ps=(6, 8, 10, 12, 14))
+            r = tune.tune(xs[i], qs[i], tol=5e-7, ps=(6, 8, 10, 12, 14))
             table[key] = r.config
     t_tune = time.perf_counter() - t_tune
     cfgs = [table[(int(np.log2(n)), i % 2)] for i, n in enumerate(ns)]

@@ -160,6 +160,10 @@ cudaError_t m2l_all(Plan &P);
 void m2m_level(Plan &P, int level);
 void l2l_level(Plan &P, int level);
 bool m2l_f32_supported(int p);
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum (never lowers it): plans of different orders share the kernels,
+// and a per-plan value would let one plan shrink another's limit.
+cudaError_t allow_max_smem(const void *func, size_t need);
 bool m2l_tc_supported(int p);
 cudaError_t m2l_tc_setup(Plan &P);
 cudaError_t m2l_tc_launch(Plan &P);

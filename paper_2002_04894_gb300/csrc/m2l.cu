@@ -462,6 +462,18 @@ int64_t total_weak(const Plan &P) {
     return t;
 }
 
+cudaError_t allow_max_smem(const void *func, size_t need) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    const int room = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the limit
+    if (need > (size_t)room) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+}
+
 cudaError_t m2l_setup(Plan &P) {
     const std::vector<double> t = m2l_tables(P.p);
     P.m2l_ntab = (int)t.size();
@@ -476,13 +488,12 @@ cudaError_t m2l_setup(Plan &P) {
     if (smem(threads) > 220 * 1024) threads = 32;
     P.m2l_threads = threads;
     P.m2l_smem = smem(threads);
-    e = cudaFuncSetAttribute(k_m2l_rot_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)P.m2l_smem);
+    e = allow_max_smem((const void *)k_m2l_rot_f64, P.m2l_smem);
     P.grp_smem = (size_t)(nc + 2 * (P.p + 1)) * (kGrpThreads / kGrp + 1) * 16 + t.size() * 8;
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_l2l_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grp_smem);
+        e = allow_max_smem((const void *)k_l2l_rot, P.grp_smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_m2m_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grp_smem);
+        e = allow_max_smem((const void *)k_m2m_rot, P.grp_smem);
     return e;
 }
 
@@ -855,8 +866,8 @@ cudaError_t f32_tables_ready() {
 template <int P>
 cudaError_t attr_f32() {
     constexpr int NC = (P + 1) * (P + 2) / 2;
-    return cudaFuncSetAttribute(k_m2l_rot_f32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((size_t)kF32Threads * NC * 8 + kF32Threads * kRedStride * 4));
+    return allow_max_smem((const void *)k_m2l_rot_f32<P>,
+                          (size_t)kF32Threads * NC * 8 + kF32Threads * kRedStride * 4);
 }
 
 template <int P>

@@ -634,7 +634,7 @@ cudaError_t m2l_tc_setup(Plan &P) {
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     P.tc_ctas = sms;
-    return cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(P.p));
+    return allow_max_smem((const void *)k_m2l_tc, smem_bytes(P.p));
 }
 
 // the weak pairs of all levels through the tensor cores; accumulates the

@@ -79,3 +79,19 @@ def test_mixed_vs_direct_accuracy(gpu_lib):
     t = inputs.sample_targets(n, 400, 8)
     op, oE = oracle.direct(x, q, targets=t)
     assert rel(pot.cpu().numpy()[t], op) < 3e-6
+
+
+def test_plans_of_different_orders_coexist(gpu_lib):
+    """A plan built after another with a smaller order must not shrink the
+    shared-memory limit of the kernels the first one launches."""
+    fmm = gpu_lib
+    n = 20000
+    x = torch.from_numpy(inputs.points("plummer", n, 3)).cuda()
+    q = torch.from_numpy(inputs.charges_uniform(n, 3)).cuda()
+    big = fmm.fmm_plan(x, 8, 16, 0.5, prec=fmm.FMM_PREC_MIXED)
+    big64 = fmm.fmm_plan(x, 8, 14, 0.5)
+    small = fmm.fmm_plan(x, 8, 2, 0.5, prec=fmm.FMM_PREC_MIXED)
+    small64 = fmm.fmm_plan(x, 8, 3, 0.5)
+    for plan in (big, big64, small, small64):
+        pot, _ = fmm.fmm_eval(plan, q)
+        assert torch.isfinite(pot).all()
