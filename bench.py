@@ -139,6 +139,24 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def max_over_ranks(values, world, device):
+    """Per-rank timings -> their maxima over all ranks (the slowest replica
+    sets the job's time). One rank: the values themselves."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_throughput(points_per_rank, world, ms):
+    """Whole-job Mpoints/s of N independent replicas: the points all ranks
+    solved over the slowest rank's time per step."""
+    return world * points_per_rank / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -257,10 +275,7 @@ def bench_ours(args, rank, world, local):
         torch.distributed.barrier()
     t_solve = sum(a.elapsed_time(c) for a, b, c in ev) / args.steps
     t_eval = sum(b.elapsed_time(c) for a, b, c in ev) / args.steps
-    if world > 1:
-        tt = torch.tensor([t_solve, t_eval], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_solve, t_eval = tt.tolist()
+    t_solve, t_eval = max_over_ranks([t_solve, t_eval], world, "cuda")
     stage_ms = {s: v / args.steps for s, v in stage_sum.items()}
 
     # accuracy vs the FP64 direct sum on 1000 sampled targets (GPU)
@@ -320,7 +335,7 @@ def bench_ours(args, rank, world, local):
     peak_tflops = SM_COUNT * fp * max_mhz * 1e6 / 1e12
     p2p_flops = FLOPS_PER_INTERACTION * stats["p2p_interactions"]
     achieved = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
-    value = world * n / (t_solve * 1e-3) / 1e6
+    value = replica_throughput(n, world, t_solve)
     out = {
         "metric": METRIC,
         "value": round(value, 4), "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
@@ -332,7 +347,7 @@ def bench_ours(args, rank, world, local):
                    "prec": args.prec, "points": WORKLOADS[args.workload][0],
                    "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "eval_only": {"value": round(world * n / (t_eval * 1e-3) / 1e6, 4), "unit": "Mpoints/s",
+        "eval_only": {"value": round(replica_throughput(n, world, t_eval), 4), "unit": "Mpoints/s",
                       "ms": round(t_eval, 3)},
         "accuracy": {"rel_l2_phi": err_phi, "rel_l2_field": err_E, "targets": len(tgt),
                      "reference": "fmm_direct (FP64, GPU)"},
