@@ -248,9 +248,8 @@ cudaError_t lists_build(Plan &P) {
     cudaMemcpyAsync(srow_prev, &zero, 4, cudaMemcpyHostToDevice, st);
     P.nweak[0] = 0;
     P.nstrong[0] = 1;
-    int32_t *totals = nullptr;
-    cudaError_t e = cudaMallocHost(&totals, 8);
-    if (e != cudaSuccess) return e;
+    int32_t totals[2] = {0, 0};  // level sizes, read back synchronously
+    cudaError_t e = cudaSuccess;
     const int step = P.step, C = 1 << step;
     for (int l = 1; l <= P.B; l++) {
         const int64_t nt = (int64_t)1 << l;
@@ -261,10 +260,7 @@ cudaError_t lists_build(Plan &P) {
             P.wsrc[l] = (int32_t *)palloc(P, 4);
             P.wrow[l] = (int32_t *)palloc(P, 4);
             P.ssrc[l] = (int32_t *)palloc(P, 4);
-            if (!P.wptr[l] || !P.sptr[l] || !P.wsrc[l] || !P.wrow[l] || !P.ssrc[l]) {
-                cudaFreeHost(totals);
-                return cudaErrorMemoryAllocation;
-            }
+            if (!P.wptr[l] || !P.sptr[l] || !P.wsrc[l] || !P.wrow[l] || !P.ssrc[l]) return cudaErrorMemoryAllocation;
             cudaMemsetAsync(P.wptr[l], 0, (nt + 1) * 4, st);
             cudaMemsetAsync(P.sptr[l], 0, (nt + 1) * 4, st);
             P.nweak[l] = 0;
@@ -275,7 +271,6 @@ cudaError_t lists_build(Plan &P) {
         const int64_t npar = P.nstrong[lp], ncand = (int64_t)C * C * npar;
         if (ncand > 0x7fffffffLL) {
             P.capacity_exceeded = true;
-            cudaFreeHost(totals);
             return cudaSuccess;
         }
         int32_t *flag = (int32_t *)dalloc(P, (size_t)ncand * 4);
@@ -284,35 +279,23 @@ cudaError_t lists_build(Plan &P) {
         int32_t *ctgt = (int32_t *)dalloc(P, (size_t)ncand * 4);
         P.wptr[l] = (int32_t *)palloc(P, (nt + 1) * 4);
         P.sptr[l] = (int32_t *)palloc(P, (nt + 1) * 4);
-        if (!flag || !wpos || !csrc || !ctgt || !P.wptr[l] || !P.sptr[l]) {
-            cudaFreeHost(totals);
-            return cudaErrorMemoryAllocation;
-        }
+        if (!flag || !wpos || !csrc || !ctgt || !P.wptr[l] || !P.sptr[l]) return cudaErrorMemoryAllocation;
         FMM_LAUNCH(k_cand, (unsigned)((npar + 127) / 128), 128, 0, st, l, step, npar, P.theta, P.sptr[lp],
                    P.ssrc[lp], srow_prev, P.centre, P.radius, flag, csrc, ctgt);
         e = scan_exclusive(P, flag, wpos, ncand);
-        if (e != cudaSuccess) {
-            cudaFreeHost(totals);
-            return e;
-        }
+        if (e != cudaSuccess) return e;
         FMM_LAUNCH(k_cand_ptrs, (unsigned)((nt + 1 + 255) / 256), 256, 0, st, l, step, P.sptr[lp], wpos,
                    ncand, P.wptr[l], P.sptr[l]);
         cudaMemcpyAsync(totals, wpos + ncand, 4, cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            cudaFreeHost(totals);
-            return e;
-        }
+        if (e != cudaSuccess) return e;
         P.nweak[l] = totals[0];
         P.nstrong[l] = ncand - totals[0];
         P.wsrc[l] = (int32_t *)palloc(P, (size_t)std::max<int64_t>(P.nweak[l], 1) * 4);
         P.wrow[l] = (int32_t *)palloc(P, (size_t)std::max<int64_t>(P.nweak[l], 1) * 4);
         P.ssrc[l] = (int32_t *)palloc(P, (size_t)std::max<int64_t>(P.nstrong[l], 1) * 4);
         int32_t *srow = (int32_t *)dalloc(P, (size_t)std::max<int64_t>(P.nstrong[l], 1) * 4);
-        if (!P.wsrc[l] || !P.wrow[l] || !P.ssrc[l] || !srow) {
-            cudaFreeHost(totals);
-            return cudaErrorMemoryAllocation;
-        }
+        if (!P.wsrc[l] || !P.wrow[l] || !P.ssrc[l] || !srow) return cudaErrorMemoryAllocation;
         FMM_LAUNCH(k_cand_scatter, (unsigned)((ncand + 255) / 256), 256, 0, st, ncand, flag, wpos, csrc,
                    ctgt, P.wsrc[l], P.wrow[l], P.ssrc[l], srow);
         srow_prev = srow;
@@ -324,10 +307,7 @@ cudaError_t lists_build(Plan &P) {
     const int64_t nl = (int64_t)1 << P.B;
     unsigned long long *acc = (unsigned long long *)dalloc(P, 8);
     long long *nsrc = (long long *)dalloc(P, (size_t)nl * 8);
-    if (!acc || !nsrc) {
-        cudaFreeHost(totals);
-        return cudaErrorMemoryAllocation;
-    }
+    if (!acc || !nsrc) return cudaErrorMemoryAllocation;
     cudaMemsetAsync(acc, 0, 8, st);
     FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.sptr[P.B], P.ssrc[P.B],
                P.count, acc, nsrc);
@@ -339,7 +319,6 @@ cudaError_t lists_build(Plan &P) {
     cudaMemcpyAsync(hcnt.data(), P.count + (nl - 1), (size_t)nl * 4, cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     P.p2p_interactions = (int64_t)h;
-    cudaFreeHost(totals);
     if (e != cudaSuccess) return e;
     std::vector<int2> units;
     std::vector<long long> uw;

@@ -171,24 +171,21 @@ class FmmServer:
             s = self._streams[k]
             n = len(req.charges)
             lv = req.levels if req.levels >= 0 else default_levels(n)
+            # host arrays straight to the library, which stages them through
+            # device buffers on the worker's stream (no per-request pinned
+            # allocation, which would serialise the workers)
+            xh = np.ascontiguousarray(req.points)
+            qh = np.ascontiguousarray(req.charges, dtype=xh.dtype)
+            ph = np.empty(n, dtype=xh.dtype)
+            fh = np.empty((n, 3), dtype=xh.dtype) if req.fields else None
             with torch.cuda.stream(s):
-                xh = torch.as_tensor(req.points).pin_memory()
-                qh = torch.as_tensor(req.charges).pin_memory()
-                xd = xh.to("cuda", non_blocking=True)
-                qd = qh.to("cuda", non_blocking=True)
-                plan = fmm_plan(xd, lv, req.p, req.theta, prec=req.prec, stream=s)
-                pot, fld = fmm_eval(plan, qd, stream=s, want_fields=req.fields)
-                ph = torch.empty(pot.shape, dtype=pot.dtype).pin_memory()
-                ph.copy_(pot, non_blocking=True)
-                fh = None
-                if fld is not None:
-                    fh = torch.empty(fld.shape, dtype=fld.dtype).pin_memory()
-                    fh.copy_(fld, non_blocking=True)
-                s.synchronize()
-                fmm_destroy(plan)
+                plan = fmm_plan(xh, lv, req.p, req.theta, prec=req.prec, stream=s)
+                try:
+                    fmm_eval(plan, qh, ph, fh, stream=s)  # host outputs: returns when complete
+                finally:
+                    fmm_destroy(plan)
             done = time.perf_counter() - t0
-            return Result(req.rid, ph.numpy(), None if fh is None else fh.numpy(), req.arrival,
-                          0.0, done, lv, 0)
+            return Result(req.rid, ph, fh, req.arrival, 0.0, done, lv, 0)
         finally:
             with self._lock:
                 self._free.append(k)
