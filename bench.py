@@ -521,6 +521,20 @@ def bench_serve(args, rank, world, local):
         tg = inputs.sample_targets(n, 100, r.rid)
         dp = fmm.fmm_direct(np.ascontiguousarray(r.points), np.ascontiguousarray(r.charges), tg)[0]
         errs.append(float(np.linalg.norm(rr.potentials[tg] - dp) / np.linalg.norm(dp)))
+    # comparator: the plain FP64 form, one solve at a time, on the first
+    # requests (same parameters), as points per second of solve time
+    t64, pts64 = 0.0, 0
+    for r in reqs[: min(len(reqs), 40)]:
+        lv = serve.default_levels(len(r.charges))
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        plan = fmm.fmm_plan(np.ascontiguousarray(r.points), lv, r.p, r.theta, prec=fmm.FMM_PREC_FP64)
+        ph = np.empty(len(r.charges))
+        fh = np.empty((len(r.charges), 3))
+        fmm.fmm_eval(plan, np.ascontiguousarray(r.charges), ph, fh)
+        fmm.fmm_destroy(plan)
+        t64 += time.perf_counter() - a
+        pts64 += len(r.charges)
     if rank != 0:
         return
     lat = serve.latency_stats(res)
@@ -534,6 +548,8 @@ def bench_serve(args, rank, world, local):
                    "p": args.serve_p, "theta": 0.5, "leaf": 100},
         "latency_ms": lat, "requests_per_s": round(args.requests / makespan, 2),
         "admission_peak_gb": round(adm.peak / (1 << 30), 3),
+        "fp64_one_solve_at_a_time": {"value": round(pts64 / t64 / 1e6, 4), "unit": "Mpoints/s",
+                                     "requests": min(len(reqs), 40)},
         "accuracy": {"max_rel_l2_phi": max(errs), "requests_checked": len(errs), "target": 1e-5},
         "gpu_launches": int(launches), "clocks": clk.summary(),
     }
