@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "fmm_internal.cuh"
@@ -474,8 +475,22 @@ cudaError_t allow_max_smem(const void *func, size_t need) {
     return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
 }
 
+// the tables of order p, computed once per process (long double sums of
+// factorials: about a million operations at p = 12)
+const std::vector<double> &m2l_tables_cached(int p) {
+    static std::mutex mu;
+    static std::vector<double> cache[FMM_MAX_P + 1];
+    static bool ready[FMM_MAX_P + 1] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[p]) {
+        cache[p] = m2l_tables(p);
+        ready[p] = true;
+    }
+    return cache[p];
+}
+
 cudaError_t m2l_setup(Plan &P) {
-    const std::vector<double> t = m2l_tables(P.p);
+    const std::vector<double> &t = m2l_tables_cached(P.p);
     P.m2l_ntab = (int)t.size();
     P.m2l_tab = (double *)palloc(P, t.size() * 8);
     if (!P.m2l_tab) return cudaErrorMemoryAllocation;
