@@ -321,12 +321,19 @@ __global__ void k_sel_init(int level, const int32_t *count, uint64_t *prefix, un
     for (int i = threadIdx.x; i < 256; i += blockDim.x) ghist[(int64_t)s * 256 + i] = 0;
 }
 
+// One chunk of one box: histogram of the keys' current digit, added to the
+// box's global histogram. The last chunk of the box to finish (a per-box
+// arrival counter) then picks the digit holding the wanted rank, clears the
+// histogram and the counter for the next pass.
 __global__ void __launch_bounds__(kThreads)
 k_sel_hist(int level, int pass, const double *__restrict__ xs, const double *__restrict__ ys,
            const double *__restrict__ zs, const int32_t *__restrict__ begin,
            const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
-           const uint64_t *__restrict__ prefix, unsigned *ghist) {
+           uint64_t *prefix, unsigned *rrem, unsigned *ghist, unsigned *arrived) {
     __shared__ unsigned h[256];
+    __shared__ bool last;
+    __shared__ uint64_t s_pre;
+    __shared__ unsigned s_rr;
     const int s = blockIdx.x, c = blockIdx.y;
     const int64_t g = ((int64_t)1 << level) - 1 + s;
     const int b = begin[g], n = count[g], ax = axis[g];
@@ -344,26 +351,29 @@ k_sel_hist(int level, int pass, const double *__restrict__ xs, const double *__r
     }
     __syncthreads();
     if (h[threadIdx.x]) atomicAdd(&ghist[(int64_t)s * 256 + threadIdx.x], h[threadIdx.x]);
-}
-
-__global__ void k_sel_pick(int pass, unsigned *ghist, uint64_t *prefix, unsigned *rrem) {
-    const int s = blockIdx.x;
-    __shared__ unsigned h[256];
-    __shared__ uint64_t pre;
-    __shared__ unsigned rr;
-    for (int i = threadIdx.x; i < 256; i += 32) {
-        h[i] = ghist[(int64_t)s * 256 + i];
-        ghist[(int64_t)s * 256 + i] = 0;
-    }
+    __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) {
-        pre = prefix[s];
-        rr = rrem[s];
+        const unsigned active = (unsigned)((n + kChunk - 1) / kChunk);
+        last = atomicAdd(&arrived[s], 1u) == active - 1;
     }
-    __syncwarp();
-    pick_digit(h, 56 - 8 * pass, &pre, &rr);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    h[threadIdx.x] = __ldcg(&ghist[(int64_t)s * 256 + threadIdx.x]);
+    ghist[(int64_t)s * 256 + threadIdx.x] = 0;
     if (threadIdx.x == 0) {
-        prefix[s] = pre;
-        rrem[s] = rr;
+        s_pre = prefix[s];
+        s_rr = rrem[s];
+        arrived[s] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        pick_digit(h, shift, &s_pre, &s_rr);
+        if (threadIdx.x == 0) {
+            prefix[s] = s_pre;
+            rrem[s] = s_rr;
+        }
     }
 }
 
@@ -617,9 +627,11 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
     uint64_t *sel_prefix = (uint64_t *)dalloc(P, (size_t)maxseg * 8);
     unsigned long long *sel_minr = (unsigned long long *)dalloc(P, (size_t)maxseg * 8);
     unsigned *sel_rrem = (unsigned *)dalloc(P, (size_t)maxseg * 4);
+    unsigned *arrived = (unsigned *)dalloc(P, (size_t)maxseg * 4);  // per-box chunk arrivals
     unsigned long long *bbox = (unsigned long long *)dalloc(P, 64);
-    if (!x2 || !y2 || !z2 || !i2 || !sel_v || !sel_prefix || !sel_minr || !sel_rrem || !bbox)
+    if (!x2 || !y2 || !z2 || !i2 || !sel_v || !sel_prefix || !sel_minr || !sel_rrem || !arrived || !bbox)
         return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(arrived, 0, (size_t)maxseg * 4, st);
 
     unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
     cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, st);
@@ -695,11 +707,9 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
             const dim3 grid(S, nch);  // boxes on x (up to 2^31 - 1), chunks on y
             if (need_median) {
                 FMM_LAUNCH(k_sel_init, S, 256, 0, st, l, P.count, sel_prefix, sel_rrem, sel_minr, ghist);
-                for (int pass = 0; pass < 8; pass++) {
+                for (int pass = 0; pass < 8; pass++)
                     FMM_LAUNCH(k_sel_hist, grid, kThreads, 0, st, l, pass, xa, ya, za, P.begin, P.count,
-                                                          P.axis, sel_prefix, ghist);
-                    FMM_LAUNCH(k_sel_pick, S, 32, 0, st, pass, ghist, sel_prefix, sel_rrem);
-                }
+                                                          P.axis, sel_prefix, sel_rrem, ghist, arrived);
                 FMM_LAUNCH(k_sel_count, grid, kThreads, 0, st, l, nch, xa, ya, za, P.begin, P.count, P.axis,
                                                        sel_prefix, chunk_lt, chunk_eq, sel_minr,
                                                        (const unsigned long long *)nullptr);
@@ -768,6 +778,7 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
     dfree(P, sel_prefix, (size_t)maxseg * 8);
     dfree(P, sel_minr, (size_t)maxseg * 8);
     dfree(P, sel_rrem, (size_t)maxseg * 4);
+    dfree(P, arrived, (size_t)maxseg * 4);
     dfree(P, bbox, 64);
     if (eta_mode) {
         dfree(P, thr, (size_t)maxseg * 8);
