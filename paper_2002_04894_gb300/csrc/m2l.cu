@@ -579,6 +579,127 @@ __device__ __forceinline__ float2 fipow(int m, float2 v) {
     }
 }
 
+// Per-pair coefficient storage between the stages: degrees 0..kTmDeg live
+// in the thread's lane of tensor memory (Re, Im interleaved: columns
+// 2 tri(n,m), 2 tri(n,m)+1), the rest in a shared-memory column of the
+// block (stride T). Tensor memory is otherwise idle in this kernel; moving
+// 55 of the 91 coefficients (p = 12) there cuts shared memory per block from
+// 111 to 55 KB, so three blocks (12 warps, register-limited) fit an SM
+// instead of two.
+constexpr int kTmDeg = 9;
+constexpr int kTmC = (kTmDeg + 1) * (kTmDeg + 2) / 2;  // first coefficient in shared memory
+
+struct VS {
+    float2 *s;    // shared column of this thread: coefficient c at s[(c - kTmC) * T]
+    uint32_t t;   // this thread's tensor-memory lane, column 0
+    int T;
+};
+
+template <int X>
+__device__ __forceinline__ void tm_st(uint32_t a, const float *v) {
+    if constexpr (X == 1)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(a), "f"(v[0]));
+    else if constexpr (X == 2)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(a), "f"(v[0]), "f"(v[1]));
+    else if constexpr (X == 4)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "f"(v[0]),
+                     "f"(v[1]), "f"(v[2]), "f"(v[3]));
+    else if constexpr (X == 8)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(a),
+                     "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]));
+    else
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+            "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(a),
+            "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+            "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]));
+}
+
+template <int X>
+__device__ __forceinline__ void tm_ld(uint32_t a, float *v) {
+    if constexpr (X == 1)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=f"(v[0]) : "r"(a));
+    else if constexpr (X == 2)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(a));
+    else if constexpr (X == 4)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                     : "r"(a));
+    else if constexpr (X == 8)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+                       "=f"(v[7])
+                     : "r"(a));
+    else
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+              "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),
+              "=f"(v[15])
+            : "r"(a));
+}
+
+// columns [OFF, OFF + REM) in power-of-two chunks
+template <int OFF, int REM>
+struct TCols {
+    static __device__ __forceinline__ void st(uint32_t a, const float *v) {
+        constexpr int X = REM >= 16 ? 16 : REM >= 8 ? 8 : REM >= 4 ? 4 : REM >= 2 ? 2 : 1;
+        if constexpr (REM > 0) {
+            tm_st<X>(a + OFF, v + OFF);
+            TCols<OFF + X, REM - X>::st(a, v);
+        }
+    }
+    static __device__ __forceinline__ void ld(uint32_t a, float *v) {
+        constexpr int X = REM >= 16 ? 16 : REM >= 8 ? 8 : REM >= 4 ? 4 : REM >= 2 ? 2 : 1;
+        if constexpr (REM > 0) {
+            tm_ld<X>(a + OFF, v + OFF);
+            TCols<OFF + X, REM - X>::ld(a, v);
+        }
+    }
+};
+
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// the loaded registers are valid only after the wait: the empty asm ties
+// every later use of them to a point after it
+template <int K>
+__device__ __forceinline__ void tm_wait_ld(float *v) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < K; j++) asm volatile("" : "+f"(v[j]));
+}
+
+template <int N>
+__device__ __forceinline__ void v_put_deg(const VS &vs, const float2 (&u)[N + 1]) {
+    if constexpr (N <= kTmDeg) {
+        float f[2 * (N + 1)];
+#pragma unroll
+        for (int m = 0; m <= N; m++) {
+            f[2 * m] = u[m].x;
+            f[2 * m + 1] = u[m].y;
+        }
+        TCols<0, 2 * (N + 1)>::st(vs.t + 2 * tri(N, 0), f);
+        tm_wait_st();
+    } else {
+#pragma unroll
+        for (int m = 0; m <= N; m++) vs.s[(tri(N, m) - kTmC) * vs.T] = u[m];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void v_get_deg(const VS &vs, float2 (&u)[N + 1]) {
+    if constexpr (N <= kTmDeg) {
+        float f[2 * (N + 1)];
+        TCols<0, 2 * (N + 1)>::ld(vs.t + 2 * tri(N, 0), f);
+        tm_wait_ld<2 * (N + 1)>(f);
+#pragma unroll
+        for (int m = 0; m <= N; m++) u[m] = make_float2(f[2 * m], f[2 * m + 1]);
+    } else {
+#pragma unroll
+        for (int m = 0; m <= N; m++) u[m] = vs.s[(tri(N, m) - kTmC) * vs.T];
+    }
+}
+
 template <int N>
 __device__ __forceinline__ void ffold(const float2 (&v)[N + 1], float2 (&out)[N + 1], bool tr) {
 #pragma unroll
@@ -598,13 +719,13 @@ __device__ __forceinline__ void ffold(const float2 (&v)[N + 1], float2 (&out)[N 
 
 // forward rotation of degree N of the scaled source multipole into V
 template <int N>
-__device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, float2 *V, int T, float2 eai,
+__device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, VS vs, bool valid, float2 eai,
                                      float2 ebv) {
     float2 u[N + 1], w[N + 1];
     float2 ph = make_float2(1.f, 0.f);
 #pragma unroll
     for (int m = 0; m <= N; m++) {
-        const float2 mv = Ms[tri(N, m)];
+        const float2 mv = valid ? Ms[tri(N, m)] : make_float2(0.f, 0.f);
         const float s = c_F[tri(N, m)] * (m ? 2.f : 1.f);
         const float2 t = fmulc(mv, ph);
         u[m] = make_float2(t.x * s, t.y * s);
@@ -620,7 +741,8 @@ __device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, float2 *V, i
     }
     ffold<N>(w, u, true);
 #pragma unroll
-    for (int m = 0; m <= N; m++) V[tri(N, m) * T] = fipow(m, u[m]);
+    for (int m = 0; m <= N; m++) u[m] = fipow(m, u[m]);
+    v_put_deg<N>(vs, u);
 }
 
 constexpr int kRedStride = 36;  // floats per lane row of the per-warp transpose buffer
@@ -631,13 +753,14 @@ constexpr int kRedStride = 36;  // floats per lane row of the per-warp transpose
 // its 2 (N+1) values per lane through shared memory and adds each column with
 // one atomic; otherwise a segmented shuffle sum over runs of equal target
 template <int N>
-__device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 ebv,
+__device__ __noinline__ void bwd_deg(VS vs, float2 ea, float2 ebv,
                                      double2 *__restrict__ Lh, unsigned same_mask, bool head,
                                      int uniform_tgt, double2 *__restrict__ Lbase, int nc, float *red) {
     float2 u[N + 1], w[N + 1];
+    v_get_deg<N>(vs, u);
 #pragma unroll
     for (int m = 0; m <= N; m++) {
-        const float2 t = fipow(m, V[tri(N, m) * T]);
+        const float2 t = fipow(m, u[m]);
         u[m] = m ? make_float2(2.f * t.x, 2.f * t.y) : t;
     }
     ffold<N>(u, w, false);
@@ -700,16 +823,28 @@ __device__ __noinline__ void bwd_deg(const float2 *V, int T, float2 ea, float2 e
 // translation along z of order L (orders P+1-L coefficients), in place in V;
 // qs = r_s / rho, qt = r_t / rho
 template <int P, int L>
-__device__ __noinline__ void axial_ord(float2 *V, int T, float qs, float qt, float rinv) {
+__device__ __noinline__ void axial_ord(VS vs, float qs, float qt, float rinv) {
     constexpr int len = P + 1 - L;
+    constexpr int ntm = L > kTmDeg ? 0 : (P < kTmDeg ? P : kTmDeg) + 1 - L;  // of them in tensor memory
     float2 s[len];
+    float f[2 * len];
+#pragma unroll
+    for (int n = L; n <= P; n++) {
+        if (n <= kTmDeg) {
+            tm_ld<2>(vs.t + 2 * tri(n, L), f + 2 * (n - L));
+        } else {
+            const float2 v = vs.s[(tri(n, L) - kTmC) * vs.T];
+            f[2 * (n - L)] = v.x;
+            f[2 * (n - L) + 1] = v.y;
+        }
+    }
+    if constexpr (ntm > 0) tm_wait_ld<2 * ntm>(f);
     float sp = 1.f;
 #pragma unroll
     for (int j = 0; j < L; j++) sp *= qs;
 #pragma unroll
     for (int n = L; n <= P; n++) {
-        const float2 mr = V[tri(n, L) * T];
-        s[n - L] = make_float2(mr.x * sp, -mr.y * sp);
+        s[n - L] = make_float2(f[2 * (n - L)] * sp, -f[2 * (n - L) + 1] * sp);
         sp *= qs;
     }
     float tp = rinv;
@@ -724,47 +859,73 @@ __device__ __noinline__ void axial_ord(float2 *V, int T, float qs, float qt, flo
             re = fmaf(a, s[n - L].x, re);
             im = fmaf(a, s[n - L].y, im);
         }
-        V[tri(k, L) * T] = make_float2(re * tp, im * tp);
+        if (k <= kTmDeg) {
+            const float o[2] = {re * tp, im * tp};
+            tm_st<2>(vs.t + 2 * tri(k, L), o);
+        } else {
+            vs.s[(tri(k, L) - kTmC) * vs.T] = make_float2(re * tp, im * tp);
+        }
         tp *= qt;
     }
+    if constexpr (ntm > 0) tm_wait_st();
 }
 
 template <int P, int N>
 struct Seq {
-    __device__ static __forceinline__ void fwd(const float2 *Ms, float2 *V, int T, float2 eai,
-                                               float2 ebv) {
-        fwd_deg<N>(Ms, V, T, eai, ebv);
-        Seq<P, N + 1>::fwd(Ms, V, T, eai, ebv);
+    __device__ static __forceinline__ void fwd(const float2 *Ms, VS vs, bool valid, float2 eai, float2 ebv) {
+        fwd_deg<N>(Ms, vs, valid, eai, ebv);
+        Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv);
     }
-    __device__ static __forceinline__ void axial(float2 *V, int T, float qs, float qt, float rinv) {
-        axial_ord<P, N>(V, T, qs, qt, rinv);
-        Seq<P, N + 1>::axial(V, T, qs, qt, rinv);
+    __device__ static __forceinline__ void axial(VS vs, float qs, float qt, float rinv) {
+        axial_ord<P, N>(vs, qs, qt, rinv);
+        Seq<P, N + 1>::axial(vs, qs, qt, rinv);
     }
-    __device__ static __forceinline__ void bwd(const float2 *V, int T, float2 ea, float2 ebv,
-                                               double2 *Lh, unsigned same, bool head, int ut,
-                                               double2 *Lbase, int nc, float *red) {
-        bwd_deg<N>(V, T, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
-        Seq<P, N + 1>::bwd(V, T, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
+    __device__ static __forceinline__ void bwd(VS vs, float2 ea, float2 ebv, double2 *Lh, unsigned same,
+                                               bool head, int ut, double2 *Lbase, int nc, float *red) {
+        bwd_deg<N>(vs, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
+        Seq<P, N + 1>::bwd(vs, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
     }
 };
 template <int P>
 struct Seq<P, P + 1> {
-    __device__ static __forceinline__ void fwd(const float2 *, float2 *, int, float2, float2) {}
-    __device__ static __forceinline__ void axial(float2 *, int, float, float, float) {}
-    __device__ static __forceinline__ void bwd(const float2 *, int, float2, float2, double2 *,
-                                               unsigned, bool, int, double2 *, int, float *) {}
+    __device__ static __forceinline__ void fwd(const float2 *, VS, bool, float2, float2) {}
+    __device__ static __forceinline__ void axial(VS, float, float, float) {}
+    __device__ static __forceinline__ void bwd(VS, float2, float2, double2 *, unsigned, bool, int, double2 *,
+                                               int, float *) {}
 };
 
 constexpr int kF32Threads = 128;
 
+// coefficients of order P kept in tensor memory / in shared memory, and the
+// tensor-memory columns a block allocates (a power of two, at least 32)
+template <int P>
+struct VSplit {
+    static constexpr int NC = (P + 1) * (P + 2) / 2;
+    static constexpr int NT = NC < kTmC ? NC : kTmC;
+    static constexpr int NS = NC - NT;
+    static constexpr int COLS = 2 * NT <= 32 ? 32 : 2 * NT <= 64 ? 64 : 128;
+};
+
 // one weak pair per thread, all levels; accumulates r_t^k L_k into Lh
 template <int P>
-__global__ void __launch_bounds__(kF32Threads)
+__global__ void __launch_bounds__(kF32Threads, 3)
 k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__restrict__ radius,
               const float2 *__restrict__ Mf, double2 *__restrict__ Lh) {
-    constexpr int NC = (P + 1) * (P + 2) / 2;
-    extern __shared__ float2 smf[];  // [NC][threads]
-    const int tid = threadIdx.x;
+    using SP = VSplit<P>;
+    constexpr int NC = SP::NC;
+    extern __shared__ float2 smf[];  // [NS][threads], then the per-warp transpose buffers
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tmem)),
+                     "r"(SP::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = s_tmem;
     const int64_t g = blockIdx.x * (int64_t)kF32Threads + tid;
     const bool valid = g < PT.off[PT.lmax + 1];
     int64_t gt = -1, gs = 0;
@@ -791,20 +952,22 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
     const float2 ebv = make_float2(dz * rinv, rxy * rinv);
     const float2 eai = make_float2(ea.y, -ea.x);
     const float qs = rs * rinv, qt = rt * rinv;
-    float2 *v = smf + tid;
-    if (valid) {
-        Seq<P, 0>::fwd(Mf + gs * NC, v, kF32Threads, eai, ebv);
-    } else {
-        for (int c = 0; c < NC; c++) v[c * kF32Threads] = make_float2(0.f, 0.f);
-    }
-    Seq<P, 0>::axial(v, kF32Threads, qs, qt, rinv);
+    // every lane runs every stage (tensor-memory accesses are warp-wide); a
+    // lane without a pair carries zeros
+    const VS vs{smf + tid, tbase + ((uint32_t)(32 * (warp & 3)) << 16), kF32Threads};
+    Seq<P, 0>::fwd(Mf + gs * NC, vs, valid, eai, ebv);
+    Seq<P, 0>::axial(vs, qs, qt, rinv);
     // the warp's pairs share one target (invalid lanes add zeros): transpose path
     const int t32 = gt >= 0 ? (int)gt : -1;
     const int tmax = __reduce_max_sync(0xffffffffu, t32);
     const bool uniform = __all_sync(0xffffffffu, t32 == tmax || t32 < 0);
-    float *red = (float *)(smf + NC * kF32Threads) + (tid >> 5) * 32 * kRedStride;
-    Seq<P, 0>::bwd(v, kF32Threads, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head,
-                   uniform ? tmax : -1, Lh, NC, red);
+    float *red = (float *)(smf + SP::NS * kF32Threads) + warp * 32 * kRedStride;
+    Seq<P, 0>::bwd(vs, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, NC,
+                   red);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SP::COLS));
 }
 
 // Mhat = M / r^n in float, every box (levels >= 1)
@@ -882,13 +1045,13 @@ template <int P>
 cudaError_t attr_f32() {
     constexpr int NC = (P + 1) * (P + 2) / 2;
     return allow_max_smem((const void *)k_m2l_rot_f32<P>,
-                          (size_t)kF32Threads * NC * 8 + kF32Threads * kRedStride * 4);
+                          (size_t)kF32Threads * VSplit<P>::NS * 8 + kF32Threads * kRedStride * 4);
 }
 
 template <int P>
 cudaError_t launch_f32(Plan &Pl, int64_t tot) {
     constexpr int NC = (P + 1) * (P + 2) / 2;
-    const size_t smem = (size_t)kF32Threads * NC * 8 + kF32Threads * kRedStride * 4;
+    const size_t smem = (size_t)kF32Threads * VSplit<P>::NS * 8 + kF32Threads * kRedStride * 4;
     FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)((tot + kF32Threads - 1) / kF32Threads), kF32Threads, smem,
                Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh);
     return cudaGetLastError();

@@ -266,6 +266,9 @@ __device__ __forceinline__ bool contract(Team &T, float (&re)[16], float (&im)[1
     ld16(T.tcol + T.lanes + kDst, re);
     ld16(T.tcol + T.lanes + kDst + 16, im);
     wait_ld();
+    // the loaded registers are valid only after the wait: tie their uses to it
+#pragma unroll
+    for (int j = 0; j < 16; j++) asm volatile("" : "+f"(re[j]), "+f"(im[j]));
     return true;
 }
 
@@ -452,6 +455,8 @@ k_m2l_tc(PairTable PT, int p, int64_t ntiles, const double *__restrict__ centre,
             }
             wait_ld();
 #pragma unroll
+            for (int j = 0; j < 16; j++) asm volatile("" : "+f"(re[j]), "+f"(im[j]));
+#pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (l + j <= p) {
                     re[j] = re[j] * sp;
@@ -483,6 +488,8 @@ k_m2l_tc(PairTable PT, int p, int64_t ntiles, const double *__restrict__ centre,
             ld16(vre + c0, re);
             ld16(vim + c0, im);
             wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; j++) asm volatile("" : "+f"(re[j]), "+f"(im[j]));
 #pragma unroll
             for (int m = 0; m < 16; m++) {
                 if (m <= n) {
