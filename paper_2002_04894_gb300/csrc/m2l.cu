@@ -873,15 +873,18 @@ __device__ __noinline__ void axial_ord(VS vs, float qs, float qt, float rinv) {
 template <int P, int N>
 struct Seq {
     __device__ static __forceinline__ void fwd(const float2 *Ms, VS vs, bool valid, float2 eai, float2 ebv) {
+        __syncthreads();  // keep the block's warps on the same code (instruction cache)
         fwd_deg<N>(Ms, vs, valid, eai, ebv);
         Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv);
     }
     __device__ static __forceinline__ void axial(VS vs, float qs, float qt, float rinv) {
+        __syncthreads();
         axial_ord<P, N>(vs, qs, qt, rinv);
         Seq<P, N + 1>::axial(vs, qs, qt, rinv);
     }
     __device__ static __forceinline__ void bwd(VS vs, float2 ea, float2 ebv, double2 *Lh, unsigned same,
                                                bool head, int ut, double2 *Lbase, int nc, float *red) {
+        __syncthreads();
         bwd_deg<N>(vs, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
         Seq<P, N + 1>::bwd(vs, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
     }
