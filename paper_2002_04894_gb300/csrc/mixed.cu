@@ -241,6 +241,7 @@ __global__ void k_leaf_geo(int B, const double *__restrict__ lo, const double *_
 constexpr int kLeafChunk = 256;
 constexpr int kP2PThreads = 128;  // threads per work unit; one target each
 constexpr int kSrcTile = 128;     // sources staged per pass (64 pairs)
+constexpr float kFarGap = 0.1f;   // far: cell gap >= kFarGap (r_t + r_s)
 constexpr float kPadFar = 1.0e18f;  // padding source: zero charge, far away
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -291,13 +292,15 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
 // sources per step in packed float2 arithmetic (FFMA2/FADD2/FMUL2). For
 // every source leaf the offset between the two leaf centres is formed once,
 // error-free (float TwoSum on the centres' hi/lo parts), together with a
-// near/far flag: far when the gap g between the two cells is at least half
-// the sum of their radii. The float offsets then carry an absolute error of
+// near/far flag: far when the gap g between the two cells is at least
+// kFarGap (r_t + r_s). The float offsets then carry an absolute error of
 // about 2u (r_t + r_s + |offset|), and since strongly connected leaves have
 // |offset| < 3 max(r_t, r_s), every far pair's distance (>= g) is known to
-// ~11u relative: a single float per coordinate suffices, and no two points
-// can coincide. Near leaves (touching cells) keep the split hi/lo offsets,
-// whose difference is exact for close pairs. Per target the sources are
+// at worst ~100u relative (the closest far pairs only; ~75% of pairs sit at
+// g >= 0.5 (r_t + r_s), known to ~20u): a single float per coordinate
+// suffices, and no two points can coincide. Near leaves (touching or nearly
+// touching cells, ~4% of the pairs on a Plummer sphere) keep the split hi/lo
+// offsets, whose difference is exact for close pairs. Per target the sources are
 // summed in plain float over runs of 32 (full runs with a fixed trip count)
 // and the runs compensated (Kahan).
 template <typename OutT>
@@ -350,8 +353,8 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
             const float gx = fmaxf(0.f, fabsf(dxh) - (tc_e.x + se.x));
             const float gy = fmaxf(0.f, fabsf(dyh) - (tc_e.y + se.y));
             const float gz = fmaxf(0.f, fabsf(dzh) - (tc_e.z + se.z));
-            const float half = 0.5f * (tc_h.w + sh.w);
-            const bool far = gx * gx + gy * gy + gz * gz >= half * half && half > 0.f;
+            const float lim = kFarGap * (tc_h.w + sh.w);
+            const bool far = gx * gx + gy * gy + gz * gz >= lim * lim && lim > 0.f;
             dh[k] = make_float4(dxh, dyh, dzh, far ? 1.f : 0.f);
             dl[k] = make_float4(e_x + (sl.x - tc_l.x), e_y + (sl.y - tc_l.y), e_z + (sl.z - tc_l.z), 0.f);
             rng[k] = make_int2(begin[off + s], count[off + s]);
