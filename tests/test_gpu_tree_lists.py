@@ -93,3 +93,16 @@ def test_nonfinite_points_rejected(gpu_lib):
     # the context is still usable afterwards
     plan = fmm.fmm_plan(torch.from_numpy(inputs.points("uniform", 100, 1)).cuda(), 3, 3, 0.5)
     assert fmm.fmm_plan_stats(plan)["n"] == 100
+
+
+@pytest.mark.parametrize("kind,n,levels", [("plummer", 30001, 10), ("gmm", 9000, 9)])
+def test_gpu_lists_are_symmetric(gpu_lib, kind, n, levels):
+    fmm = gpu_lib
+    x = make(kind, n)
+    plan = fmm.fmm_plan(torch.from_numpy(x).cuda(), levels, 3, 0.5)
+    for l in range(levels + 1):
+        for kind_ in ("weak", "strong"):
+            p, s = fmm.fmm_plan_list(plan, l, kind_)
+            a = np.repeat(np.arange(len(p) - 1), np.diff(p))
+            fwd = set(zip(a.tolist(), s.tolist()))
+            assert fwd == {(b, c) for c, b in fwd}

@@ -334,3 +334,17 @@ def test_octree_fmm_accuracy(kind, theta, p, tol):
     d_phi, d_E = oracle.direct(x, q)
     assert np.linalg.norm(phi - d_phi) / np.linalg.norm(d_phi) <= tol
     assert np.linalg.norm(E - d_E) / np.linalg.norm(d_E) <= 3 * tol
+
+
+@pytest.mark.parametrize("step,levels", [(1, 8), (3, 6)])
+@pytest.mark.parametrize("kind", ["plummer", "gmm"])
+def test_lists_are_symmetric(kind, step, levels):
+    """The theta-criterion is symmetric in the two boxes (Eq. 2.2), so every
+    weak or strong pair is stored in both orientations."""
+    x = inputs.points(kind, 3000, seed=7)
+    T = oracle.Tree(x, levels, 2, 0.5, step=step)
+    for l in range(levels + 1):
+        for kind_ in ("weak", "strong"):
+            p, s = T.lists(l, kind_)
+            pairs = {(a, int(b)) for a in range(len(p) - 1) for b in s[p[a]:p[a + 1]]}
+            assert pairs == {(b, a) for a, b in pairs}
