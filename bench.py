@@ -391,7 +391,7 @@ def bench_batch(args, rank, world, local):
     form on the same systems."""
     import torch
     import paper_2002_04894_gb300 as fmm
-    from paper_2002_04894_gb300 import tune
+    from paper_2002_04894_gb300 import serve, tune
 
     torch.cuda.set_device(local)
     fmm.load()
@@ -416,7 +416,7 @@ def bench_batch(args, rank, world, local):
     cfgs = [table[(int(np.log2(n)), i % 2)] for i, n in enumerate(ns)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plans = [fmm.fmm_plan(x, c.levels, c.p, c.theta, prec=fmm.FMM_PREC_MIXED) for x, c in zip(xs, cfgs)]
+    plans = serve.build_plans(xs, cfgs, prec=fmm.FMM_PREC_MIXED, workers=8)
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t0
     pots = [torch.empty(int(n), dtype=torch.float32, device="cuda") for n in ns]

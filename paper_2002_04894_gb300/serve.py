@@ -196,6 +196,32 @@ class FmmServer:
         return run_schedule(requests, self._execute, self.budget, self.workers, realtime)
 
 
+def build_plans(points, configs, prec: int = 1, workers: int = 8):
+    """fmm_plan for many systems at once: `workers` host threads, each with
+    its own CUDA stream, so that one plan's host-side steps (level sizes read
+    back, allocations) overlap the others' device work. `configs` holds
+    objects with levels, p and theta (e.g. tune.Config). Returns the plans in
+    input order; their streams are synchronised before returning."""
+    import concurrent.futures as cf
+
+    import torch
+
+    from . import fmm_plan
+    streams = [torch.cuda.Stream() for _ in range(workers)]
+
+    def one(i):
+        s = streams[i % workers]
+        c = configs[i]
+        with torch.cuda.stream(s):
+            return fmm_plan(points[i], c.levels, c.p, c.theta, prec=prec, stream=s)
+
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        plans = list(ex.map(one, range(len(points))))
+    for s in streams:
+        s.synchronize()
+    return plans
+
+
 def latency_stats(results) -> dict:
     lat = np.array([r.latency for r in results])
     return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
