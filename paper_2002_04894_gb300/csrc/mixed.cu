@@ -244,6 +244,11 @@ constexpr int kSrcTile = 128;     // sources staged per pass (64 pairs)
 constexpr float kFarGap = 0.1f;   // far: cell gap >= kFarGap (r_t + r_s)
 constexpr float kPadFar = 1.0e18f;  // padding source: zero charge, far away
 
+__device__ __forceinline__ float rcp_approx(float x) {  // reciprocal on the XU pipe (~1 ulp)
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -260,8 +265,9 @@ __device__ __forceinline__ void far_pair2(float2 X, float2 Y, float2 Z, const fl
     const float2 dz = add2(Z, make_float2(B.x, B.y));
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));  // XU, not the FMA pipe
     const float2 qr = mul2(make_float2(B.z, B.w), rinv);
-    const float2 qr3 = mul2(qr, mul2(rinv, rinv));
+    const float2 qr3 = mul2(qr, rinv2);
     a[0] = add2(a[0], qr);
     a[1] = fma2(qr3, dx, a[1]);
     a[2] = fma2(qr3, dy, a[2]);
@@ -279,8 +285,9 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
     const float2 dz = add2(add2(Z, make_float2(B.x, B.y)), add2(ZL, make_float2(D.x, D.y)));
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     const float2 rinv = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+    const float2 rinv2 = make_float2(r2.x > 0.f ? rcp_approx(r2.x) : 0.f, r2.y > 0.f ? rcp_approx(r2.y) : 0.f);
     const float2 qr = mul2(make_float2(B.z, B.w), rinv);
-    const float2 qr3 = mul2(qr, mul2(rinv, rinv));
+    const float2 qr3 = mul2(qr, rinv2);
     a[0] = add2(a[0], qr);
     a[1] = fma2(qr3, dx, a[1]);
     a[2] = fma2(qr3, dy, a[2]);
