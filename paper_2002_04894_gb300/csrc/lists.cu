@@ -32,11 +32,18 @@ __device__ __forceinline__ bool theta_weak(double theta, const double *ca, doubl
     const double dx = __dsub_rn(ca[0], cb[0]);
     const double dy = __dsub_rn(ca[1], cb[1]);
     const double dz = __dsub_rn(ca[2], cb[2]);
-    const double d = __dsqrt_rn(
-        __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     const double R = ra > rb ? ra : rb;
     const double r = ra > rb ? rb : ra;
-    return theta > 0.0 && d > 0.0 && __dadd_rn(R, __dmul_rn(theta, r)) <= __dmul_rn(theta, d);
+    if (!(theta > 0.0) || !(s > 0.0)) return false;
+    const double L = __dadd_rn(R, __dmul_rn(theta, r));
+    // decided on squares when clearly away from the boundary (the rounding of
+    // the sqrt form is ~2u, the margin 1e-12); the exact test otherwise, so
+    // the outcome is that of L <= theta * sqrt(s) in every case
+    const double a = L * L, b = theta * theta * s;
+    if (a < b * (1.0 - 1e-12)) return true;
+    if (a > b * (1.0 + 1e-12)) return false;
+    return L <= __dmul_rn(theta, __dsqrt_rn(s));
 }
 
 // One thread per strongly connected pair (T, S) of the parent level: its
