@@ -58,22 +58,25 @@ __global__ void k_gather_qf(const T *__restrict__ qin, const int32_t *__restrict
         q[i] = (float)qin[perm[i]];
 }
 
-// P2M on scaled offsets; the warp sums go to double accumulators, and the
-// leaf's multipole is stored unscaled in double (M_n^m = r^n Mhat_n^m).
+// P2M on scaled offsets; each warp's sums (over its batches of 32 points)
+// stay in float in shared memory, the block's warps are combined in double,
+// and the leaf's multipole is stored unscaled in double (M_n^m = r^n Mhat_n^m).
+// (A double add by one lane per coefficient would occupy GB300's narrow FP64
+// pipe as long as a full-warp one.)
 __global__ void __launch_bounds__(kThreads)
 k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__restrict__ q,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const double *__restrict__ radius, double2 *__restrict__ M) {
-    extern __shared__ double2 acc[];  // [warps][nc]
+    extern __shared__ float2 accf[];  // [warps][nc]
     const int nc = ncoef(p);
     const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
     const int b = begin[g], cnt = count[g];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const double rs = box_scale(radius[g]);
     const float rinv = (float)(1.0 / rs);
-    for (int c = threadIdx.x; c < nc * (kThreads / 32); c += kThreads) acc[c] = make_double2(0.0, 0.0);
+    for (int c = threadIdx.x; c < nc * (kThreads / 32); c += kThreads) accf[c] = make_float2(0.f, 0.f);
     __syncthreads();
-    double2 *mine = acc + w * nc;
+    float2 *mine = accf + w * nc;
     for (int base = w * 32; base < cnt; base += kThreads) {
         const int i = base + lane;
         const bool valid = i < cnt;
@@ -111,8 +114,8 @@ k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__
                     vi += __shfl_xor_sync(0xffffffffu, vi, o);
                 }
                 if (lane == 0) {
-                    double2 a = mine[tri(nn, m)];
-                    mine[tri(nn, m)] = make_double2(a.x + vr, a.y + vi);
+                    const float2 a = mine[tri(nn, m)];
+                    mine[tri(nn, m)] = make_float2(a.x + vr, a.y + vi);
                 }
             }
         }
@@ -124,7 +127,8 @@ k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__
         double s = 1.0;
         for (int j = 0; j < nn; j++) s *= rs;
         double2 v = make_double2(0.0, 0.0);
-        for (int j = 0; j < kThreads / 32; j++) v = cadd(v, acc[j * nc + c]);
+        for (int j = 0; j < kThreads / 32; j++)
+            v = cadd(v, make_double2((double)accf[j * nc + c].x, (double)accf[j * nc + c].y));
         M[g * nc + c] = make_double2(v.x * s, v.y * s);
     }
 }
@@ -472,7 +476,7 @@ cudaError_t mixed_p2m(Plan &P, const void *charges, int dtype) {
         FMM_LAUNCH(k_gather_qf<double>, gq, 256, 0, P.stream, (const double *)charges, P.perm, P.qf, n);
     else
         FMM_LAUNCH(k_gather_qf<float>, gq, 256, 0, P.stream, (const float *)charges, P.perm, P.qf, n);
-    FMM_LAUNCH(k_p2m_f32, (unsigned)P.nleaf, kThreads, sizeof(double2) * P.nc * (kThreads / 32),
+    FMM_LAUNCH(k_p2m_f32, (unsigned)P.nleaf, kThreads, sizeof(float2) * P.nc * (kThreads / 32),
                P.stream, P.B, P.p, n, P.hl, P.qf, P.begin, P.count, P.radius, P.M);
     return cudaGetLastError();
 }
