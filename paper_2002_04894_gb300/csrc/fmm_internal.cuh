@@ -61,7 +61,6 @@ struct Plan {
     double *m2l_tab = nullptr;
     int m2l_ntab = 0, m2l_threads = 0;
     size_t m2l_smem = 0;
-    size_t grp_smem = 0;  // shared bytes of the grouped M2M / L2L kernels
     // mixed precision: leaf offsets hi|lo (6n floats), float charges and far
     // field, radius-scaled float multipoles for the single-precision M2L
     float *hl = nullptr, *qf = nullptr, *far_phi_f = nullptr, *far_E_f = nullptr;

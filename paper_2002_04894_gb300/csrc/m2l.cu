@@ -179,223 +179,211 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
 // expansion onto the child offset, translate along z, rotate back:
 //   local, rotated frame (Lt = L / F):    Lt'_j^i = sum_{k>=j} Lt_k^i F_ki rho^{k-j}/(k-j)! / F_ji
 // The forward rotation of a local expansion uses the two folds of the M2L
-// back rotation with conjugate phases. One child per thread.
+// back rotation with conjugate phases.
 // ---------------------------------------------------------------------------
 
-// M2M and L2L in the rotational form, a group of kGrp = 4 threads per child
-// box: the child's coefficient vectors live in shared memory (interleaved
-// over the block's children with a padded stride, so that the group's
-// threads and neighbouring groups fall on different banks), and each thread
-// of the group computes every fourth output of the folds and of the axial
-// shift. This splits each child's serial multiply-add chains four ways and
-// packs four times as many threads into the shared memory a child needs.
+// One warp per child box. Every stage (phase, fold, axial shift) is
+// independent across degrees, so the warp's lanes take the outputs of all
+// degrees at once (coefficient c = lane, lane + 32, ...) and the child's
+// vectors sit in the warp's slice of shared memory between the stages:
 //   multipole, rotated frame (Mt = F M):  Mt'_n^m = F_nm sum_k rho^k/k! Mt_{n-k}^m / F_{n-k,m}
 //   local, rotated frame (Lt = L / F):   Lt'_j^i = sum_{k>=j} Lt_k^i F_ki rho^{k-j}/(k-j)! / F_ji
-constexpr int kGrp = 4;
-constexpr int kGrpThreads = 128;  // 32 children per block
+// GB300 retires about two FP64 multiply-adds per clock per SM, so a child
+// spread over a warp keeps each lane's serial chain to a few dozen
+// operations (the small levels near the root finish in microseconds), and
+// blocks of 1 to 8 warps spread even a small level over all SMs.
+constexpr int kWarpChildMax = 8;
 
-struct GrpCtx {
-    int lane, stride;  // lane within the group, element stride of the interleaved arrays
+__device__ __forceinline__ int degree_of(int c) {
+    int n = (int)((sqrtf(8.f * (float)c + 1.f) - 1.f) * 0.5f);
+    while (tri(n + 1, 0) <= c) n++;
+    while (n > 0 && tri(n, 0) > c) n--;
+    return n;
+}
+
+// double2 slots of one warp's slice: A, B (nc each), powers of e^{ia} and
+// e^{ib} (p+1 each), rho^k/k! (p+1 doubles)
+__host__ __device__ inline int warp_slice(int p) { return 2 * ncoef(p) + 2 * (p + 1) + (p + 2) / 2; }
+// doubles of the shared tables: D, F, 1/F, 1/k
+__host__ __device__ inline int warp_tabs(int p) {
+    return (p + 1) * (p + 2) * (2 * p + 3) / 6 + 2 * ncoef(p) + p + 2;
+}
+
+// post(c, k, out_k) for out_k = fold(D^n) of in (degree n of c, k = c - tri(n, 0))
+template <bool kTranspose, typename Post>
+__device__ __forceinline__ void fold_all(const double *__restrict__ Dt, int nc, const double2 *in, int lane,
+                                         Post post) {
+    for (int c = lane; c < nc; c += 32) {
+        const int n = degree_of(c), b = tri(n, 0), k = c - b, par = (n + k) & 1;
+        const double *Dn = Dt + n * (n + 1) * (2 * n + 1) / 6;
+        double ev = 0.0, od = 0.0;  // sums over even and odd m
+        int m = 0;
+        for (; m + 1 <= n; m += 2) {
+            const double2 v0 = in[b + m], v1 = in[b + m + 1];
+            ev = fma(kTranspose ? Dn[m * (n + 1) + k] : Dn[k * (n + 1) + m], par ? v0.y : v0.x, ev);
+            od = fma(kTranspose ? Dn[(m + 1) * (n + 1) + k] : Dn[k * (n + 1) + m + 1], par ? v1.x : v1.y, od);
+        }
+        if (m == n) {
+            const double2 v0 = in[b + m];
+            ev = fma(kTranspose ? Dn[m * (n + 1) + k] : Dn[k * (n + 1) + m], par ? v0.y : v0.x, ev);
+        }
+        post(c, k, par ? make_double2(od, ev) : make_double2(ev, od));
+    }
+}
+
+struct WarpChild {
+    double2 *A, *B, *pa, *pb;
+    double *f;
+    const double *Dt, *Ft, *iFt;
+    int64_t gc, gp;
+    int nc, lane;
 };
 
-__device__ __forceinline__ double2 cpow(double2 z, int e) {
-    double2 r = make_double2(1.0, 0.0);
-    for (int i = 0; i < e; i++) r = cmul(r, z);
-    return r;
+// Tables into shared memory; the warp's child, its parent at `step` levels
+// up, and the powers of the child-to-parent offset. Returns false for warps
+// past the end of the level (they take no further part: no block barrier
+// follows).
+__device__ __forceinline__ bool warp_child_setup(int level, int step, int p, const double *__restrict__ centre,
+                                                 const double *__restrict__ gtab, double2 *sw, WarpChild &W) {
+    const int nc = ncoef(p), nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    double *tab = (double *)(sw + nw * warp_slice(p));
+    for (int i = threadIdx.x; i < nD; i += blockDim.x) tab[i] = gtab[i];
+    for (int i = threadIdx.x; i < 2 * nc + p + 2; i += blockDim.x) tab[nD + i] = gtab[2 * nD + i];
+    __syncthreads();
+    const int64_t j = blockIdx.x * (int64_t)nw + w;
+    if (j >= ((int64_t)1 << level)) return false;
+    W.A = sw + w * warp_slice(p);
+    W.B = W.A + nc;
+    W.pa = W.B + nc;
+    W.pb = W.pa + p + 1;
+    W.f = (double *)(W.pb + p + 1);
+    W.Dt = tab;
+    W.Ft = tab + nD;
+    W.iFt = W.Ft + nc;
+    W.gc = ((int64_t)1 << level) - 1 + j;
+    W.gp = ((W.gc + 1) >> step) - 1;
+    W.nc = nc;
+    W.lane = lane;
+    if (lane < 3) {
+        const int64_t gc = W.gc, gp = W.gp;
+        const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
+                     dz = centre[3 * gc + 2] - centre[3 * gp + 2];
+        const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
+        if (lane == 2) {
+            const double *ik = W.iFt + nc;
+            double t = 1.0;
+            for (int k = 0; k <= p; k++) {
+                W.f[k] = t;
+                t = t * rho * ik[k + 1];
+            }
+        } else {
+            double2 z;
+            if (lane == 0) {
+                const double irxy = rxy > 0.0 ? 1.0 / rxy : 0.0;
+                z = rxy > 0.0 ? make_double2(dx * irxy, dy * irxy) : make_double2(1.0, 0.0);
+            } else {
+                const double irho = rho > 0.0 ? 1.0 / rho : 0.0;
+                z = rho > 0.0 ? make_double2(dz * irho, rxy * irho) : make_double2(1.0, 0.0);
+            }
+            double2 *pw = lane == 0 ? W.pa : W.pb, t = make_double2(1.0, 0.0);
+            for (int k = 0; k <= p; k++) {
+                pw[k] = t;
+                t = cmul(t, z);
+            }
+        }
+    }
+    __syncwarp();
+    return true;
 }
 
-// out_k (k = lane, lane + 4, ...; k <= n) = fold(D^n) of in, times
-// (k ? 2 : 1) * post^k when post is given
-__device__ __forceinline__ void fold_grp(const double *__restrict__ D, int n, const double2 *in,
-                                         double2 *out, const GrpCtx &g, bool transpose, bool scale,
-                                         double2 post) {
-    const double2 step = cpow(post, kGrp);
-    double2 pk = cpow(post, g.lane);
-    for (int k = g.lane; k <= n; k += kGrp) {
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_m2m_warp(int level, int step, int p, const double *__restrict__ centre, double2 *M,
+           const double *__restrict__ gtab) {
+    extern __shared__ double2 sw[];
+    WarpChild W;
+    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
+    const int nc = W.nc, lane = W.lane;
+    double2 *A = W.A, *B = W.B;
+    const double2 *pa = W.pa, *pb = W.pb;
+    const double *f = W.f, *Ft = W.Ft, *iFt = W.iFt;
+    // forward rotation: u = F M (-i e^{ia})^m, doubled for m > 0
+    for (int c = lane; c < nc; c += 32) {
+        const int m = c - tri(degree_of(c), 0);
+        A[c] = cscale(cmul(M[W.gc * nc + c], mul_ipow(4 - (m & 3), pa[m])), Ft[c] * (m ? 2.0 : 1.0));
+    }
+    __syncwarp();
+    fold_all<false>(W.Dt, nc, A, lane,
+                    [&](int c, int k, double2 r) { B[c] = cscale(cmul(r, pb[k]), k ? 2.0 : 1.0); });
+    __syncwarp();
+    // v = i^m (folded back); the axial input is v / F
+    fold_all<true>(W.Dt, nc, B, lane, [&](int c, int m, double2 r) { A[c] = cscale(mul_ipow(m, r), iFt[c]); });
+    __syncwarp();
+    // axial shift; then the back rotation's i^-m and doubling
+    for (int c = lane; c < nc; c += 32) {
+        const int n = degree_of(c), m = c - tri(n, 0);
         double re = 0.0, im = 0.0;
-        const int par = (n + k) & 1;
-        for (int m = par; m <= n; m += 2)
-            re = fma(transpose ? D[m * (n + 1) + k] : D[k * (n + 1) + m], in[m * g.stride].x, re);
-        for (int m = 1 - par; m <= n; m += 2)
-            im = fma(transpose ? D[m * (n + 1) + k] : D[k * (n + 1) + m], in[m * g.stride].y, im);
-        double2 r = make_double2(re, im);
-        if (scale) r = cscale(cmul(r, pk), k ? 2.0 : 1.0);
-        out[k * g.stride] = r;
-        pk = cmul(pk, step);
-    }
-}
-
-__global__ void k_m2m_rot(int level, int step, int p, const double *__restrict__ centre, double2 *M,
-                          const double *__restrict__ gtab, int ntab) {
-    extern __shared__ double2 sm2[];
-    const int nc = ncoef(p), C = blockDim.x / kGrp, S = C + 1, tid = threadIdx.x;
-    double2 *V = sm2, *U = V + nc * S, *W = U + (p + 1) * S;
-    double *tab = (double *)(W + (p + 1) * S);
-    for (int i = tid; i < ntab; i += blockDim.x) tab[i] = gtab[i];
-    __syncthreads();
-    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
-    const double *Dt = tab, *Ft = tab + 2 * nD, *iFt = Ft + nc, *ik = iFt + nc;
-    const int grp = tid / kGrp;
-    const GrpCtx g{tid % kGrp, S};
-    double2 *v = V + grp, *u = U + grp, *x = W + grp;
-    const int64_t j = blockIdx.x * (int64_t)C + grp;  // child index within level
-    const bool valid = j < ((int64_t)1 << level);
-    const int64_t gc = ((int64_t)1 << level) - 1 + (valid ? j : 0), gp = ((gc + 1) >> step) - 1;
-    const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
-                 dz = centre[3 * gc + 2] - centre[3 * gp + 2];
-    const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
-    const double irxy = rxy > 0.0 ? 1.0 / rxy : 0.0, irho = rho > 0.0 ? 1.0 / rho : 0.0;
-    const double2 ea = rxy > 0.0 ? make_double2(dx * irxy, dy * irxy) : make_double2(1.0, 0.0);
-    const double2 eb = rho > 0.0 ? make_double2(dz * irho, rxy * irho) : make_double2(1.0, 0.0);
-    const double2 eai = make_double2(ea.y, -ea.x), ebc = cconj(eb), eac = cconj(ea);
-    const double2 one = make_double2(1.0, 0.0);
-    // forward rotation of the child's multipole -> v (F-normalised, rotated frame)
-    const double *Dn = Dt;
-    for (int n = 0; n <= p; n++) {
-        {
-            const double2 st = cpow(eai, kGrp);
-            double2 ph = cpow(eai, g.lane);
-            for (int m = g.lane; m <= n; m += kGrp) {
-                const int c = tri(n, m);
-                const double2 mv = valid ? M[gc * nc + c] : make_double2(0.0, 0.0);
-                u[m * S] = cscale(cmul(mv, ph), Ft[c] * (m ? 2.0 : 1.0));
-                ph = cmul(ph, st);
-            }
+        for (int k = 0; k <= n - m; k++) {
+            const double2 t = A[tri(n - k, m)];
+            re = fma(f[k], t.x, re);
+            im = fma(f[k], t.y, im);
         }
-        __syncwarp();
-        fold_grp(Dn, n, u, x, g, false, true, eb);
-        __syncwarp();
-        fold_grp(Dn, n, x, u, g, true, false, one);
-        __syncwarp();
-        for (int m = g.lane; m <= n; m += kGrp) v[tri(n, m) * S] = mul_ipow(m, u[m * S]);
-        Dn += (n + 1) * (n + 1);
+        B[c] = cscale(mul_ipow(4 - (m & 3), make_double2(re, im)), Ft[c] * (m ? 2.0 : 1.0));
     }
     __syncwarp();
-    // axial shift, order by order
-    for (int m = 0; m <= p; m++) {
-        for (int n = m + g.lane; n <= p; n += kGrp) u[(n - m) * S] = cscale(v[tri(n, m) * S], iFt[tri(n, m)]);
-        __syncwarp();
-        for (int n = m + g.lane; n <= p; n += kGrp) {
-            double re = 0.0, im = 0.0, f = 1.0;
-            for (int k = 0; k <= n - m; k++) {
-                const double2 t = u[(n - m - k) * S];
-                re = fma(f, t.x, re);
-                im = fma(f, t.y, im);
-                f = f * rho * ik[k + 1];
-            }
-            v[tri(n, m) * S] = cscale(make_double2(re, im), Ft[tri(n, m)]);
-        }
-        __syncwarp();
-    }
-    // inverse rotation; add into the parent
-    Dn = Dt;
-    for (int n = 0; n <= p; n++) {
-        for (int m = g.lane; m <= n; m += kGrp)
-            u[m * S] = cscale(mul_ipow(4 - (m & 3), v[tri(n, m) * S]), m ? 2.0 : 1.0);
-        __syncwarp();
-        fold_grp(Dn, n, u, x, g, false, true, ebc);
-        __syncwarp();
-        fold_grp(Dn, n, x, u, g, true, false, one);
-        __syncwarp();
-        if (valid) {
-            const double2 st = cpow(eac, kGrp);
-            double2 ph = cpow(eac, g.lane);
-            for (int m = g.lane; m <= n; m += kGrp) {
-                const int c = tri(n, m);
-                const double2 r = cscale(cmul(mul_ipow(m, u[m * S]), ph), iFt[c]);
-                atomicAdd(&M[gp * nc + c].x, r.x);
-                atomicAdd(&M[gp * nc + c].y, r.y);
-                ph = cmul(ph, st);
-            }
-        }
-        __syncwarp();
-        Dn += (n + 1) * (n + 1);
-    }
+    fold_all<false>(W.Dt, nc, B, lane,
+                    [&](int c, int k, double2 r) { A[c] = cscale(cmul(r, cconj(pb[k])), k ? 2.0 : 1.0); });
+    __syncwarp();
+    double2 *Mp = M + W.gp * nc;
+    fold_all<true>(W.Dt, nc, A, lane, [&](int c, int m, double2 r) {
+        const double2 t = cscale(cmul(mul_ipow(m, r), cconj(pa[m])), iFt[c]);
+        atomicAdd(&Mp[c].x, t.x);
+        atomicAdd(&Mp[c].y, t.y);
+    });
 }
 
-__global__ void k_l2l_rot(int level, int step, int p, const double *__restrict__ centre, double2 *L,
-                          const double *__restrict__ gtab, int ntab) {
-    extern __shared__ double2 sm2[];
-    const int nc = ncoef(p), C = blockDim.x / kGrp, S = C + 1, tid = threadIdx.x;
-    double2 *V = sm2, *U = V + nc * S, *W = U + (p + 1) * S;
-    double *tab = (double *)(W + (p + 1) * S);
-    for (int i = tid; i < ntab; i += blockDim.x) tab[i] = gtab[i];
-    __syncthreads();
-    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
-    const double *Dt = tab, *Ft = tab + 2 * nD, *iFt = Ft + nc, *ik = iFt + nc;
-    const int grp = tid / kGrp;
-    const GrpCtx g{tid % kGrp, S};
-    double2 *v = V + grp, *u = U + grp, *x = W + grp;
-    const int64_t j = blockIdx.x * (int64_t)C + grp;  // child index within level
-    const bool valid = j < ((int64_t)1 << level);
-    const int64_t gc = ((int64_t)1 << level) - 1 + (valid ? j : 0), gp = ((gc + 1) >> step) - 1;
-    const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
-                 dz = centre[3 * gc + 2] - centre[3 * gp + 2];
-    const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
-    const double irxy = rxy > 0.0 ? 1.0 / rxy : 0.0, irho = rho > 0.0 ? 1.0 / rho : 0.0;
-    const double2 ea = rxy > 0.0 ? make_double2(dx * irxy, dy * irxy) : make_double2(1.0, 0.0);
-    const double2 eb = rho > 0.0 ? make_double2(dz * irho, rxy * irho) : make_double2(1.0, 0.0);
-    const double2 ebc = cconj(eb), eac = cconj(ea);
-    const double2 one = make_double2(1.0, 0.0);
-    // forward rotation of the parent's local expansion: v = Lt (= L / F) in the rotated frame
-    const double *Dn = Dt;
-    for (int k = 0; k <= p; k++) {
-        {
-            const double2 st = cpow(eac, kGrp);
-            double2 ph = cpow(eac, g.lane);
-            for (int l = g.lane; l <= k; l += kGrp) {
-                const int c = tri(k, l);
-                u[l * S] = cscale(cmul(mul_ipow(l, L[gp * nc + c]), ph), (l ? 2.0 : 1.0) * iFt[c]);
-                ph = cmul(ph, st);
-            }
-        }
-        __syncwarp();
-        fold_grp(Dn, k, u, x, g, false, true, ebc);
-        __syncwarp();
-        fold_grp(Dn, k, x, u, g, true, false, one);
-        __syncwarp();
-        for (int m = g.lane; m <= k; m += kGrp) v[tri(k, m) * S] = mul_ipow(4 - (m & 3), u[m * S]);
-        Dn += (k + 1) * (k + 1);
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_l2l_warp(int level, int step, int p, const double *__restrict__ centre, double2 *L,
+           const double *__restrict__ gtab) {
+    extern __shared__ double2 sw[];
+    WarpChild W;
+    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
+    const int nc = W.nc, lane = W.lane, pmax = p;
+    double2 *A = W.A, *B = W.B;
+    const double2 *pa = W.pa, *pb = W.pb;
+    const double *f = W.f, *Ft = W.Ft, *iFt = W.iFt;
+    // forward rotation of the parent's local expansion: Lt = L / F, i^l e^{-ila}, doubled for l > 0
+    for (int c = lane; c < nc; c += 32) {
+        const int l = c - tri(degree_of(c), 0);
+        A[c] = cscale(cmul(mul_ipow(l, L[W.gp * nc + c]), cconj(pa[l])), (l ? 2.0 : 1.0) * iFt[c]);
     }
     __syncwarp();
-    // axial shift, order by order
-    for (int i = 0; i <= p; i++) {
-        for (int k = i + g.lane; k <= p; k += kGrp) u[(k - i) * S] = cscale(v[tri(k, i) * S], Ft[tri(k, i)]);
-        __syncwarp();
-        for (int jj = i + g.lane; jj <= p; jj += kGrp) {
-            double re = 0.0, im = 0.0, f = 1.0;
-            for (int k = jj; k <= p; k++) {
-                const double2 t = u[(k - i) * S];
-                re = fma(f, t.x, re);
-                im = fma(f, t.y, im);
-                f = f * rho * ik[k - jj + 1];
-            }
-            v[tri(jj, i) * S] = cscale(make_double2(re, im), iFt[tri(jj, i)]);
+    fold_all<false>(W.Dt, nc, A, lane,
+                    [&](int c, int k, double2 r) { B[c] = cscale(cmul(r, cconj(pb[k])), k ? 2.0 : 1.0); });
+    __syncwarp();
+    // v = i^-m (folded back); the axial input is v F
+    fold_all<true>(W.Dt, nc, B, lane,
+                   [&](int c, int m, double2 r) { A[c] = cscale(mul_ipow(4 - (m & 3), r), Ft[c]); });
+    __syncwarp();
+    // axial shift; then the back rotation's i^m and doubling
+    for (int c = lane; c < nc; c += 32) {
+        const int j = degree_of(c), i = c - tri(j, 0);
+        double re = 0.0, im = 0.0;
+        for (int k = j; k <= pmax; k++) {
+            const double2 t = A[tri(k, i)];
+            re = fma(f[k - j], t.x, re);
+            im = fma(f[k - j], t.y, im);
         }
-        __syncwarp();
+        B[c] = cscale(mul_ipow(i, make_double2(re, im)), iFt[c] * (i ? 2.0 : 1.0));
     }
-    // back rotation (as in M2L) and add to the child
-    Dn = Dt;
-    for (int k = 0; k <= p; k++) {
-        for (int m = g.lane; m <= k; m += kGrp) u[m * S] = cscale(mul_ipow(m, v[tri(k, m) * S]), m ? 2.0 : 1.0);
-        __syncwarp();
-        fold_grp(Dn, k, u, x, g, false, true, eb);
-        __syncwarp();
-        fold_grp(Dn, k, x, u, g, true, false, one);
-        __syncwarp();
-        if (valid) {
-            const double2 st = cpow(ea, kGrp);
-            double2 ph = cpow(ea, g.lane);
-            for (int l = g.lane; l <= k; l += kGrp) {
-                const int c = tri(k, l);
-                const double2 r = cscale(cmul(mul_ipow(4 - (l & 3), u[l * S]), ph), Ft[c]);
-                L[gc * nc + c] = cadd(L[gc * nc + c], r);
-                ph = cmul(ph, st);
-            }
-        }
-        __syncwarp();
-        Dn += (k + 1) * (k + 1);
-    }
+    __syncwarp();
+    fold_all<false>(W.Dt, nc, B, lane,
+                    [&](int c, int k, double2 r) { A[c] = cscale(cmul(r, pb[k]), k ? 2.0 : 1.0); });
+    __syncwarp();
+    double2 *Lc = L + W.gc * nc;
+    fold_all<true>(W.Dt, nc, A, lane, [&](int c, int l, double2 r) {
+        Lc[c] = cadd(Lc[c], cscale(cmul(mul_ipow(4 - (l & 3), r), pa[l]), Ft[c]));
+    });
 }
 
 }  // namespace
@@ -504,29 +492,39 @@ cudaError_t m2l_setup(Plan &P) {
     P.m2l_threads = threads;
     P.m2l_smem = smem(threads);
     e = allow_max_smem((const void *)k_m2l_rot_f64, P.m2l_smem);
-    P.grp_smem = (size_t)(nc + 2 * (P.p + 1)) * (kGrpThreads / kGrp + 1) * 16 + t.size() * 8;
+    const size_t grp_max = (size_t)kWarpChildMax * warp_slice(P.p) * 16 + (size_t)warp_tabs(P.p) * 8;
     if (e == cudaSuccess)
-        e = allow_max_smem((const void *)k_l2l_rot, P.grp_smem);
+        e = allow_max_smem((const void *)k_l2l_warp, grp_max);
     if (e == cudaSuccess)
-        e = allow_max_smem((const void *)k_m2m_rot, P.grp_smem);
+        e = allow_max_smem((const void *)k_m2m_warp, grp_max);
     return e;
 }
+
+// Warps (children) per block for a level of nch children: 8, or fewer so
+// that the level still spreads over twice the SM count in blocks.
+int warps_per_block(int64_t nch) {
+    int w = kWarpChildMax;
+    while (w > 1 && (nch + w - 1) / w < 2 * 152) w >>= 1;
+    return w;
+}
+
+size_t warp_child_smem(int p, int w) { return (size_t)w * warp_slice(p) * 16 + (size_t)warp_tabs(p) * 8; }
 
 // parents of level l-step from their descendants at level l (parents zeroed first)
 void m2m_level(Plan &P, int l) {
     const int64_t np = (int64_t)1 << (l - P.step), nch = (int64_t)1 << l;
     cudaMemsetAsync(P.M + (np - 1) * P.nc, 0, (size_t)np * P.nc * sizeof(double2), P.stream);
-    const int per = kGrpThreads / kGrp;
-    FMM_LAUNCH(k_m2m_rot, (unsigned)((nch + per - 1) / per), kGrpThreads, P.grp_smem, P.stream, l, P.step,
-               P.p, P.centre, P.M, P.m2l_tab, P.m2l_ntab);
+    const int w = warps_per_block(nch);
+    FMM_LAUNCH(k_m2m_warp, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l, P.step,
+               P.p, P.centre, P.M, P.m2l_tab);
 }
 
 // level l from its ancestors at level l-step
 void l2l_level(Plan &P, int l) {
     const int64_t nch = (int64_t)1 << l;
-    const int per = kGrpThreads / kGrp;
-    FMM_LAUNCH(k_l2l_rot, (unsigned)((nch + per - 1) / per), kGrpThreads, P.grp_smem, P.stream, l, P.step,
-               P.p, P.centre, P.L, P.m2l_tab, P.m2l_ntab);
+    const int w = warps_per_block(nch);
+    FMM_LAUNCH(k_l2l_warp, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l, P.step,
+               P.p, P.centre, P.L, P.m2l_tab);
 }
 
 // FP64 M2L over all levels in one launch; accumulates into L (zeroed first)
@@ -973,41 +971,54 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SP::COLS));
 }
 
+// One warp per box: lane n <= p forms r^-n (a single division), and each
+// coefficient takes its degree's factor from that lane.
+__device__ __forceinline__ double inv_radius_pow(const double *__restrict__ radius, int64_t g, int p, int lane) {
+    double pw = 1.0;
+    if (lane <= p) {
+        const double r = radius[g] > 0.0 ? radius[g] : 1.0;
+        double b = 1.0 / r;
+        for (int e = lane; e; e >>= 1) {
+            if (e & 1) pw *= b;
+            b *= b;
+        }
+    }
+    return pw;
+}
+
 // Mhat = M / r^n in float, every box (levels >= 1)
 __global__ void k_scale_multipoles(int64_t nbox, int p, const double *__restrict__ radius,
                                    const double2 *__restrict__ M, float2 *__restrict__ Mf) {
-    const int nc = ncoef(p);
-    const int64_t total = nbox * nc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = i / nc;
-        const int c = (int)(i % nc);
-        int n = 0;
-        while (tri(n + 1, 0) <= c) n++;
-        const double r = radius[g] > 0.0 ? radius[g] : 1.0;
-        double s = 1.0;
-        for (int j = 0; j < n; j++) s /= r;
-        const double2 m = M[i];
-        Mf[i] = make_float2((float)(m.x * s), (float)(m.y * s));
+    const int nc = ncoef(p), lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < nbox; g += nw) {
+        const double pw = inv_radius_pow(radius, g, p, lane);
+        for (int c0 = 0; c0 < nc; c0 += 32) {  // warp-uniform trip count around the shuffle
+            const int c = c0 + lane;
+            const double s = __shfl_sync(0xffffffffu, pw, degree_of(min(c, nc - 1)));
+            if (c < nc) {
+                const double2 m = M[g * nc + c];
+                Mf[g * nc + c] = make_float2((float)(m.x * s), (float)(m.y * s));
+            }
+        }
     }
 }
 
 // L = Lhat / r^n, every box
 __global__ void k_unscale_locals(int64_t nbox, int p, const double *__restrict__ radius,
                                  const double2 *__restrict__ Lh, double2 *__restrict__ L) {
-    const int nc = ncoef(p);
-    const int64_t total = nbox * nc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = i / nc;
-        const int c = (int)(i % nc);
-        int n = 0;
-        while (tri(n + 1, 0) <= c) n++;
-        const double r = radius[g] > 0.0 ? radius[g] : 1.0;
-        double s = 1.0;
-        for (int j = 0; j < n; j++) s *= r;
-        const double2 h = Lh[i];
-        L[i] = make_double2(h.x / s, h.y / s);
+    const int nc = ncoef(p), lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < nbox; g += nw) {
+        const double pw = inv_radius_pow(radius, g, p, lane);
+        for (int c0 = 0; c0 < nc; c0 += 32) {
+            const int c = c0 + lane;
+            const double s = __shfl_sync(0xffffffffu, pw, degree_of(min(c, nc - 1)));
+            if (c < nc) {
+                const double2 h = Lh[g * nc + c];
+                L[g * nc + c] = make_double2(h.x * s, h.y * s);
+            }
+        }
     }
 }
 
@@ -1096,7 +1107,7 @@ cudaError_t m2l_f32_setup(Plan &P) {
 // single-precision M2L over all levels; leaves the unscaled result in L
 cudaError_t m2l_f32_all(Plan &P) {
     const int64_t total = P.nbox * P.nc;
-    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    const unsigned grid = (unsigned)std::min<int64_t>((P.nbox + 7) / 8, 152 * 16);  // 8 boxes (warps) per block
     FMM_LAUNCH(k_scale_multipoles, grid, 256, 0, P.stream, P.nbox, P.p, P.radius, P.M, P.Mf);
     cudaMemsetAsync(P.Lh, 0, (size_t)total * sizeof(double2), P.stream);
     const int64_t tot = total_weak(P);
