@@ -68,6 +68,7 @@ struct Plan {
     bool m2l_tc = false;     // mixed form: M2L on the tensor cores (else the SIMT float kernel)
     bool tc_m2l_opt = false; // FMM_FLAG_TC_M2L requested
     void *tc_tab = nullptr;  // tensor-core M2L tables (per device and order, not owned)
+    void *f32_tab = nullptr;  // packed coefficient-pair tables of the float M2L (plan-owned)
     int tc_ctas = 0;
     float2 *Mf = nullptr;
     double2 *Lh = nullptr;  // r^k-scaled locals accumulated by the float M2L

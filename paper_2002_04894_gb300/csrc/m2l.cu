@@ -545,25 +545,40 @@ cudaError_t m2l_all(Plan &P) {
 // formed as Lhat_k = r_t^k L_k, so the translation becomes
 //   Lhat r_k^l = (1/rho) (r_t/rho)^k sum_n A(k,n,l) (r_s/rho)^n conj(Mhat r_n^l)
 // with r_s/rho, r_t/rho < 1 for every weak pair: all float values stay O(1).
-// The order p is a template parameter, so every loop is unrolled, the per-
-// degree vectors live in registers and the fixed tables (D, A, F) are read as
-// constant-bank operands of the multiply-adds; the full coefficient vector
-// between the steps lives in shared memory, one column per thread. The
-// target's local expansion is accumulated in double.
+// The target's local expansion is accumulated in double.
+//
+// GPU mapping: one weak pair per thread, all levels in one launch (pairs
+// sorted by target). Every degree (and every order of the translation) is
+// its own template instance, so a degree's input vector sits in registers;
+// a fold's outputs come from a runtime loop, two per iteration (one of each
+// parity), each a dot product of packed pairs -- (Re of one parity, Im of
+// the other) against a row of matching coefficient pairs -- in FFMA2. The
+// coefficient rows are read from global memory at warp-uniform addresses
+// (L1 broadcast), so the code stays a few thousand instructions that loop
+// instead of a straight line of every multiply-add. Between the stages the
+// pair's coefficients sit in its lane of tensor memory (degrees 0..9) and
+// in a shared-memory column (higher degrees).
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kPMax = FMM_MAX_P;
-constexpr int kTabN = (kPMax + 1) * (kPMax + 2) * (2 * kPMax + 3) / 6;  // sum (n+1)^2
-__constant__ float c_D[kTabN];     // D_n quadrant, offset n(n+1)(2n+1)/6, [k][m]
-__constant__ float c_A[kTabN];     // axial, per l a (kPMax+1-l)^2 block [k-l][n-l]
 __constant__ float c_F[(kPMax + 1) * (kPMax + 2) / 2];
 
-__host__ __device__ constexpr int dof(int n) { return n * (n + 1) * (2 * n + 1) / 6; }
-__host__ __device__ constexpr int aof(int l) {
-    // sum_{j<l} (kPMax+1-j)^2
-    return dof(kPMax + 1) - dof(kPMax + 1 - l);
+// Packed coefficient-pair tables of order P (float4 = two pairs), built per
+// plan in global memory:
+//   D rows     degree n, output k = 0..n, jp(n) float4: the pairs
+//              (D_{k,2j}, D_{k,2j+1}) when n+k is even, (D_{k,2j+1}, D_{k,2j})
+//              when odd, zero past m = n (D = d^n(pi/2));
+//   D^T rows   the same for the transposed matrix, from dpo(P+1);
+//   axial rows order l, output k = l..P, ja(P,l) float4: (A(k,n,l), A(k,n,l))
+//              for n = l..P, zero-padded, from 2 dpo(P+1).
+__host__ __device__ constexpr int jp_of(int n) { return (n + 4) / 4; }
+__host__ __device__ constexpr int dpo(int n) { return n <= 0 ? 0 : dpo(n - 1) + n * jp_of(n - 1); }
+__host__ __device__ constexpr int ja_of(int P, int l) { return (P + 2 - l) / 2; }
+__host__ __device__ constexpr int apo(int P, int l) {
+    return l <= 0 ? 0 : apo(P, l - 1) + (P + 2 - l) * ja_of(P, l - 1);
 }
+__host__ __device__ constexpr int pair_tab_len(int P) { return 2 * dpo(P + 1) + apo(P, P + 1); }
 
 __device__ __forceinline__ float2 fmulc(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -668,23 +683,6 @@ __device__ __forceinline__ void tm_wait_ld(float *v) {
 }
 
 template <int N>
-__device__ __forceinline__ void v_put_deg(const VS &vs, const float2 (&u)[N + 1]) {
-    if constexpr (N <= kTmDeg) {
-        float f[2 * (N + 1)];
-#pragma unroll
-        for (int m = 0; m <= N; m++) {
-            f[2 * m] = u[m].x;
-            f[2 * m + 1] = u[m].y;
-        }
-        TCols<0, 2 * (N + 1)>::st(vs.t + 2 * tri(N, 0), f);
-        tm_wait_st();
-    } else {
-#pragma unroll
-        for (int m = 0; m <= N; m++) vs.s[(tri(N, m) - kTmC) * vs.T] = u[m];
-    }
-}
-
-template <int N>
 __device__ __forceinline__ void v_get_deg(const VS &vs, float2 (&u)[N + 1]) {
     if constexpr (N <= kTmDeg) {
         float f[2 * (N + 1)];
@@ -698,28 +696,74 @@ __device__ __forceinline__ void v_get_deg(const VS &vs, float2 (&u)[N + 1]) {
     }
 }
 
-template <int N>
-__device__ __forceinline__ void ffold(const float2 (&v)[N + 1], float2 (&out)[N + 1], bool tr) {
-#pragma unroll
-    for (int k = 0; k <= N; k++) {
-        float re = 0.f, im = 0.f;
-#pragma unroll
-        for (int m = 0; m <= N; m++) {
-            const float d = tr ? c_D[dof(N) + m * (N + 1) + k] : c_D[dof(N) + k * (N + 1) + m];
-            if (((N + k + m) & 1) == 0)
-                re = fmaf(d, v[m].x, re);
-            else
-                im = fmaf(d, v[m].y, im);
-        }
-        out[k] = make_float2(re, im);
+__device__ __forceinline__ float2 fipow_rt(int m, float2 v) {  // i^m v, m at run time
+    const float2 r = (m & 1) ? make_float2(-v.y, v.x) : v;
+    return (m & 2) ? make_float2(-r.x, -r.y) : r;
+}
+
+// coefficient c (run time) of the pair's storage
+__device__ __forceinline__ void v_put_rt(const VS &vs, int c, float2 v) {
+    if (c < kTmC) {  // warp-uniform
+        const float f[2] = {v.x, v.y};
+        tm_st<2>(vs.t + 2 * c, f);
+    } else {
+        vs.s[(c - kTmC) * vs.T] = v;
     }
 }
 
-// forward rotation of degree N of the scaled source multipole into V
+// (Re v_{2j}, Im v_{2j+1}) and (Re v_{2j+1}, Im v_{2j}), zero past m = N
 template <int N>
-__device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, VS vs, bool valid, float2 eai,
-                                     float2 ebv) {
-    float2 u[N + 1], w[N + 1];
+struct Pairs {
+    float2 e[2 * jp_of(N)], o[2 * jp_of(N)];
+};
+
+template <int N>
+__device__ __forceinline__ void make_pairs(const float2 (&v)[N + 1], Pairs<N> &q) {
+#pragma unroll
+    for (int j = 0; j < 2 * jp_of(N); j++) {
+        const float2 a = 2 * j <= N ? v[2 * j] : make_float2(0.f, 0.f);
+        const float2 b = 2 * j + 1 <= N ? v[2 * j + 1] : make_float2(0.f, 0.f);
+        q.e[j] = make_float2(a.x, b.y);
+        q.o[j] = make_float2(b.x, a.y);
+    }
+}
+
+// sum_j row_j * w_j over J float4 (two pairs each), two packed accumulators
+template <int J>
+__device__ __forceinline__ float2 dot_row(const float4 *__restrict__ row, const float2 *w) {
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < J; q++) {
+        const float4 d = row[q];
+        a0 = __ffma2_rn(make_float2(d.x, d.y), w[2 * q], a0);
+        a1 = __ffma2_rn(make_float2(d.z, d.w), w[2 * q + 1], a1);
+    }
+    return __fadd2_rn(a0, a1);
+}
+
+// out(k, fold_k) for k = 0..N of the fold with the rows of degree N; the
+// output's parity (N + k) picks the pair set
+template <int N, typename Out>
+__device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const Pairs<N> &q, Out &&out) {
+    constexpr int J = jp_of(N);
+    const float2 *w0 = (N & 1) ? q.o : q.e;
+    const float2 *w1 = (N & 1) ? q.e : q.o;
+#pragma unroll 1
+    for (int k = 0; k < N; k += 2) {
+        const float2 a0 = dot_row<J>(rows + k * J, w0);
+        const float2 a1 = dot_row<J>(rows + (k + 1) * J, w1);
+        out(k, a0);
+        out(k + 1, a1);
+    }
+    if constexpr ((N & 1) == 0) out(N, dot_row<J>(rows + N * J, w0));
+}
+
+// forward rotation of degree N of the scaled source multipole into the
+// storage; X is the thread's scratch column (stride 32)
+template <int P, int N>
+__device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS &vs, bool valid, float2 eai,
+                                        float2 ebv, const float4 *__restrict__ tab, float2 *X) {
+    float2 u[N + 1];
     float2 ph = make_float2(1.f, 0.f);
 #pragma unroll
     for (int m = 0; m <= N; m++) {
@@ -729,102 +773,108 @@ __device__ __noinline__ void fwd_deg(const float2 *__restrict__ Ms, VS vs, bool 
         u[m] = make_float2(t.x * s, t.y * s);
         ph = fmulc(ph, eai);
     }
-    ffold<N>(u, w, false);
+    Pairs<N> q;
+    make_pairs<N>(u, q);
     float2 pb = make_float2(1.f, 0.f);
-#pragma unroll
-    for (int k = 0; k <= N; k++) {
-        const float2 t = fmulc(w[k], pb);
-        w[k] = k ? make_float2(2.f * t.x, 2.f * t.y) : t;
+    fold_rt<N>(tab + dpo(N), q, [&](int k, float2 a) {
+        const float2 t = fmulc(a, pb);
         pb = fmulc(pb, ebv);
-    }
-    ffold<N>(w, u, true);
+        X[k * 32] = k ? make_float2(2.f * t.x, 2.f * t.y) : t;
+    });
+    float2 x[N + 1];
 #pragma unroll
-    for (int m = 0; m <= N; m++) u[m] = fipow(m, u[m]);
-    v_put_deg<N>(vs, u);
+    for (int k = 0; k <= N; k++) x[k] = X[k * 32];
+    make_pairs<N>(x, q);
+    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_rt(vs, tri(N, 0) + m, fipow_rt(m, a)); });
+    if constexpr (N <= kTmDeg) tm_wait_st();
 }
 
-constexpr int kRedStride = 36;  // floats per lane row of the per-warp transpose buffer
+// Row stride (floats) of the per-warp transpose buffer, odd so that both the
+// row writes and the column reads are conflict-free; the buffer shares the
+// warp's region with the scratch columns.
+template <int P>
+__host__ __device__ constexpr int red_stride() { return 2 * P + 3; }
 
 // inverse rotation of degree N, then the sum over the warp's pairs into the
 // scaled local Lh (double) of their target: a warp whose valid lanes share
 // one target (the common case: the pair list is sorted by target) transposes
 // its 2 (N+1) values per lane through shared memory and adds each column with
 // one atomic; otherwise a segmented shuffle sum over runs of equal target
-template <int N>
-__device__ __noinline__ void bwd_deg(VS vs, float2 ea, float2 ebv,
-                                     double2 *__restrict__ Lh, unsigned same_mask, bool head,
-                                     int uniform_tgt, double2 *__restrict__ Lbase, int nc, float *red) {
-    float2 u[N + 1], w[N + 1];
+template <int P, int N>
+__device__ __forceinline__ void bwd_deg(const VS &vs, float2 ea, float2 ebv, double2 *__restrict__ Lh,
+                                        unsigned same_mask, bool head, int uniform_tgt,
+                                        double2 *__restrict__ Lbase, const float4 *__restrict__ tab, float2 *X,
+                                        float *red) {
+    constexpr int NC = (P + 1) * (P + 2) / 2, RS = red_stride<P>();
+    float2 u[N + 1];
     v_get_deg<N>(vs, u);
 #pragma unroll
     for (int m = 0; m <= N; m++) {
         const float2 t = fipow(m, u[m]);
         u[m] = m ? make_float2(2.f * t.x, 2.f * t.y) : t;
     }
-    ffold<N>(u, w, false);
+    Pairs<N> q;
+    make_pairs<N>(u, q);
     float2 pb = make_float2(1.f, 0.f);
-#pragma unroll
-    for (int j = 0; j <= N; j++) {
-        const float2 t = fmulc(w[j], pb);
-        w[j] = j ? make_float2(2.f * t.x, 2.f * t.y) : t;
+    fold_rt<N>(tab + dpo(N), q, [&](int j, float2 a) {
+        const float2 t = fmulc(a, pb);
         pb = fmulc(pb, ebv);
-    }
-    ffold<N>(w, u, true);
+        X[j * 32] = j ? make_float2(2.f * t.x, 2.f * t.y) : t;
+    });
+    float2 x[N + 1];
+#pragma unroll
+    for (int k = 0; k <= N; k++) x[k] = X[k * 32];
+    make_pairs<N>(x, q);
+    __syncwarp();  // the transpose buffer overlaps the warp's scratch columns
+    const int lane = threadIdx.x & 31;
+    const bool uni = uniform_tgt >= 0;  // warp-uniform
     float2 ph = make_float2(1.f, 0.f);
-#pragma unroll
-    for (int l = 0; l <= N; l++) {
-        const int c = tri(N, l);
-        const float2 t = fmulc(fipow(4 - (l & 3), u[l]), ph);
-        u[l] = make_float2(t.x * c_F[c], t.y * c_F[c]);
+    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int l, float2 a) {
+        const float2 t = fmulc(fipow_rt(4 - (l & 3), a), ph);
         ph = fmulc(ph, ea);
-    }
-    if (N <= 15 && uniform_tgt >= 0) {  // 2 (N+1) <= 32 columns, one per lane
-        const int lane = threadIdx.x & 31;
-        float *row = red + lane * kRedStride;
+        const float f = c_F[tri(N, 0) + l];
+        const float rx = t.x * f, ry = t.y * f;
+        if (uni) {
+            red[lane * RS + l] = rx;
+            red[lane * RS + N + 1 + l] = ry;
+        } else {
+            float sx = rx, sy = ry;
 #pragma unroll
-        for (int l = 0; l <= N; l++) {
-            row[l] = u[l].x;
-            row[16 + l] = u[l].y;
-        }
-        __syncwarp();
-        const int col = lane <= N ? lane : (lane < 2 * (N + 1) ? 16 + lane - (N + 1) : -1);
-        if (col >= 0) {
-            float s = 0.f;
-#pragma unroll 8
-            for (int i = 0; i < 32; i++) s += red[i * kRedStride + col];
-            double *dst = (double *)&Lbase[(int64_t)uniform_tgt * nc + tri(N, col & 15)];
-            atomicAdd(dst + (col >= 16 ? 1 : 0), (double)s);
-        }
-        __syncwarp();
-        return;
-    }
-#pragma unroll
-    for (int l = 0; l <= N; l++) {
-        const int c = tri(N, l);
-        float rx = u[l].x, ry = u[l].y;
-#pragma unroll
-        for (int j = 0; j < 5; j++) {
-            const float ox = __shfl_down_sync(0xffffffffu, rx, 1 << j);
-            const float oy = __shfl_down_sync(0xffffffffu, ry, 1 << j);
-            if ((same_mask >> j) & 1u) {
-                rx += ox;
-                ry += oy;
+            for (int j = 0; j < 5; j++) {
+                const float ox = __shfl_down_sync(0xffffffffu, sx, 1 << j);
+                const float oy = __shfl_down_sync(0xffffffffu, sy, 1 << j);
+                if ((same_mask >> j) & 1u) {
+                    sx += ox;
+                    sy += oy;
+                }
+            }
+            if (head) {
+                atomicAdd(&Lh[tri(N, 0) + l].x, (double)sx);
+                atomicAdd(&Lh[tri(N, 0) + l].y, (double)sy);
             }
         }
-        if (head) {
-            atomicAdd(&Lh[c].x, (double)rx);
-            atomicAdd(&Lh[c].y, (double)ry);
+    });
+    if (uni) {
+        __syncwarp();
+        for (int col = lane; col < 2 * (N + 1); col += 32) {
+            float s = 0.f;
+#pragma unroll 8
+            for (int i = 0; i < 32; i++) s += red[i * RS + col];
+            const int l = col <= N ? col : col - (N + 1);
+            double *dst = (double *)&Lbase[(int64_t)uniform_tgt * NC + tri(N, l)];
+            atomicAdd(dst + (col <= N ? 0 : 1), (double)s);
         }
     }
+    __syncwarp();  // the next degree reuses the region
 }
 
-// translation along z of order L (orders P+1-L coefficients), in place in V;
-// qs = r_s / rho, qt = r_t / rho
+// translation along z of order L (orders P+1-L coefficients), in place in the
+// storage; qs = r_s / rho, qt = r_t / rho
 template <int P, int L>
-__device__ __noinline__ void axial_ord(VS vs, float qs, float qt, float rinv) {
-    constexpr int len = P + 1 - L;
+__device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, float rinv,
+                                          const float4 *__restrict__ tab) {
+    constexpr int len = P + 1 - L, J = ja_of(P, L);
     constexpr int ntm = L > kTmDeg ? 0 : (P < kTmDeg ? P : kTmDeg) + 1 - L;  // of them in tensor memory
-    float2 s[len];
     float f[2 * len];
 #pragma unroll
     for (int n = L; n <= P; n++) {
@@ -837,32 +887,23 @@ __device__ __noinline__ void axial_ord(VS vs, float qs, float qt, float rinv) {
         }
     }
     if constexpr (ntm > 0) tm_wait_ld<2 * ntm>(f);
+    float2 s[2 * J];
     float sp = 1.f;
 #pragma unroll
     for (int j = 0; j < L; j++) sp *= qs;
 #pragma unroll
-    for (int n = L; n <= P; n++) {
-        s[n - L] = make_float2(f[2 * (n - L)] * sp, -f[2 * (n - L) + 1] * sp);
+    for (int n = 0; n < 2 * J; n++) {
+        s[n] = n < len ? make_float2(f[2 * n] * sp, -f[2 * n + 1] * sp) : make_float2(0.f, 0.f);
         sp *= qs;
     }
     float tp = rinv;
 #pragma unroll
     for (int j = 0; j < L; j++) tp *= qt;
-#pragma unroll
+    const float4 *rows = tab + 2 * dpo(P + 1) + apo(P, L);
+#pragma unroll 1
     for (int k = L; k <= P; k++) {
-        float re = 0.f, im = 0.f;
-#pragma unroll
-        for (int n = L; n <= P; n++) {
-            const float a = c_A[aof(L) + (k - L) * (kPMax + 1 - L) + (n - L)];
-            re = fmaf(a, s[n - L].x, re);
-            im = fmaf(a, s[n - L].y, im);
-        }
-        if (k <= kTmDeg) {
-            const float o[2] = {re * tp, im * tp};
-            tm_st<2>(vs.t + 2 * tri(k, L), o);
-        } else {
-            vs.s[(tri(k, L) - kTmC) * vs.T] = make_float2(re * tp, im * tp);
-        }
+        const float2 a = dot_row<J>(rows + (k - L) * J, s);
+        v_put_rt(vs, tri(k, L), make_float2(a.x * tp, a.y * tp));
         tp *= qt;
     }
     if constexpr (ntm > 0) tm_wait_st();
@@ -870,29 +911,29 @@ __device__ __noinline__ void axial_ord(VS vs, float qs, float qt, float rinv) {
 
 template <int P, int N>
 struct Seq {
-    __device__ static __forceinline__ void fwd(const float2 *Ms, VS vs, bool valid, float2 eai, float2 ebv) {
-        __syncthreads();  // keep the block's warps on the same code (instruction cache)
-        fwd_deg<N>(Ms, vs, valid, eai, ebv);
-        Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv);
+    __device__ static __forceinline__ void fwd(const float2 *Ms, const VS &vs, bool valid, float2 eai, float2 ebv,
+                                               const float4 *tab, float2 *X) {
+        fwd_deg<P, N>(Ms, vs, valid, eai, ebv, tab, X);
+        Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv, tab, X);
     }
-    __device__ static __forceinline__ void axial(VS vs, float qs, float qt, float rinv) {
-        __syncthreads();
-        axial_ord<P, N>(vs, qs, qt, rinv);
-        Seq<P, N + 1>::axial(vs, qs, qt, rinv);
+    __device__ static __forceinline__ void axial(const VS &vs, float qs, float qt, float rinv, const float4 *tab) {
+        axial_ord<P, N>(vs, qs, qt, rinv, tab);
+        Seq<P, N + 1>::axial(vs, qs, qt, rinv, tab);
     }
-    __device__ static __forceinline__ void bwd(VS vs, float2 ea, float2 ebv, double2 *Lh, unsigned same,
-                                               bool head, int ut, double2 *Lbase, int nc, float *red) {
-        __syncthreads();
-        bwd_deg<N>(vs, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
-        Seq<P, N + 1>::bwd(vs, ea, ebv, Lh, same, head, ut, Lbase, nc, red);
+    __device__ static __forceinline__ void bwd(const VS &vs, float2 ea, float2 ebv, double2 *Lh, unsigned same,
+                                               bool head, int ut, double2 *Lbase, const float4 *tab, float2 *X,
+                                               float *red) {
+        bwd_deg<P, N>(vs, ea, ebv, Lh, same, head, ut, Lbase, tab, X, red);
+        Seq<P, N + 1>::bwd(vs, ea, ebv, Lh, same, head, ut, Lbase, tab, X, red);
     }
 };
 template <int P>
 struct Seq<P, P + 1> {
-    __device__ static __forceinline__ void fwd(const float2 *, VS, bool, float2, float2) {}
-    __device__ static __forceinline__ void axial(VS, float, float, float) {}
-    __device__ static __forceinline__ void bwd(VS, float2, float2, double2 *, unsigned, bool, int, double2 *,
-                                               int, float *) {}
+    __device__ static __forceinline__ void fwd(const float2 *, const VS &, bool, float2, float2, const float4 *,
+                                               float2 *) {}
+    __device__ static __forceinline__ void axial(const VS &, float, float, float, const float4 *) {}
+    __device__ static __forceinline__ void bwd(const VS &, float2, float2, double2 *, unsigned, bool, int,
+                                               double2 *, const float4 *, float2 *, float *) {}
 };
 
 constexpr int kF32Threads = 128;
@@ -905,30 +946,22 @@ struct VSplit {
     static constexpr int NT = NC < kTmC ? NC : kTmC;
     static constexpr int NS = NC - NT;
     static constexpr int COLS = 2 * NT <= 32 ? 32 : 2 * NT <= 64 ? 64 : 128;
+    // shared bytes: the storage columns, per warp the scratch / transpose
+    // region, then the coefficient-pair tables
+    static constexpr size_t TAB = (size_t)kF32Threads * NS * 8 + (size_t)kF32Threads * red_stride<P>() * 4;
+    static constexpr size_t SMEM = TAB + (size_t)pair_tab_len(P) * 16;
 };
 
-// one weak pair per thread, all levels; accumulates r_t^k L_k into Lh
+// one chunk of 128 pairs (pair g for this thread; lanes past the end carry zeros)
 template <int P>
-__global__ void __launch_bounds__(kF32Threads, 3)
-k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__restrict__ radius,
-              const float2 *__restrict__ Mf, double2 *__restrict__ Lh) {
+__device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__restrict__ centre,
+                                          const double *__restrict__ radius, const float2 *__restrict__ Mf,
+                                          double2 *__restrict__ Lh, const float4 *tab, int64_t g, int64_t npairs,
+                                          float2 *smf, uint32_t tbase) {
     using SP = VSplit<P>;
     constexpr int NC = SP::NC;
-    extern __shared__ float2 smf[];  // [NS][threads], then the per-warp transpose buffers
-    __shared__ uint32_t s_tmem;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(&s_tmem)),
-                     "r"(SP::COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = s_tmem;
-    const int64_t g = blockIdx.x * (int64_t)kF32Threads + tid;
-    const bool valid = g < PT.off[PT.lmax + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool valid = g < npairs;
     int64_t gt = -1, gs = 0;
     float dx = 1.f, dy = 0.f, dz = 0.f, rs = 1.f, rt = 1.f;
     if (valid) {
@@ -956,15 +989,44 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
     // every lane runs every stage (tensor-memory accesses are warp-wide); a
     // lane without a pair carries zeros
     const VS vs{smf + tid, tbase + ((uint32_t)(32 * (warp & 3)) << 16), kF32Threads};
-    Seq<P, 0>::fwd(Mf + gs * NC, vs, valid, eai, ebv);
-    Seq<P, 0>::axial(vs, qs, qt, rinv);
+    float *region = (float *)(smf + SP::NS * kF32Threads) + warp * 32 * red_stride<P>();
+    float2 *X = (float2 *)region + lane;
+    Seq<P, 0>::fwd(Mf + gs * NC, vs, valid, eai, ebv, tab, X);
+    Seq<P, 0>::axial(vs, qs, qt, rinv, tab);
     // the warp's pairs share one target (invalid lanes add zeros): transpose path
     const int t32 = gt >= 0 ? (int)gt : -1;
     const int tmax = __reduce_max_sync(0xffffffffu, t32);
     const bool uniform = __all_sync(0xffffffffu, t32 == tmax || t32 < 0);
-    float *red = (float *)(smf + SP::NS * kF32Threads) + warp * 32 * kRedStride;
-    Seq<P, 0>::bwd(vs, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, NC,
-                   red);
+    Seq<P, 0>::bwd(vs, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, tab, X,
+                   region);
+}
+
+// one weak pair per thread, all levels, blocks striding over chunks of 128
+// pairs; accumulates r_t^k L_k into Lh
+template <int P>
+__global__ void __launch_bounds__(kF32Threads, 3)
+k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__restrict__ radius,
+              const float2 *__restrict__ Mf, double2 *__restrict__ Lh, const float4 *__restrict__ gtab) {
+    using SP = VSplit<P>;
+    constexpr int NC = SP::NC;
+    extern __shared__ float2 smf[];  // [NS][threads], the per-warp regions, the tables
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float4 *tab = (float4 *)((char *)smf + SP::TAB);
+    for (int i = tid; i < pair_tab_len(P); i += kF32Threads) tab[i] = gtab[i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tmem)),
+                     "r"(SP::COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = s_tmem;
+    const int64_t npairs = PT.off[PT.lmax + 1];
+    for (int64_t g0 = blockIdx.x * (int64_t)kF32Threads; g0 < npairs; g0 += (int64_t)gridDim.x * kF32Threads)
+        m2l_chunk<P>(PT, centre, radius, Mf, Lh, tab, g0 + tid, npairs, smf, tbase);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -1033,41 +1095,72 @@ cudaError_t f32_tables_ready() {
     while (g_ctab_lock.exchange(1, std::memory_order_acquire)) {
     }
     if (!g_ctab_ready[dev]) {
-        std::vector<float> D, A, F;
+        std::vector<float> F;
         for (int n = 0; n <= kPMax; n++)
-            for (int k = 0; k <= n; k++)
-                for (int m = 0; m <= n; m++) D.push_back((float)wigner_half_pi(n, k, m));
-        auto Fl = [](int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); };
-        for (int l = 0; l <= kPMax; l++)
-            for (int k = l; k <= kPMax; k++)
-                for (int n = l; n <= kPMax; n++) {
-                    const long double a = factl(n + k) / (Fl(n, l) * Fl(k, l));
-                    A.push_back((float)(((k + l) & 1) ? -a : a));
-                }
-        for (int n = 0; n <= kPMax; n++)
-            for (int m = 0; m <= n; m++) F.push_back((float)Fl(n, m));
-        e = cudaMemcpyToSymbol(c_D, D.data(), D.size() * 4);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_A, A.data(), A.size() * 4);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_F, F.data(), F.size() * 4);
+            for (int m = 0; m <= n; m++) F.push_back((float)sqrtl(factl(n + m) * factl(n - m)));
+        e = cudaMemcpyToSymbol(c_F, F.data(), F.size() * 4);
         if (e == cudaSuccess) g_ctab_ready[dev] = true;
     }
     g_ctab_lock.store(0, std::memory_order_release);
     return e;
 }
 
+// the packed pair tables of order p (layout at jp_of / dpo / ja_of / apo)
+std::vector<float4> f32_pair_tables(int p) {
+    std::vector<float4> t;
+    t.reserve(pair_tab_len(p));
+    for (int tr = 0; tr < 2; tr++)
+        for (int n = 0; n <= p; n++)
+            for (int k = 0; k <= n; k++) {
+                auto M = [&](int m) -> float {
+                    if (m > n) return 0.f;
+                    return (float)(tr ? wigner_half_pi(n, m, k) : wigner_half_pi(n, k, m));
+                };
+                const bool odd = (n + k) & 1;
+                for (int q = 0; q < jp_of(n); q++) {
+                    const int a = 4 * q;  // pairs 2q, 2q+1 cover m = a .. a+3
+                    t.push_back(odd ? make_float4(M(a + 1), M(a), M(a + 3), M(a + 2))
+                                    : make_float4(M(a), M(a + 1), M(a + 2), M(a + 3)));
+                }
+            }
+    auto Fl = [](int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); };
+    for (int l = 0; l <= p; l++)
+        for (int k = l; k <= p; k++) {
+            auto A = [&](int n) -> float {
+                if (n > p) return 0.f;
+                const long double a = factl(n + k) / (Fl(n, l) * Fl(k, l));
+                return (float)(((k + l) & 1) ? -a : a);
+            };
+            for (int q = 0; q < ja_of(p, l); q++) {
+                const int n0 = l + 2 * q;
+                t.push_back(make_float4(A(n0), A(n0), A(n0 + 1), A(n0 + 1)));
+            }
+        }
+    return t;
+}
+
+const std::vector<float4> &f32_pair_tables_cached(int p) {
+    static std::mutex mu;
+    static std::vector<float4> cache[FMM_MAX_P + 1];
+    static bool ready[FMM_MAX_P + 1] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[p]) {
+        cache[p] = f32_pair_tables(p);
+        ready[p] = true;
+    }
+    return cache[p];
+}
+
 template <int P>
 cudaError_t attr_f32() {
-    constexpr int NC = (P + 1) * (P + 2) / 2;
-    return allow_max_smem((const void *)k_m2l_rot_f32<P>,
-                          (size_t)kF32Threads * VSplit<P>::NS * 8 + kF32Threads * kRedStride * 4);
+    return allow_max_smem((const void *)k_m2l_rot_f32<P>, VSplit<P>::SMEM);
 }
 
 template <int P>
 cudaError_t launch_f32(Plan &Pl, int64_t tot) {
-    constexpr int NC = (P + 1) * (P + 2) / 2;
-    const size_t smem = (size_t)kF32Threads * VSplit<P>::NS * 8 + kF32Threads * kRedStride * 4;
-    FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)((tot + kF32Threads - 1) / kF32Threads), kF32Threads, smem,
-               Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh);
+    const int64_t chunks = (tot + kF32Threads - 1) / kF32Threads;
+    FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)std::min<int64_t>(chunks, 152 * 3), kF32Threads, VSplit<P>::SMEM, Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh,
+               (const float4 *)Pl.f32_tab);
     return cudaGetLastError();
 }
 
@@ -1091,6 +1184,12 @@ cudaError_t m2l_f32_setup(Plan &P) {
         return m2l_tc_setup(P);
     }
     cudaError_t e = f32_tables_ready();
+    if (e != cudaSuccess) return e;
+    const std::vector<float4> &pt = f32_pair_tables_cached(P.p);
+    P.f32_tab = palloc(P, pt.size() * sizeof(float4));
+    if (!P.f32_tab) return cudaErrorMemoryAllocation;
+    // stream-ordered copy from pageable memory completes before return
+    e = cudaMemcpyAsync(P.f32_tab, pt.data(), pt.size() * sizeof(float4), cudaMemcpyHostToDevice, P.stream);
     if (e != cudaSuccess) return e;
     switch (P.p) {
         case 4: return attr_f32<4>();
