@@ -565,33 +565,29 @@ constexpr int kPMax = FMM_MAX_P;
 __constant__ float c_F[(kPMax + 1) * (kPMax + 2) / 2];
 
 // Packed coefficient-pair tables of order P (float4 = two pairs), built per
-// plan in global memory:
-//   D rows     degree n, output k = 0..n, jp(n) float4: the pairs
-//              (D_{k,2j}, D_{k,2j+1}) when n+k is even, (D_{k,2j+1}, D_{k,2j})
-//              when odd, zero past m = n (D = d^n(pi/2));
-//   D^T rows   the same for the transposed matrix, from dpo(P+1);
-//   axial rows order l, output k = l..P, ja(P,l) float4: (A(k,n,l), A(k,n,l))
-//              for n = l..P, zero-padded, from 2 dpo(P+1).
+// plan and staged in shared memory. A fold table has, per degree n and
+// output k = 0..n, jp(n) float4 holding the pairs (G_{k,2j}, G_{k,2j+1}) when
+// n+k is even and (G_{k,2j+1}, G_{k,2j}) when odd, zero past column n, for
+//   Df   (forward, first fold)   G_km = D_km F_nm (m?2:1) (k?2:1)
+//   DTf  (forward, second fold)  G_km = D_mk
+//   Db   (inverse, first fold)   G_km = D_km (m?2:1) (k?2:1)
+//   DTb  (inverse, second fold)  G_km = D_mk F_nk
+// (D = d^n(pi/2); the real factors of the rotation are folded in), at
+// offsets 0, 1, 2, 3 times dpo(P+1); then the axial rows: order l, output
+// k = l..P, ja(P,l) float4 of (A(k,n,l), A(k,n,l)) for n = l..P, zero-padded.
+// The i^m of the forward rotation and the i^-m of the inverse one cancel
+// through the conjugate of the translation, so neither is applied.
 __host__ __device__ constexpr int jp_of(int n) { return (n + 4) / 4; }
 __host__ __device__ constexpr int dpo(int n) { return n <= 0 ? 0 : dpo(n - 1) + n * jp_of(n - 1); }
 __host__ __device__ constexpr int ja_of(int P, int l) { return (P + 2 - l) / 2; }
 __host__ __device__ constexpr int apo(int P, int l) {
     return l <= 0 ? 0 : apo(P, l - 1) + (P + 2 - l) * ja_of(P, l - 1);
 }
-__host__ __device__ constexpr int pair_tab_len(int P) { return 2 * dpo(P + 1) + apo(P, P + 1); }
+__host__ __device__ constexpr int pair_tab_len(int P) { return 4 * dpo(P + 1) + apo(P, P + 1); }
 
 __device__ __forceinline__ float2 fmulc(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 fipow(int m, float2 v) {
-    switch (m & 3) {
-        case 0: return v;
-        case 1: return make_float2(-v.y, v.x);
-        case 2: return make_float2(-v.x, -v.y);
-        default: return make_float2(v.y, -v.x);
-    }
-}
-
 // Per-pair coefficient storage between the stages: degrees 0..kTmDeg live
 // in the thread's lane of tensor memory (Re, Im interleaved: columns
 // 2 tri(n,m), 2 tri(n,m)+1), the rest in a shared-memory column of the
@@ -696,11 +692,6 @@ __device__ __forceinline__ void v_get_deg(const VS &vs, float2 (&u)[N + 1]) {
     }
 }
 
-__device__ __forceinline__ float2 fipow_rt(int m, float2 v) {  // i^m v, m at run time
-    const float2 r = (m & 1) ? make_float2(-v.y, v.x) : v;
-    return (m & 2) ? make_float2(-r.x, -r.y) : r;
-}
-
 // coefficient c (run time) of the pair's storage
 __device__ __forceinline__ void v_put_rt(const VS &vs, int c, float2 v) {
     if (c < kTmC) {  // warp-uniform
@@ -767,33 +758,30 @@ __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS 
     float2 ph = make_float2(1.f, 0.f);
 #pragma unroll
     for (int m = 0; m <= N; m++) {
-        const float2 mv = valid ? Ms[tri(N, m)] : make_float2(0.f, 0.f);
-        const float s = c_F[tri(N, m)] * (m ? 2.f : 1.f);
-        const float2 t = fmulc(mv, ph);
-        u[m] = make_float2(t.x * s, t.y * s);
+        u[m] = fmulc(valid ? Ms[tri(N, m)] : make_float2(0.f, 0.f), ph);
         ph = fmulc(ph, eai);
     }
     Pairs<N> q;
     make_pairs<N>(u, q);
     float2 pb = make_float2(1.f, 0.f);
     fold_rt<N>(tab + dpo(N), q, [&](int k, float2 a) {
-        const float2 t = fmulc(a, pb);
+        X[k * 32] = fmulc(a, pb);
         pb = fmulc(pb, ebv);
-        X[k * 32] = k ? make_float2(2.f * t.x, 2.f * t.y) : t;
     });
     float2 x[N + 1];
 #pragma unroll
     for (int k = 0; k <= N; k++) x[k] = X[k * 32];
     make_pairs<N>(x, q);
-    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_rt(vs, tri(N, 0) + m, fipow_rt(m, a)); });
+    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_rt(vs, tri(N, 0) + m, a); });
     if constexpr (N <= kTmDeg) tm_wait_st();
 }
 
-// Row stride (floats) of the per-warp transpose buffer, odd so that both the
-// row writes and the column reads are conflict-free; the buffer shares the
-// warp's region with the scratch columns.
+// Floats of a warp's region: the scratch columns ((P+1) x 32 float2) or the
+// transpose buffer, column-major with a column stride of 36 floats (lane i
+// of column c at 36 c + i: conflict-free writes, 16-byte column reads).
+constexpr int kRedCol = 36;
 template <int P>
-__host__ __device__ constexpr int red_stride() { return 2 * P + 3; }
+__host__ __device__ constexpr int region_floats() { return 2 * (P + 1) * kRedCol; }
 
 // inverse rotation of degree N, then the sum over the warp's pairs into the
 // scaled local Lh (double) of their target: a warp whose valid lanes share
@@ -801,25 +789,19 @@ __host__ __device__ constexpr int red_stride() { return 2 * P + 3; }
 // its 2 (N+1) values per lane through shared memory and adds each column with
 // one atomic; otherwise a segmented shuffle sum over runs of equal target
 template <int P, int N>
-__device__ __forceinline__ void bwd_deg(const VS &vs, float2 ea, float2 ebv, double2 *__restrict__ Lh,
+__device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, double2 *__restrict__ Lh,
                                         unsigned same_mask, bool head, int uniform_tgt,
                                         double2 *__restrict__ Lbase, const float4 *__restrict__ tab, float2 *X,
                                         float *red) {
-    constexpr int NC = (P + 1) * (P + 2) / 2, RS = red_stride<P>();
+    constexpr int NC = (P + 1) * (P + 2) / 2, DP = dpo(P + 1);
     float2 u[N + 1];
     v_get_deg<N>(vs, u);
-#pragma unroll
-    for (int m = 0; m <= N; m++) {
-        const float2 t = fipow(m, u[m]);
-        u[m] = m ? make_float2(2.f * t.x, 2.f * t.y) : t;
-    }
     Pairs<N> q;
     make_pairs<N>(u, q);
     float2 pb = make_float2(1.f, 0.f);
-    fold_rt<N>(tab + dpo(N), q, [&](int j, float2 a) {
-        const float2 t = fmulc(a, pb);
+    fold_rt<N>(tab + 2 * DP + dpo(N), q, [&](int j, float2 a) {
+        X[j * 32] = fmulc(a, pb);
         pb = fmulc(pb, ebv);
-        X[j * 32] = j ? make_float2(2.f * t.x, 2.f * t.y) : t;
     });
     float2 x[N + 1];
 #pragma unroll
@@ -829,14 +811,13 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 ea, float2 ebv, dou
     const int lane = threadIdx.x & 31;
     const bool uni = uniform_tgt >= 0;  // warp-uniform
     float2 ph = make_float2(1.f, 0.f);
-    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int l, float2 a) {
-        const float2 t = fmulc(fipow_rt(4 - (l & 3), a), ph);
-        ph = fmulc(ph, ea);
-        const float f = c_F[tri(N, 0) + l];
-        const float rx = t.x * f, ry = t.y * f;
+    fold_rt<N>(tab + 3 * DP + dpo(N), q, [&](int l, float2 a) {
+        const float2 t = fmulc(a, ph);  // (-i e^{ia})^l
+        ph = fmulc(ph, eai);
+        const float rx = t.x, ry = t.y;
         if (uni) {
-            red[lane * RS + l] = rx;
-            red[lane * RS + N + 1 + l] = ry;
+            red[l * kRedCol + lane] = rx;
+            red[(N + 1 + l) * kRedCol + lane] = ry;
         } else {
             float sx = rx, sy = ry;
 #pragma unroll
@@ -857,9 +838,15 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 ea, float2 ebv, dou
     if (uni) {
         __syncwarp();
         for (int col = lane; col < 2 * (N + 1); col += 32) {
-            float s = 0.f;
-#pragma unroll 8
-            for (int i = 0; i < 32; i++) s += red[i * RS + col];
+            const float4 *c4 = (const float4 *)(red + col * kRedCol);
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const float4 v = c4[i];
+                a0 = __fadd2_rn(a0, make_float2(v.x, v.y));
+                a1 = __fadd2_rn(a1, make_float2(v.z, v.w));
+            }
+            const float s = (a0.x + a0.y) + (a1.x + a1.y);
             const int l = col <= N ? col : col - (N + 1);
             double *dst = (double *)&Lbase[(int64_t)uniform_tgt * NC + tri(N, l)];
             atomicAdd(dst + (col <= N ? 0 : 1), (double)s);
@@ -899,7 +886,7 @@ __device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, floa
     float tp = rinv;
 #pragma unroll
     for (int j = 0; j < L; j++) tp *= qt;
-    const float4 *rows = tab + 2 * dpo(P + 1) + apo(P, L);
+    const float4 *rows = tab + 4 * dpo(P + 1) + apo(P, L);
 #pragma unroll 1
     for (int k = L; k <= P; k++) {
         const float2 a = dot_row<J>(rows + (k - L) * J, s);
@@ -920,11 +907,11 @@ struct Seq {
         axial_ord<P, N>(vs, qs, qt, rinv, tab);
         Seq<P, N + 1>::axial(vs, qs, qt, rinv, tab);
     }
-    __device__ static __forceinline__ void bwd(const VS &vs, float2 ea, float2 ebv, double2 *Lh, unsigned same,
+    __device__ static __forceinline__ void bwd(const VS &vs, float2 eai, float2 ebv, double2 *Lh, unsigned same,
                                                bool head, int ut, double2 *Lbase, const float4 *tab, float2 *X,
                                                float *red) {
-        bwd_deg<P, N>(vs, ea, ebv, Lh, same, head, ut, Lbase, tab, X, red);
-        Seq<P, N + 1>::bwd(vs, ea, ebv, Lh, same, head, ut, Lbase, tab, X, red);
+        bwd_deg<P, N>(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, X, red);
+        Seq<P, N + 1>::bwd(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, X, red);
     }
 };
 template <int P>
@@ -948,7 +935,7 @@ struct VSplit {
     static constexpr int COLS = 2 * NT <= 32 ? 32 : 2 * NT <= 64 ? 64 : 128;
     // shared bytes: the storage columns, per warp the scratch / transpose
     // region, then the coefficient-pair tables
-    static constexpr size_t TAB = (size_t)kF32Threads * NS * 8 + (size_t)kF32Threads * red_stride<P>() * 4;
+    static constexpr size_t TAB = (size_t)kF32Threads * NS * 8 + (size_t)(kF32Threads / 32) * region_floats<P>() * 4;
     static constexpr size_t SMEM = TAB + (size_t)pair_tab_len(P) * 16;
 };
 
@@ -989,7 +976,7 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
     // every lane runs every stage (tensor-memory accesses are warp-wide); a
     // lane without a pair carries zeros
     const VS vs{smf + tid, tbase + ((uint32_t)(32 * (warp & 3)) << 16), kF32Threads};
-    float *region = (float *)(smf + SP::NS * kF32Threads) + warp * 32 * red_stride<P>();
+    float *region = (float *)(smf + SP::NS * kF32Threads) + warp * region_floats<P>();
     float2 *X = (float2 *)region + lane;
     Seq<P, 0>::fwd(Mf + gs * NC, vs, valid, eai, ebv, tab, X);
     Seq<P, 0>::axial(vs, qs, qt, rinv, tab);
@@ -997,7 +984,7 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
     const int t32 = gt >= 0 ? (int)gt : -1;
     const int tmax = __reduce_max_sync(0xffffffffu, t32);
     const bool uniform = __all_sync(0xffffffffu, t32 == tmax || t32 < 0);
-    Seq<P, 0>::bwd(vs, ea, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, tab, X,
+    Seq<P, 0>::bwd(vs, eai, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, tab, X,
                    region);
 }
 
@@ -1008,10 +995,9 @@ __global__ void __launch_bounds__(kF32Threads, 3)
 k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__restrict__ radius,
               const float2 *__restrict__ Mf, double2 *__restrict__ Lh, const float4 *__restrict__ gtab) {
     using SP = VSplit<P>;
-    constexpr int NC = SP::NC;
     extern __shared__ float2 smf[];  // [NS][threads], the per-warp regions, the tables
     __shared__ uint32_t s_tmem;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     float4 *tab = (float4 *)((char *)smf + SP::TAB);
     for (int i = tid; i < pair_tab_len(P); i += kF32Threads) tab[i] = gtab[i];
     if (warp == 0) {
@@ -1109,21 +1095,26 @@ cudaError_t f32_tables_ready() {
 std::vector<float4> f32_pair_tables(int p) {
     std::vector<float4> t;
     t.reserve(pair_tab_len(p));
-    for (int tr = 0; tr < 2; tr++)
+    auto Fl = [](int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); };
+    for (int tab = 0; tab < 4; tab++)  // Df, DTf, Db, DTb
         for (int n = 0; n <= p; n++)
             for (int k = 0; k <= n; k++) {
-                auto M = [&](int m) -> float {
+                auto G = [&](int m) -> float {
                     if (m > n) return 0.f;
-                    return (float)(tr ? wigner_half_pi(n, m, k) : wigner_half_pi(n, k, m));
+                    const bool tr = tab & 1;
+                    long double g = tr ? wigner_half_pi(n, m, k) : wigner_half_pi(n, k, m);
+                    if (!tr) g *= (m ? 2.0L : 1.0L) * (k ? 2.0L : 1.0L);
+                    if (tab == 0) g *= Fl(n, m);
+                    if (tab == 3) g *= Fl(n, k);
+                    return (float)g;
                 };
                 const bool odd = (n + k) & 1;
                 for (int q = 0; q < jp_of(n); q++) {
                     const int a = 4 * q;  // pairs 2q, 2q+1 cover m = a .. a+3
-                    t.push_back(odd ? make_float4(M(a + 1), M(a), M(a + 3), M(a + 2))
-                                    : make_float4(M(a), M(a + 1), M(a + 2), M(a + 3)));
+                    t.push_back(odd ? make_float4(G(a + 1), G(a), G(a + 3), G(a + 2))
+                                    : make_float4(G(a), G(a + 1), G(a + 2), G(a + 3)));
                 }
             }
-    auto Fl = [](int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); };
     for (int l = 0; l <= p; l++)
         for (int k = l; k <= p; k++) {
             auto A = [&](int n) -> float {
