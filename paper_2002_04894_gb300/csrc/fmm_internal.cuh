@@ -115,6 +115,9 @@ inline void stage_mark(Plan &P, int stage, int edge) {
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
 __host__ __device__ inline int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
+// row stride (coefficients) of the float multipoles Mf: even, so that
+// coefficient pairs (2i, 2i+1) are 16-byte aligned
+__host__ __device__ inline int mf_stride(int p) { return (ncoef(p) + 1) & ~1; }
 
 // Order-preserving map from doubles to unsigned 64-bit keys (no NaN; -0 was
 // canonicalised to +0 on input).

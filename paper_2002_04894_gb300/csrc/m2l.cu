@@ -754,11 +754,25 @@ __device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const P
 template <int P, int N>
 __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS &vs, bool valid, float2 eai,
                                         float2 ebv, const float4 *__restrict__ tab, float2 *X) {
+    // the degree's coefficients, two per 16-byte load where the pair is aligned
+    constexpr int c0 = N * (N + 1) / 2, m0 = c0 & 1;
     float2 u[N + 1];
+#pragma unroll
+    for (int m = 0; m <= N; m++) u[m] = make_float2(0.f, 0.f);
+    if (valid) {
+        if constexpr (m0 == 1) u[0] = Ms[c0];
+#pragma unroll
+        for (int m = m0; m + 1 <= N; m += 2) {
+            const float4 t = *(const float4 *)(Ms + c0 + m);
+            u[m] = make_float2(t.x, t.y);
+            u[m + 1] = make_float2(t.z, t.w);
+        }
+        if constexpr (((N + 1 - m0) & 1) == 1) u[N] = Ms[c0 + N];
+    }
     float2 ph = make_float2(1.f, 0.f);
 #pragma unroll
     for (int m = 0; m <= N; m++) {
-        u[m] = fmulc(valid ? Ms[tri(N, m)] : make_float2(0.f, 0.f), ph);
+        u[m] = fmulc(u[m], ph);
         ph = fmulc(ph, eai);
     }
     Pairs<N> q;
@@ -978,7 +992,7 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
     const VS vs{smf + tid, tbase + ((uint32_t)(32 * (warp & 3)) << 16), kF32Threads};
     float *region = (float *)(smf + SP::NS * kF32Threads) + warp * region_floats<P>();
     float2 *X = (float2 *)region + lane;
-    Seq<P, 0>::fwd(Mf + gs * NC, vs, valid, eai, ebv, tab, X);
+    Seq<P, 0>::fwd(Mf + gs * mf_stride(P), vs, valid, eai, ebv, tab, X);
     Seq<P, 0>::axial(vs, qs, qt, rinv, tab);
     // the warp's pairs share one target (invalid lanes add zeros): transpose path
     const int t32 = gt >= 0 ? (int)gt : -1;
@@ -1046,7 +1060,7 @@ __global__ void k_scale_multipoles(int64_t nbox, int p, const double *__restrict
             const double s = __shfl_sync(0xffffffffu, pw, degree_of(min(c, nc - 1)));
             if (c < nc) {
                 const double2 m = M[g * nc + c];
-                Mf[g * nc + c] = make_float2((float)(m.x * s), (float)(m.y * s));
+                Mf[g * mf_stride(p) + c] = make_float2((float)(m.x * s), (float)(m.y * s));
             }
         }
     }
@@ -1167,7 +1181,7 @@ cudaError_t m2l_f32_setup(Plan &P) {
     // for orders without a SIMT instance
     const bool tc = m2l_tc_supported(P.p) && (P.tc_m2l_opt || !m2l_f32_supported(P.p));
     if (!tc && !m2l_f32_supported(P.p)) return cudaSuccess;  // FP64 M2L
-    P.Mf = (float2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(float2));
+    P.Mf = (float2 *)palloc(P, (size_t)P.nbox * mf_stride(P.p) * sizeof(float2));
     P.Lh = (double2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(double2));
     if (!P.Mf || !P.Lh) return cudaErrorMemoryAllocation;
     if (tc) {

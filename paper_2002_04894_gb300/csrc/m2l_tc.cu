@@ -383,7 +383,7 @@ k_m2l_tc(PairTable PT, int p, int64_t ntiles, const double *__restrict__ centre,
         const float2 ebv = make_float2(dz * rinv, rxy * rinv);
         const float2 eai = make_float2(ea.y, -ea.x);
         const float qs = rs * rinv, qt = rt * rinv;
-        const float2 *Ms = Mf + (valid ? gs : 0) * nc;
+        const float2 *Ms = Mf + (valid ? gs : 0) * mf_stride(p);
         bool ok = true;
 
         // 1-2. forward rotation, degree by degree: V_n = i^m fold^T(e^{ikb} fold(F e^{ima} M_n))
