@@ -750,10 +750,10 @@ __device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const P
 }
 
 // forward rotation of degree N of the scaled source multipole into the
-// storage; X is the thread's scratch column (stride 32)
+// storage
 template <int P, int N>
 __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS &vs, bool valid, float2 eai,
-                                        float2 ebv, const float4 *__restrict__ tab, float2 *X) {
+                                        float2 ebv, const float4 *__restrict__ tab) {
     // the degree's coefficients, two per 16-byte load where the pair is aligned
     constexpr int c0 = N * (N + 1) / 2, m0 = c0 & 1;
     float2 u[N + 1];
@@ -777,22 +777,23 @@ __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS 
     }
     Pairs<N> q;
     make_pairs<N>(u, q);
+    // the first fold's outputs go through the degree's own (still empty) slots
     float2 pb = make_float2(1.f, 0.f);
     fold_rt<N>(tab + dpo(N), q, [&](int k, float2 a) {
-        X[k * 32] = fmulc(a, pb);
+        v_put_rt(vs, c0 + k, fmulc(a, pb));
         pb = fmulc(pb, ebv);
     });
+    if constexpr (N <= kTmDeg) tm_wait_st();
     float2 x[N + 1];
-#pragma unroll
-    for (int k = 0; k <= N; k++) x[k] = X[k * 32];
+    v_get_deg<N>(vs, x);
     make_pairs<N>(x, q);
-    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_rt(vs, tri(N, 0) + m, a); });
+    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_rt(vs, c0 + m, a); });
     if constexpr (N <= kTmDeg) tm_wait_st();
 }
 
-// Floats of a warp's region: the scratch columns ((P+1) x 32 float2) or the
-// transpose buffer, column-major with a column stride of 36 floats (lane i
-// of column c at 36 c + i: conflict-free writes, 16-byte column reads).
+// Floats of a warp's transpose buffer: column-major with a column stride of
+// 36 floats (lane i of column c at 36 c + i: conflict-free writes, 16-byte
+// column reads).
 constexpr int kRedCol = 36;
 template <int P>
 __host__ __device__ constexpr int region_floats() { return 2 * (P + 1) * kRedCol; }
@@ -805,23 +806,22 @@ __host__ __device__ constexpr int region_floats() { return 2 * (P + 1) * kRedCol
 template <int P, int N>
 __device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, double2 *__restrict__ Lh,
                                         unsigned same_mask, bool head, int uniform_tgt,
-                                        double2 *__restrict__ Lbase, const float4 *__restrict__ tab, float2 *X,
-                                        float *red) {
+                                        double2 *__restrict__ Lbase, const float4 *__restrict__ tab, float *red) {
     constexpr int NC = (P + 1) * (P + 2) / 2, DP = dpo(P + 1);
     float2 u[N + 1];
     v_get_deg<N>(vs, u);
     Pairs<N> q;
     make_pairs<N>(u, q);
+    // the first fold's outputs go through the degree's slots (read above)
     float2 pb = make_float2(1.f, 0.f);
     fold_rt<N>(tab + 2 * DP + dpo(N), q, [&](int j, float2 a) {
-        X[j * 32] = fmulc(a, pb);
+        v_put_rt(vs, tri(N, 0) + j, fmulc(a, pb));
         pb = fmulc(pb, ebv);
     });
+    if constexpr (N <= kTmDeg) tm_wait_st();
     float2 x[N + 1];
-#pragma unroll
-    for (int k = 0; k <= N; k++) x[k] = X[k * 32];
+    v_get_deg<N>(vs, x);
     make_pairs<N>(x, q);
-    __syncwarp();  // the transpose buffer overlaps the warp's scratch columns
     const int lane = threadIdx.x & 31;
     const bool uni = uniform_tgt >= 0;  // warp-uniform
     float2 ph = make_float2(1.f, 0.f);
@@ -913,28 +913,26 @@ __device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, floa
 template <int P, int N>
 struct Seq {
     __device__ static __forceinline__ void fwd(const float2 *Ms, const VS &vs, bool valid, float2 eai, float2 ebv,
-                                               const float4 *tab, float2 *X) {
-        fwd_deg<P, N>(Ms, vs, valid, eai, ebv, tab, X);
-        Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv, tab, X);
+                                               const float4 *tab) {
+        fwd_deg<P, N>(Ms, vs, valid, eai, ebv, tab);
+        Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv, tab);
     }
     __device__ static __forceinline__ void axial(const VS &vs, float qs, float qt, float rinv, const float4 *tab) {
         axial_ord<P, N>(vs, qs, qt, rinv, tab);
         Seq<P, N + 1>::axial(vs, qs, qt, rinv, tab);
     }
     __device__ static __forceinline__ void bwd(const VS &vs, float2 eai, float2 ebv, double2 *Lh, unsigned same,
-                                               bool head, int ut, double2 *Lbase, const float4 *tab, float2 *X,
-                                               float *red) {
-        bwd_deg<P, N>(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, X, red);
-        Seq<P, N + 1>::bwd(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, X, red);
+                                               bool head, int ut, double2 *Lbase, const float4 *tab, float *red) {
+        bwd_deg<P, N>(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, red);
+        Seq<P, N + 1>::bwd(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, red);
     }
 };
 template <int P>
 struct Seq<P, P + 1> {
-    __device__ static __forceinline__ void fwd(const float2 *, const VS &, bool, float2, float2, const float4 *,
-                                               float2 *) {}
+    __device__ static __forceinline__ void fwd(const float2 *, const VS &, bool, float2, float2, const float4 *) {}
     __device__ static __forceinline__ void axial(const VS &, float, float, float, const float4 *) {}
     __device__ static __forceinline__ void bwd(const VS &, float2, float2, double2 *, unsigned, bool, int,
-                                               double2 *, const float4 *, float2 *, float *) {}
+                                               double2 *, const float4 *, float *) {}
 };
 
 constexpr int kF32Threads = 128;
@@ -947,7 +945,7 @@ struct VSplit {
     static constexpr int NT = NC < kTmC ? NC : kTmC;
     static constexpr int NS = NC - NT;
     static constexpr int COLS = 2 * NT <= 32 ? 32 : 2 * NT <= 64 ? 64 : 128;
-    // shared bytes: the storage columns, per warp the scratch / transpose
+    // shared bytes: the storage columns, per warp the transpose
     // region, then the coefficient-pair tables
     static constexpr size_t TAB = (size_t)kF32Threads * NS * 8 + (size_t)(kF32Threads / 32) * region_floats<P>() * 4;
     static constexpr size_t SMEM = TAB + (size_t)pair_tab_len(P) * 16;
@@ -961,7 +959,7 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
                                           float2 *smf, uint32_t tbase) {
     using SP = VSplit<P>;
     constexpr int NC = SP::NC;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const bool valid = g < npairs;
     int64_t gt = -1, gs = 0;
     float dx = 1.f, dy = 0.f, dz = 0.f, rs = 1.f, rt = 1.f;
@@ -991,15 +989,13 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
     // lane without a pair carries zeros
     const VS vs{smf + tid, tbase + ((uint32_t)(32 * (warp & 3)) << 16), kF32Threads};
     float *region = (float *)(smf + SP::NS * kF32Threads) + warp * region_floats<P>();
-    float2 *X = (float2 *)region + lane;
-    Seq<P, 0>::fwd(Mf + gs * mf_stride(P), vs, valid, eai, ebv, tab, X);
+    Seq<P, 0>::fwd(Mf + gs * mf_stride(P), vs, valid, eai, ebv, tab);
     Seq<P, 0>::axial(vs, qs, qt, rinv, tab);
     // the warp's pairs share one target (invalid lanes add zeros): transpose path
     const int t32 = gt >= 0 ? (int)gt : -1;
     const int tmax = __reduce_max_sync(0xffffffffu, t32);
     const bool uniform = __all_sync(0xffffffffu, t32 == tmax || t32 < 0);
-    Seq<P, 0>::bwd(vs, eai, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, tab, X,
-                   region);
+    Seq<P, 0>::bwd(vs, eai, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, tab, region);
 }
 
 // one weak pair per thread, all levels, blocks striding over chunks of 128
