@@ -8,8 +8,8 @@
 // centre with an error-free float TwoSum, so the difference of a close pair is
 // taken between two nearly equal hi parts, which is exact (Sterbenz), and
 // close pairs keep full relative precision. Per-target sums are plain float
-// over runs of 32 sources and Kahan-compensated across runs (the rounding of
-// a 32-term sum stays near the float unit roundoff while the compensation
+// over runs of 64 sources and Kahan-compensated across runs (the rounding of
+// a 64-term sum stays near the float unit roundoff while the compensation
 // costs a fraction of an instruction per pair). The expansions are evaluated
 // on scaled offsets a / r (r the
 // box radius, so |a / r| <= 1) and with scaled coefficients M_n / r^n and
@@ -247,6 +247,7 @@ constexpr int kP2PThreads = 128;  // threads per work unit; one target each
 constexpr int kSrcTile = 128;     // sources staged per pass (64 pairs)
 constexpr float kFarGap = 0.1f;   // far: cell gap >= kFarGap (r_t + r_s)
 constexpr float kPadFar = 1.0e18f;  // padding source: zero charge, far away
+constexpr int kRun = 64;  // sources summed in float before the compensated add
 
 __device__ __forceinline__ float rcp_approx(float x) {  // reciprocal on the XU pipe (~1 ulp)
     float r;
@@ -320,7 +321,7 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
 // suffices, and no two points can coincide. Near leaves (touching or nearly
 // touching cells, ~4% of the pairs on a Plummer sphere) keep the split hi/lo
 // offsets, whose difference is exact for close pairs. Per target the sources are
-// summed in plain float over runs of 32 (full runs with a fixed trip count)
+// summed in plain float over runs of 64 (full runs with a fixed trip count)
 // and the runs compensated (Kahan).
 template <typename OutT>
 __global__ void __launch_bounds__(kP2PThreads)
@@ -417,24 +418,24 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
                 }
                 __syncthreads();
                 const int mcount = min(kSrcTile, ns - sb);
-                for (int j0 = 0; j0 < mcount; j0 += 32) {
-                    const int npair = (min(32, mcount - j0) + 1) >> 1;
+                for (int j0 = 0; j0 < mcount; j0 += kRun) {
+                    const int npair = (min(kRun, mcount - j0) + 1) >> 1;
                     const int p0 = j0 >> 1;
                     float2 a[4];
 #pragma unroll
                     for (int c = 0; c < 4; c++) a[c] = make_float2(0.f, 0.f);
                     if (far) {
-                        if (npair == 16) {
+                        if (npair == kRun / 2) {
 #pragma unroll 8
-                            for (int pp = 0; pp < 16; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
+                            for (int pp = 0; pp < kRun / 2; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
                         } else {
 #pragma unroll 4
                             for (int pp = 0; pp < npair; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
                         }
                     } else {
-                        if (npair == 16) {
+                        if (npair == kRun / 2) {
 #pragma unroll 8
-                            for (int pp = 0; pp < 16; pp++)
+                            for (int pp = 0; pp < kRun / 2; pp++)
                                 near_pair2(X, Y, Z, XL, YL, ZL, sA[p0 + pp], sB[p0 + pp], sC[p0 + pp], sD[p0 + pp], a);
                         } else {
 #pragma unroll 4
