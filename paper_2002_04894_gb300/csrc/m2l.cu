@@ -692,6 +692,17 @@ __device__ __forceinline__ void v_get_deg(const VS &vs, float2 (&u)[N + 1]) {
     }
 }
 
+// coefficient c of degree N of the pair's storage (where it lives is fixed by N)
+template <int N>
+__device__ __forceinline__ void v_put_deg(const VS &vs, int c, float2 v) {
+    if constexpr (N <= kTmDeg) {
+        const float f[2] = {v.x, v.y};
+        tm_st<2>(vs.t + 2 * c, f);
+    } else {
+        vs.s[(c - kTmC) * vs.T] = v;
+    }
+}
+
 // coefficient c (run time) of the pair's storage
 __device__ __forceinline__ void v_put_rt(const VS &vs, int c, float2 v) {
     if (c < kTmC) {  // warp-uniform
@@ -780,14 +791,14 @@ __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS 
     // the first fold's outputs go through the degree's own (still empty) slots
     float2 pb = make_float2(1.f, 0.f);
     fold_rt<N>(tab + dpo(N), q, [&](int k, float2 a) {
-        v_put_rt(vs, c0 + k, fmulc(a, pb));
+        v_put_deg<N>(vs, c0 + k, fmulc(a, pb));
         pb = fmulc(pb, ebv);
     });
     if constexpr (N <= kTmDeg) tm_wait_st();
     float2 x[N + 1];
     v_get_deg<N>(vs, x);
     make_pairs<N>(x, q);
-    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_rt(vs, c0 + m, a); });
+    fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_deg<N>(vs, c0 + m, a); });
     if constexpr (N <= kTmDeg) tm_wait_st();
 }
 
@@ -797,6 +808,45 @@ __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS 
 constexpr int kRedCol = 36;
 template <int P>
 __host__ __device__ constexpr int region_floats() { return 2 * (P + 1) * kRedCol; }
+
+// Segmented sum of one contribution over runs of equal target (warp-wide:
+// every lane calls it) and the add of each run's sum into its target's
+// coefficient; out of line, as warps with mixed targets are the rare case.
+__device__ __noinline__ void seg_add(float sx, float sy, unsigned same_mask, bool head, double2 *dst) {
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        const float ox = __shfl_down_sync(0xffffffffu, sx, 1 << j);
+        const float oy = __shfl_down_sync(0xffffffffu, sy, 1 << j);
+        if ((same_mask >> j) & 1u) {
+            sx += ox;
+            sy += oy;
+        }
+    }
+    if (head) {
+        atomicAdd(&dst->x, (double)sx);
+        atomicAdd(&dst->y, (double)sy);
+    }
+}
+
+// Column sums of a warp's transpose buffer (2 (N+1) columns: Re of orders
+// 0..N, then Im) into the target's coefficients c0..c0+N.
+__device__ __noinline__ void col_add(const float *red, int N, double2 *dst) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int col = lane; col < 2 * (N + 1); col += 32) {
+        const float4 *c4 = (const float4 *)(red + col * kRedCol);
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const float4 v = c4[i];
+            a0 = __fadd2_rn(a0, make_float2(v.x, v.y));
+            a1 = __fadd2_rn(a1, make_float2(v.z, v.w));
+        }
+        const float s = (a0.x + a0.y) + (a1.x + a1.y);
+        const int l = col <= N ? col : col - (N + 1);
+        atomicAdd((double *)&dst[l] + (col <= N ? 0 : 1), (double)s);
+    }
+}
 
 // inverse rotation of degree N, then the sum over the warp's pairs into the
 // scaled local Lh (double) of their target: a warp whose valid lanes share
@@ -815,7 +865,7 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, do
     // the first fold's outputs go through the degree's slots (read above)
     float2 pb = make_float2(1.f, 0.f);
     fold_rt<N>(tab + 2 * DP + dpo(N), q, [&](int j, float2 a) {
-        v_put_rt(vs, tri(N, 0) + j, fmulc(a, pb));
+        v_put_deg<N>(vs, tri(N, 0) + j, fmulc(a, pb));
         pb = fmulc(pb, ebv);
     });
     if constexpr (N <= kTmDeg) tm_wait_st();
@@ -833,39 +883,10 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, do
             red[l * kRedCol + lane] = rx;
             red[(N + 1 + l) * kRedCol + lane] = ry;
         } else {
-            float sx = rx, sy = ry;
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                const float ox = __shfl_down_sync(0xffffffffu, sx, 1 << j);
-                const float oy = __shfl_down_sync(0xffffffffu, sy, 1 << j);
-                if ((same_mask >> j) & 1u) {
-                    sx += ox;
-                    sy += oy;
-                }
-            }
-            if (head) {
-                atomicAdd(&Lh[tri(N, 0) + l].x, (double)sx);
-                atomicAdd(&Lh[tri(N, 0) + l].y, (double)sy);
-            }
+            seg_add(rx, ry, same_mask, head, &Lh[tri(N, 0) + l]);
         }
     });
-    if (uni) {
-        __syncwarp();
-        for (int col = lane; col < 2 * (N + 1); col += 32) {
-            const float4 *c4 = (const float4 *)(red + col * kRedCol);
-            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const float4 v = c4[i];
-                a0 = __fadd2_rn(a0, make_float2(v.x, v.y));
-                a1 = __fadd2_rn(a1, make_float2(v.z, v.w));
-            }
-            const float s = (a0.x + a0.y) + (a1.x + a1.y);
-            const int l = col <= N ? col : col - (N + 1);
-            double *dst = (double *)&Lbase[(int64_t)uniform_tgt * NC + tri(N, l)];
-            atomicAdd(dst + (col <= N ? 0 : 1), (double)s);
-        }
-    }
+    if (uni) col_add(red, N, Lbase + (int64_t)uniform_tgt * NC + tri(N, 0));
     __syncwarp();  // the next degree reuses the region
 }
 
