@@ -730,6 +730,40 @@ __device__ __forceinline__ void make_pairs(const float2 (&v)[N + 1], Pairs<N> &q
     }
 }
 
+// The first fold's outputs x_k, x_{k+1} (k even) go to the degree's slots k,
+// k+1 as (Re x_k, Im x_{k+1}) and (Re x_{k+1}, Im x_k): read back, they are
+// the pair operands of the second fold as they stand. A last unpaired output
+// (N even) keeps (Re x_N, Im x_N).
+template <int N>
+__device__ __forceinline__ void put_paired(const VS &vs, int c, float2 a0, float2 a1) {
+    if constexpr (N <= kTmDeg) {
+        const float f[4] = {a0.x, a1.y, a1.x, a0.y};
+        tm_st<4>(vs.t + 2 * c, f);
+    } else {
+        vs.s[(c - kTmC) * vs.T] = make_float2(a0.x, a1.y);
+        vs.s[(c + 1 - kTmC) * vs.T] = make_float2(a1.x, a0.y);
+    }
+}
+
+// the pair operands of degree N from slots written by put_paired
+template <int N>
+__device__ __forceinline__ void get_paired(const VS &vs, Pairs<N> &q) {
+    float2 u[N + 1];
+    v_get_deg<N>(vs, u);
+#pragma unroll
+    for (int j = 0; j < 2 * jp_of(N); j++) {
+        if (2 * j + 1 <= N) {
+            q.e[j] = u[2 * j];
+            q.o[j] = u[2 * j + 1];
+        } else if (2 * j == N) {
+            q.e[j] = make_float2(u[N].x, 0.f);
+            q.o[j] = make_float2(0.f, u[N].y);
+        } else {
+            q.e[j] = q.o[j] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
 // sum_j row_j * w_j over J float4 (two pairs each), two packed accumulators
 template <int J>
 __device__ __forceinline__ float2 dot_row(const float4 *__restrict__ row, const float2 *w) {
@@ -743,10 +777,11 @@ __device__ __forceinline__ float2 dot_row(const float4 *__restrict__ row, const 
     return __fadd2_rn(a0, a1);
 }
 
-// out(k, fold_k) for k = 0..N of the fold with the rows of degree N; the
-// output's parity (N + k) picks the pair set
-template <int N, typename Out>
-__device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const Pairs<N> &q, Out &&out) {
+// out2(k, fold_k, fold_k+1) for even k < N and out1(N, fold_N) when N is
+// even, over the rows of degree N; the output's parity (N + k) picks the pair set
+template <int N, typename Out2, typename Out1>
+__device__ __forceinline__ void fold_rt2(const float4 *__restrict__ rows, const Pairs<N> &q, Out2 &&out2,
+                                         Out1 &&out1) {
     constexpr int J = jp_of(N);
     const float2 *w0 = (N & 1) ? q.o : q.e;
     const float2 *w1 = (N & 1) ? q.e : q.o;
@@ -754,10 +789,18 @@ __device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const P
     for (int k = 0; k < N; k += 2) {
         const float2 a0 = dot_row<J>(rows + k * J, w0);
         const float2 a1 = dot_row<J>(rows + (k + 1) * J, w1);
+        out2(k, a0, a1);
+    }
+    if constexpr ((N & 1) == 0) out1(N, dot_row<J>(rows + N * J, w0));
+}
+
+// out(k, fold_k) for k = 0..N of the fold with the rows of degree N
+template <int N, typename Out>
+__device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const Pairs<N> &q, Out &&out) {
+    fold_rt2<N>(rows, q, [&](int k, float2 a0, float2 a1) {
         out(k, a0);
         out(k + 1, a1);
-    }
-    if constexpr ((N & 1) == 0) out(N, dot_row<J>(rows + N * J, w0));
+    }, out);
 }
 
 // forward rotation of degree N of the scaled source multipole into the
@@ -790,14 +833,15 @@ __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS 
     make_pairs<N>(u, q);
     // the first fold's outputs go through the degree's own (still empty) slots
     float2 pb = make_float2(1.f, 0.f);
-    fold_rt<N>(tab + dpo(N), q, [&](int k, float2 a) {
-        v_put_deg<N>(vs, c0 + k, fmulc(a, pb));
+    fold_rt2<N>(tab + dpo(N), q, [&](int k, float2 a0, float2 a1) {
+        const float2 x0 = fmulc(a0, pb);
         pb = fmulc(pb, ebv);
-    });
+        const float2 x1 = fmulc(a1, pb);
+        pb = fmulc(pb, ebv);
+        put_paired<N>(vs, c0 + k, x0, x1);
+    }, [&](int k, float2 a) { v_put_deg<N>(vs, c0 + k, fmulc(a, pb)); });
     if constexpr (N <= kTmDeg) tm_wait_st();
-    float2 x[N + 1];
-    v_get_deg<N>(vs, x);
-    make_pairs<N>(x, q);
+    get_paired<N>(vs, q);
     fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_deg<N>(vs, c0 + m, a); });
     if constexpr (N <= kTmDeg) tm_wait_st();
 }
@@ -864,14 +908,15 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, do
     make_pairs<N>(u, q);
     // the first fold's outputs go through the degree's slots (read above)
     float2 pb = make_float2(1.f, 0.f);
-    fold_rt<N>(tab + 2 * DP + dpo(N), q, [&](int j, float2 a) {
-        v_put_deg<N>(vs, tri(N, 0) + j, fmulc(a, pb));
+    fold_rt2<N>(tab + 2 * DP + dpo(N), q, [&](int j, float2 a0, float2 a1) {
+        const float2 x0 = fmulc(a0, pb);
         pb = fmulc(pb, ebv);
-    });
+        const float2 x1 = fmulc(a1, pb);
+        pb = fmulc(pb, ebv);
+        put_paired<N>(vs, tri(N, 0) + j, x0, x1);
+    }, [&](int j, float2 a) { v_put_deg<N>(vs, tri(N, 0) + j, fmulc(a, pb)); });
     if constexpr (N <= kTmDeg) tm_wait_st();
-    float2 x[N + 1];
-    v_get_deg<N>(vs, x);
-    make_pairs<N>(x, q);
+    get_paired<N>(vs, q);
     const int lane = threadIdx.x & 31;
     const bool uni = uniform_tgt >= 0;  // warp-uniform
     float2 ph = make_float2(1.f, 0.f);
