@@ -902,10 +902,8 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, do
                                         unsigned same_mask, bool head, int uniform_tgt,
                                         double2 *__restrict__ Lbase, const float4 *__restrict__ tab, float *red) {
     constexpr int NC = (P + 1) * (P + 2) / 2, DP = dpo(P + 1);
-    float2 u[N + 1];
-    v_get_deg<N>(vs, u);
     Pairs<N> q;
-    make_pairs<N>(u, q);
+    get_paired<N>(vs, q);  // the translation left the degree in the pair layout
     // the first fold's outputs go through the degree's slots (read above)
     float2 pb = make_float2(1.f, 0.f);
     fold_rt2<N>(tab + 2 * DP + dpo(N), q, [&](int j, float2 a0, float2 a1) {
@@ -935,12 +933,11 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, do
     __syncwarp();  // the next degree reuses the region
 }
 
-// translation along z of order L (orders P+1-L coefficients), in place in the
-// storage; qs = r_s / rho, qt = r_t / rho
-template <int P, int L>
-__device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, float rinv,
-                                          const float4 *__restrict__ tab) {
-    constexpr int len = P + 1 - L, J = ja_of(P, L);
+// column L (degrees n = L..P) of the storage, conjugated and scaled by qs^n,
+// as the packed operands of the translation rows (zero past P)
+template <int P, int L, int J>
+__device__ __forceinline__ void axial_col(const VS &vs, float qs, float2 (&s)[2 * J]) {
+    constexpr int len = P + 1 - L;
     constexpr int ntm = L > kTmDeg ? 0 : (P < kTmDeg ? P : kTmDeg) + 1 - L;  // of them in tensor memory
     float f[2 * len];
 #pragma unroll
@@ -954,7 +951,6 @@ __device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, floa
         }
     }
     if constexpr (ntm > 0) tm_wait_ld<2 * ntm>(f);
-    float2 s[2 * J];
     float sp = 1.f;
 #pragma unroll
     for (int j = 0; j < L; j++) sp *= qs;
@@ -963,17 +959,49 @@ __device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, floa
         s[n] = n < len ? make_float2(f[2 * n] * sp, -f[2 * n + 1] * sp) : make_float2(0.f, 0.f);
         sp *= qs;
     }
+}
+
+// translation along z of orders L and L+1 (L even), in place in the storage;
+// qs = r_s / rho, qt = r_t / rho. The outputs of degree k go to slots L, L+1
+// as (Re of order L, Im of order L+1) and (Re of L+1, Im of L), the pair
+// layout the inverse rotation's first fold reads; order L alone at k = L (the
+// last slot of an even degree) keeps (Re, Im).
+template <int P, int L>
+__device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, float rinv,
+                                          const float4 *__restrict__ tab) {
+    constexpr int J0 = ja_of(P, L), J1 = ja_of(P, L + 1);
+    float2 s0[2 * J0];
+    axial_col<P, L, J0>(vs, qs, s0);
     float tp = rinv;
 #pragma unroll
     for (int j = 0; j < L; j++) tp *= qt;
-    const float4 *rows = tab + 4 * dpo(P + 1) + apo(P, L);
-#pragma unroll 1
-    for (int k = L; k <= P; k++) {
-        const float2 a = dot_row<J>(rows + (k - L) * J, s);
-        v_put_rt(vs, tri(k, L), make_float2(a.x * tp, a.y * tp));
+    const float4 *rows0 = tab + 4 * dpo(P + 1) + apo(P, L);
+    {
+        const float2 a = dot_row<J0>(rows0, s0);
+        v_put_rt(vs, tri(L, L), make_float2(a.x * tp, a.y * tp));
         tp *= qt;
     }
-    if constexpr (ntm > 0) tm_wait_st();
+    if constexpr (L + 1 <= P) {
+        float2 s1[2 * J1];
+        axial_col<P, L + 1, J1>(vs, qs, s1);
+        const float4 *rows1 = tab + 4 * dpo(P + 1) + apo(P, L + 1);
+#pragma unroll 1
+        for (int k = L + 1; k <= P; k++) {
+            const float2 a0 = dot_row<J0>(rows0 + (k - L) * J0, s0);
+            const float2 a1 = dot_row<J1>(rows1 + (k - L - 1) * J1, s1);
+            const int c = tri(k, L);
+            const float2 x0 = make_float2(a0.x * tp, a0.y * tp), x1 = make_float2(a1.x * tp, a1.y * tp);
+            if (k <= kTmDeg) {  // warp-uniform
+                const float f[4] = {x0.x, x1.y, x1.x, x0.y};
+                tm_st<4>(vs.t + 2 * c, f);
+            } else {
+                vs.s[(c - kTmC) * vs.T] = make_float2(x0.x, x1.y);
+                vs.s[(c + 1 - kTmC) * vs.T] = make_float2(x1.x, x0.y);
+            }
+            tp *= qt;
+        }
+    }
+    if constexpr (L <= kTmDeg) tm_wait_st();
 }
 
 template <int P, int N>
@@ -984,7 +1012,7 @@ struct Seq {
         Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv, tab);
     }
     __device__ static __forceinline__ void axial(const VS &vs, float qs, float qt, float rinv, const float4 *tab) {
-        axial_ord<P, N>(vs, qs, qt, rinv, tab);
+        if constexpr ((N & 1) == 0) axial_ord<P, N>(vs, qs, qt, rinv, tab);
         Seq<P, N + 1>::axial(vs, qs, qt, rinv, tab);
     }
     __device__ static __forceinline__ void bwd(const VS &vs, float2 eai, float2 ebv, double2 *Lh, unsigned same,
