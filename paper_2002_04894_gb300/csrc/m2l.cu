@@ -602,6 +602,7 @@ struct VS {
     float2 *s;    // shared column of this thread: coefficient c at s[(c - kTmC) * T]
     uint32_t t;   // this thread's tensor-memory lane, column 0
     int T;
+    uint32_t ph;  // this thread's lane of the phase columns: e^{ik beta} at 2k, 2k+1
 };
 
 template <int X>
@@ -794,6 +795,34 @@ __device__ __forceinline__ void fold_rt2(const float4 *__restrict__ rows, const 
     if constexpr ((N & 1) == 0) out1(N, dot_row<J>(rows + N * J, w0));
 }
 
+// The first fold of either rotation multiplies output k by e^{ik beta}
+// (doubled for k > 0 in the tables): the powers are formed once per pair into
+// tensor-memory columns, and each iteration reads its two with one load
+// issued before the iteration's products.
+template <int N, typename Put2, typename Put1>
+__device__ __forceinline__ void fold1_phased(const float4 *__restrict__ rows, const Pairs<N> &q, const VS &vs,
+                                             Put2 &&put2, Put1 &&put1) {
+    constexpr int J = jp_of(N);
+    const float2 *w0 = (N & 1) ? q.o : q.e;
+    const float2 *w1 = (N & 1) ? q.e : q.o;
+#pragma unroll 1
+    for (int k = 0; k < N; k += 2) {
+        float f[4];
+        tm_ld<4>(vs.ph + 2 * k, f);
+        const float2 a0 = dot_row<J>(rows + k * J, w0);
+        const float2 a1 = dot_row<J>(rows + (k + 1) * J, w1);
+        tm_wait_ld<4>(f);
+        put2(k, fmulc(a0, make_float2(f[0], f[1])), fmulc(a1, make_float2(f[2], f[3])));
+    }
+    if constexpr ((N & 1) == 0) {
+        float f[2];
+        tm_ld<2>(vs.ph + 2 * N, f);
+        const float2 a = dot_row<J>(rows + N * J, w0);
+        tm_wait_ld<2>(f);
+        put1(N, fmulc(a, make_float2(f[0], f[1])));
+    }
+}
+
 // out(k, fold_k) for k = 0..N of the fold with the rows of degree N
 template <int N, typename Out>
 __device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const Pairs<N> &q, Out &&out) {
@@ -832,14 +861,8 @@ __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS 
     Pairs<N> q;
     make_pairs<N>(u, q);
     // the first fold's outputs go through the degree's own (still empty) slots
-    float2 pb = make_float2(1.f, 0.f);
-    fold_rt2<N>(tab + dpo(N), q, [&](int k, float2 a0, float2 a1) {
-        const float2 x0 = fmulc(a0, pb);
-        pb = fmulc(pb, ebv);
-        const float2 x1 = fmulc(a1, pb);
-        pb = fmulc(pb, ebv);
-        put_paired<N>(vs, c0 + k, x0, x1);
-    }, [&](int k, float2 a) { v_put_deg<N>(vs, c0 + k, fmulc(a, pb)); });
+    fold1_phased<N>(tab + dpo(N), q, vs, [&](int k, float2 x0, float2 x1) { put_paired<N>(vs, c0 + k, x0, x1); },
+                    [&](int k, float2 x) { v_put_deg<N>(vs, c0 + k, x); });
     if constexpr (N <= kTmDeg) tm_wait_st();
     get_paired<N>(vs, q);
     fold_rt<N>(tab + dpo(P + 1) + dpo(N), q, [&](int m, float2 a) { v_put_deg<N>(vs, c0 + m, a); });
@@ -905,14 +928,9 @@ __device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, do
     Pairs<N> q;
     get_paired<N>(vs, q);  // the translation left the degree in the pair layout
     // the first fold's outputs go through the degree's slots (read above)
-    float2 pb = make_float2(1.f, 0.f);
-    fold_rt2<N>(tab + 2 * DP + dpo(N), q, [&](int j, float2 a0, float2 a1) {
-        const float2 x0 = fmulc(a0, pb);
-        pb = fmulc(pb, ebv);
-        const float2 x1 = fmulc(a1, pb);
-        pb = fmulc(pb, ebv);
-        put_paired<N>(vs, tri(N, 0) + j, x0, x1);
-    }, [&](int j, float2 a) { v_put_deg<N>(vs, tri(N, 0) + j, fmulc(a, pb)); });
+    fold1_phased<N>(tab + 2 * DP + dpo(N), q, vs,
+                    [&](int j, float2 x0, float2 x1) { put_paired<N>(vs, tri(N, 0) + j, x0, x1); },
+                    [&](int j, float2 x) { v_put_deg<N>(vs, tri(N, 0) + j, x); });
     if constexpr (N <= kTmDeg) tm_wait_st();
     get_paired<N>(vs, q);
     const int lane = threadIdx.x & 31;
@@ -1039,6 +1057,7 @@ struct VSplit {
     static constexpr int NT = NC < kTmC ? NC : kTmC;
     static constexpr int NS = NC - NT;
     static constexpr int COLS = 2 * NT <= 32 ? 32 : 2 * NT <= 64 ? 64 : 128;
+    static constexpr int PHC = 2 * (P + 1) <= 32 ? 32 : 64;  // columns of the e^{ik beta} table
     // shared bytes: the storage columns, per warp the transpose
     // region, then the coefficient-pair tables
     static constexpr size_t TAB = (size_t)kF32Threads * NS * 8 + (size_t)(kF32Threads / 32) * region_floats<P>() * 4;
@@ -1050,7 +1069,7 @@ template <int P>
 __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__restrict__ centre,
                                           const double *__restrict__ radius, const float2 *__restrict__ Mf,
                                           double2 *__restrict__ Lh, const float4 *tab, int64_t g, int64_t npairs,
-                                          float2 *smf, uint32_t tbase) {
+                                          float2 *smf, uint32_t tbase, uint32_t tphase) {
     using SP = VSplit<P>;
     constexpr int NC = SP::NC;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -1081,7 +1100,20 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
     const float qs = rs * rinv, qt = rt * rinv;
     // every lane runs every stage (tensor-memory accesses are warp-wide); a
     // lane without a pair carries zeros
-    const VS vs{smf + tid, tbase + ((uint32_t)(32 * (warp & 3)) << 16), kF32Threads};
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    const VS vs{smf + tid, tbase + lanes, kF32Threads, tphase + lanes};
+    {
+        float f[2 * (P + 1)];
+        float2 pb = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int k = 0; k <= P; k++) {
+            f[2 * k] = pb.x;
+            f[2 * k + 1] = pb.y;
+            pb = fmulc(pb, ebv);
+        }
+        TCols<0, 2 * (P + 1)>::st(vs.ph, f);
+        tm_wait_st();
+    }
     float *region = (float *)(smf + SP::NS * kF32Threads) + warp * region_floats<P>();
     Seq<P, 0>::fwd(Mf + gs * mf_stride(P), vs, valid, eai, ebv, tab);
     Seq<P, 0>::axial(vs, qs, qt, rinv, tab);
@@ -1100,7 +1132,7 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
               const float2 *__restrict__ Mf, double2 *__restrict__ Lh, const float4 *__restrict__ gtab) {
     using SP = VSplit<P>;
     extern __shared__ float2 smf[];  // [NS][threads], the per-warp regions, the tables
-    __shared__ uint32_t s_tmem;
+    __shared__ uint32_t s_tmem, s_tphase;
     const int tid = threadIdx.x, warp = tid >> 5;
     float4 *tab = (float4 *)((char *)smf + SP::TAB);
     for (int i = tid; i < pair_tab_len(P); i += kF32Threads) tab[i] = gtab[i];
@@ -1108,19 +1140,24 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(&s_tmem)),
                      "r"(SP::COLS));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tphase)),
+                     "r"(SP::PHC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = s_tmem;
+    const uint32_t tbase = s_tmem, tphase = s_tphase;
     const int64_t npairs = PT.off[PT.lmax + 1];
     for (int64_t g0 = blockIdx.x * (int64_t)kF32Threads; g0 < npairs; g0 += (int64_t)gridDim.x * kF32Threads)
-        m2l_chunk<P>(PT, centre, radius, Mf, Lh, tab, g0 + tid, npairs, smf, tbase);
+        m2l_chunk<P>(PT, centre, radius, Mf, Lh, tab, g0 + tid, npairs, smf, tbase, tphase);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SP::COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tphase), "r"(SP::PHC));
+    }
 }
 
 // One warp per box: lane n <= p forms r^-n (a single division), and each
