@@ -278,7 +278,7 @@ __device__ __forceinline__ void far_pair2(float2 X, float2 Y, float2 Z, const fl
     const float2 dz = add2(Z, make_float2(B.x, B.y));
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     const float2 rinv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-    const float2 rinv2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));  // XU, not the FMA pipe
+    const float2 rinv2 = mul2(rinv, rinv);  // one packed product: fewer issue slots than two XU reciprocals
     const float2 qr = mul2(make_float2(B.z, B.w), rinv);
     const float2 qr3 = mul2(qr, rinv2);
     a[0] = add2(a[0], qr);
