@@ -28,6 +28,8 @@ CASES = [
     ("plummer", 12000, 8, 10, 0.5, np.float64),
     ("gmm", 9000, 9, 12, 0.5, np.float32),
     ("uniform", 5000, 7, 14, 0.6, np.float64),
+    ("plummer", 4000, 7, 16, 0.6, np.float64),   # highest float M2L order: one pair per thread
+    ("gmm", 6000, 8, 6, 0.5, np.float64),
     ("plummer", 3000, 6, 7, 0.5, np.float64),    # p without a float M2L instance
     ("uniform", 300, 10, 4, 0.5, np.float64),    # empty leaves
     ("uniform", 1000, 5, 6, 0.0, np.float32),    # theta = 0: near field only
