@@ -194,7 +194,8 @@ typedef struct fmm_stats {
     int64_t weak_pairs_level[FMM_MAX_LEVELS + 1];
 } fmm_stats;
 
-/* fmm_plan_stats -- fill *out. Errors: FMM_EINVAL. */
+/* fmm_plan_stats -- fill *out (synchronises the plan's stream for the
+ * near-field pair count). Errors: FMM_EINVAL, FMM_ECUDA. */
 int fmm_plan_stats(fmm_plan_t plan, fmm_stats *out);
 
 /*

@@ -478,7 +478,13 @@ int fmm_plan_stats(fmm_plan_t plan, fmm_stats *out) {
         out->weak_pairs += P.nweak[l];
     }
     out->strong_leaf_pairs = P.nstrong[P.B];
-    out->p2p_interactions = P.p2p_interactions;
+    unsigned long long work = 0;
+    if (P.p2p_work_dev) {
+        cudaError_t e = cudaStreamSynchronize(P.stream);
+        if (e == cudaSuccess) e = cudaMemcpy(&work, P.p2p_work_dev, 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    out->p2p_interactions = (int64_t)work;
     return FMM_OK;
 }
 

@@ -51,10 +51,12 @@ struct Plan {
     int32_t *sptr[FMM_MAX_LEVELS + 1] = {}, *ssrc[FMM_MAX_LEVELS + 1] = {};
     int32_t *wrow[FMM_MAX_LEVELS + 1] = {};  // target of every weak pair (flat M2L)
     int64_t nweak[FMM_MAX_LEVELS + 1] = {}, nstrong[FMM_MAX_LEVELS + 1] = {};
-    int64_t p2p_interactions = 0;
+    unsigned long long *p2p_work_dev = nullptr;  // exact near-field pair count (device)
     // near-field work units (target leaf, first target of a kP2PTile tile),
-    // heaviest first
+    // heaviest first; their number on the device, and an upper bound for
+    // the launch (blocks past the count return at once)
     int2 *p2p_units = nullptr;
+    const int32_t *p2p_nunits_dev = nullptr;
     int64_t p2p_nunits = 0;
     bool capacity_exceeded = false;
     // M2L rotation tables (D = d(pi/2) quadrants, axial coefficients, F_nm)

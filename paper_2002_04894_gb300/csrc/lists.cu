@@ -195,8 +195,10 @@ __global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *tile_sums) {
 
 // per target leaf the near source points (sum of n_s over its strong leaf
 // pairs), and in total the sum over strong leaf pairs (t, s) of n_t * n_s
+// per leaf: its sources over the strong list, its number of near-field work
+// units (tiles of kP2PTile targets); the total pair count into acc
 __global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, const int32_t *count,
-                           unsigned long long *acc, long long *per_leaf) {
+                           unsigned long long *acc, long long *per_leaf, int32_t *units_per_leaf) {
     const int64_t nt = (int64_t)1 << B;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long v = 0;
@@ -206,9 +208,71 @@ __global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, cons
         for (int32_t e = sptr[t]; e < sptr[t + 1]; e++) ns += (unsigned long long)count[off + ssrc[e]];
         v = ns * (unsigned long long)count[off + t];
         per_leaf[t] = (long long)ns;
+        units_per_leaf[t] = (count[off + t] + kP2PTile - 1) / kP2PTile;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+}
+
+// Work units heaviest first, on the device: each unit's weight (targets x the
+// leaf's sources) is quantised to a quarter-octave bucket (0 = heaviest), and a
+// stable counting sort over the buckets orders them (within a bucket, leaf
+// order). The exact order only affects the near field's load balance.
+constexpr int kUnitBlock = 256;
+__device__ __forceinline__ int unit_bucket(unsigned long long w) {
+    if (w == 0) return 255;
+    const int lg = 63 - __clzll((long long)w);
+    const int frac = lg >= 2 ? (int)((w >> (lg - 2)) & 3ull) : (int)((w << (2 - lg)) & 3ull);
+    return 255 - min(255, 4 * lg + frac);
+}
+
+__global__ void k_units_gen(int B, const int32_t *count, const long long *nsrc, const int32_t *uoff,
+                            int2 *units, uint8_t *bucket) {
+    const int64_t nt = (int64_t)1 << B;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int cnt = count[nt - 1 + t];
+    int u = uoff[t];
+    for (int tb = 0; tb < cnt; tb += kP2PTile, u++) {
+        units[u] = make_int2((int)t, tb);
+        bucket[u] = (uint8_t)unit_bucket((unsigned long long)min(kP2PTile, cnt - tb) * (unsigned long long)nsrc[t]);
+    }
+}
+
+// counts per (bucket, block of kUnitBlock units), bucket-major
+__global__ void __launch_bounds__(kUnitBlock)
+k_units_hist(const int32_t *total, const uint8_t *bucket, int nblocks, int32_t *bh) {
+    __shared__ int32_t h[256];
+    const int tid = threadIdx.x, k = blockIdx.x;
+    h[tid] = 0;
+    __syncthreads();
+    const int u = k * kUnitBlock + tid;
+    if (u < *total) atomicAdd(&h[bucket[u]], 1);
+    __syncthreads();
+    bh[(int64_t)tid * nblocks + k] = h[tid];
+}
+
+// stable scatter: a unit's place is its bucket's offset for its block plus the
+// units of the same bucket before it in the block (warp match, then warps)
+__global__ void __launch_bounds__(kUnitBlock)
+k_units_scatter(const int32_t *total, const uint8_t *bucket, const int2 *units, int nblocks,
+                const int32_t *boff, int2 *sorted) {
+    __shared__ int32_t wc[kUnitBlock / 32][256];
+    const int tid = threadIdx.x, k = blockIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < (kUnitBlock / 32) * 256; i += kUnitBlock) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const int u = k * kUnitBlock + tid;
+    const bool valid = u < *total;
+    const int b = valid ? bucket[u] : 256;  // 256: no bucket
+    const unsigned same = __match_any_sync(0xffffffffu, b);
+    const int rank_w = __popc(same & ((1u << lane) - 1u));
+    if (valid && rank_w == 0) wc[w][b] = __popc(same);
+    __syncthreads();
+    if (valid) {
+        int r = boff[(int64_t)b * nblocks + k] + rank_w;
+        for (int j = 0; j < w; j++) r += wc[j][b];
+        sorted[r] = units[u];
+    }
 }
 
 }  // namespace
@@ -311,43 +375,35 @@ cudaError_t lists_build(Plan &P) {
     // field runs as work units of up to kP2PTile targets of one leaf, so that
     // a few large leaves still fill the GPU; units go heaviest first, so that
     // the long ones start early instead of forming the tail of the launch.
+    // All of it stays on the device: the near-field launch takes an upper
+    // bound on the number of units and reads the actual count.
     const int64_t nl = (int64_t)1 << P.B;
-    unsigned long long *acc = (unsigned long long *)dalloc(P, 8);
+    const int64_t umax = nl + (P.n + kP2PTile - 1) / kP2PTile;  // sum of ceil(count / tile) <= this
+    const int nblk = (int)((umax + kUnitBlock - 1) / kUnitBlock);
+    P.p2p_work_dev = (unsigned long long *)palloc(P, 8);
     long long *nsrc = (long long *)dalloc(P, (size_t)nl * 8);
-    if (!acc || !nsrc) return cudaErrorMemoryAllocation;
-    cudaMemsetAsync(acc, 0, 8, st);
+    int32_t *upl = (int32_t *)dalloc(P, (size_t)nl * 4);
+    int32_t *uoff = (int32_t *)palloc(P, (size_t)(nl + 1) * 4);
+    int2 *units = (int2 *)dalloc(P, (size_t)umax * sizeof(int2));
+    uint8_t *bucket = (uint8_t *)dalloc(P, (size_t)umax);
+    int32_t *bh = (int32_t *)dalloc(P, (size_t)256 * nblk * 4);
+    int32_t *boff = (int32_t *)dalloc(P, ((size_t)256 * nblk + 1) * 4);
+    P.p2p_units = (int2 *)palloc(P, (size_t)umax * sizeof(int2));
+    if (!P.p2p_work_dev || !nsrc || !upl || !uoff || !units || !bucket || !bh || !boff || !P.p2p_units)
+        return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(P.p2p_work_dev, 0, 8, st);
     FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.sptr[P.B], P.ssrc[P.B],
-               P.count, acc, nsrc);
-    std::vector<long long> hns((size_t)nl);
-    std::vector<int32_t> hcnt((size_t)nl);
-    unsigned long long h = 0;
-    cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hns.data(), nsrc, (size_t)nl * 8, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hcnt.data(), P.count + (nl - 1), (size_t)nl * 4, cudaMemcpyDeviceToHost, st);
-    e = cudaStreamSynchronize(st);
-    P.p2p_interactions = (int64_t)h;
+               P.count, P.p2p_work_dev, nsrc, upl);
+    e = scan_exclusive(P, upl, uoff, nl);
     if (e != cudaSuccess) return e;
-    std::vector<int2> units;
-    std::vector<long long> uw;
-    units.reserve((size_t)nl);
-    uw.reserve((size_t)nl);
-    for (int64_t t = 0; t < nl; t++)
-        for (int32_t tb = 0; tb < hcnt[t]; tb += kP2PTile) {
-            units.push_back(make_int2((int)t, tb));
-            uw.push_back((long long)std::min(kP2PTile, hcnt[t] - tb) * hns[t]);
-        }
-    std::vector<int32_t> idx(units.size());
-    for (size_t i = 0; i < idx.size(); i++) idx[i] = (int32_t)i;
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return uw[a] > uw[b]; });
-    std::vector<int2> sorted(units.size());
-    for (size_t i = 0; i < idx.size(); i++) sorted[i] = units[idx[i]];
-    P.p2p_nunits = (int64_t)sorted.size();
-    P.p2p_units = (int2 *)palloc(P, std::max<size_t>(sorted.size(), 1) * sizeof(int2));
-    if (!P.p2p_units) return cudaErrorMemoryAllocation;
-    if (!sorted.empty())
-        e = cudaMemcpyAsync(P.p2p_units, sorted.data(), sorted.size() * sizeof(int2),
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    P.p2p_nunits_dev = uoff + nl;
+    P.p2p_nunits = umax;
+    FMM_LAUNCH(k_units_gen, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.count, nsrc, uoff, units, bucket);
+    FMM_LAUNCH(k_units_hist, (unsigned)nblk, kUnitBlock, 0, st, P.p2p_nunits_dev, bucket, nblk, bh);
+    e = scan_exclusive(P, bh, boff, (int64_t)256 * nblk);
+    if (e != cudaSuccess) return e;
+    FMM_LAUNCH(k_units_scatter, (unsigned)nblk, kUnitBlock, 0, st, P.p2p_nunits_dev, bucket, units, nblk, boff,
+               P.p2p_units);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(kP2PThreads)
 k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const float4 *__restrict__ geo, const int32_t *__restrict__ sptr,
-          const int32_t *__restrict__ ssrc, const int2 *__restrict__ units,
+          const int32_t *__restrict__ ssrc, const int2 *__restrict__ units, const int32_t *__restrict__ nunits,
           const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
           const float *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
     __shared__ float4 sA[kSrcTile / 2], sB[kSrcTile / 2];  // hi parts and charges, per source pair
@@ -338,6 +338,7 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
     __shared__ int2 rng[kLeafChunk];    // begin, count
     static_assert(kP2PThreads == kP2PTile, "one target per thread");
     const int64_t off = ((int64_t)1 << B) - 1;
+    if ((int)blockIdx.x >= *nunits) return;  // launched for an upper bound on the units
     const int2 unit = units[blockIdx.x];
     const int t = unit.x;
     const int64_t gt = off + t;
@@ -499,11 +500,11 @@ cudaError_t mixed_l2p(Plan &P) {
 cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
     if (dtype == FMM_F64)
         FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.p2p_nunits, kP2PThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.perm,
+                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev, P.perm,
                    P.far_phi_f, P.far_E_f, (double *)pot, (double *)field);
     else
         FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.p2p_nunits, kP2PThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.perm,
+                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev, P.perm,
                    P.far_phi_f, P.far_E_f, (float *)pot, (float *)field);
     return cudaGetLastError();
 }

@@ -26,12 +26,13 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
           const double *__restrict__ z, const double *__restrict__ q,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const int32_t *__restrict__ sptr, const int32_t *__restrict__ ssrc,
-          const int2 *__restrict__ units, const int32_t *__restrict__ perm,
+          const int2 *__restrict__ units, const int32_t *__restrict__ nunits, const int32_t *__restrict__ perm,
           const double *__restrict__ far_phi,
           const double *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
     __shared__ double4 tile[kP2PThreads];
     const int64_t off = ((int64_t)1 << B) - 1;
     static_assert(kP2PThreads == kP2PTile, "one target per thread");
+    if ((int)blockIdx.x >= *nunits) return;  // launched for an upper bound on the units
     const int2 unit = units[blockIdx.x];
     const int t = unit.x;
     const int bt = begin[off + t], nt = count[off + t];
@@ -146,11 +147,11 @@ cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
     }
     if (dtype == FMM_F64)
         FMM_LAUNCH(k_p2p_f64<double>, grid, kP2PThreads, 0, P.stream, 
-            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units,
+            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev,
             P.perm, P.far_phi, P.far_E, (double *)pot, (double *)field);
     else
         FMM_LAUNCH(k_p2p_f64<float>, grid, kP2PThreads, 0, P.stream, 
-            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units,
+            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev,
             P.perm, P.far_phi, P.far_E, (float *)pot, (float *)field);
     stage_mark(P, FMM_STAGE_P2P, 1);
     return cudaGetLastError();
