@@ -23,6 +23,19 @@ namespace fmm {
 
 namespace {
 
+// 1/k for k = 0..FMM_MAX_P^2 (0 at k = 0): the harmonic recurrences divide by
+// (n - m)(n + m) = n^2 - m^2 once per term; the reciprocal of that integer,
+// correctly rounded, is read here (warp-uniform index, constant cache)
+struct InvTable {
+    float v[FMM_MAX_P * FMM_MAX_P + 1];
+};
+constexpr InvTable make_inv_table() {
+    InvTable t{};
+    for (int k = 1; k <= FMM_MAX_P * FMM_MAX_P; k++) t.v[k] = 1.0f / (float)k;
+    return t;
+}
+__constant__ InvTable c_inv = make_inv_table();
+
 constexpr int kThreads = 128;
 
 __device__ __forceinline__ float2 fcmul(float2 a, float2 b) {
@@ -100,7 +113,7 @@ k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__
                     if (nn == m + 1) {
                         nxt = make_float2(cur.x * sz, cur.y * sz);
                     } else {
-                        const float s = 1.f / ((float)(nn - m) * (float)(nn + m));
+                        const float s = c_inv.v[nn * nn - m * m];  // 1 / ((n - m)(n + m))
                         const float a = (2 * nn - 1) * sz;
                         nxt = make_float2((a * cur.x - r2 * prev.x) * s, (a * cur.y - r2 * prev.y) * s);
                     }
@@ -176,7 +189,7 @@ k_l2p_f32(int B, int p, int64_t n, const float *__restrict__ hl, const int32_t *
                     if (nn == m + 1) {
                         nxt = make_float2(cur.x * sz, cur.y * sz);
                     } else {
-                        const float s = 1.f / ((float)(nn - m) * (float)(nn + m));
+                        const float s = c_inv.v[nn * nn - m * m];  // 1 / ((n - m)(n + m))
                         const float a = (2 * nn - 1) * sz;
                         nxt = make_float2((a * cur.x - r2 * prev.x) * s, (a * cur.y - r2 * prev.y) * s);
                     }
