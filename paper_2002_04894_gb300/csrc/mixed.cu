@@ -71,78 +71,99 @@ __global__ void k_gather_qf(const T *__restrict__ qin, const int32_t *__restrict
         q[i] = (float)qin[perm[i]];
 }
 
-// P2M on scaled offsets; each warp's sums (over its batches of 32 points)
-// stay in float in shared memory, the block's warps are combined in double,
-// and the leaf's multipole is stored unscaled in double (M_n^m = r^n Mhat_n^m).
-// (A double add by one lane per coefficient would occupy GB300's narrow FP64
-// pipe as long as a full-warp one.)
-__global__ void __launch_bounds__(kThreads)
+// P2M on scaled offsets, one warp per leaf: each lane carries kP2MSlots
+// points, and two warp sums per coefficient (slots 0-1 and 2-3, 64 points
+// each) cover a batch of 128; the two sums stay apart in float in shared
+// memory and are combined in double, so each float sum is no deeper than
+// a 64-term tree. The leaf's multipole is stored unscaled in double
+// (M_n^m = r^n Mhat_n^m).
+constexpr int kP2MSlots = 4;
+__global__ void __launch_bounds__(32)
 k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__restrict__ q,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const double *__restrict__ radius, double2 *__restrict__ M) {
-    extern __shared__ float2 accf[];  // [warps][nc]
+    extern __shared__ float2 accf[];  // [2][nc]
     const int nc = ncoef(p);
     const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
     const int b = begin[g], cnt = count[g];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x;
     const double rs = box_scale(radius[g]);
     const float rinv = (float)(1.0 / rs);
-    for (int c = threadIdx.x; c < nc * (kThreads / 32); c += kThreads) accf[c] = make_float2(0.f, 0.f);
-    __syncthreads();
-    float2 *mine = accf + w * nc;
-    for (int base = w * 32; base < cnt; base += kThreads) {
-        const int i = base + lane;
-        const bool valid = i < cnt;
-        const float sx = valid ? (hl[b + i] + hl[3 * n + b + i]) * rinv : 0.f;
-        const float sy = valid ? (hl[n + b + i] + hl[4 * n + b + i]) * rinv : 0.f;
-        const float sz = valid ? (hl[2 * n + b + i] + hl[5 * n + b + i]) * rinv : 0.f;
-        const float qi = valid ? q[b + i] : 0.f;
-        const float r2 = sx * sx + sy * sy + sz * sz;
-        float2 mm = make_float2(1.f, 0.f);
+    for (int c = lane; c < 2 * nc; c += 32) accf[c] = make_float2(0.f, 0.f);
+    __syncwarp();
+    for (int base = 0; base < cnt; base += 32 * kP2MSlots) {
+        float sx[kP2MSlots], sy[kP2MSlots], sz[kP2MSlots], r2[kP2MSlots], qi[kP2MSlots];
+        float2 mm[kP2MSlots];
+#pragma unroll
+        for (int r = 0; r < kP2MSlots; r++) {
+            const int i = base + 32 * r + lane;
+            const bool valid = i < cnt;
+            sx[r] = valid ? (hl[b + i] + hl[3 * n + b + i]) * rinv : 0.f;
+            sy[r] = valid ? (hl[n + b + i] + hl[4 * n + b + i]) * rinv : 0.f;
+            sz[r] = valid ? (hl[2 * n + b + i] + hl[5 * n + b + i]) * rinv : 0.f;
+            qi[r] = valid ? q[b + i] : 0.f;
+            r2[r] = sx[r] * sx[r] + sy[r] * sy[r] + sz[r] * sz[r];
+            mm[r] = make_float2(1.f, 0.f);
+        }
         for (int m = 0; m <= p; m++) {
-            if (m > 0) {
-                mm = fcmul(mm, make_float2(sx, sy));
-                const float s = 0.5f / m;
-                mm = make_float2(mm.x * s, mm.y * s);
-            }
-            float2 cur = mm, prev = make_float2(0.f, 0.f);
-            const float sg = (m & 1) ? -qi : qi;
-            for (int nn = m; nn <= p; nn++) {
-                if (nn > m) {
-                    float2 nxt;
-                    if (nn == m + 1) {
-                        nxt = make_float2(cur.x * sz, cur.y * sz);
-                    } else {
-                        const float s = c_inv.v[nn * nn - m * m];  // 1 / ((n - m)(n + m))
-                        const float a = (2 * nn - 1) * sz;
-                        nxt = make_float2((a * cur.x - r2 * prev.x) * s, (a * cur.y - r2 * prev.y) * s);
-                    }
-                    prev = cur;
-                    cur = nxt;
+            float2 cur[kP2MSlots], prev[kP2MSlots];
+#pragma unroll
+            for (int r = 0; r < kP2MSlots; r++) {
+                if (m > 0) {
+                    mm[r] = fcmul(mm[r], make_float2(sx[r], sy[r]));
+                    const float s = 0.5f / m;
+                    mm[r] = make_float2(mm[r].x * s, mm[r].y * s);
                 }
-                float vr = sg * cur.x, vi = -sg * cur.y;
+                cur[r] = mm[r];
+                prev[r] = make_float2(0.f, 0.f);
+            }
+            for (int nn = m; nn <= p; nn++) {
+                float vr[2] = {0.f, 0.f}, vi[2] = {0.f, 0.f};
+#pragma unroll
+                for (int r = 0; r < kP2MSlots; r++) {
+                    if (nn > m) {
+                        float2 nxt;
+                        if (nn == m + 1) {
+                            nxt = make_float2(cur[r].x * sz[r], cur[r].y * sz[r]);
+                        } else {
+                            const float s = c_inv.v[nn * nn - m * m];  // 1 / ((n - m)(n + m))
+                            const float a = (2 * nn - 1) * sz[r];
+                            nxt = make_float2((a * cur[r].x - r2[r] * prev[r].x) * s,
+                                              (a * cur[r].y - r2[r] * prev[r].y) * s);
+                        }
+                        prev[r] = cur[r];
+                        cur[r] = nxt;
+                    }
+                    const float sg = (m & 1) ? -qi[r] : qi[r];
+                    vr[r >> 1] = fmaf(sg, cur[r].x, vr[r >> 1]);
+                    vi[r >> 1] = fmaf(-sg, cur[r].y, vi[r >> 1]);
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    vr += __shfl_xor_sync(0xffffffffu, vr, o);
-                    vi += __shfl_xor_sync(0xffffffffu, vi, o);
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        vr[h] += __shfl_xor_sync(0xffffffffu, vr[h], o);
+                        vi[h] += __shfl_xor_sync(0xffffffffu, vi[h], o);
+                    }
                 }
                 if (lane == 0) {
-                    const float2 a = mine[tri(nn, m)];
-                    mine[tri(nn, m)] = make_float2(a.x + vr, a.y + vi);
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const float2 a = accf[h * nc + tri(nn, m)];
+                        accf[h * nc + tri(nn, m)] = make_float2(a.x + vr[h], a.y + vi[h]);
+                    }
                 }
             }
         }
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += kThreads) {
+    __syncwarp();
+    for (int c = lane; c < nc; c += 32) {
         int nn = 0;
         while (tri(nn + 1, 0) <= c) nn++;
         double s = 1.0;
         for (int j = 0; j < nn; j++) s *= rs;
-        double2 v = make_double2(0.0, 0.0);
-        for (int j = 0; j < kThreads / 32; j++)
-            v = cadd(v, make_double2((double)accf[j * nc + c].x, (double)accf[j * nc + c].y));
-        M[g * nc + c] = make_double2(v.x * s, v.y * s);
+        M[g * nc + c] = make_double2(((double)accf[c].x + (double)accf[nc + c].x) * s,
+                                     ((double)accf[c].y + (double)accf[nc + c].y) * s);
     }
 }
 
@@ -499,7 +520,7 @@ cudaError_t mixed_p2m(Plan &P, const void *charges, int dtype) {
         FMM_LAUNCH(k_gather_qf<double>, gq, 256, 0, P.stream, (const double *)charges, P.perm, P.qf, n);
     else
         FMM_LAUNCH(k_gather_qf<float>, gq, 256, 0, P.stream, (const float *)charges, P.perm, P.qf, n);
-    FMM_LAUNCH(k_p2m_f32, (unsigned)P.nleaf, kThreads, sizeof(float2) * P.nc * (kThreads / 32),
+    FMM_LAUNCH(k_p2m_f32, (unsigned)P.nleaf, 32, sizeof(float2) * P.nc * 2,
                P.stream, P.B, P.p, n, P.hl, P.qf, P.begin, P.count, P.radius, P.M);
     return cudaGetLastError();
 }
