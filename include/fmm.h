@@ -119,7 +119,9 @@ typedef struct fmm_opts {
 /*
  * Optional device allocator. alloc returns device memory of at least `bytes`
  * usable in stream order on `stream` (or NULL on failure); free releases it.
- * Without one the library uses cudaMallocAsync / cudaFreeAsync.
+ * Without one the library allocates from a stream-ordered memory pool of its
+ * own per device, which keeps freed memory for later plans instead of
+ * returning it at every synchronisation; fmm_pool_trim releases it.
  */
 typedef void *(*fmm_alloc_fn)(size_t bytes, void *ctx, void *stream);
 typedef void (*fmm_free_fn)(void *ptr, size_t bytes, void *ctx, void *stream);
@@ -321,6 +323,14 @@ const char *fmm_strerror(int status);
 
 /* fmm_last_cuda_error -- the cudaError_t behind the calling thread's last FMM_ECUDA. */
 int fmm_last_cuda_error(void);
+
+/*
+ * fmm_pool_trim -- return the memory cached by the library's own pool on CUDA
+ * device `device` (plans made without an allocator) to the system; memory
+ * of live plans stays. A device whose pool was never used: FMM_OK.
+ * Errors: FMM_EINVAL (device outside 0..63), FMM_ECUDA.
+ */
+int fmm_pool_trim(int device);
 
 #ifdef __cplusplus
 }

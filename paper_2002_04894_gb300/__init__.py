@@ -63,7 +63,7 @@ EXPORTS = ("fmm_plan", "fmm_eval", "fmm_destroy", "fmm_direct", "fmm_plan_stats"
            "fmm_plan_tree", "fmm_plan_list", "fmm_eval_expansions", "fmm_strerror",
            "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches",
            "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy",
-           "fmm_eval_check")
+           "fmm_eval_check", "fmm_pool_trim")
 FMM_NOALLOC_MAX_POINTS, FMM_NOALLOC_MAX_LEVELS = 4096, 12
 
 
@@ -104,6 +104,8 @@ def load(build: bool = True) -> C.CDLL:
     lib.fmm_strerror.argtypes = [i32]
     lib.fmm_strerror.restype = C.c_char_p
     lib.fmm_last_cuda_error.restype = i32
+    lib.fmm_pool_trim.argtypes = [i32]
+    lib.fmm_pool_trim.restype = i32
     lib.fmm_stage_times.argtypes = [vp, vp]
     lib.fmm_stage_times.restype = i32
     lib.fmm_kernel_launches.argtypes = []
@@ -346,6 +348,12 @@ def fmm_stage_times(plan: Plan) -> dict:
     ms = np.zeros(len(STAGES))
     _check(load().fmm_stage_times(plan.handle, ms.ctypes.data), "fmm_stage_times")
     return dict(zip(STAGES, ms.tolist()))
+
+
+def fmm_pool_trim(device: int = 0) -> None:
+    """Return the memory cached by the library's own pool on `device` (plans
+    made with allocator=None) to the system."""
+    _check(load().fmm_pool_trim(int(device)), "fmm_pool_trim")
 
 
 def fmm_kernel_launches() -> int:

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -19,10 +20,41 @@ cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype);
 
 namespace {
 
+// Without a caller's allocator, plan memory comes from a stream-ordered pool
+// of the library's own per device that keeps freed memory for the next plan
+// (the device's default pool returns it at every synchronisation, so each
+// plan would map its ~100 bytes per point anew); fmm_pool_trim releases it.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t library_pool(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
 void *raw_alloc(Plan &P, size_t bytes) {
     if (P.has_alloc) return P.alloc.alloc(bytes, P.alloc.ctx, (void *)P.stream);
+    int dev = 0;
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, P.stream) != cudaSuccess) {
+    cudaMemPool_t pool = cudaGetDevice(&dev) == cudaSuccess ? library_pool(dev) : nullptr;
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, P.stream)
+                               : cudaMallocAsync(&p, bytes, P.stream);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -147,6 +179,17 @@ const char *fmm_strerror(int status) {
 }
 
 int fmm_last_cuda_error(void) { return g_last_cuda; }
+
+int fmm_pool_trim(int device) {
+    if (device < 0 || device >= 64) return FMM_EINVAL;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(fmm::g_pool_mu);
+        pool = fmm::g_pool[device];
+    }
+    if (!pool) return FMM_OK;
+    return cuda_status(cudaMemPoolTrimTo(pool, 0));
+}
 
 int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
              const fmm_allocator *alloc, void *stream, fmm_plan_t *out) {

@@ -72,6 +72,29 @@ def test_host_buffers_give_identical_bits(gpu_lib):
     np.testing.assert_array_equal(ea.cpu().numpy(), eb)
 
 
+def test_library_pool_reuse_and_trim(gpu_lib):
+    """Plans without an allocator draw from the library's pool: a plan built
+    after another was destroyed (memory kept in the pool), and after the pool
+    was trimmed, gives the same results."""
+    fmm = gpu_lib
+    x = inputs.points("plummer", 6000, 4)
+    q = inputs.charges_uniform(6000, 4)
+    p1 = fmm.fmm_plan(x, 7, 6, 0.5, allocator=None)
+    a, ea = fmm.fmm_eval(p1, q)
+    fmm.fmm_destroy(p1)
+    p2 = fmm.fmm_plan(x, 7, 6, 0.5, allocator=None)
+    b, eb = fmm.fmm_eval(p2, q)
+    fmm.fmm_destroy(p2)
+    fmm.fmm_pool_trim(torch.cuda.current_device())
+    p3 = fmm.fmm_plan(x, 7, 6, 0.5, allocator=None)
+    c, ec = fmm.fmm_eval(p3, q)
+    fmm.fmm_destroy(p3)
+    for u, v in ((a, b), (ea, eb), (a, c), (ea, ec)):
+        np.testing.assert_array_equal(u, v)
+    with pytest.raises(RuntimeError):
+        fmm.fmm_pool_trim(64)
+
+
 def test_repeated_eval_and_recharge(gpu_lib):
     fmm = gpu_lib
     x = inputs.points("uniform", 4000, 3)
