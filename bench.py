@@ -61,9 +61,9 @@ FP64_FLOPS_PER_CLK_SM = 4    # GB300 nominal 1.25 TFLOP/s FP64 at 2.07 GHz / 152
 # (profiles/k_p2p_f32_plummer2m_l14_p12.md), valid only while the kernel's
 # source is the one that was captured (checked by hash; otherwise null).
 MEASURED_TRAFFIC = {
-    ("plummer2m_l14_p12", "k_p2p_f32"): {"bytes": 273070336 + 146899968,
+    ("plummer2m_l14_p12", "k_p2p_f32"): {"bytes": 274585600 + 123338496,
                                          "source": "paper_2002_04894_gb300/csrc/mixed.cu",
-                                         "sha256_16": "6596a520f469e17c"},
+                                         "sha256_16": "6511125a5290178c"},
 }
 
 
