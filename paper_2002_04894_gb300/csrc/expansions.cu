@@ -29,25 +29,6 @@ namespace {
 
 constexpr int kExpThreads = 128;
 
-// (n, m) from a packed triangle index
-__device__ __forceinline__ void untri(int c, int &n, int &m) {
-    n = (int)((sqrt(8.0 * c + 1.0) - 1.0) * 0.5);
-    while (tri(n + 1, 0) <= c) n++;
-    while (tri(n, 0) > c) n--;
-    m = c - tri(n, 0);
-}
-
-// signed-order view of a stored harmonic table H (R or I): (-1)^m H_n^m for
-// m >= 0 and conj(H_n^|m|) for m < 0
-__device__ __forceinline__ double2 sview(const double2 *H, int n, int m) {
-    if (n < 0 || m > n || -m > n) return make_double2(0.0, 0.0);
-    if (m >= 0) {
-        const double2 h = H[tri(n, m)];
-        return (m & 1) ? make_double2(-h.x, -h.y) : h;
-    }
-    return cconj(H[tri(n, -m)]);
-}
-
 template <typename T>
 __global__ void k_gather_q(const T *__restrict__ qin, const int32_t *__restrict__ perm,
                            double *__restrict__ q, int64_t n) {

@@ -548,16 +548,18 @@ cudaError_t m2l_all(Plan &P) {
 // The target's local expansion is accumulated in double.
 //
 // GPU mapping: one weak pair per thread, all levels in one launch (pairs
-// sorted by target). Every degree (and every order of the translation) is
-// its own template instance, so a degree's input vector sits in registers;
-// a fold's outputs come from a runtime loop, two per iteration (one of each
-// parity), each a dot product of packed pairs -- (Re of one parity, Im of
-// the other) against a row of matching coefficient pairs -- in FFMA2. The
-// coefficient rows are read from global memory at warp-uniform addresses
-// (L1 broadcast), so the code stays a few thousand instructions that loop
-// instead of a straight line of every multiply-add. Between the stages the
-// pair's coefficients sit in its lane of tensor memory (degrees 0..9) and
-// in a shared-memory column (higher degrees).
+// sorted by target), blocks striding over chunks of 128 pairs. Every degree
+// (and every two orders of the translation) is its own template instance,
+// so a degree's input vector sits in registers; a fold's outputs come from a
+// runtime loop, two per iteration (one of each parity), each a dot product
+// of packed pairs -- (Re of one parity, Im of the other) against a row of
+// matching coefficient pairs -- in FFMA2. The coefficient rows are staged in
+// shared memory once per block and read at warp-uniform addresses, so the
+// code stays a few thousand instructions that loop instead of a straight
+// line of every multiply-add. Between the stages the pair's coefficients sit
+// in its lane of tensor memory (degrees 0..9) and in a shared-memory column
+// (higher degrees); outputs that feed another fold are stored in the pair
+// layout that fold reads.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -836,7 +838,7 @@ __device__ __forceinline__ void fold_rt(const float4 *__restrict__ rows, const P
 // storage
 template <int P, int N>
 __device__ __forceinline__ void fwd_deg(const float2 *__restrict__ Ms, const VS &vs, bool valid, float2 eai,
-                                        float2 ebv, const float4 *__restrict__ tab) {
+                                        const float4 *__restrict__ tab) {
     // the degree's coefficients, two per 16-byte load where the pair is aligned
     constexpr int c0 = N * (N + 1) / 2, m0 = c0 & 1;
     float2 u[N + 1];
@@ -921,7 +923,7 @@ __device__ __noinline__ void col_add(const float *red, int N, double2 *dst) {
 // its 2 (N+1) values per lane through shared memory and adds each column with
 // one atomic; otherwise a segmented shuffle sum over runs of equal target
 template <int P, int N>
-__device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, float2 ebv, double2 *__restrict__ Lh,
+__device__ __forceinline__ void bwd_deg(const VS &vs, float2 eai, double2 *__restrict__ Lh,
                                         unsigned same_mask, bool head, int uniform_tgt,
                                         double2 *__restrict__ Lbase, const float4 *__restrict__ tab, float *red) {
     constexpr int NC = (P + 1) * (P + 2) / 2, DP = dpo(P + 1);
@@ -1024,27 +1026,27 @@ __device__ __forceinline__ void axial_ord(const VS &vs, float qs, float qt, floa
 
 template <int P, int N>
 struct Seq {
-    __device__ static __forceinline__ void fwd(const float2 *Ms, const VS &vs, bool valid, float2 eai, float2 ebv,
+    __device__ static __forceinline__ void fwd(const float2 *Ms, const VS &vs, bool valid, float2 eai,
                                                const float4 *tab) {
-        fwd_deg<P, N>(Ms, vs, valid, eai, ebv, tab);
-        Seq<P, N + 1>::fwd(Ms, vs, valid, eai, ebv, tab);
+        fwd_deg<P, N>(Ms, vs, valid, eai, tab);
+        Seq<P, N + 1>::fwd(Ms, vs, valid, eai, tab);
     }
     __device__ static __forceinline__ void axial(const VS &vs, float qs, float qt, float rinv, const float4 *tab) {
         if constexpr ((N & 1) == 0) axial_ord<P, N>(vs, qs, qt, rinv, tab);
         Seq<P, N + 1>::axial(vs, qs, qt, rinv, tab);
     }
-    __device__ static __forceinline__ void bwd(const VS &vs, float2 eai, float2 ebv, double2 *Lh, unsigned same,
+    __device__ static __forceinline__ void bwd(const VS &vs, float2 eai, double2 *Lh, unsigned same,
                                                bool head, int ut, double2 *Lbase, const float4 *tab, float *red) {
-        bwd_deg<P, N>(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, red);
-        Seq<P, N + 1>::bwd(vs, eai, ebv, Lh, same, head, ut, Lbase, tab, red);
+        bwd_deg<P, N>(vs, eai, Lh, same, head, ut, Lbase, tab, red);
+        Seq<P, N + 1>::bwd(vs, eai, Lh, same, head, ut, Lbase, tab, red);
     }
 };
 template <int P>
 struct Seq<P, P + 1> {
-    __device__ static __forceinline__ void fwd(const float2 *, const VS &, bool, float2, float2, const float4 *) {}
+    __device__ static __forceinline__ void fwd(const float2 *, const VS &, bool, float2, const float4 *) {}
     __device__ static __forceinline__ void axial(const VS &, float, float, float, const float4 *) {}
-    __device__ static __forceinline__ void bwd(const VS &, float2, float2, double2 *, unsigned, bool, int,
-                                               double2 *, const float4 *, float *) {}
+    __device__ static __forceinline__ void bwd(const VS &, float2, double2 *, unsigned, bool, int, double2 *,
+                                               const float4 *, float *) {}
 };
 
 constexpr int kF32Threads = 128;
@@ -1115,13 +1117,13 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
         tm_wait_st();
     }
     float *region = (float *)(smf + SP::NS * kF32Threads) + warp * region_floats<P>();
-    Seq<P, 0>::fwd(Mf + gs * mf_stride(P), vs, valid, eai, ebv, tab);
+    Seq<P, 0>::fwd(Mf + gs * mf_stride(P), vs, valid, eai, tab);
     Seq<P, 0>::axial(vs, qs, qt, rinv, tab);
     // the warp's pairs share one target (invalid lanes add zeros): transpose path
     const int t32 = gt >= 0 ? (int)gt : -1;
     const int tmax = __reduce_max_sync(0xffffffffu, t32);
     const bool uniform = __all_sync(0xffffffffu, t32 == tmax || t32 < 0);
-    Seq<P, 0>::bwd(vs, eai, ebv, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, tab, region);
+    Seq<P, 0>::bwd(vs, eai, Lh + (gt >= 0 ? gt : 0) * NC, same_mask, head, uniform ? tmax : -1, Lh, tab, region);
 }
 
 // one weak pair per thread, all levels, blocks striding over chunks of 128
@@ -1232,23 +1234,34 @@ cudaError_t f32_tables_ready() {
     return e;
 }
 
+long double norm_F(int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); }
+
+// entry (k, m) of fold table `tab` (Df, DTf, Db, DTb) of degree n, zero past m = n
+float fold_entry(int tab, int n, int k, int m) {
+    if (m > n) return 0.f;
+    const bool tr = tab & 1;
+    long double g = tr ? wigner_half_pi(n, m, k) : wigner_half_pi(n, k, m);
+    if (!tr) g *= (m ? 2.0L : 1.0L) * (k ? 2.0L : 1.0L);
+    if (tab == 0) g *= norm_F(n, m);
+    if (tab == 3) g *= norm_F(n, k);
+    return (float)g;
+}
+
+// entry (k, n) of the translation table of order l, zero past n = p
+float axial_entry(int p, int l, int k, int n) {
+    if (n > p) return 0.f;
+    const long double a = factl(n + k) / (norm_F(n, l) * norm_F(k, l));
+    return (float)(((k + l) & 1) ? -a : a);
+}
+
 // the packed pair tables of order p (layout at jp_of / dpo / ja_of / apo)
 std::vector<float4> f32_pair_tables(int p) {
     std::vector<float4> t;
     t.reserve(pair_tab_len(p));
-    auto Fl = [](int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); };
     for (int tab = 0; tab < 4; tab++)  // Df, DTf, Db, DTb
         for (int n = 0; n <= p; n++)
             for (int k = 0; k <= n; k++) {
-                auto G = [&](int m) -> float {
-                    if (m > n) return 0.f;
-                    const bool tr = tab & 1;
-                    long double g = tr ? wigner_half_pi(n, m, k) : wigner_half_pi(n, k, m);
-                    if (!tr) g *= (m ? 2.0L : 1.0L) * (k ? 2.0L : 1.0L);
-                    if (tab == 0) g *= Fl(n, m);
-                    if (tab == 3) g *= Fl(n, k);
-                    return (float)g;
-                };
+                auto G = [&](int m) { return fold_entry(tab, n, k, m); };
                 const bool odd = (n + k) & 1;
                 for (int q = 0; q < jp_of(n); q++) {
                     const int a = 4 * q;  // pairs 2q, 2q+1 cover m = a .. a+3
@@ -1258,14 +1271,10 @@ std::vector<float4> f32_pair_tables(int p) {
             }
     for (int l = 0; l <= p; l++)
         for (int k = l; k <= p; k++) {
-            auto A = [&](int n) -> float {
-                if (n > p) return 0.f;
-                const long double a = factl(n + k) / (Fl(n, l) * Fl(k, l));
-                return (float)(((k + l) & 1) ? -a : a);
-            };
             for (int q = 0; q < ja_of(p, l); q++) {
                 const int n0 = l + 2 * q;
-                t.push_back(make_float4(A(n0), A(n0), A(n0 + 1), A(n0 + 1)));
+                const float a0 = axial_entry(p, l, k, n0), a1 = axial_entry(p, l, k, n0 + 1);
+                t.push_back(make_float4(a0, a0, a1, a1));
             }
         }
     return t;

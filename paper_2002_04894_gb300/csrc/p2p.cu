@@ -29,7 +29,10 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
           const int2 *__restrict__ units, const int32_t *__restrict__ nunits, const int32_t *__restrict__ perm,
           const double *__restrict__ far_phi,
           const double *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
-    __shared__ double4 tile[kP2PThreads];
+    struct alignas(16) Src {
+        double x, y, z, q;
+    };
+    __shared__ Src tile[kP2PThreads];
     const int64_t off = ((int64_t)1 << B) - 1;
     static_assert(kP2PThreads == kP2PTile, "one target per thread");
     if ((int)blockIdx.x >= *nunits) return;  // launched for an upper bound on the units
@@ -50,16 +53,15 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
             const int bs = begin[gs], ns = count[gs];
             for (int sb = 0; sb < ns; sb += kP2PThreads) {
                 const int j = sb + threadIdx.x;
-                tile[threadIdx.x] = j < ns ? make_double4(x[bs + j], y[bs + j], z[bs + j], q[bs + j])
-                                           : make_double4(0.0, 0.0, 0.0, 0.0);
+                tile[threadIdx.x] = j < ns ? Src{x[bs + j], y[bs + j], z[bs + j], q[bs + j]} : Src{0.0, 0.0, 0.0, 0.0};
                 __syncthreads();
                 const int mcount = min(kP2PThreads, ns - sb);
                 for (int jj = 0; jj < mcount; jj++) {
-                    const double4 s = tile[jj];
+                    const Src s = tile[jj];
                     const double dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
                     const double r2 = dx * dx + dy * dy + dz * dz;
                     const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
-                    const double qr = s.w * rinv;
+                    const double qr = s.q * rinv;
                     const double qr3 = qr * rinv * rinv;
                     phi += qr;
                     ex += qr3 * dx;
