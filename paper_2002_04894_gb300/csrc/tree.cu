@@ -129,7 +129,9 @@ __global__ void k_root(const unsigned long long *bbox, double *lo, double *hi, d
 
 // One warp: find the digit whose bucket holds rank *rrem among hist[0..255],
 // update the key prefix and the remaining rank.
-__device__ void pick_digit(const unsigned *hist, int shift, uint64_t *prefix, unsigned *rrem) {
+// (cnt, when given, receives the number of keys in the chosen bucket)
+__device__ void pick_digit(const unsigned *hist, int shift, uint64_t *prefix, unsigned *rrem,
+                           unsigned *cnt = nullptr) {
     const int lane = threadIdx.x & 31;
     unsigned c[8], sum = 0;
 #pragma unroll
@@ -153,6 +155,7 @@ __device__ void pick_digit(const unsigned *hist, int shift, uint64_t *prefix, un
             if (r < acc + c[j]) {
                 *rrem = r - acc;
                 *prefix = pre | ((uint64_t)(lane * 8 + j) << shift);
+                if (cnt) *cnt = c[j];
                 break;
             }
             acc += c[j];
@@ -309,7 +312,7 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
 // Large regime: many CTAs per box
 // --------------------------------------------------------------------------
 __global__ void k_sel_init(int level, const int32_t *count, uint64_t *prefix, unsigned *rrem,
-                           unsigned long long *minr, unsigned *ghist) {
+                           unsigned long long *minr, unsigned *ghist, unsigned *found) {
     const int s = blockIdx.x;
     const int64_t g = ((int64_t)1 << level) - 1 + s;
     if (threadIdx.x == 0) {
@@ -317,6 +320,7 @@ __global__ void k_sel_init(int level, const int32_t *count, uint64_t *prefix, un
         prefix[s] = 0;
         rrem[s] = n >= 2 ? (unsigned)(n / 2 - 1) : 0u;
         minr[s] = ~0ull;
+        found[s] = 0;
     }
     for (int i = threadIdx.x; i < 256; i += blockDim.x) ghist[(int64_t)s * 256 + i] = 0;
 }
@@ -324,12 +328,14 @@ __global__ void k_sel_init(int level, const int32_t *count, uint64_t *prefix, un
 // One chunk of one box: histogram of the keys' current digit, added to the
 // box's global histogram. The last chunk of the box to finish (a per-box
 // arrival counter) then picks the digit holding the wanted rank, clears the
-// histogram and the counter for the next pass.
+// histogram and the counter for the next pass. When the chosen bucket holds
+// a single key (found = 1), the next pass just finds that key (found = 2) and
+// the remaining passes of the box return at once.
 __global__ void __launch_bounds__(kThreads)
 k_sel_hist(int level, int pass, const double *__restrict__ xs, const double *__restrict__ ys,
            const double *__restrict__ zs, const int32_t *__restrict__ begin,
            const int32_t *__restrict__ count, const int32_t *__restrict__ axis,
-           uint64_t *prefix, unsigned *rrem, unsigned *ghist, unsigned *arrived) {
+           uint64_t *prefix, unsigned *rrem, unsigned *ghist, unsigned *arrived, unsigned *found) {
     __shared__ unsigned h[256];
     __shared__ bool last;
     __shared__ uint64_t s_pre;
@@ -341,10 +347,22 @@ k_sel_hist(int level, int pass, const double *__restrict__ xs, const double *__r
     if (start >= n) return;
     const int end = min(n, start + kChunk);
     const double *src = ax == 0 ? xs : (ax == 1 ? ys : zs);
-    h[threadIdx.x] = 0;
-    __syncthreads();
+    const unsigned state = found[s];  // uniform over the block
+    if (state == 2u) return;
     const int shift = 56 - 8 * pass;
     const uint64_t pre = prefix[s];
+    if (state == 1u) {  // the one key under the prefix is the wanted one
+        for (int i = start + threadIdx.x; i < end; i += kThreads) {
+            const uint64_t kk = dkey(src[b + i]);
+            if (prefix_match(kk, pre, shift)) {
+                prefix[s] = kk;
+                found[s] = 2u;
+            }
+        }
+        return;
+    }
+    h[threadIdx.x] = 0;
+    __syncthreads();
     for (int i = start + threadIdx.x; i < end; i += kThreads) {
         const uint64_t kk = dkey(src[b + i]);
         if (prefix_match(kk, pre, shift)) atomicAdd(&h[(kk >> shift) & 255u], 1u);
@@ -369,11 +387,15 @@ k_sel_hist(int level, int pass, const double *__restrict__ xs, const double *__r
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        pick_digit(h, shift, &s_pre, &s_rr);
+        unsigned c = 0;
+        pick_digit(h, shift, &s_pre, &s_rr, &c);
         if (threadIdx.x == 0) {
             prefix[s] = s_pre;
             rrem[s] = s_rr;
         }
+        // the lane that picked wrote c; bring it to lane 0
+        c = __reduce_max_sync(0xffffffffu, c);
+        if (threadIdx.x == 0 && c == 1u && pass < 7) found[s] = 1u;
     }
 }
 
@@ -628,8 +650,10 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
     unsigned long long *sel_minr = (unsigned long long *)dalloc(P, (size_t)maxseg * 8);
     unsigned *sel_rrem = (unsigned *)dalloc(P, (size_t)maxseg * 4);
     unsigned *arrived = (unsigned *)dalloc(P, (size_t)maxseg * 4);  // per-box chunk arrivals
+    unsigned *sel_found = (unsigned *)dalloc(P, (size_t)maxseg * 4);  // per-box early finish of the select
     unsigned long long *bbox = (unsigned long long *)dalloc(P, 64);
-    if (!x2 || !y2 || !z2 || !i2 || !sel_v || !sel_prefix || !sel_minr || !sel_rrem || !arrived || !bbox)
+    if (!x2 || !y2 || !z2 || !i2 || !sel_v || !sel_prefix || !sel_minr || !sel_rrem || !arrived || !sel_found ||
+        !bbox)
         return cudaErrorMemoryAllocation;
     cudaMemsetAsync(arrived, 0, (size_t)maxseg * 4, st);
 
@@ -706,10 +730,11 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
             }
             const dim3 grid(S, nch);  // boxes on x (up to 2^31 - 1), chunks on y
             if (need_median) {
-                FMM_LAUNCH(k_sel_init, S, 256, 0, st, l, P.count, sel_prefix, sel_rrem, sel_minr, ghist);
+                FMM_LAUNCH(k_sel_init, S, 256, 0, st, l, P.count, sel_prefix, sel_rrem, sel_minr, ghist,
+                           sel_found);
                 for (int pass = 0; pass < 8; pass++)
                     FMM_LAUNCH(k_sel_hist, grid, kThreads, 0, st, l, pass, xa, ya, za, P.begin, P.count,
-                                                          P.axis, sel_prefix, sel_rrem, ghist, arrived);
+                                                          P.axis, sel_prefix, sel_rrem, ghist, arrived, sel_found);
                 FMM_LAUNCH(k_sel_count, grid, kThreads, 0, st, l, nch, xa, ya, za, P.begin, P.count, P.axis,
                                                        sel_prefix, chunk_lt, chunk_eq, sel_minr,
                                                        (const unsigned long long *)nullptr);
