@@ -727,7 +727,7 @@ def bench_galaxy(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)  # ~0.7 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["batch", "serve", "params", "galaxy_eta"])
     ap.add_argument("--prec", default=None, choices=["fp64", "mixed"])
