@@ -188,6 +188,7 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
     __shared__ unsigned s_rrem;
     __shared__ unsigned long long s_minr;
     __shared__ unsigned w_eq[kWarps], w_left[kWarps];
+    __shared__ bool s_one;
 
     const int s = blockIdx.x;
     const int64_t g = ((int64_t)1 << level) - 1 + s;
@@ -230,8 +231,22 @@ k_split_small(int level, const double *__restrict__ xin, const double *__restric
             if (prefix_match(kk, pre, shift)) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
         }
         __syncthreads();
-        if (w == 0) pick_digit(hist, shift, &s_prefix, &s_rrem);
+        if (w == 0) {
+            unsigned c = 0;
+            pick_digit(hist, shift, &s_prefix, &s_rrem, &c);
+            c = __reduce_max_sync(0xffffffffu, c);  // the picking lane's bucket count
+            if (lane == 0) s_one = c == 1u;
+        }
         __syncthreads();
+        if (s_one && pass < 7) {  // one key under the prefix: it is the wanted one
+            const uint64_t pre2 = s_prefix;
+            for (int i = tid; i < n; i += kThreads) {
+                const uint64_t kk = keys[i];
+                if ((kk >> shift) == (pre2 >> shift)) s_prefix = kk;
+            }
+            __syncthreads();
+            break;
+        }
     }
     const uint64_t v = thr ? (uint64_t)thr[s] : s_prefix;
     const unsigned need_eq = thr ? 0u : s_rrem + 1;  // equal keys that go left, in position order
