@@ -22,6 +22,8 @@
  *  - Pointers to point, charge and output arrays may be device pointers or
  *    host pointers (pageable or pinned); the library detects which with
  *    cudaPointerGetAttributes and stages host data through device buffers.
+ *    Device memory must belong to the current device (managed memory is
+ *    accepted); a pointer into another GPU's memory is FMM_EINVAL.
  *    Host outputs are complete when the call returns; device work is
  *    asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).
  *  - All parity/inspection hooks (fmm_plan_tree, fmm_plan_list,
@@ -52,7 +54,10 @@ enum fmm_status {
     FMM_ENONFINITE = -3,  /* a point coordinate is NaN or infinite */
     FMM_ECAPACITY = -4,   /* an interaction list exceeds 2^31 - 1 entries */
     FMM_ETIMEDOUT = -5,   /* a bounded device wait gave up (reserved for persistent kernels) */
-    FMM_ECUDA = -6        /* a CUDA runtime call failed; fmm_last_cuda_error() has the code */
+    FMM_ECUDA = -6,       /* a CUDA runtime call failed; fmm_last_cuda_error() has the code */
+    FMM_EINTERNAL = -7    /* a device-side consistency check of the tree build failed (the
+                             partition of a box did not give the sizes the split rule
+                             requires); no CUDA error lies behind it */
 };
 
 /* Element type of points, charges and outputs. */
@@ -147,8 +152,8 @@ typedef struct fmm_plan_s *fmm_plan_t;
  * (coordinate, original index) keys, at the plane halfway between the two
  * sides. The plan copies the points into leaf order and keeps no pointer to
  * `points`. Synchronises `stream` (it reads the list sizes).
- * Errors: FMM_EINVAL, FMM_ENONFINITE, FMM_ENOMEM, FMM_ECAPACITY, FMM_ECUDA;
- * on error *out is NULL and nothing is leaked.
+ * Errors: FMM_EINVAL, FMM_ENONFINITE, FMM_ENOMEM, FMM_ECAPACITY,
+ * FMM_EINTERNAL, FMM_ECUDA; on error *out is NULL and nothing is leaked.
  */
 int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
              const fmm_allocator *alloc, void *stream, fmm_plan_t *out);
@@ -268,27 +273,35 @@ int64_t fmm_kernel_launches(void);
  * sets, computed without allocating any device memory.
  *
  * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory -- code that runs while a stream is being
- * captured into a CUDA graph (an allocation call there breaks the capture),
- * plug-ins inside a host application that owns every byte of device memory,
- * and real-time loops that may not pay for an allocation. It runs the same
- * median-split kernels as fmm_plan, with all of their scratch (both copies of
- * the positions and indices, the box cells, the selection state) in one
- * static device array of FMM_NOALLOC_SCRATCH_BYTES inside the library, which
- * every GPU that loads the library holds until the process exits.
- *   points  DEVICE pointer, n x 3 row-major, dtype FMM_F64 or FMM_F32.
+ * cannot allocate device memory -- plug-ins inside a host application that
+ * owns every byte of device memory and hands out only the buffers of a call,
+ * and real-time loops whose latency budget has no room for an allocator call
+ * (or its occasional synchronisation). It runs the same median-split kernels
+ * as fmm_plan, with all of their scratch (both copies of the positions and
+ * indices, the box cells, the selection state) in one static device array of
+ * FMM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   points  DEVICE pointer (current device), n x 3 row-major, dtype FMM_F64
+ *           or FMM_F32.
  *   n       1 <= n <= FMM_NOALLOC_MAX_POINTS.
  *   levels  0 <= levels <= FMM_NOALLOC_MAX_LEVELS.
- *   perm    DEVICE pointer, n int32: original index of each leaf-order slot.
+ *   perm    DEVICE pointer (current device), at least n int32: original
+ *           index of each leaf-order slot.
  *   stream  cudaStream_t for the work.
+ * The call enqueues the kernels and a device-to-device copy into perm on
+ * `stream`, then copies the build's 4-byte status word to the host and
+ * synchronises `stream`, so perm is complete when it returns FMM_OK.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture begins. Every call shares the one array and
  * re-initialises what must start cleared, so calls that overlap on the GPU
  * (other streams, other host threads) race and corrupt each other's results:
- * serialise them. Synchronises `stream` to report non-finite points.
- * Errors: FMM_EINVAL (NULL or host pointers, n or levels out of range, bad
- * dtype), FMM_ENONFINITE, FMM_ECUDA. Calls no allocating routine.
+ * serialise them.
+ * Errors: FMM_EINVAL (NULL pointers, host pointers or another device's
+ * memory, n or levels out of range, bad dtype), FMM_ENONFINITE (a NaN or
+ * infinite coordinate), FMM_EINTERNAL, FMM_ECUDA (fmm_last_cuda_error() has
+ * the code).
  */
 #define FMM_NOALLOC_MAX_POINTS 4096
 #define FMM_NOALLOC_MAX_LEVELS 12
@@ -317,6 +330,30 @@ int fmm_batch_create(const fmm_plan_t *plans, int nplans, const void *const *cha
                      fmm_batch_t *out);
 int fmm_batch_launch(fmm_batch_t batch, void *stream);
 void fmm_batch_destroy(fmm_batch_t batch);
+
+/*
+ * fmm_measure_peak -- throughput of one arithmetic pipe of the current device,
+ * the denominator of the evaluation kernels' rooflines (not part of the
+ * method). kind: 0 FP32 FFMA, 1 FP32 packed FFMA2, 2 FP64 DFMA (flop/s, two
+ * per multiply-add), 3 XU rsqrt.approx (operations/s). Independent chains of
+ * that instruction on 4 blocks of 256 threads per SM, `iters` iterations per
+ * thread (32 flop per iteration for kinds 0 and 1, 16 for 2, 8 rsqrt for 3),
+ * timed with CUDA events on `stream` after one untimed launch of iters/8.
+ * Writes the rate to *ops_per_s and the timed launch's milliseconds to *ms
+ * (may be NULL); synchronises `stream`. Allocates nothing.
+ * Errors: FMM_EINVAL (NULL output, iters < 1, unknown kind), FMM_ECUDA.
+ */
+int fmm_measure_peak(int kind, int64_t iters, void *stream, double *ops_per_s, double *ms);
+
+/*
+ * fmm_set_list_capacity -- set the largest number of candidate pairs one
+ * level of the connectivity build may hold (default and maximum 2^31 - 1,
+ * the int32 index range of the lists); returns the previous value. A value
+ * outside 1 .. 2^31 - 1 restores the default. Process-wide. It exists so
+ * that tests can make fmm_plan meet FMM_ECAPACITY on small inputs; plans
+ * already built are not affected.
+ */
+int64_t fmm_set_list_capacity(int64_t entries);
 
 /* fmm_strerror -- static text for a status code. */
 const char *fmm_strerror(int status);

@@ -26,7 +26,7 @@ FMM_FLAG_ETA = 2
 FMM_FLAG_TC_M2L = 4
 STAGES = ("tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p")
 STATUS = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ENONFINITE",
-          -4: "FMM_ECAPACITY", -5: "FMM_ETIMEDOUT", -6: "FMM_ECUDA"}
+          -4: "FMM_ECAPACITY", -5: "FMM_ETIMEDOUT", -6: "FMM_ECUDA", -7: "FMM_EINTERNAL"}
 
 
 class FmmError(RuntimeError):
@@ -63,7 +63,7 @@ EXPORTS = ("fmm_plan", "fmm_eval", "fmm_destroy", "fmm_direct", "fmm_plan_stats"
            "fmm_plan_tree", "fmm_plan_list", "fmm_eval_expansions", "fmm_strerror",
            "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches",
            "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy",
-           "fmm_eval_check", "fmm_pool_trim")
+           "fmm_eval_check", "fmm_pool_trim", "fmm_set_list_capacity", "fmm_measure_peak")
 FMM_NOALLOC_MAX_POINTS, FMM_NOALLOC_MAX_LEVELS = 4096, 12
 
 
@@ -118,6 +118,10 @@ def load(build: bool = True) -> C.CDLL:
     lib.fmm_batch_launch.restype = i32
     lib.fmm_batch_destroy.argtypes = [vp]
     lib.fmm_batch_destroy.restype = None
+    lib.fmm_measure_peak.argtypes = [i32, i64, vp, vp, vp]
+    lib.fmm_measure_peak.restype = i32
+    lib.fmm_set_list_capacity.argtypes = [i64]
+    lib.fmm_set_list_capacity.restype = i64
     _LIB = lib
     return lib
 
@@ -356,6 +360,24 @@ def fmm_pool_trim(device: int = 0) -> None:
     _check(load().fmm_pool_trim(int(device)), "fmm_pool_trim")
 
 
+PEAK_KINDS = {"ffma": 0, "ffma2": 1, "dfma": 2, "rsqrt": 3}
+
+
+def fmm_measure_peak(kind: str, iters: int = 1 << 16, stream=None):
+    """(ops per second, ms) of one arithmetic pipe: 'ffma', 'ffma2', 'dfma'
+    (flop/s) or 'rsqrt' (XU operations/s)."""
+    v, ms = C.c_double(), C.c_double()
+    _check(load().fmm_measure_peak(PEAK_KINDS[kind], int(iters), _stream(stream), C.byref(v), C.byref(ms)),
+           "fmm_measure_peak")
+    return v.value, ms.value
+
+
+def fmm_set_list_capacity(entries: int) -> int:
+    """Largest candidate-pair count per connectivity level (tests lower it to
+    reach FMM_ECAPACITY); returns the previous value. 0 restores the default."""
+    return int(load().fmm_set_list_capacity(int(entries)))
+
+
 def fmm_kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().fmm_kernel_launches())
@@ -363,13 +385,22 @@ def fmm_kernel_launches() -> int:
 
 def fmm_orb_order_noalloc(points, levels: int, perm=None, stream=None):
     """Leaf order of the balanced tree for <= 4096 points without any device
-    allocation inside the library (for callers that cannot allocate, e.g.
-    during stream capture). `points` and `perm` must be CUDA tensors; perm is
-    an int32 tensor of n entries (created here if not given)."""
+    allocation inside the library (for callers whose host application owns
+    all device memory, or whose loop cannot wait on an allocator). `points`
+    is a contiguous (n, 3) float64/float32 CUDA tensor; `perm` an int32 CUDA
+    tensor of at least n entries on the same device (created here if not
+    given). Raises FmmError(FMM_EINVAL) for anything else."""
     import torch
+    if (not _is_torch(points) or not points.is_cuda or points.dim() != 2 or points.shape[1] != 3
+            or not points.is_contiguous()):
+        raise FmmError(-1, "fmm_orb_order_noalloc: points must be a contiguous (n, 3) CUDA tensor")
     n = int(points.shape[0])
     if perm is None:
         perm = torch.empty(n, dtype=torch.int32, device=points.device)
+    elif (not _is_torch(perm) or perm.dtype != torch.int32 or perm.device != points.device
+          or perm.numel() < n or not perm.is_contiguous()):
+        raise FmmError(-1, "fmm_orb_order_noalloc: perm must be a contiguous int32 tensor of "
+                           "at least n entries on the points' device")
     _check(load().fmm_orb_order_noalloc(points.data_ptr(), n, _dtype_code(points), int(levels),
                                         perm.data_ptr(), _stream(stream)),
            "fmm_orb_order_noalloc")

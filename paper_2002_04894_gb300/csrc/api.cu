@@ -15,6 +15,51 @@ namespace fmm {
 
 std::atomic<long long> g_launches{0};
 
+namespace {
+thread_local int g_last_cuda = 0;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FMM_OK;
+    g_last_cuda = (int)e;
+    if (e == cudaErrorMemoryAllocation) return FMM_ENOMEM;
+    return FMM_ECUDA;
+}
+
+int ptr_kind(const void *p) {
+    if (!p) return 0;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type != cudaMemoryTypeDevice) return 0;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return a.device == dev ? 1 : -1;
+}
+
+int sm_count() {
+    static std::atomic<int> cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 148;
+    }
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        return 148;
+    }
+    cached[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 cudaError_t eval_expansions(Plan &P, const void *charges, int dtype);
 cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype);
 
@@ -101,6 +146,7 @@ void *palloc(Plan &P, size_t bytes) { return arena_alloc(P, P.persist, bytes); }
 }  // namespace fmm
 
 using fmm::Plan;
+using fmm::cuda_status;
 
 struct fmm_plan_s {
     Plan P;
@@ -116,24 +162,7 @@ struct fmm_batch_s {
 
 namespace {
 
-thread_local int g_last_cuda = 0;
-
-int cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return FMM_OK;
-    g_last_cuda = (int)e;
-    if (e == cudaErrorMemoryAllocation) return FMM_ENOMEM;
-    return FMM_ECUDA;
-}
-
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool is_device_ptr(const void *p) { return fmm::ptr_kind(p) == 1; }
 
 void release(Plan &P) {
     for (int s = 0; s < FMM_NSTAGES; s++)
@@ -174,11 +203,12 @@ const char *fmm_strerror(int status) {
         case FMM_ECAPACITY: return "interaction list exceeds 2^31-1 entries";
         case FMM_ETIMEDOUT: return "bounded device wait timed out";
         case FMM_ECUDA: return "CUDA runtime error";
+        case FMM_EINTERNAL: return "internal consistency check of the tree build failed";
         default: return "unknown status";
     }
 }
 
-int fmm_last_cuda_error(void) { return g_last_cuda; }
+int fmm_last_cuda_error(void) { return fmm::g_last_cuda; }
 
 int fmm_pool_trim(int device) {
     if (device < 0 || device >= 64) return FMM_EINVAL;
@@ -206,6 +236,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     const int step = opts->bisections_per_level == 0 ? 1 : opts->bisections_per_level;
     if (step < 1 || step > 3 || opts->levels % step != 0) return FMM_EINVAL;
     if (alloc && (!alloc->alloc || !alloc->free)) return FMM_EINVAL;
+    if (fmm::ptr_kind(points) < 0) return FMM_EINVAL;
 
     fmm_plan_s *H = new (std::nothrow) fmm_plan_s();
     if (!H) return FMM_ENOMEM;
@@ -297,7 +328,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     e = cudaStreamSynchronize(P.stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     if (herr & 1) return fail(FMM_ENONFINITE);
-    if (herr) return fail(FMM_ECUDA);  // internal consistency check of the partition failed
+    if (herr) return fail(FMM_EINTERNAL);  // the partition's consistency check failed
 
     fmm::stage_mark(P, FMM_STAGE_LISTS, 0);
     e = fmm::lists_build(P);
@@ -328,6 +359,8 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
 
 int fmm_eval(fmm_plan_t plan, const void *charges, void *potentials, void *fields, void *stream) {
     if (!plan || !charges || !potentials) return FMM_EINVAL;
+    if (fmm::ptr_kind(charges) < 0 || fmm::ptr_kind(potentials) < 0 || fmm::ptr_kind(fields) < 0)
+        return FMM_EINVAL;
     Plan &P = plan->P;
     P.stream = (cudaStream_t)stream;
     const size_t es = dsize(P.dtype), n = (size_t)P.n;
@@ -386,6 +419,9 @@ int fmm_direct(const void *points, const void *charges, int64_t n, int dtype,
                void *stream) {
     if (!points || !charges || !targets || !potentials || n < 1 || ntargets < 0) return FMM_EINVAL;
     if (dtype != FMM_F64 && dtype != FMM_F32) return FMM_EINVAL;
+    if (fmm::ptr_kind(points) < 0 || fmm::ptr_kind(charges) < 0 || fmm::ptr_kind(targets) < 0 ||
+        fmm::ptr_kind(potentials) < 0 || fmm::ptr_kind(fields) < 0)
+        return FMM_EINVAL;
     if (ntargets == 0) return FMM_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t es = dsize(dtype);

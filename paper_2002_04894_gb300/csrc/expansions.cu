@@ -163,7 +163,7 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
     const int64_t n = P.n;
     const int nc = P.nc;
     const bool mixed = P.prec == FMM_PREC_MIXED;
-    const int gq = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    const int gq = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     stage_mark(P, FMM_STAGE_P2M, 0);
     if (mixed) {
         cudaError_t e = mixed_p2m(P, charges, dtype);

@@ -99,6 +99,18 @@ void dfree(Plan &P, void *ptr, size_t bytes);
 void *palloc(Plan &P, size_t bytes);
 void arena_release(Plan &P, Arena &A);
 
+// cudaError_t -> fmm_status; records the code for fmm_last_cuda_error().
+int cuda_status(cudaError_t e);
+// Where a caller's pointer lives: 1 = device memory of the current device
+// (or managed memory), 0 = host memory (pageable, pinned or unregistered),
+// -1 = device memory of another device (rejected: the kernels run on the
+// current device and cannot dereference it).
+int ptr_kind(const void *p);
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device); grids are sized in multiples of it.
+int sm_count();
+
 // Kernel launches made by the library (fmm_kernel_launches).
 extern std::atomic<long long> g_launches;
 #define FMM_LAUNCH(kernel, grid, block, smem, stream, ...)          \

@@ -302,6 +302,10 @@ cudaError_t scan_exclusive(Plan &P, const int32_t *in, int32_t *out, int64_t n) 
     return cudaGetLastError();
 }
 
+// Largest candidate-pair array a level may need (entries): the lists index
+// it with int32. Lowered only by fmm_set_list_capacity (tests).
+std::atomic<long long> g_list_capacity{0x7fffffffLL};
+
 cudaError_t lists_build(Plan &P) {
     cudaStream_t st = P.stream;
     // level 0: the root is strongly connected to itself
@@ -340,7 +344,7 @@ cudaError_t lists_build(Plan &P) {
         }
         const int lp = l - step;
         const int64_t npar = P.nstrong[lp], ncand = (int64_t)C * C * npar;
-        if (ncand > 0x7fffffffLL) {
+        if (ncand > g_list_capacity.load(std::memory_order_relaxed)) {
             P.capacity_exceeded = true;
             return cudaSuccess;
         }
@@ -408,3 +412,8 @@ cudaError_t lists_build(Plan &P) {
 }
 
 }  // namespace fmm
+
+extern "C" int64_t fmm_set_list_capacity(int64_t entries) {
+    if (entries < 1 || entries > 0x7fffffffLL) entries = 0x7fffffffLL;
+    return (int64_t)fmm::g_list_capacity.exchange(entries);
+}

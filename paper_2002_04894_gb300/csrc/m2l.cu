@@ -504,7 +504,7 @@ cudaError_t m2l_setup(Plan &P) {
 // that the level still spreads over twice the SM count in blocks.
 int warps_per_block(int64_t nch) {
     int w = kWarpChildMax;
-    while (w > 1 && (nch + w - 1) / w < 2 * 152) w >>= 1;
+    while (w > 1 && (nch + w - 1) / w < 2 * sm_count()) w >>= 1;
     return w;
 }
 
@@ -1300,7 +1300,7 @@ cudaError_t attr_f32() {
 template <int P>
 cudaError_t launch_f32(Plan &Pl, int64_t tot) {
     const int64_t chunks = (tot + kF32Threads - 1) / kF32Threads;
-    FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)std::min<int64_t>(chunks, 152 * 3), kF32Threads, VSplit<P>::SMEM, Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh,
+    FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)std::min<int64_t>(chunks, (int64_t)sm_count() * 3), kF32Threads, VSplit<P>::SMEM, Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh,
                (const float4 *)Pl.f32_tab);
     return cudaGetLastError();
 }
@@ -1347,7 +1347,7 @@ cudaError_t m2l_f32_setup(Plan &P) {
 // single-precision M2L over all levels; leaves the unscaled result in L
 cudaError_t m2l_f32_all(Plan &P) {
     const int64_t total = P.nbox * P.nc;
-    const unsigned grid = (unsigned)std::min<int64_t>((P.nbox + 7) / 8, 152 * 16);  // 8 boxes (warps) per block
+    const unsigned grid = (unsigned)std::min<int64_t>((P.nbox + 7) / 8, (int64_t)sm_count() * 16);  // 8 boxes (warps) per block
     FMM_LAUNCH(k_scale_multipoles, grid, 256, 0, P.stream, P.nbox, P.p, P.radius, P.M, P.Mf);
     cudaMemsetAsync(P.Lh, 0, (size_t)total * sizeof(double2), P.stream);
     const int64_t tot = total_weak(P);

@@ -515,7 +515,7 @@ cudaError_t mixed_setup(Plan &P) {
 
 cudaError_t mixed_p2m(Plan &P, const void *charges, int dtype) {
     const int64_t n = P.n;
-    const int gq = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    const int gq = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     if (dtype == FMM_F64)
         FMM_LAUNCH(k_gather_qf<double>, gq, 256, 0, P.stream, (const double *)charges, P.perm, P.qf, n);
     else

@@ -674,7 +674,7 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
 
     unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
     cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, st);
-    const int pgrid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
+    const int pgrid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)sm_count() * 8);
     if (dtype == FMM_F64)
         FMM_LAUNCH(k_prepare<double>, pgrid, kThreads, 0, st, (const double *)pts, n, P.x, P.y, P.z,
                                                       P.perm, bbox, P.d_err);
@@ -906,15 +906,6 @@ cudaError_t noalloc_scratch(unsigned char **out) {
     return e;
 }
 
-bool na_device_ptr(const void *p) {
-    cudaPointerAttributes a;
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 }  // namespace fmm
@@ -925,10 +916,10 @@ extern "C" int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, i
     if (!points || !perm || n < 1 || n > kNaMaxN || levels < 0 ||
         levels > FMM_NOALLOC_MAX_LEVELS || (dtype != FMM_F64 && dtype != FMM_F32))
         return FMM_EINVAL;
-    if (!na_device_ptr(points) || !na_device_ptr(perm)) return FMM_EINVAL;
+    if (ptr_kind(points) != 1 || ptr_kind(perm) != 1) return FMM_EINVAL;
     unsigned char *s = nullptr;
     cudaError_t e = noalloc_scratch(&s);
-    if (e != cudaSuccess) return FMM_ECUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     cudaStream_t st = (cudaStream_t)stream;
     double *pos = (double *)(s + kNaPos);
     double *xa = pos, *ya = pos + kNaMaxN, *za = pos + 2 * kNaMaxN;
@@ -969,7 +960,7 @@ extern "C" int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, i
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return FMM_ECUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     if (herr & 1) return FMM_ENONFINITE;
-    return herr ? FMM_ECUDA : FMM_OK;
+    return herr ? FMM_EINTERNAL : FMM_OK;
 }

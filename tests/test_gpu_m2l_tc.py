@@ -3,19 +3,35 @@ rotation form as tcgen05 TF32 products, three per contraction) against the
 FP64 oracle and against the default single-precision CUDA-core kernel on the
 same plan.
 
-Tolerances: the local expansions and results within 1e-5 of the oracle's
-FMM (as for the whole mixed form); tensor-core vs CUDA-core locals within
-2e-6 of their scale: both are single-precision evaluations of the same
-products, ~3e-7 per product for the split TF32 against 6e-8 for FP32,
-grown by the five chained contractions."""
+Tolerances: against the oracle's FMM every case is held element by element
+(parity.py: relative L2, worst target, worst box after scaling every degree
+to the box's size) to twice the value measured for it on a GB300, rounded up
+to one significant digit (DEFAULT for a case not yet measured); tensor-core
+vs CUDA-core locals within 2e-6 of their scale: both are single-precision
+evaluations of the same products, ~3e-7 per product for the split TF32
+against 6e-8 for FP32, grown by the five chained contractions."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
+import parity
 from paper_2002_04894_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+DEFAULT = {"l2_phi": 1e-5, "l2_field": 1e-5, "point_phi": 1e-2, "point_field": 1e-2, "box_L": 1e-2}
+MEASURED = {
+    "tc/gmm/9000/9/10/0.6": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 9e-07, "box_L": 0.0002},
+    "tc/plummer/12000/8/12/0.5": {"l2_phi": 5e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 1e-06, "box_L": 5e-05},
+    "tc/plummer/6000/9/5/0.5": {"l2_phi": 4e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 1e-06, "box_L": 7e-06},
+    "tc/shell/4000/9/11/0.5": {"l2_phi": 3e-07, "l2_field": 2e-07, "point_phi": 7e-06, "point_field": 8e-07, "box_L": 6e-05},
+    "tc/uniform/2000/8/1/0.4": {"l2_phi": 4e-07, "l2_field": 9e-08, "point_phi": 2e-05, "point_field": 5e-07, "box_L": 7e-06},
+    "tc/uniform/20000/8/8/0.5": {"l2_phi": 4e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 3e-06, "box_L": 2e-05},
+    "tc/uniform/700/5/12/0.7": {"l2_phi": 2e-07, "l2_field": 2e-07, "point_phi": 4e-06, "point_field": 8e-07, "box_L": 2e-05},
+}
+# p -> bounds of the tensor-core vs CUDA-core comparison (2 x measured, rounded up)
+VS_SIMT = {4: (4e-6, 1e-5), 6: (2e-5, 2e-5), 8: (3e-5, 2e-6), 10: (9e-5, 2e-5), 12: (3e-4, 2e-5)}
 
 
 def rel(a, b):
@@ -46,9 +62,14 @@ def test_tc_m2l_matches_oracle(gpu_lib, kind, n, levels, p, theta):
     op, oE = T.eval(q)
     gL, oL = fmm.fmm_eval_expansions(plan, "L"), T.expansions("L")
     assert fmm.fmm_plan_stats(plan)["weak_pairs"] > 0
-    assert np.abs(gL - oL).max() <= 1e-5 * np.abs(oL).max()
-    assert rel(pot.cpu().numpy(), op) <= 1e-5
-    assert rel(fld.cpu().numpy(), oE) <= 1e-5
+    g, e = pot.cpu().numpy(), fld.cpu().numpy()
+    tid = f"tc/{kind}/{n}/{levels}/{p}/{theta}"
+    tol = {**DEFAULT, **MEASURED.get(tid, {})}
+    got = {"l2_phi": rel(g, op), "l2_field": rel(e, oE),
+           "point_phi": parity.pointwise_phi(g, op), "point_field": parity.pointwise_field(e, oE),
+           "box_L": parity.box_degree(gL, oL, T.tree()["radius"], p, "L")}
+    for k, v in got.items():
+        parity.check(tid, k, v, tol[k])
 
 
 @pytest.mark.parametrize("p", [4, 6, 8, 10, 12])
@@ -66,6 +87,10 @@ def test_tc_m2l_matches_cuda_core_kernel(gpu_lib, p):
     La, Lb = fmm.fmm_eval_expansions(a, "L"), fmm.fmm_eval_expansions(b, "L")
     assert np.abs(La - Lb).max() <= 2e-6 * np.abs(Lb).max()
     assert rel(pa.cpu().numpy(), pb.cpu().numpy()) <= 2e-6
+    radius = fmm.fmm_plan_tree(b)["radius"]
+    parity.check(f"tc_vs_simt/{p}", "box_L", parity.box_degree(La, Lb, radius, p, "L"), VS_SIMT[p][0])
+    parity.check(f"tc_vs_simt/{p}", "point_phi", parity.pointwise_phi(pa.cpu().numpy(), pb.cpu().numpy()),
+                 VS_SIMT[p][1])
 
 
 def test_tc_m2l_benchmark_accuracy(gpu_lib):
@@ -81,5 +106,6 @@ def test_tc_m2l_benchmark_accuracy(gpu_lib):
     fmm.fmm_eval_check(plan)
     t = inputs.sample_targets(n, 500, 2)
     dp, dE = oracle.direct(x, q, targets=t)
-    assert rel(pot.cpu().numpy()[t], dp) <= 1e-6
-    assert rel(fld.cpu().numpy()[t], dE) <= 1e-6
+    parity.check("tc_vs_direct", "l2_phi", rel(pot.cpu().numpy()[t], dp), 8e-7)
+    parity.check("tc_vs_direct", "l2_field", rel(fld.cpu().numpy()[t], dE), 3e-7)
+    parity.check("tc_vs_direct", "point_phi", parity.pointwise_phi(pot.cpu().numpy()[t], dp), 2e-5)
