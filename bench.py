@@ -1,21 +1,25 @@
 """Benchmark: Mpoints/s of one balanced-tree FMM solve (fmm_plan + fmm_eval).
 
-Default workload (N=1): 2,000,000 points from a Plummer sphere (scale radius
-0.1, truncated at 10 radii), charges uniform in [-1, 1], 14 binary levels
-(~122 points per leaf), theta = 0.5, expansion order p = 12 -- the smallest
-order that meets the 1e-6 potential error against the FP64 direct sum --
-in the mixed-precision form (float P2M/M2L/L2P/P2P, double geometry, lists,
-M2M and L2L). The plain FP64 form is timed on the same inputs beside it.
-A step is one whole solve: tree, lists, P2M, M2M, M2L, L2L, L2P, P2P. Inputs
-are resident on the device when a step starts; the L2 cache is flushed
-between steps (a 512 MB write, outside the timed events).
+Default workload (N=1), the mixed-precision configuration as stated:
+8,000,000 points from a 16-component Gaussian mixture (sigma log-uniform in
+[1e-3, 1e-1], centres uniform in the unit cube), positions float32, charges
++-1, theta = 0.5, expansion order p = 12, 17 binary levels (~61 points per
+leaf, inside the 50-200 points-per-leaf range the parameter study favours)
+and box geometry from the points (each box's centre and radius from its own
+points' bounding box, FMM_FLAG_TIGHT); float P2M/M2L/L2P/P2P with double
+geometry, lists, M2M and L2L. A step is one whole solve: tree, lists, P2M,
+M2M, M2L, L2L, L2P, P2P. Inputs are resident on the device when a step
+starts; the L2 cache is flushed between steps (a 512 MB write, outside the
+timed events).
 
 Reported beside the throughput: fmm_eval-only throughput, relative L2 error
 of potential and field against the FP64 direct sum on 1000 sampled targets
 (GPU fmm_direct; cross-checked with the CPU oracle's direct sum on rank 0),
 per-stage device times, the end-to-end number through host buffers, the
-roofline of the dominant kernel, SM clocks sampled during the timed region,
-and the CPU oracle timed on a bounded sample of the same workload.
+rooflines of the near field (dominant) and of the M2L against arithmetic-pipe
+peaks measured in the same run (fmm_measure_peak), SM clocks sampled during
+the timed region, the plain FP64 form on the same inputs, and the CPU oracle
+timed on a bounded sample of the same workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--prec fp64|mixed] [--impl ours|reference]
@@ -41,25 +45,40 @@ sys.path.insert(0, ROOT)
 from paper_2002_04894_gb300 import inputs  # noqa: E402
 
 WORKLOADS = {
-    # name: (distribution, N, levels, p, theta, point dtype, charges, precision)
-    # 2M Plummer points: p = 12 is the smallest order whose potential error
-    # against the FP64 direct sum is below 1e-6 (p = 10 gives 3.5e-6).
-    "plummer2m_l14_p12": ("plummer", 2_000_000, 14, 12, 0.5, "f64", "uniform", "mixed"),
-    "plummer2m_l14_p10_fp64": ("plummer", 2_000_000, 14, 10, 0.5, "f64", "uniform", "fp64"),
-    "uniform20k_l8_p8": ("uniform", 20_000, 8, 8, 0.5, "f64", "uniform", "fp64"),
-    "gmm8m_l16_p12": ("gmm", 8_000_000, 16, 12, 0.5, "f32", "pm1", "mixed"),
+    # name: (distribution, N, levels, p, theta, point dtype, charges, precision, tight geometry)
+    # the mixed-precision configuration (8M Gaussian-mixture points, float32
+    # positions, charges +-1, p = 12, theta = 0.5); levels from the
+    # points-per-leaf rule, box geometry from the points
+    "gmm8m_l17_p12": ("gmm", 8_000_000, 17, 12, 0.5, "f32", "pm1", "mixed", True),
+    # the same with cell geometry and 16 levels (~122 points per leaf)
+    "gmm8m_l16_p12_cells": ("gmm", 8_000_000, 16, 12, 0.5, "f32", "pm1", "mixed", False),
+    # 2M Plummer points at scale, raised to p = 12, the smallest order whose
+    # potential error against the FP64 direct sum is below 1e-6 (p = 10 gives
+    # 3.5e-6), mixed form; and the configuration as stated (plain FP64, p = 10)
+    "plummer2m_l14_p12": ("plummer", 2_000_000, 14, 12, 0.5, "f64", "uniform", "mixed", False),
+    "plummer2m_l14_p12_tight": ("plummer", 2_000_000, 14, 12, 0.5, "f64", "uniform", "mixed", True),
+    "plummer2m_l14_p10_fp64": ("plummer", 2_000_000, 14, 10, 0.5, "f64", "uniform", "fp64", False),
+    # the small uniform configuration (8 levels: ~78 points per leaf)
+    "uniform20k_l8_p8": ("uniform", 20_000, 8, 8, 0.5, "f64", "uniform", "fp64", False),
 }
-DEFAULT = "plummer2m_l14_p12"
+DEFAULT = "gmm8m_l17_p12"
 METRIC = "Mpoints/s per FMM solve (plan+eval) at rel err <= 1e-6 vs FP64 direct"
 FLOPS_PER_INTERACTION = 20   # P2P convention (N-body): 20 flops per pair
-SM_COUNT = 152
-FP32_FLOPS_PER_CLK_SM = 256  # 128 FP32 lanes x FMA
-FP64_FLOPS_PER_CLK_SM = 4    # GB300 nominal 1.25 TFLOP/s FP64 at 2.07 GHz / 152 SMs
 
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture
-# (profiles/k_p2p_f32_plummer2m_l14_p12.md), valid only while the kernel's
-# source is the one that was captured (checked by hash; otherwise null).
+def m2l_flops_per_pair(p):
+    """Algorithmic flops of one rotational M2L (real-source form): four folds
+    by the fixed d^n(pi/2) matrices, each (n+1)^2 multiply-adds per degree n
+    (the parity of n+k+m selects the real or imaginary part, so a fold of
+    degree n is n+1 outputs of n+1 terms), and the axial translation,
+    2 (p+1-l)^2 multiply-adds per order l; 2 flop per multiply-add:
+    12 * sum_{n<=p} (n+1)^2 (9,828 at p = 12)."""
+    return 12 * sum((n + 1) ** 2 for n in range(p + 1))
+
+
+# DRAM bytes per launch of a kernel from one ncu capture of the named
+# workload, valid only while the kernel's source is the one that was captured
+# (checked by hash; otherwise null).
 MEASURED_TRAFFIC = {
     ("plummer2m_l14_p12", "k_p2p_f32"): {"bytes": 274585600 + 123338496,
                                          "source": "paper_2002_04894_gb300/csrc/mixed.cu",
@@ -163,7 +182,7 @@ def dist_env():
 
 
 def make_inputs(name, seed):
-    dist, n, levels, p, theta, pdt, ch, _ = WORKLOADS[name]
+    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name][:7]
     x = inputs.points(dist, n, seed)
     q = inputs.charges_uniform(n, seed) if ch == "uniform" else inputs.charges_pm1(n, seed)
     if pdt == "f32":
@@ -174,7 +193,7 @@ def make_inputs(name, seed):
 def cpu_sample_config(name):
     """The bounded CPU sample of a workload: same distribution, charges, p and
     theta; N reduced and levels lowered so that points per leaf stay equal."""
-    dist, n, levels, p, theta, pdt, ch, _ = WORKLOADS[name]
+    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name][:7]
     ns = min(n, 1 << 17)
     ls = max(0, levels - int(round(np.log2(n / ns))))
     return dist, ns, ls, p, theta, ch
@@ -186,7 +205,7 @@ def run_oracle_sample(name, seed=0):
     x = inputs.points(dist, ns, seed)
     q = inputs.charges_uniform(ns, seed) if ch == "uniform" else inputs.charges_pm1(ns, seed)
     t0 = time.perf_counter()
-    T = oracle.Tree(x, ls, p, theta)
+    T = oracle.Tree(x, ls, p, theta, tight=WORKLOADS[name][8])
     T.eval(q)
     dt = time.perf_counter() - t0
     return ns, ls, dt, oracle.num_threads()
@@ -205,8 +224,10 @@ def bench_reference(args, rank, world):
         times.append(dt)
     ms = 1e3 * sum(times) / len(times)
     val = ns / (ms / 1e3) / 1e6
-    dist, n, levels, p, theta, pdt, ch, _ = WORKLOADS[name]
-    sample = f"{dist} N={ns} levels={ls} p={p} theta={theta} (same points/leaf as N={n}, {levels} levels)"
+    dist, n, levels, p, theta, pdt, ch = WORKLOADS[name][:7]
+    geo = "tight" if WORKLOADS[name][8] else "cell"
+    sample = (f"{dist} N={ns} levels={ls} p={p} theta={theta} {geo} boxes "
+              f"(same points/leaf as N={n}, {levels} levels)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(val, 6),
         "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -232,6 +253,7 @@ def bench_ours(args, rank, world, local):
     args.prec = args.prec or WORKLOADS[args.workload][7]
     prec = fmm.FMM_PREC_MIXED if args.prec == "mixed" else fmm.FMM_PREC_FP64
     x, q, levels, p, theta = make_inputs(args.workload, seed=rank)
+    tight = WORKLOADS[args.workload][8]
     n = x.shape[0]
     xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
     pot = torch.empty(n, dtype=qd.dtype, device="cuda")
@@ -240,10 +262,13 @@ def bench_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
 
     def solve():
-        plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True)
+        plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True, tight=tight)
         fmm.fmm_eval(plan, qd, pot, fld)
         return plan
 
+    # arithmetic-pipe peaks of this GPU, measured now (the rooflines' denominators)
+    pk = {k: fmm.fmm_measure_peak(k, it)[0] for k, it in
+          (("ffma", 1 << 19), ("ffma2", 1 << 18), ("dfma", 1 << 14), ("rsqrt", 1 << 17))}
     for _ in range(args.warmup):
         fmm.fmm_destroy(solve())
     torch.cuda.synchronize()
@@ -260,7 +285,7 @@ def bench_ours(args, rank, world, local):
             flush.zero_()
             e0, e1, e2 = ev[k]
             e0.record(stream)
-            plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True)
+            plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True, tight=tight)
             e1.record(stream)
             fmm.fmm_eval(plan, qd, pot, fld)
             e2.record(stream)
@@ -292,11 +317,11 @@ def bench_ours(args, rank, world, local):
     poth = torch.empty(n, dtype=qh.dtype).pin_memory()
     fldh = torch.empty((n, 3), dtype=qh.dtype).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
-    fmm.fmm_destroy(fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None))
+    fmm.fmm_destroy(fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None, tight=tight))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        plan = fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None)
+        plan = fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None, tight=tight)
         fmm.fmm_eval(plan, qh, poth, fldh)
         fmm.fmm_destroy(plan)
     torch.cuda.synchronize()
@@ -308,13 +333,13 @@ def bench_ours(args, rank, world, local):
     if args.fp64_steps > 0 and prec != fmm.FMM_PREC_FP64:
         pot64 = torch.empty_like(pot)
         fld64 = torch.empty_like(fld)
-        fmm.fmm_destroy(fmm.fmm_plan(xd, levels, p, theta, prec=fmm.FMM_PREC_FP64))
+        fmm.fmm_destroy(fmm.fmm_plan(xd, levels, p, theta, prec=fmm.FMM_PREC_FP64, tight=tight))
         times = []
         for _ in range(args.fp64_steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            pl = fmm.fmm_plan(xd, levels, p, theta, prec=fmm.FMM_PREC_FP64)
+            pl = fmm.fmm_plan(xd, levels, p, theta, prec=fmm.FMM_PREC_FP64, tight=tight)
             fmm.fmm_eval(pl, qd, pot64, fld64)
             b.record(stream)
             torch.cuda.synchronize()
@@ -328,13 +353,14 @@ def bench_ours(args, rank, world, local):
 
     if rank != 0:
         return
-    peaks = measured_peaks()
     clocks = clk.summary()
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp = FP64_FLOPS_PER_CLK_SM if prec == fmm.FMM_PREC_FP64 else FP32_FLOPS_PER_CLK_SM
-    peak_tflops = SM_COUNT * fp * max_mhz * 1e6 / 1e12
+    fp32_peak = max(pk["ffma"], pk["ffma2"]) / 1e12
+    peak_tflops = fp32_peak if prec == fmm.FMM_PREC_MIXED else pk["dfma"] / 1e12
     p2p_flops = FLOPS_PER_INTERACTION * stats["p2p_interactions"]
     achieved = p2p_flops / (stage_ms["p2p"] * 1e-3) / 1e12
+    m2l_flops = m2l_flops_per_pair(p) * stats["weak_pairs"]
+    m2l_achieved = m2l_flops / (stage_ms["m2l"] * 1e-3) / 1e12
+    kname = "k_p2p_f32" if prec == fmm.FMM_PREC_MIXED else "k_p2p_f64"
     value = replica_throughput(n, world, t_solve)
     out = {
         "metric": METRIC,
@@ -345,6 +371,8 @@ def bench_ours(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "levels": levels, "p": p, "theta": theta,
                    "prec": args.prec, "points": WORKLOADS[args.workload][0],
+                   "positions": WORKLOADS[args.workload][5], "charges": WORKLOADS[args.workload][6],
+                   "box_geometry": "tight (points' bounding box)" if tight else "cell",
                    "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "eval_only": {"value": round(replica_throughput(n, world, t_eval), 4), "unit": "Mpoints/s",
@@ -354,15 +382,23 @@ def bench_ours(args, rank, world, local):
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "work": {"p2p_interactions": stats["p2p_interactions"], "weak_pairs": stats["weak_pairs"],
                  "strong_leaf_pairs": stats["strong_leaf_pairs"]},
-        "roofline": {"kernel": "k_p2p_f32" if prec == fmm.FMM_PREC_MIXED else "k_p2p_f64",
-                     "bound": "alu", "achieved": round(achieved, 4),
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": round(achieved, 4),
                      "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
                      "frac": round(achieved / peak_tflops, 4),
-                     "traffic": measured_traffic(args.workload,
-                                                 "k_p2p_f32" if prec == fmm.FMM_PREC_MIXED else "k_p2p_f64"),
-                     "peak_basis": (f"{SM_COUNT} SMs x {fp} flop/clk x {max_mhz:.0f} MHz "
-                                    f"({'FP64' if fp == FP64_FLOPS_PER_CLK_SM else 'FP32'} pipe)"),
-                     "flops_basis": f"{FLOPS_PER_INTERACTION} flop per pair x exact pair count"},
+                     "traffic": measured_traffic(args.workload, kname),
+                     "peak_basis": ("measured in this run: fmm_measure_peak "
+                                    + ("max(FFMA, FFMA2) FP32 pipe" if prec == fmm.FMM_PREC_MIXED
+                                       else "DFMA FP64 pipe")),
+                     "flops_basis": f"{FLOPS_PER_INTERACTION} flop per pair x exact pair count",
+                     "time_basis": "stage CUDA events on the plan's stream, mean over the timed steps"},
+        "roofline_m2l": {"kernel": "k_m2l_rot_f32" if prec == fmm.FMM_PREC_MIXED else "k_m2l_rot_f64",
+                         "bound": "alu", "achieved": round(m2l_achieved, 4), "peak": round(peak_tflops, 3),
+                         "unit": "TFLOP/s", "frac": round(m2l_achieved / peak_tflops, 4),
+                         "flops_basis": f"{m2l_flops_per_pair(p)} flop per weak pair (12 sum (n+1)^2, "
+                                        f"rotation form) x {stats['weak_pairs']} pairs"},
+        "peaks_measured": {"ffma_tflops": round(pk["ffma"] / 1e12, 3), "ffma2_tflops": round(pk["ffma2"] / 1e12, 3),
+                           "dfma_tflops": round(pk["dfma"] / 1e12, 4), "rsqrt_gops": round(pk["rsqrt"] / 1e9, 1),
+                           "hbm_gbs": measured_peaks().get("hbm_gbs")},
         "e2e": {"value": round(world * n / (t_e2e * 1e-3) / 1e6, 4), "unit": "Mpoints/s",
                 "h2d_bytes_per_step": int(n * 3 * es + n * es),
                 "d2h_bytes_per_step": int(n * es + 3 * n * es)},
@@ -376,7 +412,8 @@ def bench_ours(args, rank, world, local):
         dist, _, _, pp, th, ch = cpu_sample_config(args.workload)
         out["cpu_baseline"] = {"value": round(ns / dt / 1e6, 6), "unit": "Mpoints/s", "cores": cores,
                                "kind": "oracle",
-                               "sample": f"{dist} N={ns} levels={ls} p={pp} theta={th}, tree+lists+eval"}
+                               "sample": f"{dist} N={ns} levels={ls} p={pp} theta={th} "
+                                         f"{'tight' if tight else 'cell'} boxes, tree+lists+eval"}
         import oracle
         op = oracle.direct(x.astype(np.float64), q.astype(np.float64), targets=tgt, field=False)
         out["accuracy"]["rel_l2_phi_vs_oracle_direct"] = float(np.linalg.norm(gp - op) / np.linalg.norm(op))
@@ -731,7 +768,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["batch", "serve", "params", "galaxy_eta"])
     ap.add_argument("--prec", default=None, choices=["fp64", "mixed"])
-    ap.add_argument("--fp64-steps", type=int, default=1,
+    ap.add_argument("--fp64-steps", type=int, default=3,
                     help="steps of the plain FP64 form timed as the comparator (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -78,6 +78,13 @@ enum fmm_prec { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
 /* fmm_opts.flags bits */
 #define FMM_FLAG_PROFILE 1  /* record per-stage device times (fmm_stage_times) */
 #define FMM_FLAG_ETA 2      /* use fmm_opts.eta; without it eta = 1 (median splits) */
+#define FMM_FLAG_TIGHT 8    /* box geometry from the points: the expansion centre and
+                               radius of a box are the midpoint and half diagonal of
+                               the bounding box of its own points (radius at least
+                               2^-10 of the cell's; an empty box keeps its cell
+                               midpoint) instead of its cell's. The cells still decide
+                               the splits (fmm_plan_tree's lo/hi stay the cells).
+                               Clustered inputs then get far fewer near-field pairs. */
 #define FMM_FLAG_TC_M2L 4   /* mixed form, p <= 12: M2L contractions on the tensor
                                cores (tcgen05, split TF32) instead of the CUDA cores;
                                same accuracy, slower at the orders measured (the

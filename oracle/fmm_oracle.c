@@ -34,7 +34,11 @@
  *    eta*s + (1-eta)*midpoint and the left child takes the points strictly
  *    below it (Sec. 2.1.2's adaptivity parameter);
  *  - root cell = tight bounding box; box centre = cell midpoint; radius =
- *    half the cell diagonal;
+ *    half the cell diagonal (the default), or, with `tight` set, the
+ *    midpoint and half diagonal of the bounding box of the box's own points,
+ *    the radius never below 2^-10 of the cell's (a box of one point keeps a
+ *    positive size; an empty box keeps its cell midpoint); the cells still
+ *    decide the splits;
  *  - weak iff theta > 0, d > 0 and R + theta*r <= theta*d;
  *  - M2L at every level that has weak pairs (leaf level included);
  *  - the paper's octree levels (8 children per box) are `step` = 3
@@ -322,6 +326,7 @@ typedef struct {
     double theta;
     double eta;         /* adaptivity parameter of Sec. 2.1.2, [0, 1] */
     int step;           /* bisections per FMM level (1 binary, 3 octree) */
+    int tight;          /* 1: centre/radius from each box's points (see above) */
     double *x;          /* n x 3 canonical positions (-0.0 -> +0.0), input order */
     int64_t *perm;      /* slot -> original index, leaf order */
     int64_t *begin;     /* per box (heap order), first slot; nbox + 1 entries by level */
@@ -446,6 +451,38 @@ static void orc_build_tree(orc_fmm *F)
     free(tmp);
     free(keys);
     free(left);
+}
+
+/*
+ * Tight box geometry: the bounding box of a box's points, its midpoint as
+ * the expansion centre and its half diagonal as the radius, floored at 2^-10
+ * of the cell radius. Min and max are exact, so the result does not depend
+ * on the order in which the points are visited.
+ */
+static void orc_tight_geometry(orc_fmm *F)
+{
+    int64_t nb = nbox_of(F->levels);
+    for (int64_t g = 0; g < nb; g++) {
+        double floor_r = ldexp(F->radius[g], -10);
+        int64_t b = F->begin[g], nn = F->count[g];
+        if (nn == 0) {
+            F->radius[g] = floor_r;
+            continue;
+        }
+        double lo[3], hi[3], e[3];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = hi[a] = F->x[3 * F->perm[b] + a];
+            for (int64_t t = 1; t < nn; t++) {
+                double v = F->x[3 * F->perm[b + t] + a];
+                if (v < lo[a]) lo[a] = v;
+                if (v > hi[a]) hi[a] = v;
+            }
+            e[a] = hi[a] - lo[a];
+            F->centre[3 * g + a] = 0.5 * (lo[a] + hi[a]);
+        }
+        double r = 0.5 * sqrt((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2]);
+        F->radius[g] = r > floor_r ? r : floor_r;
+    }
 }
 
 /*
@@ -575,7 +612,7 @@ static void orc_build_lists(orc_fmm *F)
 /* ------------------------------------------------------------------ */
 
 orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, double eta,
-                   int step)
+                   int step, int tight)
 {
     if (step < 1 || levels % step != 0)
         return NULL;
@@ -583,6 +620,7 @@ orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, 
     int64_t nb = nbox_of(levels);
     F->eta = eta;
     F->step = step;
+    F->tight = tight;
     F->n = n;
     F->levels = levels;
     F->p = p;
@@ -602,6 +640,8 @@ orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, 
     F->M = calloc(nb * orc_ncoef(p), sizeof(cplx));
     F->L = calloc(nb * orc_ncoef(p), sizeof(cplx));
     orc_build_tree(F);
+    if (F->tight)
+        orc_tight_geometry(F);
     orc_build_lists(F);
     return F;
 }

@@ -24,6 +24,7 @@ FMM_MAX_LEVELS, FMM_MAX_P = 24, 20
 FMM_FLAG_PROFILE = 1
 FMM_FLAG_ETA = 2
 FMM_FLAG_TC_M2L = 4
+FMM_FLAG_TIGHT = 8
 STAGES = ("tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p")
 STATUS = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ENONFINITE",
           -4: "FMM_ECAPACITY", -5: "FMM_ETIMEDOUT", -6: "FMM_ECUDA", -7: "FMM_EINTERNAL"}
@@ -218,16 +219,17 @@ class Plan:
 # ---------------------------------------------------------------------------
 def fmm_plan(points, levels: int, p: int, theta: float, prec: int = FMM_PREC_FP64,
              stream=None, allocator="torch", profile: bool = False, eta: float = 1.0,
-             bisections_per_level: int = 1, tc_m2l: bool = False) -> Plan:
+             bisections_per_level: int = 1, tc_m2l: bool = False, tight: bool = False) -> Plan:
     """Build the tree and connectivity for n x 3 `points`; eta in [0, 1] is
     the split adaptivity (1: balanced median splits, 0: cell bisection);
-    bisections_per_level = 3 makes octree levels (`levels` counts bisections)."""
+    bisections_per_level = 3 makes octree levels (`levels` counts bisections);
+    tight = True takes box centres and radii from the boxes' own points."""
     lib = load()
     ptr, keep = _ptr(points)
     n = int(points.shape[0])
     dt = _dtype_code(points)
     flags = ((FMM_FLAG_PROFILE if profile else 0) | (FMM_FLAG_ETA if float(eta) != 1.0 else 0)
-             | (FMM_FLAG_TC_M2L if tc_m2l else 0))
+             | (FMM_FLAG_TC_M2L if tc_m2l else 0) | (FMM_FLAG_TIGHT if tight else 0))
     opts = fmm_opts(int(levels), int(p), float(theta), int(prec), flags, float(eta),
                     int(bisections_per_level))
     alloc, cbs = (None, None)

@@ -231,7 +231,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     if (opts->p < 0 || opts->p > FMM_MAX_P) return FMM_EINVAL;
     if (!(opts->theta >= 0.0 && opts->theta < 1.0)) return FMM_EINVAL;
     if (opts->prec != FMM_PREC_FP64 && opts->prec != FMM_PREC_MIXED) return FMM_EINVAL;
-    if (opts->flags & ~(FMM_FLAG_PROFILE | FMM_FLAG_ETA | FMM_FLAG_TC_M2L)) return FMM_EINVAL;
+    if (opts->flags & ~(FMM_FLAG_PROFILE | FMM_FLAG_ETA | FMM_FLAG_TC_M2L | FMM_FLAG_TIGHT)) return FMM_EINVAL;
     if ((opts->flags & FMM_FLAG_ETA) && !(opts->eta >= 0.0 && opts->eta <= 1.0)) return FMM_EINVAL;
     const int step = opts->bisections_per_level == 0 ? 1 : opts->bisections_per_level;
     if (step < 1 || step > 3 || opts->levels % step != 0) return FMM_EINVAL;
@@ -260,6 +260,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     cudaGetDevice(&P.device);
     P.profile = (opts->flags & FMM_FLAG_PROFILE) != 0;
     P.tc_m2l_opt = (opts->flags & FMM_FLAG_TC_M2L) != 0;
+    P.tight = (opts->flags & FMM_FLAG_TIGHT) != 0;
 
     auto fail = [&](int status) {
         release(P);
@@ -320,6 +321,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     }
     fmm::stage_mark(P, FMM_STAGE_TREE, 0);
     cudaError_t e = fmm::tree_build(P, pts, dtype);
+    if (e == cudaSuccess && P.tight) e = fmm::tight_geometry(P);
     fmm::stage_mark(P, FMM_STAGE_TREE, 1);
     if (staged) fmm::dfree(P, staged, pbytes);
     if (e != cudaSuccess) return fail(cuda_status(e));

@@ -46,6 +46,10 @@ struct Plan {
     double *lo = nullptr, *hi = nullptr, *centre = nullptr;   // nbox x 3
     double *radius = nullptr, *plane = nullptr;               // nbox
     int32_t *axis = nullptr;                                  // nbox
+    // FMM_FLAG_TIGHT: centre/radius from each box's points; their bounding
+    // boxes (nbox x 3 each) live until fmm_plan returns
+    bool tight = false;
+    double *tlo = nullptr, *thi = nullptr;
     // connectivity: CSR per level over the 2^l target boxes of level l
     int32_t *wptr[FMM_MAX_LEVELS + 1] = {}, *wsrc[FMM_MAX_LEVELS + 1] = {};
     int32_t *sptr[FMM_MAX_LEVELS + 1] = {}, *ssrc[FMM_MAX_LEVELS + 1] = {};
@@ -168,6 +172,7 @@ __device__ __forceinline__ double2 coef_at(const double2 *C, int n, int m) {
 // Host-side launchers (each in its own translation unit)
 // ---------------------------------------------------------------------------
 cudaError_t tree_build(Plan &P, const void *points_dev, int dtype);
+cudaError_t tight_geometry(Plan &P);
 cudaError_t lists_build(Plan &P);
 cudaError_t direct_run(const void *points, const void *charges, int64_t n, int dtype,
                        const int64_t *targets, int64_t nt, void *pot, void *field,

@@ -508,8 +508,10 @@ cudaError_t mixed_setup(Plan &P) {
     if (!P.hl || !P.qf || !P.far_phi_f || !P.far_E_f || !P.lgeo) return cudaErrorMemoryAllocation;
     FMM_LAUNCH(k_leaf_offsets, (unsigned)P.nleaf, 128, 0, P.stream, P.B, n, P.x, P.y, P.z, P.begin,
                P.count, P.centre, P.hl);
-    FMM_LAUNCH(k_leaf_geo, (unsigned)((P.nleaf + 127) / 128), 128, 0, P.stream, P.B, P.lo, P.hi,
-               P.centre, P.radius, P.lgeo);
+    // half extents of the box that holds the leaf's points: its cell, or with
+    // tight geometry the points' own bounding box
+    FMM_LAUNCH(k_leaf_geo, (unsigned)((P.nleaf + 127) / 128), 128, 0, P.stream, P.B, P.tight ? P.tlo : P.lo,
+               P.tight ? P.thi : P.hi, P.centre, P.radius, P.lgeo);
     return cudaGetLastError();
 }
 

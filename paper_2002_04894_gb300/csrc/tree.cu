@@ -830,6 +830,110 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
 }
 
 // ---------------------------------------------------------------------------
+// Tight box geometry (FMM_FLAG_TIGHT): the expansion centre and radius of a
+// box from the bounding box of its own points, the radius floored at 2^-10
+// of the cell radius (a box of one point keeps a positive size; an empty box
+// keeps its cell midpoint). The cells, which decide the splits, are kept.
+// Min and max are exact, so any reduction order gives the oracle's bits.
+// ---------------------------------------------------------------------------
+namespace {
+
+// One warp per leaf reduces its points; the lane-0 thread then walks up the
+// tree: a parent is formed by the second of its two children to arrive
+// (an arrival counter per internal box), so no thread ever waits.
+__global__ void k_tight_boxes(int B, const double *__restrict__ x, const double *__restrict__ y,
+                              const double *__restrict__ z, const int32_t *__restrict__ begin,
+                              const int32_t *__restrict__ count, double *tlo, double *thi,
+                              unsigned *arrive) {
+    const int64_t nl = (int64_t)1 << B;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double *src[3] = {x, y, z};
+    for (int64_t j = warp; j < nl; j += nwarps) {
+        int64_t g = nl - 1 + j;
+        const int b = begin[g], n = count[g];
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            double l = __longlong_as_double(0x7ff0000000000000LL), h = -l;  // +inf, -inf
+            for (int i = lane; i < n; i += 32) {
+                const double v = src[a][b + i];
+                l = fmin(l, v);
+                h = fmax(h, v);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+                h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+            }
+            lo[a] = l;
+            hi[a] = h;
+        }
+        if (lane == 0) {
+            for (int a = 0; a < 3; a++) {
+                tlo[3 * g + a] = lo[a];
+                thi[3 * g + a] = hi[a];
+            }
+            while (g > 0) {
+                __threadfence();
+                const int64_t par = (g - 1) >> 1;
+                if (atomicAdd(&arrive[par], 1u) == 0) break;  // the sibling forms the parent
+                __threadfence();
+                const int64_t c0 = 2 * par + 1, c1 = c0 + 1;
+                for (int a = 0; a < 3; a++) {
+                    tlo[3 * par + a] = fmin(__ldcg(tlo + 3 * c0 + a), __ldcg(tlo + 3 * c1 + a));
+                    thi[3 * par + a] = fmax(__ldcg(thi + 3 * c0 + a), __ldcg(thi + 3 * c1 + a));
+                }
+                g = par;
+            }
+        }
+    }
+}
+
+// centre = 0.5 (lo + hi), radius = max(0.5 sqrt((ex^2 + ey^2) + ez^2), 2^-10 r_cell)
+// in the oracle's operation order without contraction; empty boxes keep the
+// cell midpoint and take the floor, and their point box becomes that point.
+__global__ void k_tight_geometry(int64_t nbox, const int32_t *__restrict__ count, double *__restrict__ centre,
+                                 double *__restrict__ radius, double *__restrict__ tlo,
+                                 double *__restrict__ thi) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nbox) return;
+    const double floor_r = __dmul_rn(radius[g], 0x1p-10);
+    if (count[g] == 0) {
+        radius[g] = floor_r;
+        for (int a = 0; a < 3; a++) tlo[3 * g + a] = thi[3 * g + a] = centre[3 * g + a];
+        return;
+    }
+    double e[3];
+    for (int a = 0; a < 3; a++) {
+        const double l = tlo[3 * g + a], h = thi[3 * g + a];
+        e[a] = __dsub_rn(h, l);
+        centre[3 * g + a] = __dmul_rn(0.5, __dadd_rn(l, h));
+    }
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
+    const double r = __dmul_rn(0.5, __dsqrt_rn(s));
+    radius[g] = r > floor_r ? r : floor_r;
+}
+
+}  // namespace
+
+cudaError_t tight_geometry(Plan &P) {
+    cudaStream_t st = P.stream;
+    const size_t nb = (size_t)P.nbox;
+    P.tlo = (double *)dalloc(P, nb * 24);
+    P.thi = (double *)dalloc(P, nb * 24);
+    unsigned *arrive = (unsigned *)dalloc(P, nb * 4);
+    if (!P.tlo || !P.thi || !arrive) return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(arrive, 0, nb * 4, st);
+    const int64_t warps = P.nleaf;
+    const unsigned grid = (unsigned)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)sm_count() * 16);
+    FMM_LAUNCH(k_tight_boxes, grid, 256, 0, st, P.B, P.x, P.y, P.z, P.begin, P.count, P.tlo, P.thi, arrive);
+    FMM_LAUNCH(k_tight_geometry, (unsigned)((nb + 255) / 256), 256, 0, st, P.nbox, P.count, P.centre, P.radius,
+               P.tlo, P.thi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free ORB leaf order for small point sets (fmm_orb_order_noalloc).
 //
 // For callers that cannot allocate device memory (stream capture, host

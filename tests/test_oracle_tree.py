@@ -348,3 +348,70 @@ def test_lists_are_symmetric(kind, step, levels):
             p, s = T.lists(l, kind_)
             pairs = {(a, int(b)) for a in range(len(p) - 1) for b in s[p[a]:p[a + 1]]}
             assert pairs == {(b, a) for a, b in pairs}
+
+
+# ---------------------------------------------------------------------------
+# tight box geometry (centre and radius from the box's own points)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,n,levels,eta", [("gmm", 4000, 7, 1.0), ("plummer", 3000, 6, 1.0),
+                                               ("uniform", 100, 8, 1.0), ("gmm", 3000, 7, 0.3)])
+def test_tight_boxes_hold_their_points_and_keep_the_cells(kind, n, levels, eta):
+    x = inputs.points(kind, n, seed=7)
+    a = oracle.Tree(x, levels, 2, 0.5, eta=eta).tree()
+    b = oracle.Tree(x, levels, 2, 0.5, eta=eta, tight=True).tree()
+    for k in ("perm", "begin", "count", "lo", "hi", "axis", "plane"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)   # same splits and cells
+    xs = x[b["perm"]]
+    for g in range(len(b["count"])):
+        c, r = b["centre"][g], b["radius"][g]
+        assert r >= a["radius"][g] * 2.0 ** -10
+        assert r <= a["radius"][g] * (1 + 1e-15)           # inside the cell
+        pts = xs[b["begin"][g]:b["begin"][g] + b["count"][g]]
+        if len(pts) == 0:
+            np.testing.assert_array_equal(c, a["centre"][g])
+            assert r == a["radius"][g] * 2.0 ** -10
+            continue
+        lo, hi = pts.min(0), pts.max(0)
+        np.testing.assert_array_equal(c, 0.5 * (lo + hi))   # brute force, numpy
+        assert np.all(np.linalg.norm(pts - c, axis=1) <= r * (1 + 1e-13))  # rounding at a corner
+        if len(pts) > 1 and np.any(hi > lo):
+            assert np.isclose(r, max(0.5 * np.linalg.norm(hi - lo), a["radius"][g] * 2.0 ** -10), rtol=1e-15)
+
+
+@pytest.mark.parametrize("theta", [0.35, 0.5, 0.8])
+def test_tight_lists_match_brute_force(theta):
+    x = inputs.points("gmm", 300, seed=9)
+    levels = 5
+    T = oracle.Tree(x, levels, 2, theta, tight=True)
+    t = T.tree()
+    for l in range(1, levels + 1):
+        wp, ws = T.lists(l, "weak")
+        sp, ss = T.lists(l, "strong")
+        for a in range(1 << l):
+            want_w, want_s = [], []
+            for b in range(1 << l):
+                if ancestors_weak(t, theta, l, a, b):
+                    continue
+                ga, gb = (1 << l) - 1 + a, (1 << l) - 1 + b
+                if oracle.theta_weak(theta, t["centre"][ga], t["radius"][ga], t["centre"][gb], t["radius"][gb]):
+                    want_w.append(b)
+                else:
+                    want_s.append(b)
+            assert list(ws[wp[a]:wp[a + 1]]) == want_w
+            assert list(ss[sp[a]:sp[a + 1]]) == want_s
+
+
+def test_tight_fmm_converges_to_the_direct_sum():
+    n = 3000
+    x = inputs.points("gmm", n, seed=2)
+    q = inputs.charges_uniform(n, seed=2)
+    ref = oracle.direct(x, q, field=False)
+    errs = []
+    for p in (2, 4, 6, 8, 10):
+        phi = oracle.Tree(x, 7, p, 0.5, tight=True).eval(q, field=False)
+        errs.append(np.linalg.norm(phi - ref) / np.linalg.norm(ref))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-6
+    # theta = 0: no weak pairs, so the sum is the direct one
+    phi0 = oracle.Tree(x, 7, 3, 0.0, tight=True).eval(q, field=False)
+    assert np.linalg.norm(phi0 - ref) / np.linalg.norm(ref) < 1e-14
