@@ -45,7 +45,7 @@ def test_invalid_arguments_rejected_before_any_device_work():
     for bad in (fmm.fmm_opts(-1, 4, 0.5, 0, 0), fmm.fmm_opts(25, 4, 0.5, 0, 0),
                 fmm.fmm_opts(3, 21, 0.5, 0, 0), fmm.fmm_opts(3, 4, 1.0, 0, 0),
                 fmm.fmm_opts(3, 4, -0.1, 0, 0), fmm.fmm_opts(3, 4, float("nan"), 0, 0),
-                fmm.fmm_opts(3, 4, 0.5, 7, 0), fmm.fmm_opts(3, 4, 0.5, 0, 8),
+                fmm.fmm_opts(3, 4, 0.5, 7, 0), fmm.fmm_opts(3, 4, 0.5, 0, 16),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, 1.5),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, -0.25),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, float("nan")),
