@@ -206,6 +206,10 @@ typedef struct fmm_stats {
     int64_t strong_leaf_pairs;   /* directed P2P leaf pairs, self pairs included */
     int64_t p2p_interactions;    /* sum over strong leaf pairs of n_t * n_s */
     int64_t weak_pairs_level[FMM_MAX_LEVELS + 1];
+    int64_t p2p_units;           /* near-field work units: a tile of a target leaf's points
+                                    against a segment of its strong list */
+    int64_t p2p_partial_slots;   /* partial sums of leaves whose strong list holds more than
+                                    about 65536 source points and was cut into segments */
 } fmm_stats;
 
 /* fmm_plan_stats -- fill *out (synchronises the plan's stream for the

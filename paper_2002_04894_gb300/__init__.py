@@ -56,7 +56,8 @@ class fmm_stats(C.Structure):
                 ("levels", C.c_int), ("p", C.c_int), ("prec", C.c_int), ("dtype", C.c_int),
                 ("theta", C.c_double), ("weak_pairs", C.c_int64),
                 ("strong_leaf_pairs", C.c_int64), ("p2p_interactions", C.c_int64),
-                ("weak_pairs_level", C.c_int64 * (FMM_MAX_LEVELS + 1))]
+                ("weak_pairs_level", C.c_int64 * (FMM_MAX_LEVELS + 1)),
+                ("p2p_units", C.c_int64), ("p2p_partial_slots", C.c_int64)]
 
 
 _LIB = None

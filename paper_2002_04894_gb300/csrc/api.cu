@@ -559,6 +559,8 @@ int fmm_plan_stats(fmm_plan_t plan, fmm_stats *out) {
         out->weak_pairs += P.nweak[l];
     }
     out->strong_leaf_pairs = P.nstrong[P.B];
+    out->p2p_units = P.p2p_nunits;
+    out->p2p_partial_slots = P.p2p_nparts;
     unsigned long long work = 0;
     if (P.p2p_work_dev) {
         cudaError_t e = cudaStreamSynchronize(P.stream);

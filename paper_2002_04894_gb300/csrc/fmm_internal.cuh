@@ -12,8 +12,14 @@
 
 namespace fmm {
 
-// targets per near-field work unit (one CTA, one target per thread)
+// targets per near-field work unit (one CTA, one target per thread): at most
+// kP2PTile; the mixed form takes kP2PTileSmall when the leaves hold 64 points
+// or fewer on average, so that a unit's threads are not half idle
 constexpr int kP2PTile = 128;
+constexpr int kP2PTileSmall = 64;
+// sources per near-field work unit at most (about): a target leaf whose
+// strong list holds more is cut into segments, each its own unit
+constexpr int kP2PSegSources = 1 << 16;
 
 // ---------------------------------------------------------------------------
 // Plan: everything lives in device memory owned by the plan.
@@ -56,12 +62,18 @@ struct Plan {
     int32_t *wrow[FMM_MAX_LEVELS + 1] = {};  // target of every weak pair (flat M2L)
     int64_t nweak[FMM_MAX_LEVELS + 1] = {}, nstrong[FMM_MAX_LEVELS + 1] = {};
     unsigned long long *p2p_work_dev = nullptr;  // exact near-field pair count (device)
-    // near-field work units (target leaf, first target of a kP2PTile tile),
-    // heaviest first; their number on the device, and an upper bound for
-    // the launch (blocks past the count return at once)
-    int2 *p2p_units = nullptr;
+    // near-field work units (target leaf, first target, strong-list segment
+    // [begin, end)), heaviest first; their number on the device and on the
+    // host; per unit its partial-sum slot base (-1: the leaf is not split);
+    // per leaf the offset of its k * n_t partial slots (scan); the slots
+    int4 *p2p_units = nullptr;
+    int32_t *p2p_upart = nullptr;
     const int32_t *p2p_nunits_dev = nullptr;
     int64_t p2p_nunits = 0;
+    int32_t *p2p_poff = nullptr;
+    int64_t p2p_nparts = 0;
+    double4 *p2p_partial = nullptr;
+    int p2p_tile = kP2PTile;  // targets per work unit (kP2PTile or kP2PTileSmall)
     bool capacity_exceeded = false;
     // M2L rotation tables (D = d(pi/2) quadrants, axial coefficients, F_nm)
     double *m2l_tab = nullptr;
@@ -195,6 +207,9 @@ cudaError_t mixed_setup(Plan &P);
 cudaError_t mixed_p2m(Plan &P, const void *charges, int dtype);
 cudaError_t mixed_l2p(Plan &P);
 cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype);
+// adds the partial near-field sums of split leaves in segment order, plus the
+// far field, and writes those leaves' outputs in input order
+cudaError_t p2p_combine(Plan &P, void *pot, void *field, int dtype);
 // device-wide exclusive scan of int32 counts (n + 1 outputs, last = total)
 cudaError_t scan_exclusive(Plan &P, const int32_t *in, int32_t *out, int64_t n);
 

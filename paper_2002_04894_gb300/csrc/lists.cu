@@ -194,24 +194,41 @@ __global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *tile_sums) {
 }
 
 // per target leaf the near source points (sum of n_s over its strong leaf
-// pairs), and in total the sum over strong leaf pairs (t, s) of n_t * n_s
-// per leaf: its sources over the strong list, its number of near-field work
-// units (tiles of kP2PTile targets); the total pair count into acc
-__global__ void k_p2p_work(int B, const int32_t *sptr, const int32_t *ssrc, const int32_t *count,
-                           unsigned long long *acc, long long *per_leaf, int32_t *units_per_leaf) {
+// pairs), and in total the sum over strong leaf pairs (t, s) of n_t * n_s.
+// Per leaf: its sources over the strong list, its number of near-field work
+// units -- tiles of `tile` targets times k source segments, k = ceil(sources /
+// smax) -- and, when k > 1, the k * n_t partial-sum slots its split units fill;
+// the totals (pairs, units, slots) into acc[0..2] in 64 bits
+__global__ void k_p2p_work(int B, int tile, long long smax, const int32_t *sptr, const int32_t *ssrc,
+                           const int32_t *count, unsigned long long *acc, long long *per_leaf,
+                           int32_t *units_per_leaf, int32_t *parts_per_leaf) {
     const int64_t nt = (int64_t)1 << B;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long v = 0;
+    unsigned long long v = 0, vu = 0, vp = 0;
     if (t < nt) {
         const int64_t off = nt - 1;
         unsigned long long ns = 0;
         for (int32_t e = sptr[t]; e < sptr[t + 1]; e++) ns += (unsigned long long)count[off + ssrc[e]];
-        v = ns * (unsigned long long)count[off + t];
+        const int n_t = count[off + t];
+        v = ns * (unsigned long long)n_t;
         per_leaf[t] = (long long)ns;
-        units_per_leaf[t] = (count[off + t] + kP2PTile - 1) / kP2PTile;
+        const unsigned long long k = ns > (unsigned long long)smax ? (ns + smax - 1) / smax : 1;
+        vu = (unsigned long long)((n_t + tile - 1) / tile) * k;
+        vp = k > 1 ? k * (unsigned long long)n_t : 0;
+        // stored as int32; the host rejects the plan if a total exceeds 2^31 - 1
+        units_per_leaf[t] = (int32_t)min(vu, 0x7fffffffull);
+        parts_per_leaf[t] = (int32_t)min(vp, 0x7fffffffull);
     }
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        vu += __shfl_xor_sync(0xffffffffu, vu, o);
+        vp += __shfl_xor_sync(0xffffffffu, vp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (v) atomicAdd(acc, v);
+        if (vu) atomicAdd(acc + 1, vu);
+        if (vp) atomicAdd(acc + 2, vp);
+    }
 }
 
 // Work units heaviest first, on the device: each unit's weight (targets x the
@@ -226,16 +243,46 @@ __device__ __forceinline__ int unit_bucket(unsigned long long w) {
     return 255 - min(255, 4 * lg + frac);
 }
 
-__global__ void k_units_gen(int B, const int32_t *count, const long long *nsrc, const int32_t *uoff,
-                            int2 *units, uint8_t *bucket) {
+// One thread per leaf: cuts the leaf's strong list into k segments of about
+// nsrc / k sources each (cumulative source count along the list) and emits
+// its units (leaf, first target, segment begin, segment end) with their
+// partial-sum slot (-1 when the leaf is not split) and weight bucket.
+__global__ void k_units_gen(int B, int tile, long long smax, const int32_t *count, const long long *nsrc,
+                            const int32_t *sptr, const int32_t *ssrc, const int32_t *uoff,
+                            const int32_t *poff, int4 *units, int32_t *upart, uint8_t *bucket) {
     const int64_t nt = (int64_t)1 << B;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
-    const int cnt = count[nt - 1 + t];
+    const int64_t off = nt - 1;
+    const int cnt = count[off + t];
+    if (cnt == 0) return;
+    const long long ns = nsrc[t];
+    const int k = ns > smax ? (int)((ns + smax - 1) / smax) : 1;
     int u = uoff[t];
-    for (int tb = 0; tb < cnt; tb += kP2PTile, u++) {
-        units[u] = make_int2((int)t, tb);
-        bucket[u] = (uint8_t)unit_bucket((unsigned long long)min(kP2PTile, cnt - tb) * (unsigned long long)nsrc[t]);
+    int e_lo = sptr[t];
+    long long c_lo = 0;
+    int e = e_lo;
+    long long c = 0;
+    for (int j = 0; j < k; j++) {
+        // segment j ends at the first list position where the cumulative
+        // source count reaches (j + 1) ns / k (the last one at the list's end)
+        const long long goal = j + 1 == k ? ns : (long long)(((unsigned long long)ns * (j + 1)) / k);
+        int e_hi = e;
+        long long c_hi = c;
+        if (j + 1 == k) {
+            e_hi = sptr[t + 1];
+            c_hi = ns;
+        } else {
+            while (e_hi < sptr[t + 1] && c_hi < goal) c_hi += count[off + ssrc[e_hi++]];
+        }
+        for (int tb = 0; tb < cnt; tb += tile, u++) {
+            units[u] = make_int4((int)t, tb, e_lo, e_hi);
+            upart[u] = k > 1 ? poff[t] + j * cnt : -1;
+            bucket[u] = (uint8_t)unit_bucket((unsigned long long)min(tile, cnt - tb) *
+                                             (unsigned long long)(c_hi - c_lo));
+        }
+        e_lo = e = e_hi;
+        c_lo = c = c_hi;
     }
 }
 
@@ -255,8 +302,8 @@ k_units_hist(const int32_t *total, const uint8_t *bucket, int nblocks, int32_t *
 // stable scatter: a unit's place is its bucket's offset for its block plus the
 // units of the same bucket before it in the block (warp match, then warps)
 __global__ void __launch_bounds__(kUnitBlock)
-k_units_scatter(const int32_t *total, const uint8_t *bucket, const int2 *units, int nblocks,
-                const int32_t *boff, int2 *sorted) {
+k_units_scatter(const int32_t *total, const uint8_t *bucket, const int4 *units, const int32_t *upart,
+                int nblocks, const int32_t *boff, int4 *sorted, int32_t *sorted_part) {
     __shared__ int32_t wc[kUnitBlock / 32][256];
     const int tid = threadIdx.x, k = blockIdx.x, lane = tid & 31, w = tid >> 5;
     for (int i = tid; i < (kUnitBlock / 32) * 256; i += kUnitBlock) (&wc[0][0])[i] = 0;
@@ -272,6 +319,7 @@ k_units_scatter(const int32_t *total, const uint8_t *bucket, const int2 *units, 
         int r = boff[(int64_t)b * nblocks + k] + rank_w;
         for (int j = 0; j < w; j++) r += wc[j][b];
         sorted[r] = units[u];
+        sorted_part[r] = upart[u];
     }
 }
 
@@ -376,38 +424,62 @@ cudaError_t lists_build(Plan &P) {
         srow_prev = srow;
     }
     // exact P2P work (sum of n_t * n_s over strong leaf pairs). The near
-    // field runs as work units of up to kP2PTile targets of one leaf, so that
-    // a few large leaves still fill the GPU; units go heaviest first, so that
-    // the long ones start early instead of forming the tail of the launch.
-    // All of it stays on the device: the near-field launch takes an upper
-    // bound on the number of units and reads the actual count.
+    // field runs as work units of up to `tile` targets of one leaf against a
+    // segment of its strong list of at most about kP2PSegSources sources, so
+    // that neither a few large leaves nor the leaves strongly connected to
+    // most of the tree (large boxes in sparse regions of clustered inputs)
+    // leave the GPU waiting on a handful of blocks; units go heaviest first,
+    // so that the long ones start early instead of forming the tail of the
+    // launch. A leaf cut into k segments gets k partial sums per target,
+    // added in segment order by the combine pass. The unit and slot totals
+    // are read back once to size the arrays.
     const int64_t nl = (int64_t)1 << P.B;
-    const int64_t umax = nl + (P.n + kP2PTile - 1) / kP2PTile;  // sum of ceil(count / tile) <= this
-    const int nblk = (int)((umax + kUnitBlock - 1) / kUnitBlock);
-    P.p2p_work_dev = (unsigned long long *)palloc(P, 8);
+    P.p2p_tile = (P.prec == FMM_PREC_MIXED && P.n <= (int64_t)kP2PTileSmall * nl) ? kP2PTileSmall : kP2PTile;
+    const int tile = P.p2p_tile;
+    P.p2p_work_dev = (unsigned long long *)palloc(P, 24);  // pairs, units, partial slots
     long long *nsrc = (long long *)dalloc(P, (size_t)nl * 8);
     int32_t *upl = (int32_t *)dalloc(P, (size_t)nl * 4);
-    int32_t *uoff = (int32_t *)palloc(P, (size_t)(nl + 1) * 4);
-    int2 *units = (int2 *)dalloc(P, (size_t)umax * sizeof(int2));
-    uint8_t *bucket = (uint8_t *)dalloc(P, (size_t)umax);
+    int32_t *ppl = (int32_t *)dalloc(P, (size_t)nl * 4);
+    int32_t *uoff = (int32_t *)palloc(P, (size_t)(nl + 1) * 4);  // its total is read at evaluation
+    P.p2p_poff = (int32_t *)palloc(P, (size_t)(nl + 1) * 4);
+    if (!P.p2p_work_dev || !nsrc || !upl || !ppl || !uoff || !P.p2p_poff) return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(P.p2p_work_dev, 0, 24, st);
+    FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, tile, (long long)kP2PSegSources,
+               P.sptr[P.B], P.ssrc[P.B], P.count, P.p2p_work_dev, nsrc, upl, ppl);
+    e = scan_exclusive(P, upl, uoff, nl);
+    if (e == cudaSuccess) e = scan_exclusive(P, ppl, P.p2p_poff, nl);
+    if (e != cudaSuccess) return e;
+    unsigned long long tot[3] = {0, 0, 0};
+    cudaMemcpyAsync(tot, P.p2p_work_dev, 24, cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (tot[1] > 0x7fffffffull || tot[2] > 0x7fffffffull) {  // the int32 scans would overflow
+        P.capacity_exceeded = true;
+        return cudaSuccess;
+    }
+    const int64_t nunits = (int64_t)tot[1];
+    P.p2p_nparts = (int64_t)tot[2];
+    const int nblk = (int)std::max<int64_t>((nunits + kUnitBlock - 1) / kUnitBlock, 1);
+    int4 *units = (int4 *)dalloc(P, (size_t)std::max<int64_t>(nunits, 1) * sizeof(int4));
+    int32_t *upart = (int32_t *)dalloc(P, (size_t)std::max<int64_t>(nunits, 1) * 4);
+    uint8_t *bucket = (uint8_t *)dalloc(P, (size_t)std::max<int64_t>(nunits, 1));
     int32_t *bh = (int32_t *)dalloc(P, (size_t)256 * nblk * 4);
     int32_t *boff = (int32_t *)dalloc(P, ((size_t)256 * nblk + 1) * 4);
-    P.p2p_units = (int2 *)palloc(P, (size_t)umax * sizeof(int2));
-    if (!P.p2p_work_dev || !nsrc || !upl || !uoff || !units || !bucket || !bh || !boff || !P.p2p_units)
+    P.p2p_units = (int4 *)palloc(P, (size_t)std::max<int64_t>(nunits, 1) * sizeof(int4));
+    P.p2p_upart = (int32_t *)palloc(P, (size_t)std::max<int64_t>(nunits, 1) * 4);
+    P.p2p_partial = P.p2p_nparts ? (double4 *)palloc(P, (size_t)P.p2p_nparts * sizeof(double4)) : nullptr;
+    if (!units || !upart || !bucket || !bh || !boff || !P.p2p_units || !P.p2p_upart ||
+        (P.p2p_nparts && !P.p2p_partial))
         return cudaErrorMemoryAllocation;
-    cudaMemsetAsync(P.p2p_work_dev, 0, 8, st);
-    FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.sptr[P.B], P.ssrc[P.B],
-               P.count, P.p2p_work_dev, nsrc, upl);
-    e = scan_exclusive(P, upl, uoff, nl);
-    if (e != cudaSuccess) return e;
     P.p2p_nunits_dev = uoff + nl;
-    P.p2p_nunits = umax;
-    FMM_LAUNCH(k_units_gen, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, P.count, nsrc, uoff, units, bucket);
+    P.p2p_nunits = nunits;
+    FMM_LAUNCH(k_units_gen, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, tile, (long long)kP2PSegSources,
+               P.count, nsrc, P.sptr[P.B], P.ssrc[P.B], uoff, P.p2p_poff, units, upart, bucket);
     FMM_LAUNCH(k_units_hist, (unsigned)nblk, kUnitBlock, 0, st, P.p2p_nunits_dev, bucket, nblk, bh);
     e = scan_exclusive(P, bh, boff, (int64_t)256 * nblk);
     if (e != cudaSuccess) return e;
-    FMM_LAUNCH(k_units_scatter, (unsigned)nblk, kUnitBlock, 0, st, P.p2p_nunits_dev, bucket, units, nblk, boff,
-               P.p2p_units);
+    FMM_LAUNCH(k_units_scatter, (unsigned)nblk, kUnitBlock, 0, st, P.p2p_nunits_dev, bucket, units, upart, nblk,
+               boff, P.p2p_units, P.p2p_upart);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

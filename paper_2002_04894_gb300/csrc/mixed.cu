@@ -277,8 +277,6 @@ __global__ void k_leaf_geo(int B, const double *__restrict__ lo, const double *_
 }
 
 constexpr int kLeafChunk = 256;
-constexpr int kP2PThreads = 128;  // threads per work unit; one target each
-constexpr int kSrcTile = 128;     // sources staged per pass (64 pairs)
 constexpr float kFarGap = 0.1f;   // far: cell gap >= kFarGap (r_t + r_s)
 constexpr float kPadFar = 1.0e18f;  // padding source: zero charge, far away
 constexpr int kRun = 64;  // sources summed in float before the compensated add
@@ -341,8 +339,9 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
     a[3] = fma2(qr3, dz, a[3]);
 }
 
-// Near field in float. One CTA per work unit (a tile of up to 128 targets
-// of one leaf; heaviest units first), one target point per thread, two
+// Near field in float. One CTA per work unit (a tile of up to T = 128 or 64
+// targets of one leaf, by the plan's mean leaf size; heaviest units first),
+// T sources staged per pass, one target point per thread, two
 // sources per step in packed float2 arithmetic (FFMA2/FADD2/FMUL2). For
 // every source leaf the offset between the two leaf centres is formed once,
 // error-free (float TwoSum on the centres' hi/lo parts), together with a
@@ -357,27 +356,31 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
 // offsets, whose difference is exact for close pairs. Per target the sources are
 // summed in plain float over runs of 64 (full runs with a fixed trip count)
 // and the runs compensated (Kahan).
-template <typename OutT>
-__global__ void __launch_bounds__(kP2PThreads)
+template <typename OutT, int T>
+__global__ void __launch_bounds__(T)
 k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
-          const float4 *__restrict__ geo, const int32_t *__restrict__ sptr,
-          const int32_t *__restrict__ ssrc, const int2 *__restrict__ units, const int32_t *__restrict__ nunits,
+          const float4 *__restrict__ geo, const int32_t *__restrict__ ssrc, const int4 *__restrict__ units,
+          const int32_t *__restrict__ upart, const int32_t *__restrict__ nunits,
           const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
-          const float *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
+          const float *__restrict__ far_E, double4 *__restrict__ partial, OutT *__restrict__ pot,
+          OutT *__restrict__ field) {
+    constexpr int kP2PThreads = T, kSrcTile = T;
     __shared__ float4 sA[kSrcTile / 2], sB[kSrcTile / 2];  // hi parts and charges, per source pair
     __shared__ float4 sC[kSrcTile / 2], sD[kSrcTile / 2];  // lo parts (near leaves)
     __shared__ float4 dh[kLeafChunk];   // per source leaf: centre offset hi, near flag
     __shared__ float4 dl[kLeafChunk];   // centre offset lo
     __shared__ int2 rng[kLeafChunk];    // begin, count
-    static_assert(kP2PThreads == kP2PTile, "one target per thread");
+    static_assert(T == kP2PTile || T == kP2PTileSmall, "one target per thread");
+    static_assert(kRun <= kSrcTile, "a run fits in a staged tile");
     const int64_t off = ((int64_t)1 << B) - 1;
     if ((int)blockIdx.x >= *nunits) return;  // launched for an upper bound on the units
-    const int2 unit = units[blockIdx.x];
+    const int4 unit = units[blockIdx.x];
+    const int part = upart[blockIdx.x];
     const int t = unit.x;
     const int64_t gt = off + t;
     const int bt = begin[gt], nt = count[gt];
-    const int e0 = sptr[t], e1 = sptr[t + 1];
+    const int e0 = unit.z, e1 = unit.w;  // this unit's segment of the strong list
     const float4 tc_h = geo[3 * t], tc_l = geo[3 * t + 1], tc_e = geo[3 * t + 2];
     const int tid = threadIdx.x;
     const int i = unit.y + tid;
@@ -484,7 +487,10 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
             }
         }
     }
-    if (active) {
+    if (active && part >= 0) {  // one segment of a split leaf: its partial sums
+        partial[part + i] = make_double4((double)sum[0] - (double)comp[0], (double)sum[1] - (double)comp[1],
+                                         (double)sum[2] - (double)comp[2], (double)sum[3] - (double)comp[3]);
+    } else if (active) {
         const int64_t a = bt + i;
         const int64_t o = perm[a];
         pot[o] = (OutT)((double)far_phi[a] + ((double)sum[0] - (double)comp[0]));
@@ -533,16 +539,24 @@ cudaError_t mixed_l2p(Plan &P) {
     return cudaGetLastError();
 }
 
-cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
+template <int T>
+static void launch_p2p_f32(Plan &P, void *pot, void *field, int dtype) {
     if (dtype == FMM_F64)
-        FMM_LAUNCH(k_p2p_f32<double>, (unsigned)P.p2p_nunits, kP2PThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev, P.perm,
-                   P.far_phi_f, P.far_E_f, (double *)pot, (double *)field);
+        FMM_LAUNCH((k_p2p_f32<double, T>), (unsigned)P.p2p_nunits, T, 0, P.stream, P.B, P.n, P.hl, P.qf, P.begin,
+                   P.count, P.lgeo, P.ssrc[P.B], P.p2p_units, P.p2p_upart, P.p2p_nunits_dev, P.perm, P.far_phi_f,
+                   P.far_E_f, P.p2p_partial, (double *)pot, (double *)field);
     else
-        FMM_LAUNCH(k_p2p_f32<float>, (unsigned)P.p2p_nunits, kP2PThreads, 0, P.stream, P.B, P.n, P.hl, P.qf,
-                   P.begin, P.count, P.lgeo, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev, P.perm,
-                   P.far_phi_f, P.far_E_f, (float *)pot, (float *)field);
-    return cudaGetLastError();
+        FMM_LAUNCH((k_p2p_f32<float, T>), (unsigned)P.p2p_nunits, T, 0, P.stream, P.B, P.n, P.hl, P.qf, P.begin,
+                   P.count, P.lgeo, P.ssrc[P.B], P.p2p_units, P.p2p_upart, P.p2p_nunits_dev, P.perm, P.far_phi_f,
+                   P.far_E_f, P.p2p_partial, (float *)pot, (float *)field);
+}
+
+cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
+    if (P.p2p_tile == kP2PTileSmall)
+        launch_p2p_f32<kP2PTileSmall>(P, pot, field, dtype);
+    else
+        launch_p2p_f32<kP2PTile>(P, pot, field, dtype);
+    return p2p_combine(P, pot, field, dtype);
 }
 
 }  // namespace fmm

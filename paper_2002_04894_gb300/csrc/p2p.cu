@@ -2,10 +2,13 @@
 //
 // P2P: for every target leaf, the direct interaction with the points of all
 // strongly connected leaves (itself included), pairs at zero distance
-// skipped. One CTA per target leaf, one target point per thread; source
-// leaves are staged through shared memory in tiles of (x, y, z, q). The
-// kernel adds the far field left by L2P and writes phi and E straight to the
-// caller's arrays in input order (the un-permute step).
+// skipped. One CTA per work unit (a tile of a target leaf's points against a
+// segment of its strong list), one target point per thread; source leaves
+// are staged through shared memory in tiles of (x, y, z, q). The kernel adds
+// the far field left by L2P and writes phi and E straight to the caller's
+// arrays in input order (the un-permute step); a leaf whose strong list was
+// cut into segments leaves per-segment partial sums instead, which the
+// combine pass adds in segment order.
 //
 // Direct: one CTA per target, threads stride over all sources with
 // Neumaier-compensated partial sums, then a block reduction.
@@ -25,10 +28,10 @@ __global__ void __launch_bounds__(kP2PThreads)
 k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__restrict__ y,
           const double *__restrict__ z, const double *__restrict__ q,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
-          const int32_t *__restrict__ sptr, const int32_t *__restrict__ ssrc,
-          const int2 *__restrict__ units, const int32_t *__restrict__ nunits, const int32_t *__restrict__ perm,
-          const double *__restrict__ far_phi,
-          const double *__restrict__ far_E, OutT *__restrict__ pot, OutT *__restrict__ field) {
+          const int32_t *__restrict__ ssrc, const int4 *__restrict__ units, const int32_t *__restrict__ upart,
+          const int32_t *__restrict__ nunits, const int32_t *__restrict__ perm,
+          const double *__restrict__ far_phi, const double *__restrict__ far_E, double4 *__restrict__ partial,
+          OutT *__restrict__ pot, OutT *__restrict__ field) {
     struct alignas(16) Src {
         double x, y, z, q;
     };
@@ -36,10 +39,11 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
     const int64_t off = ((int64_t)1 << B) - 1;
     static_assert(kP2PThreads == kP2PTile, "one target per thread");
     if ((int)blockIdx.x >= *nunits) return;  // launched for an upper bound on the units
-    const int2 unit = units[blockIdx.x];
+    const int4 unit = units[blockIdx.x];
+    const int part = upart[blockIdx.x];
     const int t = unit.x;
     const int bt = begin[off + t], nt = count[off + t];
-    const int e0 = sptr[t], e1 = sptr[t + 1];
+    const int e0 = unit.z, e1 = unit.w;  // this unit's segment of the strong list
     {
         const int tb = unit.y;
         const int i = tb + threadIdx.x;
@@ -71,7 +75,9 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
                 __syncthreads();
             }
         }
-        if (active) {
+        if (active && part >= 0) {  // one segment of a split leaf: its partial sums
+            partial[part + i] = make_double4(phi, ex, ey, ez);
+        } else if (active) {
             const int64_t a = bt + i;
             const int64_t o = perm[a];
             pot[o] = (OutT)(far_phi[a] + phi);
@@ -137,6 +143,42 @@ k_direct(const T *__restrict__ pts, const T *__restrict__ q, int64_t n,
     }
 }
 
+// Finishes the leaves whose strong list was cut into segments: per target,
+// the segments' partial sums added in segment order, then the far field;
+// outputs in input order. Leaves without partial slots are skipped.
+template <typename OutT, typename FarT>
+__global__ void __launch_bounds__(128)
+k_p2p_combine(int B, int64_t npts, const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+              const int32_t *__restrict__ poff, const double4 *__restrict__ partial,
+              const int32_t *__restrict__ perm, const FarT *__restrict__ far_phi, const FarT *__restrict__ far_E,
+              OutT *__restrict__ pot, OutT *__restrict__ field) {
+    const int64_t nl = (int64_t)1 << B;
+    for (int64_t t = blockIdx.x; t < nl; t += gridDim.x) {
+        const int p0 = poff[t], np = poff[t + 1] - p0;
+        if (np == 0) continue;
+        const int nt = count[nl - 1 + t], bt = begin[nl - 1 + t];
+        const int k = np / nt;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            double4 s = partial[p0 + i];
+            for (int j = 1; j < k; j++) {
+                const double4 v = partial[p0 + j * nt + i];
+                s.x += v.x;
+                s.y += v.y;
+                s.z += v.z;
+                s.w += v.w;
+            }
+            const int64_t a = bt + i;
+            const int64_t o = perm[a];
+            pot[o] = (OutT)((double)far_phi[a] + s.x);
+            if (field) {
+                field[3 * o] = (OutT)((double)far_E[a] + s.y);
+                field[3 * o + 1] = (OutT)((double)far_E[npts + a] + s.z);
+                field[3 * o + 2] = (OutT)((double)far_E[2 * npts + a] + s.w);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
@@ -148,14 +190,34 @@ cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
         return e;
     }
     if (dtype == FMM_F64)
-        FMM_LAUNCH(k_p2p_f64<double>, grid, kP2PThreads, 0, P.stream, 
-            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev,
-            P.perm, P.far_phi, P.far_E, (double *)pot, (double *)field);
+        FMM_LAUNCH(k_p2p_f64<double>, grid, kP2PThreads, 0, P.stream, P.B, P.n, P.x, P.y, P.z, P.q, P.begin,
+                   P.count, P.ssrc[P.B], P.p2p_units, P.p2p_upart, P.p2p_nunits_dev, P.perm, P.far_phi, P.far_E,
+                   P.p2p_partial, (double *)pot, (double *)field);
     else
-        FMM_LAUNCH(k_p2p_f64<float>, grid, kP2PThreads, 0, P.stream, 
-            P.B, P.n, P.x, P.y, P.z, P.q, P.begin, P.count, P.sptr[P.B], P.ssrc[P.B], P.p2p_units, P.p2p_nunits_dev,
-            P.perm, P.far_phi, P.far_E, (float *)pot, (float *)field);
+        FMM_LAUNCH(k_p2p_f64<float>, grid, kP2PThreads, 0, P.stream, P.B, P.n, P.x, P.y, P.z, P.q, P.begin,
+                   P.count, P.ssrc[P.B], P.p2p_units, P.p2p_upart, P.p2p_nunits_dev, P.perm, P.far_phi, P.far_E,
+                   P.p2p_partial, (float *)pot, (float *)field);
+    cudaError_t e = p2p_combine(P, pot, field, dtype);
     stage_mark(P, FMM_STAGE_P2P, 1);
+    return e;
+}
+
+cudaError_t p2p_combine(Plan &P, void *pot, void *field, int dtype) {
+    if (P.p2p_nparts == 0) return cudaGetLastError();
+    const unsigned grid = (unsigned)std::min<int64_t>(P.nleaf, (int64_t)sm_count() * 8);
+    const bool mixed = P.prec == FMM_PREC_MIXED;
+    if (mixed && dtype == FMM_F64)
+        FMM_LAUNCH((k_p2p_combine<double, float>), grid, 128, 0, P.stream, P.B, P.n, P.begin, P.count, P.p2p_poff,
+                   P.p2p_partial, P.perm, P.far_phi_f, P.far_E_f, (double *)pot, (double *)field);
+    else if (mixed)
+        FMM_LAUNCH((k_p2p_combine<float, float>), grid, 128, 0, P.stream, P.B, P.n, P.begin, P.count, P.p2p_poff,
+                   P.p2p_partial, P.perm, P.far_phi_f, P.far_E_f, (float *)pot, (float *)field);
+    else if (dtype == FMM_F64)
+        FMM_LAUNCH((k_p2p_combine<double, double>), grid, 128, 0, P.stream, P.B, P.n, P.begin, P.count,
+                   P.p2p_poff, P.p2p_partial, P.perm, P.far_phi, P.far_E, (double *)pot, (double *)field);
+    else
+        FMM_LAUNCH((k_p2p_combine<float, double>), grid, 128, 0, P.stream, P.B, P.n, P.begin, P.count,
+                   P.p2p_poff, P.p2p_partial, P.perm, P.far_phi, P.far_E, (float *)pot, (float *)field);
     return cudaGetLastError();
 }
 
