@@ -522,7 +522,12 @@ def bench_serve(args, rank, world, local):
     [1e3, 1e6], uniform / Plummer / Gaussian-mixture points (1/3 each),
     target error 1e-5 (p = args.serve_p, theta = 0.5, ~100 points per leaf,
     mixed form), admitted under a device-memory budget by the continuous-batching
-    server; throughput and p50/p99 latency."""
+    server: throughput and p50/p99 latency at the offered rate, then the same
+    requests all queued at once (the server's capacity). A share of the
+    requests (--repeat-frac) repeats an earlier request's point set with new
+    charges and names it, so its plan stays resident. Comparator: the plain
+    FP64 form, one solve at a time, on an evenly spaced sample of the same
+    requests."""
     import torch
     import paper_2002_04894_gb300 as fmm
     from paper_2002_04894_gb300 import serve
@@ -534,34 +539,54 @@ def bench_serve(args, rank, world, local):
             for k in kinds for s in range(2)}
     rng = np.random.default_rng([rank, 11])
     arr = serve.poisson_arrivals(args.requests, args.rate, seed=rank)
-    reqs = []
+    reqs, sets = [], []
     for i in range(args.requests):
-        n = int(10 ** rng.uniform(3.0, 6.0))
-        k = kinds[rng.integers(0, 3)]
-        x, q = pool[(k, int(rng.integers(0, 2)))]
-        o = int(rng.integers(0, 1_000_000 - n + 1))
-        reqs.append(serve.Request(i, x[o:o + n], q[o:o + n], arrival=float(arr[i]), p=args.serve_p,
-                                  theta=0.5, prec=fmm.FMM_PREC_MIXED))
-    srv = serve.FmmServer(budget=int(args.budget_gb * (1 << 30)), workers=args.workers)
+        if sets and rng.random() < args.repeat_frac:
+            j = int(rng.integers(0, len(sets)))
+            x, n, geom = sets[j]
+            q = np.random.default_rng([rank, 13, i]).uniform(-1.0, 1.0, size=n)
+        else:
+            n = int(10 ** rng.uniform(3.0, 6.0))
+            k = kinds[rng.integers(0, 3)]
+            x, q = pool[(k, int(rng.integers(0, 2)))]
+            o = int(rng.integers(0, 1_000_000 - n + 1))
+            x, q = x[o:o + n], q[o:o + n]
+            geom = ("req", i) if args.repeat_frac > 0 else None
+            sets.append((x, n, geom))
+        reqs.append(serve.Request(i, x, q, arrival=float(arr[i]), p=args.serve_p, theta=0.5,
+                                  prec=fmm.FMM_PREC_MIXED, geom=geom))
+    cache = int(args.cache_gb * (1 << 30)) if args.repeat_frac > 0 else 0
+    srv = serve.FmmServer(budget=int(args.budget_gb * (1 << 30)), workers=args.workers, cache_bytes=cache)
     warm = [serve.Request(-1 - j, reqs[j].points, reqs[j].charges, 0.0, p=args.serve_p) for j in range(4)]
     srv.run(warm, realtime=False)
+    pts = sum(len(r.charges) for r in reqs)
     launches0 = fmm.fmm_kernel_launches()
     t0 = time.perf_counter()
     with ClockSampler(local) as clk:
         res, adm = srv.run(reqs, realtime=True)
     makespan = time.perf_counter() - t0
     launches = fmm.fmm_kernel_launches() - launches0
-    pts = sum(len(r.charges) for r in reqs)
+    hits_rt = srv.hits
+    # capacity: every request queued at t = 0
+    srv.close()
+    srv2 = serve.FmmServer(budget=int(args.budget_gb * (1 << 30)), workers=args.workers, cache_bytes=cache)
+    sat = [serve.Request(r.rid, r.points, r.charges, 0.0, p=r.p, theta=r.theta, prec=r.prec, geom=r.geom)
+           for r in reqs]
+    t1 = time.perf_counter()
+    res_sat, _ = srv2.run(sat, realtime=False)
+    t_sat = time.perf_counter() - t1
+    srv2.close()
     errs = []
     for r, rr in list(zip(reqs, res))[:: max(1, len(reqs) // 20)]:
         n = len(r.charges)
         tg = inputs.sample_targets(n, 100, r.rid)
         dp = fmm.fmm_direct(np.ascontiguousarray(r.points), np.ascontiguousarray(r.charges), tg)[0]
         errs.append(float(np.linalg.norm(rr.potentials[tg] - dp) / np.linalg.norm(dp)))
-    # comparator: the plain FP64 form, one solve at a time, on the first
-    # requests (same parameters), as points per second of solve time
+    # comparator: the plain FP64 form, one solve at a time, on an evenly
+    # spaced sample of the same requests, as points per second of solve time
+    sample = reqs[:: max(1, len(reqs) // args.fp64_sample)]
     t64, pts64 = 0.0, 0
-    for r in reqs[: min(len(reqs), 40)]:
+    for r in sample:
         lv = serve.default_levels(len(r.charges))
         torch.cuda.synchronize()
         a = time.perf_counter()
@@ -582,11 +607,17 @@ def bench_serve(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serve", "requests": args.requests, "rate_per_s": args.rate,
                    "n_range": [1000, 1000000], "budget_gb": args.budget_gb, "workers": args.workers,
-                   "p": args.serve_p, "theta": 0.5, "leaf": 100},
+                   "p": args.serve_p, "theta": 0.5, "leaf": 100, "repeat_frac": args.repeat_frac,
+                   "resident_cache_gb": cache / (1 << 30)},
         "latency_ms": lat, "requests_per_s": round(args.requests / makespan, 2),
+        "points": int(pts), "resident_hits": hits_rt,
+        "capacity": {"value": round(pts / t_sat / 1e6, 4), "unit": "Mpoints/s", "s": round(t_sat, 2),
+                     "requests_per_s": round(args.requests / t_sat, 2),
+                     "how": "the same requests all queued at t = 0"},
         "admission_peak_gb": round(adm.peak / (1 << 30), 3),
         "fp64_one_solve_at_a_time": {"value": round(pts64 / t64 / 1e6, 4), "unit": "Mpoints/s",
-                                     "requests": min(len(reqs), 40)},
+                                     "requests": len(sample), "points": int(pts64),
+                                     "sample": f"every {max(1, len(reqs) // args.fp64_sample)}th request"},
         "accuracy": {"max_rel_l2_phi": max(errs), "requests_checked": len(errs), "target": 1e-5},
         "gpu_launches": int(launches), "clocks": clk.summary(),
     }
@@ -773,7 +804,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--systems", type=int, default=512, help="batch mode: number of systems")
-    ap.add_argument("--requests", type=int, default=2000, help="serve mode: number of requests")
+    ap.add_argument("--requests", type=int, default=10000, help="serve mode: number of requests")
+    ap.add_argument("--repeat-frac", type=float, default=0.0,
+                    help="serve mode: share of requests repeating an earlier point set (resident plans)")
+    ap.add_argument("--cache-gb", type=float, default=40.0, help="serve mode: resident-plan share of the budget")
+    ap.add_argument("--fp64-sample", type=int, default=60, help="serve mode: requests in the FP64 comparator")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve mode: device memory budget")
     ap.add_argument("--workers", type=int, default=8, help="serve mode: concurrent solves")

@@ -85,6 +85,13 @@ enum fmm_prec { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
                                midpoint) instead of its cell's. The cells still decide
                                the splits (fmm_plan_tree's lo/hi stay the cells).
                                Clustered inputs then get far fewer near-field pairs. */
+#define FMM_FLAG_ROOT_CELL 16 /* the root cell is fmm_opts.root_lo/root_hi instead of the
+                               points' bounding box. It must hold every point
+                               (FMM_EINVAL otherwise). With it, the plan of the points
+                               of one box of a larger tree, given in ascending original
+                               index with that box's cell, is that box's subtree bit for
+                               bit: how a rank builds its part of a tree split over
+                               several devices. */
 #define FMM_FLAG_TC_M2L 4   /* mixed form, p <= 12: M2L contractions on the tensor
                                cores (tcgen05, split TF32) instead of the CUDA cores;
                                same accuracy, slower at the orders measured (the
@@ -126,6 +133,9 @@ typedef struct fmm_opts {
                        4^s candidate pairs), M2M, M2L and L2L then act only on
                        every s-th bisection level, and the levels between carry
                        empty lists and zero expansions. */
+    double root_lo[3], root_hi[3];
+                    /* root cell, read only with FMM_FLAG_ROOT_CELL (lo <= hi,
+                       finite) */
 } fmm_opts;
 
 /*
@@ -341,6 +351,56 @@ int fmm_batch_create(const fmm_plan_t *plans, int nplans, const void *const *cha
                      fmm_batch_t *out);
 int fmm_batch_launch(fmm_batch_t batch, void *stream);
 void fmm_batch_destroy(fmm_batch_t batch);
+
+/*
+ * One rank's part of a system split over several devices (Sec. 2.2 and
+ * Algorithms 2-4: local trees under the ranks' boxes of the top levels,
+ * halo lists between ranks, multipoles and leaf points exchanged for the
+ * cross-rank M2L and P2P). The caller does the bookkeeping and the exchange
+ * (paper_2002_04894_gb300/dist.py); these calls do the arithmetic. Plain FP64
+ * plans only (FMM_EINVAL otherwise). All pointers are DEVICE memory of the
+ * current device; work is asynchronous on `stream`. Boxes are given as
+ * (level, index within the level) of the plan's own tree; coefficient arrays
+ * are n x ncoef complex doubles, (n, m) at n(n+1)/2 + m as for
+ * fmm_eval_expansions. Errors: FMM_EINVAL, FMM_ENOMEM, FMM_ECUDA.
+ *
+ * fmm_theta_test      weak[i] = 1 if boxes (ca[i], ra[i]) and (cb[i], rb[i])
+ *                     are weakly connected by Eq. 2.2 (the list build's test,
+ *                     bit for bit), else 0; centres n x 3.
+ * fmm_eval_upward     charge gather, P2M and M2M on every level of the plan
+ *                     (its root included); clears the received terms.
+ * fmm_plan_multipoles out[i] = multipole of box idx[i] of `level`.
+ * fmm_plan_add_locals adds L[i] to the local expansion of box idx[i].
+ * fmm_m2l_external    adds the M2L of multipole M[i] about centre[i] to the
+ *                     local expansion of box tgt[i] of `level`.
+ * fmm_plan_leaf_points the points of leaves leaf[i] as (x, y, z, q) doubles
+ *                     from row off[i] of out (off: n + 1 int64, the caller's
+ *                     prefix sum of the leaves' counts from fmm_plan_tree).
+ * fmm_p2p_external    adds to the points of leaf tgt[i] the potential and
+ *                     field of the sources src[off[i] .. off[i+1]) (x, y, z, q
+ *                     rows; pairs at zero distance skipped).
+ * fmm_eval_downward   M2L within the plan, the added local expansions, L2L,
+ *                     L2P, the received near-field terms and P2P: potentials
+ *                     and fields in the order the plan's points were given.
+ * fmm_translate       for i < n, dst[i] += the translation of src[i] about
+ *                     csrc[i] to cdst[i]: kind 0 M2M, 1 M2L, 2 L2L (direct
+ *                     sums; for the few boxes above the ranks' subtrees).
+ */
+int fmm_theta_test(double theta, int64_t n, const double *ca, const double *ra, const double *cb,
+                   const double *rb, uint8_t *weak, void *stream);
+int fmm_eval_upward(fmm_plan_t plan, const void *charges, void *stream);
+int fmm_plan_multipoles(fmm_plan_t plan, int level, int64_t n, const int32_t *idx, double *out, void *stream);
+int fmm_plan_add_locals(fmm_plan_t plan, int level, int64_t n, const int32_t *idx, const double *L,
+                        void *stream);
+int fmm_m2l_external(fmm_plan_t plan, int level, int64_t n, const int32_t *tgt, const double *M,
+                     const double *centre, void *stream);
+int fmm_plan_leaf_points(fmm_plan_t plan, int64_t n, const int32_t *leaf, const int64_t *off, double *out,
+                         void *stream);
+int fmm_p2p_external(fmm_plan_t plan, int64_t n, const int32_t *tgt, const int64_t *off, const double *src,
+                     void *stream);
+int fmm_eval_downward(fmm_plan_t plan, void *potentials, void *fields, void *stream);
+int fmm_translate(int kind, int p, int64_t n, const double *src, const double *csrc, const double *cdst,
+                  double *dst, void *stream);
 
 /*
  * fmm_measure_peak -- throughput of one arithmetic pipe of the current device,

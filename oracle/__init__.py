@@ -69,7 +69,7 @@ def _lib():
     lib.orc_theta_weak.argtypes = [C.c_double, _f64p, C.c_double, _f64p, C.c_double]
     lib.orc_theta_weak.restype = C.c_int
     lib.orc_build.argtypes = [C.c_int64, _f64p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
-                              C.c_int]
+                              C.c_int, C.c_void_p, C.c_void_p]
     lib.orc_build.restype = C.c_void_p
     lib.orc_free.argtypes = [C.c_void_p]
     lib.orc_nbox.argtypes = [C.c_void_p]
@@ -181,16 +181,22 @@ class Tree:
     """Balanced tree, connectivity and expansions of one point set."""
 
     def __init__(self, x, levels: int, p: int, theta: float, eta: float = 1.0, step: int = 1,
-                 tight: bool = False):
+                 tight: bool = False, root_cell=None):
         """`levels` bisections; `step` bisections per FMM level (3: octree
         levels of 8 children), `levels` a multiple of it; `tight`: box centres
-        and radii from each box's own points instead of its cell."""
+        and radii from each box's own points instead of its cell; `root_cell`
+        = (lo[3], hi[3]) replaces the points' bounding box as the root cell."""
         x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
         if step < 1 or levels % step:
             raise ValueError("levels must be a multiple of step >= 1")
         self.n, self.levels, self.p, self.theta, self.eta, self.step = len(x), levels, p, theta, eta, step
         self.tight = bool(tight)
-        self._h = _lib().orc_build(self.n, x, levels, p, theta, eta, step, int(self.tight))
+        rl = rh = None
+        if root_cell is not None:
+            self._root = (np.ascontiguousarray(root_cell[0], np.float64).reshape(3),
+                          np.ascontiguousarray(root_cell[1], np.float64).reshape(3))
+            rl, rh = self._root[0].ctypes.data, self._root[1].ctypes.data
+        self._h = _lib().orc_build(self.n, x, levels, p, theta, eta, step, int(self.tight), rl, rh)
         if not self._h:
             raise MemoryError("oracle build failed")
 

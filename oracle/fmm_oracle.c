@@ -364,7 +364,7 @@ static void set_geometry(orc_fmm *F, int64_t g)
  * bounding box. Each box's point list is kept in ascending original index;
  * the left child takes the floor(n/2) smallest (coordinate, index) keys.
  */
-static void orc_build_tree(orc_fmm *F)
+static void orc_build_tree(orc_fmm *F, const double *root_lo, const double *root_hi)
 {
     int64_t n = F->n, nb = nbox_of(F->levels);
     int64_t *lists = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
@@ -373,15 +373,16 @@ static void orc_build_tree(orc_fmm *F)
     char *left = malloc(n > 0 ? n : 1);
     for (int64_t i = 0; i < n; i++)
         lists[i] = i;
-    /* root cell: tight bounding box */
+    /* root cell: tight bounding box, or the given cell (a box of a larger
+     * tree, whose subtree this tree then is) */
     for (int a = 0; a < 3; a++) {
         double lo = F->x[a], hi = F->x[a];
         for (int64_t i = 1; i < n; i++) {
             if (F->x[3 * i + a] < lo) lo = F->x[3 * i + a];
             if (F->x[3 * i + a] > hi) hi = F->x[3 * i + a];
         }
-        F->lo[a] = lo;
-        F->hi[a] = hi;
+        F->lo[a] = root_lo ? root_lo[a] + 0.0 : lo;
+        F->hi[a] = root_hi ? root_hi[a] + 0.0 : hi;
     }
     F->begin[0] = 0;
     F->count[0] = n;
@@ -612,7 +613,7 @@ static void orc_build_lists(orc_fmm *F)
 /* ------------------------------------------------------------------ */
 
 orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, double eta,
-                   int step, int tight)
+                   int step, int tight, const double *root_lo, const double *root_hi)
 {
     if (step < 1 || levels % step != 0)
         return NULL;
@@ -639,7 +640,7 @@ orc_fmm *orc_build(int64_t n, const double *x, int levels, int p, double theta, 
     F->plane = calloc(nb, sizeof(double));
     F->M = calloc(nb * orc_ncoef(p), sizeof(cplx));
     F->L = calloc(nb * orc_ncoef(p), sizeof(cplx));
-    orc_build_tree(F);
+    orc_build_tree(F, root_lo, root_hi);
     if (F->tight)
         orc_tight_geometry(F);
     orc_build_lists(F);

@@ -25,6 +25,7 @@ FMM_FLAG_PROFILE = 1
 FMM_FLAG_ETA = 2
 FMM_FLAG_TC_M2L = 4
 FMM_FLAG_TIGHT = 8
+FMM_FLAG_ROOT_CELL = 16
 STAGES = ("tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p")
 STATUS = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ENONFINITE",
           -4: "FMM_ECAPACITY", -5: "FMM_ETIMEDOUT", -6: "FMM_ECUDA", -7: "FMM_EINTERNAL"}
@@ -40,7 +41,8 @@ class FmmError(RuntimeError):
 class fmm_opts(C.Structure):
     _fields_ = [("levels", C.c_int), ("p", C.c_int), ("theta", C.c_double),
                 ("prec", C.c_int), ("flags", C.c_int), ("eta", C.c_double),
-                ("bisections_per_level", C.c_int)]
+                ("bisections_per_level", C.c_int), ("root_lo", C.c_double * 3),
+                ("root_hi", C.c_double * 3)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -65,8 +67,16 @@ EXPORTS = ("fmm_plan", "fmm_eval", "fmm_destroy", "fmm_direct", "fmm_plan_stats"
            "fmm_plan_tree", "fmm_plan_list", "fmm_eval_expansions", "fmm_strerror",
            "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches",
            "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy",
-           "fmm_eval_check", "fmm_pool_trim", "fmm_set_list_capacity", "fmm_measure_peak")
+           "fmm_eval_check", "fmm_pool_trim", "fmm_set_list_capacity", "fmm_measure_peak",
+           "fmm_theta_test", "fmm_eval_upward", "fmm_plan_multipoles", "fmm_plan_add_locals",
+           "fmm_m2l_external", "fmm_plan_leaf_points", "fmm_p2p_external", "fmm_eval_downward",
+           "fmm_translate")
 FMM_NOALLOC_MAX_POINTS, FMM_NOALLOC_MAX_LEVELS = 4096, 12
+
+
+def ncoef_of(p: int) -> int:
+    """Stored coefficients (n, m), 0 <= m <= n <= p, of one expansion."""
+    return (p + 1) * (p + 2) // 2
 
 
 def lib_path() -> str:
@@ -120,6 +130,17 @@ def load(build: bool = True) -> C.CDLL:
     lib.fmm_batch_launch.restype = i32
     lib.fmm_batch_destroy.argtypes = [vp]
     lib.fmm_batch_destroy.restype = None
+    for name, args in (("fmm_theta_test", [C.c_double, i64, vp, vp, vp, vp, vp, vp]),
+                       ("fmm_eval_upward", [vp, vp, vp]),
+                       ("fmm_plan_multipoles", [vp, i32, i64, vp, vp, vp]),
+                       ("fmm_plan_add_locals", [vp, i32, i64, vp, vp, vp]),
+                       ("fmm_m2l_external", [vp, i32, i64, vp, vp, vp, vp]),
+                       ("fmm_plan_leaf_points", [vp, i64, vp, vp, vp, vp]),
+                       ("fmm_p2p_external", [vp, i64, vp, vp, vp, vp]),
+                       ("fmm_eval_downward", [vp, vp, vp, vp]),
+                       ("fmm_translate", [i32, i32, i64, vp, vp, vp, vp, vp])):
+        getattr(lib, name).argtypes = args
+        getattr(lib, name).restype = i32
     lib.fmm_measure_peak.argtypes = [i32, i64, vp, vp, vp]
     lib.fmm_measure_peak.restype = i32
     lib.fmm_set_list_capacity.argtypes = [i64]
@@ -220,19 +241,25 @@ class Plan:
 # ---------------------------------------------------------------------------
 def fmm_plan(points, levels: int, p: int, theta: float, prec: int = FMM_PREC_FP64,
              stream=None, allocator="torch", profile: bool = False, eta: float = 1.0,
-             bisections_per_level: int = 1, tc_m2l: bool = False, tight: bool = False) -> Plan:
+             bisections_per_level: int = 1, tc_m2l: bool = False, tight: bool = False,
+             root_cell=None) -> Plan:
     """Build the tree and connectivity for n x 3 `points`; eta in [0, 1] is
     the split adaptivity (1: balanced median splits, 0: cell bisection);
     bisections_per_level = 3 makes octree levels (`levels` counts bisections);
-    tight = True takes box centres and radii from the boxes' own points."""
+    tight = True takes box centres and radii from the boxes' own points;
+    root_cell = (lo[3], hi[3]) fixes the root cell (it must hold every point)."""
     lib = load()
     ptr, keep = _ptr(points)
     n = int(points.shape[0])
     dt = _dtype_code(points)
     flags = ((FMM_FLAG_PROFILE if profile else 0) | (FMM_FLAG_ETA if float(eta) != 1.0 else 0)
-             | (FMM_FLAG_TC_M2L if tc_m2l else 0) | (FMM_FLAG_TIGHT if tight else 0))
+             | (FMM_FLAG_TC_M2L if tc_m2l else 0) | (FMM_FLAG_TIGHT if tight else 0)
+             | (FMM_FLAG_ROOT_CELL if root_cell is not None else 0))
     opts = fmm_opts(int(levels), int(p), float(theta), int(prec), flags, float(eta),
                     int(bisections_per_level))
+    if root_cell is not None:
+        opts.root_lo[:] = [float(v) for v in root_cell[0]]
+        opts.root_hi[:] = [float(v) for v in root_cell[1]]
     alloc, cbs = (None, None)
     if allocator == "torch":
         alloc, cbs = _torch_allocator()

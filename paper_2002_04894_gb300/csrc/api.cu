@@ -60,9 +60,6 @@ int sm_count() {
     return v;
 }
 
-cudaError_t eval_expansions(Plan &P, const void *charges, int dtype);
-cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype);
-
 namespace {
 
 // Without a caller's allocator, plan memory comes from a stream-ordered pool
@@ -148,10 +145,6 @@ void *palloc(Plan &P, size_t bytes) { return arena_alloc(P, P.persist, bytes); }
 using fmm::Plan;
 using fmm::cuda_status;
 
-struct fmm_plan_s {
-    Plan P;
-};
-
 struct fmm_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -231,7 +224,13 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     if (opts->p < 0 || opts->p > FMM_MAX_P) return FMM_EINVAL;
     if (!(opts->theta >= 0.0 && opts->theta < 1.0)) return FMM_EINVAL;
     if (opts->prec != FMM_PREC_FP64 && opts->prec != FMM_PREC_MIXED) return FMM_EINVAL;
-    if (opts->flags & ~(FMM_FLAG_PROFILE | FMM_FLAG_ETA | FMM_FLAG_TC_M2L | FMM_FLAG_TIGHT)) return FMM_EINVAL;
+    if (opts->flags & ~(FMM_FLAG_PROFILE | FMM_FLAG_ETA | FMM_FLAG_TC_M2L | FMM_FLAG_TIGHT | FMM_FLAG_ROOT_CELL))
+        return FMM_EINVAL;
+    if (opts->flags & FMM_FLAG_ROOT_CELL)
+        for (int a = 0; a < 3; a++)
+            if (!(std::isfinite(opts->root_lo[a]) && std::isfinite(opts->root_hi[a]) &&
+                  opts->root_lo[a] <= opts->root_hi[a]))
+                return FMM_EINVAL;
     if ((opts->flags & FMM_FLAG_ETA) && !(opts->eta >= 0.0 && opts->eta <= 1.0)) return FMM_EINVAL;
     const int step = opts->bisections_per_level == 0 ? 1 : opts->bisections_per_level;
     if (step < 1 || step > 3 || opts->levels % step != 0) return FMM_EINVAL;
@@ -261,6 +260,13 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     P.profile = (opts->flags & FMM_FLAG_PROFILE) != 0;
     P.tc_m2l_opt = (opts->flags & FMM_FLAG_TC_M2L) != 0;
     P.tight = (opts->flags & FMM_FLAG_TIGHT) != 0;
+    if (opts->flags & FMM_FLAG_ROOT_CELL) {
+        P.root.given = 1;
+        for (int a = 0; a < 3; a++) {
+            P.root.lo[a] = opts->root_lo[a];
+            P.root.hi[a] = opts->root_hi[a];
+        }
+    }
 
     auto fail = [&](int status) {
         release(P);
@@ -330,6 +336,7 @@ int fmm_plan(const void *points, int64_t n, int dtype, const fmm_opts *opts,
     e = cudaStreamSynchronize(P.stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     if (herr & 1) return fail(FMM_ENONFINITE);
+    if (herr & 4) return fail(FMM_EINVAL);  // a point lies outside the given root cell
     if (herr) return fail(FMM_EINTERNAL);  // the partition's consistency check failed
 
     fmm::stage_mark(P, FMM_STAGE_LISTS, 0);
@@ -364,6 +371,7 @@ int fmm_eval(fmm_plan_t plan, const void *charges, void *potentials, void *field
     if (fmm::ptr_kind(charges) < 0 || fmm::ptr_kind(potentials) < 0 || fmm::ptr_kind(fields) < 0)
         return FMM_EINVAL;
     Plan &P = plan->P;
+    P.full_upward = P.ext_active = false;  // a whole evaluation: nothing from other ranks
     P.stream = (cudaStream_t)stream;
     const size_t es = dsize(P.dtype), n = (size_t)P.n;
     const bool dq = is_device_ptr(charges), dp = is_device_ptr(potentials),

@@ -158,7 +158,19 @@ k_l2p(int B, int p, int64_t npts, const double *__restrict__ x, const double *__
 
 }  // namespace
 
-cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
+// the first level with weak pairs: multipoles above it are never read (no
+// M2L there, and M2M into them would only feed unused levels), so they are
+// left zero unless the plan forms every level (a rank of a split system
+// sends its root's multipole); local expansions above it are exactly zero
+static int first_weak_level(const Plan &P) {
+    int lw = P.B + 1;
+    for (int l = P.B; l >= 1; l--)
+        if (P.nweak[l] > 0) lw = l;
+    return P.full_upward ? 0 : lw;
+}
+
+// P2M and M2M (Algorithm 1)
+cudaError_t eval_upward(Plan &P, const void *charges, int dtype) {
     cudaStream_t st = P.stream;
     const int64_t n = P.n;
     const int nc = P.nc;
@@ -177,12 +189,7 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
                    st, P.B, P.p, P.x, P.y, P.z, P.q, P.begin, P.count, P.centre, P.M);
     }
     stage_mark(P, FMM_STAGE_P2M, 1);
-    // the first level with weak pairs: multipoles above it are never read (no
-    // M2L there, and M2M into them would only feed unused levels), so they are
-    // left zero; local expansions above it are exactly zero
-    int lw = P.B + 1;
-    for (int l = P.B; l >= 1; l--)
-        if (P.nweak[l] > 0) lw = l;
+    const int lw = first_weak_level(P);
     // with 2^step children per box only every step-th bisection level holds
     // expansions; the levels in between stay zero
     const int sp = P.step;
@@ -195,29 +202,53 @@ cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
                             (size_t)((int64_t)1 << pl) * nc * sizeof(double2), st);
     }
     stage_mark(P, FMM_STAGE_M2M, 1);
-    // Algorithm 3: M2L at every level (each overwrites its level's L), then L2L downward
+    return cudaGetLastError();
+}
+
+// M2L at every level, then L2L downward (Algorithm 3), then L2P (Algorithm 4).
+// Local expansions and near-field terms from outside the plan (a split
+// system's other ranks) are added between M2L and L2L and after L2P.
+cudaError_t eval_downward(Plan &P) {
+    cudaStream_t st = P.stream;
+    const int64_t n = P.n;
+    const bool mixed = P.prec == FMM_PREC_MIXED;
+    const int lw = first_weak_level(P);
+    const int sp = P.step;
     stage_mark(P, FMM_STAGE_M2L, 0);
     {
         // all levels in one launch; every L is (re)written, the root's stays zero
         cudaError_t e = (mixed && P.Mf) ? m2l_f32_all(P) : m2l_all(P);
         if (e != cudaSuccess) return e;
+        if (P.ext_active) {
+            e = add_external_locals(P);
+            if (e != cudaSuccess) return e;
+        }
     }
     stage_mark(P, FMM_STAGE_M2L, 1);
     stage_mark(P, FMM_STAGE_L2L, 0);
     // L2L into a level whose parents hold nothing would only add zeros
     for (int l = sp; l <= P.B; l += sp)
-        if (l - sp >= lw) l2l_level(P, l);
+        if (l - sp >= lw || P.ext_active) l2l_level(P, l);
     stage_mark(P, FMM_STAGE_L2L, 1);
     stage_mark(P, FMM_STAGE_L2P, 0);
     if (mixed) {
         cudaError_t e = mixed_l2p(P);
         if (e != cudaSuccess) return e;
     } else {
-        FMM_LAUNCH(k_l2p, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * nc, st, P.B, P.p, n, P.x,
+        FMM_LAUNCH(k_l2p, (unsigned)P.nleaf, kExpThreads, sizeof(double2) * P.nc, st, P.B, P.p, n, P.x,
                    P.y, P.z, P.begin, P.count, P.centre, P.L, P.far_phi, P.far_E);
+        if (P.ext_active) {
+            cudaError_t e = add_external_near(P);
+            if (e != cudaSuccess) return e;
+        }
     }
     stage_mark(P, FMM_STAGE_L2P, 1);
     return cudaGetLastError();
+}
+
+cudaError_t eval_expansions(Plan &P, const void *charges, int dtype) {
+    cudaError_t e = eval_upward(P, charges, dtype);
+    return e == cudaSuccess ? eval_downward(P) : e;
 }
 
 }  // namespace fmm

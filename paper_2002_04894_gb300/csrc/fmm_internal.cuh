@@ -32,6 +32,12 @@ struct Arena {
     size_t left = 0, hint = 0;
 };
 
+// A given root cell (FMM_FLAG_ROOT_CELL), passed to the root kernel by value.
+struct RootCell {
+    double lo[3] = {0.0, 0.0, 0.0}, hi[3] = {0.0, 0.0, 0.0};
+    int given = 0;
+};
+
 struct Plan {
     int64_t n = 0;
     int B = 0, p = 0, nc = 0, prec = 0, dtype = 0, device = 0;
@@ -56,6 +62,14 @@ struct Plan {
     // boxes (nbox x 3 each) live until fmm_plan returns
     bool tight = false;
     double *tlo = nullptr, *thi = nullptr;
+    RootCell root;  // FMM_FLAG_ROOT_CELL
+    // one rank's part of a system split over several devices: every level's
+    // multipoles are formed; local expansions (nbox x nc) and near-field
+    // terms (4 per point, leaf order) from the other ranks are added during
+    // the downward pass
+    bool full_upward = false, ext_active = false;
+    double2 *L_ext = nullptr;
+    double *near_ext = nullptr;
     // connectivity: CSR per level over the 2^l target boxes of level l
     int32_t *wptr[FMM_MAX_LEVELS + 1] = {}, *wsrc[FMM_MAX_LEVELS + 1] = {};
     int32_t *sptr[FMM_MAX_LEVELS + 1] = {}, *ssrc[FMM_MAX_LEVELS + 1] = {};
@@ -190,6 +204,18 @@ cudaError_t direct_run(const void *points, const void *charges, int64_t n, int d
                        const int64_t *targets, int64_t nt, void *pot, void *field,
                        cudaStream_t s);
 cudaError_t m2l_setup(Plan &P);
+cudaError_t theta_pairs(double theta, int64_t n, const double *ca, const double *ra, const double *cb,
+                        const double *rb, uint8_t *weak, cudaStream_t st);
+cudaError_t eval_upward(Plan &P, const void *charges, int dtype);
+cudaError_t eval_expansions(Plan &P, const void *charges, int dtype);
+cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype);
+cudaError_t eval_downward(Plan &P);
+cudaError_t add_external_locals(Plan &P);
+cudaError_t add_external_near(Plan &P);
+// FP64 M2L from multipoles outside the plan into L_ext: n pairs (target box
+// `tgt[i]` of `level`, source i with multipole M[i] about centre[i])
+cudaError_t m2l_external(Plan &P, int level, int64_t n, const int32_t *tgt, const double2 *M,
+                         const double *centre);
 cudaError_t m2l_all(Plan &P);
 void m2m_level(Plan &P, int level);
 void l2l_level(Plan &P, int level);
@@ -214,3 +240,8 @@ cudaError_t p2p_combine(Plan &P, void *pot, void *field, int dtype);
 cudaError_t scan_exclusive(Plan &P, const int32_t *in, int32_t *out, int64_t n);
 
 }  // namespace fmm
+
+// The handle behind fmm_plan_t.
+struct fmm_plan_s {
+    fmm::Plan P;
+};

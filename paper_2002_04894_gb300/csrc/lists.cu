@@ -198,33 +198,39 @@ __global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *tile_sums) {
 // Per leaf: its sources over the strong list, its number of near-field work
 // units -- tiles of `tile` targets times k source segments, k = ceil(sources /
 // smax) -- and, when k > 1, the k * n_t partial-sum slots its split units fill;
-// the totals (pairs, units, slots) into acc[0..2] in 64 bits
+// the totals (pairs, units, slots) into acc[0..2] in 64 bits. One warp per
+// leaf, its lanes striding over the strong list (lists of large boxes in
+// sparse regions hold a good part of the tree).
 __global__ void k_p2p_work(int B, int tile, long long smax, const int32_t *sptr, const int32_t *ssrc,
                            const int32_t *count, unsigned long long *acc, long long *per_leaf,
                            int32_t *units_per_leaf, int32_t *parts_per_leaf) {
-    const int64_t nt = (int64_t)1 << B;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long v = 0, vu = 0, vp = 0;
-    if (t < nt) {
-        const int64_t off = nt - 1;
+    const int64_t nt = (int64_t)1 << B, off = nt - 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long v = 0, vu = 0, vp = 0;  // this warp's totals (lane 0)
+    for (int64_t t = warp; t < nt; t += nwarps) {
         unsigned long long ns = 0;
-        for (int32_t e = sptr[t]; e < sptr[t + 1]; e++) ns += (unsigned long long)count[off + ssrc[e]];
-        const int n_t = count[off + t];
-        v = ns * (unsigned long long)n_t;
-        per_leaf[t] = (long long)ns;
-        const unsigned long long k = ns > (unsigned long long)smax ? (ns + smax - 1) / smax : 1;
-        vu = (unsigned long long)((n_t + tile - 1) / tile) * k;
-        vp = k > 1 ? k * (unsigned long long)n_t : 0;
-        // stored as int32; the host rejects the plan if a total exceeds 2^31 - 1
-        units_per_leaf[t] = (int32_t)min(vu, 0x7fffffffull);
-        parts_per_leaf[t] = (int32_t)min(vp, 0x7fffffffull);
+        const int e1 = sptr[t + 1];
+#pragma unroll 4
+        for (int e = sptr[t] + lane; e < e1; e += 32) ns += (unsigned long long)count[off + ssrc[e]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        if (lane == 0) {
+            const int n_t = count[off + t];
+            per_leaf[t] = (long long)ns;
+            const unsigned long long k = ns > (unsigned long long)smax ? (ns + smax - 1) / smax : 1;
+            const unsigned long long u = (unsigned long long)((n_t + tile - 1) / tile) * k;
+            const unsigned long long pp = k > 1 ? k * (unsigned long long)n_t : 0;
+            // stored as int32; the host rejects the plan if a total exceeds 2^31 - 1
+            units_per_leaf[t] = (int32_t)min(u, 0x7fffffffull);
+            parts_per_leaf[t] = (int32_t)min(pp, 0x7fffffffull);
+            v += ns * (unsigned long long)n_t;
+            vu += u;
+            vp += pp;
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        v += __shfl_xor_sync(0xffffffffu, v, o);
-        vu += __shfl_xor_sync(0xffffffffu, vu, o);
-        vp += __shfl_xor_sync(0xffffffffu, vp, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (v) atomicAdd(acc, v);
         if (vu) atomicAdd(acc + 1, vu);
         if (vp) atomicAdd(acc + 2, vp);
@@ -243,46 +249,70 @@ __device__ __forceinline__ int unit_bucket(unsigned long long w) {
     return 255 - min(255, 4 * lg + frac);
 }
 
-// One thread per leaf: cuts the leaf's strong list into k segments of about
-// nsrc / k sources each (cumulative source count along the list) and emits
-// its units (leaf, first target, segment begin, segment end) with their
-// partial-sum slot (-1 when the leaf is not split) and weight bucket.
+// One warp per leaf: cuts the leaf's strong list into k segments of about
+// nsrc / k sources each and emits its units (leaf, first target, segment
+// begin, segment end) with their partial-sum slot (-1 when the leaf is not
+// split) and weight bucket. Segment j ends just after the first list entry
+// at which the cumulative source count reaches floor((j + 1) nsrc / k) (the
+// last one at the list's end); the lanes scan 32 entries at a time and a
+// ballot finds the entry for each such goal.
 __global__ void k_units_gen(int B, int tile, long long smax, const int32_t *count, const long long *nsrc,
                             const int32_t *sptr, const int32_t *ssrc, const int32_t *uoff,
                             const int32_t *poff, int4 *units, int32_t *upart, uint8_t *bucket) {
-    const int64_t nt = (int64_t)1 << B;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nt) return;
-    const int64_t off = nt - 1;
-    const int cnt = count[off + t];
-    if (cnt == 0) return;
-    const long long ns = nsrc[t];
-    const int k = ns > smax ? (int)((ns + smax - 1) / smax) : 1;
-    int u = uoff[t];
-    int e_lo = sptr[t];
-    long long c_lo = 0;
-    int e = e_lo;
-    long long c = 0;
-    for (int j = 0; j < k; j++) {
-        // segment j ends at the first list position where the cumulative
-        // source count reaches (j + 1) ns / k (the last one at the list's end)
-        const long long goal = j + 1 == k ? ns : (long long)(((unsigned long long)ns * (j + 1)) / k);
-        int e_hi = e;
-        long long c_hi = c;
-        if (j + 1 == k) {
-            e_hi = sptr[t + 1];
-            c_hi = ns;
-        } else {
-            while (e_hi < sptr[t + 1] && c_hi < goal) c_hi += count[off + ssrc[e_hi++]];
+    const int64_t nt = (int64_t)1 << B, off = nt - 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < nt; t += nwarps) {
+        const int cnt = count[off + t];
+        if (cnt == 0) continue;
+        const long long ns = nsrc[t];
+        const int k = ns > smax ? (int)((ns + smax - 1) / smax) : 1;
+        const int ntile = (cnt + tile - 1) / tile;
+        const int l0 = sptr[t], l1 = sptr[t + 1];
+        // emits segment j = [e_lo, e_hi) holding w sources (lanes over its tiles)
+        auto emit = [&](int j, int e_lo, int e_hi, long long w) {
+            for (int ti = lane; ti < ntile; ti += 32) {
+                const int u = uoff[t] + j * ntile + ti, tb = ti * tile;
+                units[u] = make_int4((int)t, tb, e_lo, e_hi);
+                upart[u] = k > 1 ? poff[t] + j * cnt : -1;
+                bucket[u] = (uint8_t)unit_bucket((unsigned long long)min(tile, cnt - tb) * (unsigned long long)w);
+            }
+        };
+        if (k == 1) {
+            emit(0, l0, l1, ns);
+            continue;
         }
-        for (int tb = 0; tb < cnt; tb += tile, u++) {
-            units[u] = make_int4((int)t, tb, e_lo, e_hi);
-            upart[u] = k > 1 ? poff[t] + j * cnt : -1;
-            bucket[u] = (uint8_t)unit_bucket((unsigned long long)min(tile, cnt - tb) *
-                                             (unsigned long long)(c_hi - c_lo));
+        int j = 0, e_lo = l0;
+        long long c_lo = 0, run = 0;  // cumulative sources before the chunk
+        for (int base = l0; base < l1 && j < k - 1; base += 32) {
+            const int e = base + lane;
+            long long c = e < l1 ? (long long)count[off + ssrc[e]] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {  // inclusive scan over the chunk
+                const long long y = __shfl_up_sync(0xffffffffu, c, o);
+                if (lane >= o) c += y;
+            }
+            const long long total = __shfl_sync(0xffffffffu, c, 31);
+            while (j < k - 1) {
+                const long long goal = (long long)(((unsigned long long)ns * (unsigned long long)(j + 1)) / k);
+                const unsigned hit = __ballot_sync(0xffffffffu, e < l1 && run + c >= goal);
+                if (!hit) break;
+                const int f = __ffs(hit) - 1;
+                const int e_hi = base + f + 1;
+                const long long c_hi = run + __shfl_sync(0xffffffffu, c, f);
+                emit(j, e_lo, e_hi, c_hi - c_lo);
+                e_lo = e_hi;
+                c_lo = c_hi;
+                j++;
+            }
+            run += total;
         }
-        e_lo = e = e_hi;
-        c_lo = c = c_hi;
+        for (; j < k; j++) {  // the last segment (and any left empty) end at the list's end
+            emit(j, e_lo, l1, ns - c_lo);
+            e_lo = l1;
+            c_lo = ns;
+        }
     }
 }
 
@@ -324,6 +354,23 @@ k_units_scatter(const int32_t *total, const uint8_t *bucket, const int4 *units, 
 }
 
 }  // namespace
+
+namespace {
+// the theta-criterion of the list build, on n given box pairs
+__global__ void k_theta_pairs(double theta, int64_t n, const double *ca, const double *ra, const double *cb,
+                              const double *rb, uint8_t *weak) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        weak[i] = theta_weak(theta, ca + 3 * i, ra[i], cb + 3 * i, rb[i]) ? 1 : 0;
+}
+}  // namespace
+
+cudaError_t theta_pairs(double theta, int64_t n, const double *ca, const double *ra, const double *cb,
+                        const double *rb, uint8_t *weak, cudaStream_t st) {
+    if (n == 0) return cudaGetLastError();
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    FMM_LAUNCH(k_theta_pairs, grid, 256, 0, st, theta, n, ca, ra, cb, rb, weak);
+    return cudaGetLastError();
+}
 
 cudaError_t scan_exclusive(Plan &P, const int32_t *in, int32_t *out, int64_t n) {
     if (n <= 0) {
@@ -444,7 +491,8 @@ cudaError_t lists_build(Plan &P) {
     P.p2p_poff = (int32_t *)palloc(P, (size_t)(nl + 1) * 4);
     if (!P.p2p_work_dev || !nsrc || !upl || !ppl || !uoff || !P.p2p_poff) return cudaErrorMemoryAllocation;
     cudaMemsetAsync(P.p2p_work_dev, 0, 24, st);
-    FMM_LAUNCH(k_p2p_work, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, tile, (long long)kP2PSegSources,
+    const unsigned wgrid = (unsigned)std::min<int64_t>((nl * 32 + 255) / 256, (int64_t)sm_count() * 32);
+    FMM_LAUNCH(k_p2p_work, wgrid, 256, 0, st, P.B, tile, (long long)kP2PSegSources,
                P.sptr[P.B], P.ssrc[P.B], P.count, P.p2p_work_dev, nsrc, upl, ppl);
     e = scan_exclusive(P, upl, uoff, nl);
     if (e == cudaSuccess) e = scan_exclusive(P, ppl, P.p2p_poff, nl);
@@ -473,7 +521,7 @@ cudaError_t lists_build(Plan &P) {
         return cudaErrorMemoryAllocation;
     P.p2p_nunits_dev = uoff + nl;
     P.p2p_nunits = nunits;
-    FMM_LAUNCH(k_units_gen, (unsigned)((nl + 255) / 256), 256, 0, st, P.B, tile, (long long)kP2PSegSources,
+    FMM_LAUNCH(k_units_gen, wgrid, 256, 0, st, P.B, tile, (long long)kP2PSegSources,
                P.count, nsrc, P.sptr[P.B], P.ssrc[P.B], uoff, P.p2p_poff, units, upart, bucket);
     FMM_LAUNCH(k_units_hist, (unsigned)nblk, kUnitBlock, 0, st, P.p2p_nunits_dev, bucket, nblk, bh);
     e = scan_exclusive(P, bh, boff, (int64_t)256 * nblk);

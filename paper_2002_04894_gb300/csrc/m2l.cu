@@ -63,9 +63,15 @@ __device__ __forceinline__ void fold_apply(const double *__restrict__ D, int n, 
     }
 }
 
+// With ext_M set, the sources are not boxes of the plan: pair g is (target
+// box PT.tgt[PT.lmin][g] of level PT.lmin, source g with multipole ext_M[g]
+// about ext_centre[g]) -- a split system's multipoles from another rank; the
+// targets are then in no particular order, so each pair adds its own result.
 __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ centre,
                               const double2 *__restrict__ M, double2 *__restrict__ L,
-                              const double *__restrict__ gtab, int ntab) {
+                              const double *__restrict__ gtab, int ntab,
+                              const double *__restrict__ ext_centre = nullptr,
+                              const double2 *__restrict__ ext_M = nullptr) {
     extern __shared__ double2 sm2[];
     const int nc = ncoef(p), T = blockDim.x, tid = threadIdx.x;
     // shared layout: [V: nc*T][U: (p+1)*T][W: (p+1)*T][tables: ntab doubles]
@@ -86,14 +92,26 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
     const bool valid = g < PT.off[PT.lmax + 1];
     int64_t gt = -1, gs = 0;
     double dx = 1.0, dy = 0.0, dz = 0.0;
+    const double *cs = ext_M ? ext_centre : centre;
+    const double2 *Ms = ext_M ? ext_M : M;
     if (valid) {
-        pair_of(PT, g, gt, gs);
-        dx = centre[3 * gt] - centre[3 * gs];
-        dy = centre[3 * gt + 1] - centre[3 * gs + 1];
-        dz = centre[3 * gt + 2] - centre[3 * gs + 2];
+        if (ext_M) {
+            gt = ((int64_t)1 << PT.lmin) - 1 + PT.tgt[PT.lmin][g];
+            gs = g;
+        } else {
+            pair_of(PT, g, gt, gs);
+        }
+        dx = centre[3 * gt] - cs[3 * gs];
+        dy = centre[3 * gt + 1] - cs[3 * gs + 1];
+        dz = centre[3 * gt + 2] - cs[3 * gs + 2];
     }
     bool same[5], head;
     seg_setup(gt, same, head);
+    if (ext_M) {  // external pairs come in any order: no run sums, one atomic add per pair
+#pragma unroll
+        for (int j = 0; j < 5; j++) same[j] = false;
+        head = valid;
+    }
     const double rxy = sqrt(dx * dx + dy * dy);
     const double rho = sqrt(dx * dx + dy * dy + dz * dz);
     const double rinv = 1.0 / rho;
@@ -107,7 +125,7 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
         double2 ph = make_double2(1.0, 0.0);
         for (int m = 0; m <= n; m++) {
             const int c = tri(n, m);
-            const double2 mv = valid ? M[gs * nc + c] : make_double2(0.0, 0.0);
+            const double2 mv = valid ? Ms[gs * nc + c] : make_double2(0.0, 0.0);
             u[m * T] = cscale(cmul(mv, ph), Ft[c] * (m ? 2.0 : 1.0));
             ph = cmul(ph, eai);
         }
@@ -525,6 +543,19 @@ void l2l_level(Plan &P, int l) {
     const int w = warps_per_block(nch);
     FMM_LAUNCH(k_l2l_warp, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l, P.step,
                P.p, P.centre, P.L, P.m2l_tab);
+}
+
+cudaError_t m2l_external(Plan &P, int level, int64_t n, const int32_t *tgt, const double2 *Msrc,
+                         const double *csrc) {
+    if (n == 0) return cudaGetLastError();
+    PairTable PT{};
+    PT.lmin = PT.lmax = level;
+    PT.tgt[level] = tgt;
+    PT.off[level] = 0;
+    PT.off[level + 1] = n;
+    FMM_LAUNCH(k_m2l_rot_f64, (unsigned)((n + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads, P.m2l_smem,
+               P.stream, PT, P.p, P.centre, (const double2 *)nullptr, P.L_ext, P.m2l_tab, P.m2l_ntab, csrc, Msrc);
+    return cudaGetLastError();
 }
 
 // FP64 M2L over all levels in one launch; accumulates into L (zeroed first)

@@ -113,12 +113,21 @@ k_prepare(const T *__restrict__ pts, int64_t n, double *__restrict__ x, double *
     }
 }
 
-__global__ void k_root(const unsigned long long *bbox, double *lo, double *hi, double *centre,
-                       double *radius, int32_t *axis) {
+// The root cell: the points' bounding box, or a given cell (FMM_FLAG_ROOT_CELL:
+// a box of a larger tree, so that this tree is that box's subtree) that must
+// hold every point (else error bit 4).
+__global__ void k_root(const unsigned long long *bbox, RootCell rc, double *lo, double *hi, double *centre,
+                       double *radius, int32_t *axis, int *err) {
     if (threadIdx.x != 0) return;
     for (int a = 0; a < 3; a++) {
-        lo[a] = dkey_inv(bbox[a]);
-        hi[a] = dkey_inv(bbox[3 + a]);
+        if (rc.given) {
+            lo[a] = rc.lo[a] + 0.0;  // -0.0 -> +0.0, as the points
+            hi[a] = rc.hi[a] + 0.0;
+            if (dkey(lo[a]) > bbox[a] || bbox[3 + a] > dkey(hi[a])) atomicOr(err, 4);
+        } else {
+            lo[a] = dkey_inv(bbox[a]);
+            hi[a] = dkey_inv(bbox[3 + a]);
+        }
     }
     box_geometry(lo, hi, centre, radius, axis, 0);
 }
@@ -681,7 +690,7 @@ cudaError_t tree_build(Plan &P, const void *pts, int dtype) {
     else
         FMM_LAUNCH(k_prepare<float>, pgrid, kThreads, 0, st, (const float *)pts, n, P.x, P.y, P.z,
                                                      P.perm, bbox, P.d_err);
-    FMM_LAUNCH(k_root, 1, 32, 0, st, bbox, P.lo, P.hi, P.centre, P.radius, P.axis);
+    FMM_LAUNCH(k_root, 1, 32, 0, st, bbox, P.root, P.lo, P.hi, P.centre, P.radius, P.axis, P.d_err);
 
     double *xa = P.x, *ya = P.y, *za = P.z, *xb = x2, *yb = y2, *zb = z2;
     int32_t *ia = P.perm, *ib = i2;
@@ -1047,7 +1056,7 @@ extern "C" int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, i
     else
         FMM_LAUNCH(k_prepare<float>, pgrid, kThreads, 0, st, (const float *)points, n, xa, ya, za, ia,
                    bbox, err);
-    FMM_LAUNCH(k_root, 1, 32, 0, st, bbox, lo, hi, centre, radius, axis);
+    FMM_LAUNCH(k_root, 1, 32, 0, st, bbox, RootCell{}, lo, hi, centre, radius, axis, err);
     for (int l = 0; l < levels; l++) {
         const int S = 1 << l;
         FMM_LAUNCH(k_split_small, S, kThreads, 0, st, l, xa, ya, za, ia, xb, yb, zb, ib, begin, count,

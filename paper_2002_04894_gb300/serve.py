@@ -9,6 +9,15 @@ expansions and near field of different requests interleave. Memory is given
 back when a solve completes, which admits the next requests in arrival order.
 Latency is measured from arrival to the result on the host.
 
+Resident plans. A request may name its point set (`geom`, any hashable key:
+the caller promises that requests with the same key carry the same points and
+parameters). The tree, lists and expansion storage of a named point set stay
+on the device after its first solve, in a least-recently-used cache bounded
+by `cache_bytes` of the budget; a later request with the same key and new
+charges runs only the evaluation. A resident plan serves one request at a
+time (a plan must not be used from two threads at once): a request that finds
+its plan busy builds a transient one.
+
 The admission policy (`Admission`) is plain Python and is unit-tested on the
 CPU with a stand-in executor; `FmmServer` runs it against the CUDA library.
 """
@@ -33,6 +42,7 @@ class Request:
     theta: float = 0.5
     prec: int = 1             # FMM_PREC_MIXED
     fields: bool = True
+    geom: object = None       # name of the point set (resident plan), or None
 
 
 @dataclass
@@ -45,6 +55,7 @@ class Result:
     done: float
     levels: int
     bytes_reserved: int
+    resident: bool = False    # served by a resident plan (evaluation only)
 
     @property
     def latency(self) -> float:
@@ -95,10 +106,18 @@ class Admission:
         self.active -= 1
 
 
-def run_schedule(requests, execute, budget: int, slots: int, realtime: bool = True, clock=time.perf_counter):
+def eval_bytes(n: int) -> int:
+    """Device memory of one evaluation on a resident plan: the request's input
+    and output copies."""
+    return n * 8 * 8 + (1 << 20)
+
+
+def run_schedule(requests, execute, budget: int, slots: int, realtime: bool = True, clock=time.perf_counter,
+                 need_of=None):
     """Admit requests in arrival order as slots and memory free up; `execute`
-    (request, t0) -> Result runs on a worker thread. Returns results in
-    request order and the admission record."""
+    (request, t0) -> Result runs on a worker thread; `need_of(request)` gives
+    the bytes to reserve (default: a whole plan, plan_bytes). Returns results
+    in request order and the admission record."""
     adm = Admission(budget, slots)
     pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
     results = {}
@@ -124,8 +143,11 @@ def run_schedule(requests, execute, budget: int, slots: int, realtime: bool = Tr
     i = 0
     while i < len(pending):
         req = pending[i]
-        lv = req.levels if req.levels >= 0 else default_levels(len(req.charges))
-        need = plan_bytes(len(req.charges), lv, req.p, req.prec == 1)
+        if need_of is not None:
+            need = need_of(req)
+        else:
+            lv = req.levels if req.levels >= 0 else default_levels(len(req.charges))
+            need = plan_bytes(len(req.charges), lv, req.p, req.prec == 1)
         with cv:
             while True:
                 now = clock() - t0
@@ -149,17 +171,74 @@ def run_schedule(requests, execute, budget: int, slots: int, realtime: bool = Tr
 
 class FmmServer:
     """Runs requests through the CUDA library with `workers` concurrent
-    solves, each on its own stream, under a device memory budget (bytes)."""
+    solves, each on its own stream, under a device memory budget (bytes), of
+    which `cache_bytes` may hold resident plans of named point sets."""
 
-    def __init__(self, budget: int, workers: int = 8):
+    def __init__(self, budget: int, workers: int = 8, cache_bytes: int = 0):
         import torch
 
         from . import load
         load()
         self.budget, self.workers = int(budget), int(workers)
+        self.cache_bytes = int(min(cache_bytes, budget))
         self._streams = [torch.cuda.Stream() for _ in range(self.workers)]
         self._free = list(range(self.workers))
         self._lock = threading.Lock()
+        self._cache = {}      # key -> [plan, bytes, last use, busy]
+        self._cached = 0
+        self._tick = 0
+        self.hits = 0
+        self._claims = {}     # rid -> resident plan claimed at admission
+
+    @staticmethod
+    def _key(req: Request):
+        lv = req.levels if req.levels >= 0 else default_levels(len(req.charges))
+        return (req.geom, lv, req.p, req.theta, req.prec)
+
+    def _need(self, req: Request) -> int:
+        """Bytes to reserve at admission. An idle resident plan of the
+        request's point set is claimed here (so the reservation holds: the
+        evaluation's copies only); otherwise a whole transient plan."""
+        n = len(req.charges)
+        if req.geom is not None:
+            with self._lock:
+                e = self._cache.get(self._key(req))
+                if e is not None and not e[3]:
+                    e[3] = True
+                    self._tick += 1
+                    e[2] = self._tick
+                    self.hits += 1
+                    self._claims[req.rid] = e[0]
+                    return eval_bytes(n)
+        lv = req.levels if req.levels >= 0 else default_levels(n)
+        return plan_bytes(n, lv, req.p, req.prec == 1)
+
+    def _keep(self, key, plan, nbytes) -> bool:
+        """Make `plan` resident (busy: its builder evaluates it next) if it
+        fits the cache after evicting idle least-recently-used plans; returns
+        False if it does not."""
+        from . import fmm_destroy
+        if nbytes > self.cache_bytes:
+            return False
+        with self._lock:
+            if key in self._cache:
+                return False
+            while self._cached + nbytes > self.cache_bytes:
+                idle = [(v[2], k) for k, v in self._cache.items() if not v[3]]
+                if not idle:
+                    return False
+                _, k = min(idle)
+                fmm_destroy(self._cache.pop(k)[0])
+                self._cached = sum(v[1] for v in self._cache.values())
+            self._tick += 1
+            self._cache[key] = [plan, nbytes, self._tick, True]  # busy: the caller evaluates it now
+            self._cached += nbytes
+            return True
+
+    def _release(self, key):
+        with self._lock:
+            if key in self._cache:
+                self._cache[key][3] = False
 
     def _execute(self, req: Request, t0: float) -> Result:
         import torch
@@ -178,22 +257,45 @@ class FmmServer:
             qh = np.ascontiguousarray(req.charges, dtype=xh.dtype)
             ph = np.empty(n, dtype=xh.dtype)
             fh = np.empty((n, 3), dtype=xh.dtype) if req.fields else None
+            key = self._key(req) if req.geom is not None else None
+            with self._lock:
+                plan = self._claims.pop(req.rid, None)
+            resident = plan is not None
             with torch.cuda.stream(s):
-                plan = fmm_plan(xh, lv, req.p, req.theta, prec=req.prec, stream=s)
+                if plan is None:
+                    plan = fmm_plan(xh, lv, req.p, req.theta, prec=req.prec, stream=s)
+                    keep = key is not None and self._keep(key, plan, plan_bytes(n, lv, req.p, req.prec == 1))
+                else:
+                    keep = True
                 try:
                     fmm_eval(plan, qh, ph, fh, stream=s)  # host outputs: returns when complete
                 finally:
-                    fmm_destroy(plan)
+                    if keep:
+                        self._release(key)
+                    else:
+                        fmm_destroy(plan)
             done = time.perf_counter() - t0
-            return Result(req.rid, ph, fh, req.arrival, 0.0, done, lv, 0)
+            return Result(req.rid, ph, fh, req.arrival, 0.0, done, lv, 0, resident)
         finally:
             with self._lock:
                 self._free.append(k)
 
     def run(self, requests, realtime: bool = True):
         """Serve `requests` (arrival times relative to now). Returns
-        (results in request order, admission record)."""
-        return run_schedule(requests, self._execute, self.budget, self.workers, realtime)
+        (results in request order, admission record). Resident plans live in
+        their own share of the budget (cache_bytes); transient work is
+        admitted against the rest."""
+        return run_schedule(requests, self._execute, self.budget - self.cache_bytes, self.workers, realtime,
+                            need_of=self._need)
+
+    def close(self):
+        """Destroy the resident plans."""
+        from . import fmm_destroy
+        with self._lock:
+            for v in self._cache.values():
+                fmm_destroy(v[0])
+            self._cache.clear()
+            self._cached = 0
 
 
 def build_plans(points, configs, prec: int = 1, workers: int = 8):

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "fmm.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(fmm_[a-z_]+)\s*\(", text)) - {"fmm_alloc_fn", "fmm_free_fn"})
+    return sorted(set(re.findall(r"\b(fmm_[a-z0-9_]+)\s*\(", text)) - {"fmm_alloc_fn", "fmm_free_fn"})
 
 
 def test_header_declares_the_boundary():
@@ -45,7 +45,7 @@ def test_invalid_arguments_rejected_before_any_device_work():
     for bad in (fmm.fmm_opts(-1, 4, 0.5, 0, 0), fmm.fmm_opts(25, 4, 0.5, 0, 0),
                 fmm.fmm_opts(3, 21, 0.5, 0, 0), fmm.fmm_opts(3, 4, 1.0, 0, 0),
                 fmm.fmm_opts(3, 4, -0.1, 0, 0), fmm.fmm_opts(3, 4, float("nan"), 0, 0),
-                fmm.fmm_opts(3, 4, 0.5, 7, 0), fmm.fmm_opts(3, 4, 0.5, 0, 16),
+                fmm.fmm_opts(3, 4, 0.5, 7, 0), fmm.fmm_opts(3, 4, 0.5, 0, 64),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, 1.5),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, -0.25),
                 fmm.fmm_opts(3, 4, 0.5, 0, fmm.FMM_FLAG_ETA, float("nan")),

@@ -93,3 +93,29 @@ def test_tuner_meets_target(gpu_lib):
     assert r.error <= 1e-5
     assert 32 <= 60000 / 2 ** r.config.levels <= 256
     assert r.config.theta in (0.4, 0.5, 0.6)
+
+
+def test_server_resident_plans_equal_fresh_solves(gpu_lib):
+    """Requests naming their point set (geom) reuse a resident plan with new
+    charges: each result equals a fresh solve of the same points and charges,
+    later requests of a point set are served resident, and a plan is never
+    used by two requests at once (same key arriving together)."""
+    fmm = gpu_lib
+    geoms = {g: inputs.points(kind, n, seed=200 + g)
+             for g, (kind, n) in enumerate([("plummer", 12000), ("uniform", 3000), ("gmm", 20000)])}
+    reqs = []
+    for i in range(12):
+        g = i % 3
+        x = geoms[g]
+        q = inputs.charges_uniform(len(x), seed=300 + i)
+        reqs.append(serve.Request(i, x, q, arrival=0.0 if i < 6 else 0.05 * i, p=8, prec=1, geom=("set", g)))
+    srv = serve.FmmServer(budget=1 << 31, workers=4, cache_bytes=1 << 30)
+    res, adm = srv.run(reqs, realtime=True)
+    assert srv.hits >= 3 and sum(r.resident for r in res) == srv.hits
+    for r in res:
+        q = reqs[r.rid]
+        plan = fmm.fmm_plan(q.points, serve.default_levels(len(q.charges)), q.p, q.theta, prec=1, allocator=None)
+        a, b = fmm.fmm_eval(plan, q.charges)
+        assert rel(r.potentials, a) <= TOL[1], r.rid
+        assert rel(r.fields, b) <= TOL[1], r.rid
+    srv.close()

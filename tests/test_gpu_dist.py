@@ -1,0 +1,135 @@
+"""The split of one system over G ranks (Sec. 2.2, Algorithms 2-4) with the
+device kernels doing the arithmetic, on ONE GPU: the G ranks are threads of
+this process, each with its own plan and stream, exchanging through the host
+(dist.ThreadComm) -- no kernel of one rank ever waits on another's. The
+assembled potentials and fields must equal the single plan of the whole
+system and the oracle's FMM (same lists and translations; only rounding
+differs), and every rank's plan must be the global tree's subtree.
+
+Also pinned directly: fmm_translate (the top levels' M2M, M2L, L2L) against
+the oracle's operators, and a plan built with a given root cell against the
+subtree of the global plan."""
+import threading
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+from paper_2002_04894_gb300 import dist, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_translate_matches_oracle_operators(gpu_lib, kind):
+    fmm = gpu_lib
+    rng = np.random.default_rng(kind)
+    p, n = 8, 6
+    nc = oracle.ncoef(p)
+    x = inputs.points("uniform", 200, seed=kind)
+    q = inputs.charges_uniform(200, seed=kind)
+    cs = rng.random((n, 3)) * 0.2 + 0.4
+    far = np.array([1.0, 0.5, -0.7]) if kind == 1 else np.zeros(3)   # M2L: well separated
+    cd = cs + far + (rng.random((n, 3)) - 0.5) * 0.2
+    src = np.zeros((n, nc), complex)
+    want = np.zeros((n, nc), complex)
+    for i in range(n):
+        if kind == 2:   # a local expansion: the M2L of a far cluster
+            oracle.m2l(oracle.p2m(x + 5.0, q, np.full(3, 5.5), p), np.full(3, 5.5), cs[i], p, src[i])
+            oracle.l2l(src[i], cs[i], cd[i], p, want[i])
+        else:
+            oracle.p2m(x * 0.1 + cs[i] - 0.05, q, cs[i], p, src[i])
+            (oracle.m2m if kind == 0 else oracle.m2l)(src[i], cs[i], cd[i], p, want[i])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s, a, b = d(src.view(np.float64)), d(cs), d(cd)
+    out = torch.zeros_like(s)
+    lib = fmm.load()
+    assert lib.fmm_translate(kind, p, n, s.data_ptr(), a.data_ptr(), b.data_ptr(), out.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream) == 0
+    got = out.cpu().numpy().view(complex)
+    for i in range(n):
+        assert np.abs(got[i] - want[i]).max() <= 1e-12 * np.abs(want[i]).max()
+
+
+@pytest.mark.parametrize("g", [1, 2])
+def test_root_cell_plan_is_the_global_subtree(gpu_lib, g):
+    fmm = gpu_lib
+    n, B = 30000, 10
+    x = inputs.points("plummer", n, seed=9)
+    glob = fmm.fmm_plan_tree(fmm.fmm_plan(torch.from_numpy(x).cuda(), B, 4, 0.5))
+    part = dist.Partition.from_tree(glob, g, B)
+    for r in range(1 << g):
+        mine = part.points_of[r]
+        loc = fmm.fmm_plan_tree(fmm.fmm_plan(torch.from_numpy(x[mine]).cuda(), B - g, 4, 0.5,
+                                             root_cell=(part.lo[r], part.hi[r])))
+        for l in range(B - g + 1):
+            hs = dist.heap(l + g, np.arange(*dist.owned(r, g, l + g)))
+            sl = slice((1 << l) - 1, (2 << l) - 1)
+            for k in ("centre", "radius", "lo", "hi", "count"):
+                np.testing.assert_array_equal(loc[k][sl], glob[k][hs], err_msg=f"{k} level {l}")
+        np.testing.assert_array_equal(mine[loc["perm"]], glob["perm"][glob["begin"][dist.heap(g, r)]:][:len(mine)])
+    # a point outside the given cell is rejected
+    with pytest.raises(fmm.FmmError):
+        fmm.fmm_plan(torch.from_numpy(x[part.points_of[0]]).cuda(), 3, 4, 0.5,
+                     root_cell=(part.lo[1], part.hi[1]))
+
+
+def _run_split(fmm, x, q, world, B, p, theta, tight):
+    g = world.bit_length() - 1
+    glob_plan = fmm.fmm_plan(torch.from_numpy(x).cuda(), B, p, theta, tight=tight)
+    part = dist.Partition.from_tree(fmm.fmm_plan_tree(glob_plan), g, B)
+    hub = dist.ThreadComm.Hub(world)
+    out, errors = {}, []
+
+    def run(rank):
+        try:
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                be = dist.GpuBackend(p, theta, tight, stream=stream)
+                comm = dist.ThreadComm(hub, rank, timeout=300.0)
+                mine = part.points_of[rank]
+                P = be.plan(x[mine], B - g, (part.lo[rank], part.hi[rank]))
+                H = dist.build_halo(rank, world, part, theta, lambda l: be.geo(P, l - g), comm, be)
+                phi, E = dist.evaluate(rank, world, part, H, P, q[mine], theta, comm, be)
+                m2l = sum(len(w) for (qq, l), w in H.weak.items() if l > g)
+                p2p = sum(len(s) for (qq, l), s in H.strong.items() if l == B)
+                out[rank] = (mine, phi, E, m2l, p2p)
+        except BaseException as e:  # noqa: BLE001 -- reported below
+            errors.append(e)
+
+    ts = [threading.Thread(target=run, args=(r,)) for r in range(world)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=600)
+    if errors:
+        raise errors[0]
+    assert len(out) == world
+    phi = np.zeros(len(q))
+    E = np.zeros((len(q), 3))
+    for mine, ph, e, _, _ in out.values():
+        phi[mine], E[mine] = ph, e
+    return glob_plan, phi, E, sum(o[3] for o in out.values()), sum(o[4] for o in out.values())
+
+
+@pytest.mark.parametrize("world,kind,n,B,p,tight", [
+    (2, "plummer", 20000, 9, 8, False),
+    (4, "gmm", 20000, 9, 8, True),
+    (2, "uniform", 8000, 8, 6, False),
+])
+def test_split_on_one_gpu_matches_single_plan(gpu_lib, world, kind, n, B, p, tight):
+    fmm = gpu_lib
+    x = inputs.points(kind, n, seed=5)
+    q = inputs.charges_uniform(n, seed=5)
+    glob_plan, phi, E, m2l, p2p = _run_split(fmm, x, q, world, B, p, 0.5, tight)
+    assert m2l > 0 and p2p > 0          # the halos carried cross-rank work
+    gp, gE = fmm.fmm_eval(glob_plan, torch.from_numpy(q).cuda())
+    gp, gE = gp.cpu().numpy(), gE.cpu().numpy()
+    tid = f"split{world}/{kind}/{n}/{B}/{p}"
+    assert parity.rel_l2(phi, gp) <= 1e-12 and parity.rel_l2(E, gE) <= 1e-12
+    parity.check(tid, "point_phi_vs_plan", parity.pointwise_phi(phi, gp), 1e-10)
+    op, oE = oracle.Tree(x, B, p, 0.5, tight=tight).eval(q)
+    assert parity.rel_l2(phi, op) <= 1e-12 and parity.rel_l2(E, oE) <= 1e-12
+    parity.check(tid, "point_phi_vs_oracle", parity.pointwise_phi(phi, op), 1e-10)
