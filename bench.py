@@ -80,9 +80,9 @@ def m2l_flops_per_pair(p):
 # workload, valid only while the kernel's source is the one that was captured
 # (checked by hash; otherwise null).
 MEASURED_TRAFFIC = {
-    ("plummer2m_l14_p12", "k_p2p_f32"): {"bytes": 274585600 + 123338496,
-                                         "source": "paper_2002_04894_gb300/csrc/mixed.cu",
-                                         "sha256_16": "6511125a5290178c"},
+    ("gmm8m_l17_p12", "k_p2p_f32"): {"bytes": 7879.7e6 + 537.0e6,
+                                     "source": "paper_2002_04894_gb300/csrc/mixed.cu",
+                                     "sha256_16": "bdf8d2bf19cbabc2"},
 }
 
 
@@ -792,6 +792,21 @@ def bench_galaxy(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def profile_solve(args):
+    """One plan + evaluation of the workload (device-resident inputs), then
+    exit: the command the ncu summaries are taken from."""
+    import torch
+    import paper_2002_04894_gb300 as fmm
+    fmm.load()
+    x, q, levels, p, theta = make_inputs(args.workload, seed=0)
+    prec = fmm.FMM_PREC_MIXED if (args.prec or WORKLOADS[args.workload][7]) == "mixed" else fmm.FMM_PREC_FP64
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, tight=WORKLOADS[args.workload][8])
+    pot, _ = fmm.fmm_eval(plan, qd)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "n": int(x.shape[0]), "checksum": float(pot.double().sum())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -803,6 +818,8 @@ def main():
                     help="steps of the plain FP64 form timed as the comparator (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="run one solve of the workload and nothing else (for ncu launch lists and captures)")
     ap.add_argument("--systems", type=int, default=512, help="batch mode: number of systems")
     ap.add_argument("--requests", type=int, default=10000, help="serve mode: number of requests")
     ap.add_argument("--repeat-frac", type=float, default=0.0,
@@ -815,6 +832,9 @@ def main():
     ap.add_argument("--serve-p", type=int, default=8, help="serve mode: expansion order (target 1e-5)")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.profile_solve:
+        profile_solve(args)
+        return
     if args.impl == "reference":
         bench_reference(args, rank, world)
     elif args.workload == "batch":

@@ -32,10 +32,25 @@ __device__ __forceinline__ bool theta_weak(double theta, const double *ca, doubl
     const double dx = __dsub_rn(ca[0], cb[0]);
     const double dy = __dsub_rn(ca[1], cb[1]);
     const double dz = __dsub_rn(ca[2], cb[2]);
-    const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     const double R = ra > rb ? ra : rb;
     const double r = ra > rb ? rb : ra;
-    if (!(theta > 0.0) || !(s > 0.0)) return false;
+    if (!(theta > 0.0)) return false;
+    {
+        // most candidates are far from the boundary: decided in single
+        // precision (relative error ~1e-6 of L^2 / (theta^2 s)) with a 1e-4
+        // margin, which cannot change the outcome; the rest, and any value
+        // out of the comfortable float range, go to the double-precision test
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz, ft = (float)theta;
+        const float fs = fx * fx + fy * fy + fz * fz;
+        const float fl = (float)R + ft * (float)r;
+        const float fa = fl * fl, fb = ft * ft * fs;
+        if (fs > 1e-30f && fs < 1e30f && fa > 1e-30f && fa < 1e30f && fb > 1e-30f && fb < 1e30f) {
+            if (fa < fb * (1.0f - 1e-4f)) return true;
+            if (fa > fb * (1.0f + 1e-4f)) return false;
+        }
+    }
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (!(s > 0.0)) return false;
     const double L = __dadd_rn(R, __dmul_rn(theta, r));
     // decided on squares when clearly away from the boundary (the rounding of
     // the sqrt form is ~2u, the margin 1e-12); the exact test otherwise, so

@@ -133,3 +133,33 @@ def test_split_on_one_gpu_matches_single_plan(gpu_lib, world, kind, n, B, p, tig
     op, oE = oracle.Tree(x, B, p, 0.5, tight=tight).eval(q)
     assert parity.rel_l2(phi, op) <= 1e-12 and parity.rel_l2(E, oE) <= 1e-12
     parity.check(tid, "point_phi_vs_oracle", parity.pointwise_phi(phi, op), 1e-10)
+
+
+def test_theta_test_matches_oracle_near_the_boundary(gpu_lib):
+    """fmm_theta_test (the list build's criterion, single-precision pre-test
+    with an exact double-precision decision near the boundary) agrees with
+    the oracle bit for bit on random pairs and on pairs placed within 1e-5,
+    1e-9 and 1e-15 of R + theta r = theta d."""
+    fmm = gpu_lib
+    rng = np.random.default_rng(17)
+    m = 4000
+    ca = rng.random((m, 3))
+    ra = rng.random(m) * 0.2
+    rb = rng.random(m) * 0.2
+    u = rng.normal(size=(m, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    theta = 0.5
+    d0 = (np.maximum(ra, rb) + theta * np.minimum(ra, rb)) / theta      # on the boundary
+    eps = np.concatenate([rng.uniform(-1, 1, m // 4) * 1.0,
+                          rng.choice([-1, 1], m // 4) * 1e-5, rng.choice([-1, 1], m // 4) * 1e-9,
+                          rng.choice([-1, 1], m - 3 * (m // 4)) * 1e-15])
+    cb = ca + u * (d0 * (1 + eps))[:, None]
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    out = torch.empty(m, dtype=torch.uint8, device="cuda")
+    t = [d(v) for v in (ca, ra, cb, rb)]
+    assert fmm.load().fmm_theta_test(theta, m, *[v.data_ptr() for v in t], out.data_ptr(),
+                                     torch.cuda.current_stream().cuda_stream) == 0
+    got = out.cpu().numpy().astype(bool)
+    want = np.array([oracle.theta_weak(theta, ca[i], ra[i], cb[i], rb[i]) for i in range(m)])
+    np.testing.assert_array_equal(got, want)
+    assert 0.2 < want.mean() < 0.8
