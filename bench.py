@@ -420,74 +420,109 @@ def bench_ours(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def batch_workload(systems, rank):
+    """The batched workload's systems (N log-uniform in [1e3, 2e5], even ones
+    uniform, odd ones Plummer, float32) and the autotuner's parameters (leaf
+    size 32..256, p in {6, 8, 10, 12}, theta in {0.4, 0.5, 0.6}): one
+    representative per size class (log2 N) and kind, tuned to half the 1e-6
+    target so that the class's other systems stay below it, by its evaluation
+    time in a batch of copies; then (levels, theta) again at the largest p of
+    any class."""
+    import torch
+    from paper_2002_04894_gb300 import tune
+    rng = np.random.default_rng([rank, 7])
+    ns = np.floor(10 ** rng.uniform(3.0, np.log10(2e5), size=systems)).astype(int)
+    xs, qs = [], []
+    for i, n in enumerate(ns):
+        kind = "uniform" if i % 2 == 0 else "plummer"
+        xs.append(torch.from_numpy(inputs.points(kind, int(n), 1000 * rank + i).astype(np.float32)).cuda())
+        qs.append(torch.from_numpy(inputs.charges_uniform(int(n), 1000 * rank + i).astype(np.float32)).cuda())
+    t_tune = time.perf_counter()
+    reps = {}
+    for i, n in enumerate(ns):
+        reps.setdefault((int(np.log2(n)), i % 2), i)
+    ps = (6, 8, 10, 12)
+    cost = lambda i: tune.batch_copies(int(ns[i]))   # cost: evaluation time per system in a batch
+    table = {k: tune.tune(xs[i], qs[i], tol=5e-7, ps=ps, batch=cost(i)).config for k, i in reps.items()}
+    pc = max(c.p for c in table.values())
+    table_c = {k: tune.tune(xs[i], qs[i], tol=5e-7, ps=(pc,), batch=cost(i)).config for k, i in reps.items()}
+    return ns, xs, qs, table, table_c, pc, time.perf_counter() - t_tune
+
+
 def bench_batch(args, rank, world, local):
     """Batched form: many independent systems (N log-uniform in [1e3, 2e5],
     even ones uniform, odd ones Plummer, float32 points and charges), their
     parameters chosen by the autotuner per size class, all evaluations in one
-    graph launch per step; compared with the plain one-solve-per-launch FP64
-    form on the same systems."""
+    graph launch per step: one kernel per stage over every system, every
+    system at one common order p (the largest any size class needs), nine
+    kernels per launch. Also timed: each class at its own order (the
+    order-dependent stages M2M, M2L, L2L then run once per order present),
+    and the plain one-solve-per-launch FP64 form on the same systems."""
     import torch
     import paper_2002_04894_gb300 as fmm
     from paper_2002_04894_gb300 import serve, tune
 
     torch.cuda.set_device(local)
     fmm.load()
-    rng = np.random.default_rng([rank, 7])
-    ns = np.floor(10 ** rng.uniform(3.0, np.log10(2e5), size=args.systems)).astype(int)
-    xs, qs = [], []
-    for i, n in enumerate(ns):
-        kind = "uniform" if i % 2 == 0 else "plummer"
-        xs.append(torch.from_numpy(inputs.points(kind, int(n), 1000 * rank + i).astype(np.float32)).cuda())
-        qs.append(torch.from_numpy(inputs.charges_uniform(int(n), 1000 * rank + i).astype(np.float32)).cuda())
+    ns, xs, qs, table, table_c, pc, t_tune = batch_workload(args.systems, rank)
     total = int(ns.sum())
-    # autotune one representative per size class (log2 N) and kind; tuned to
-    # half the 1e-6 target, so that the class's other systems stay below it
-    t_tune = time.perf_counter()
-    table = {}
-    for i, n in enumerate(ns):
-        key = (int(np.log2(n)), i % 2)
-        if key not in table:
-            r = tune.tune(xs[i], qs[i], tol=5e-7, ps=(6, 8, 10, 12, 14))
-            table[key] = r.config
-    t_tune = time.perf_counter() - t_tune
-    cfgs = [table[(int(np.log2(n)), i % 2)] for i, n in enumerate(ns)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    plans = serve.build_plans(xs, cfgs, prec=fmm.FMM_PREC_MIXED, workers=8)
-    torch.cuda.synchronize()
-    t_plan = time.perf_counter() - t0
-    pots = [torch.empty(int(n), dtype=torch.float32, device="cuda") for n in ns]
-    flds = [torch.empty((int(n), 3), dtype=torch.float32, device="cuda") for n in ns]
-    k0 = fmm.fmm_kernel_launches()
-    batch = fmm.fmm_batch_create(plans, qs, pots, flds, nstreams=32)
-    graph_kernels = fmm.fmm_kernel_launches() - k0  # kernels recorded in the graph
+    key = lambda i, n: (int(np.log2(n)), i % 2)
+    cfgs = [table[key(i, n)] for i, n in enumerate(ns)]
+    cfgs_c = [table_c[key(i, n)] for i, n in enumerate(ns)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        fmm.fmm_batch_launch(batch)
-    torch.cuda.synchronize()
-    times = []
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+
+    def timed(batch, steps, warmup):
+        for _ in range(warmup):
+            fmm.fmm_batch_launch(batch)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             fmm.fmm_batch_launch(batch)
             b.record(stream)
             torch.cuda.synchronize()
-            times.append(a.elapsed_time(b))
-    launches = graph_kernels * args.steps
-    t_eval = sum(times) / len(times)
-    # accuracy on a sample of systems (FP64 direct, 200 targets each)
-    errs = []
-    for i in range(0, len(ns), max(1, len(ns) // 16)):
-        tg = torch.from_numpy(inputs.sample_targets(int(ns[i]), 200, i)).cuda()
-        dp = fmm.fmm_direct(xs[i].double(), qs[i].double(), tg)[0]
-        g = pots[i].double()[tg]
-        errs.append(float(torch.linalg.norm(g - dp) / torch.linalg.norm(dp)))
+            ts.append(a.elapsed_time(b))
+        return sum(ts) / len(ts)
+
+    def errors(pots):  # FP64 direct on 200 targets of every 32nd system
+        errs = []
+        for i in range(0, len(ns), max(1, len(ns) // 16)):
+            tg = torch.from_numpy(inputs.sample_targets(int(ns[i]), 200, i)).cuda()
+            dp = fmm.fmm_direct(xs[i].double(), qs[i].double(), tg)[0]
+            g = pots[i].double()[tg]
+            errs.append(float(torch.linalg.norm(g - dp) / torch.linalg.norm(dp)))
+        return errs
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plans = serve.build_plans(xs, cfgs_c, prec=fmm.FMM_PREC_MIXED, workers=8)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t0
+    pots = [torch.empty(int(n), dtype=torch.float32, device="cuda") for n in ns]
+    flds = [torch.empty((int(n), 3), dtype=torch.float32, device="cuda") for n in ns]
+    batch = fmm.fmm_batch_create(plans, qs, pots, flds)
+    info = fmm.fmm_batch_info(batch)
+    with ClockSampler(local) as clk:
+        t_eval = timed(batch, args.steps, args.warmup)
+    for plan in plans:
+        fmm.fmm_eval_check(plan)
+    errs = errors(pots)
+    fmm.fmm_batch_destroy(batch)
+    del plans
+    # each size class at its own order: M2M, M2L, L2L once per order present
+    plans_k = serve.build_plans(xs, cfgs, prec=fmm.FMM_PREC_MIXED, workers=8)
+    batch_k = fmm.fmm_batch_create(plans_k, qs, pots, flds)
+    info_k = fmm.fmm_batch_info(batch_k)
+    t_k = timed(batch_k, args.steps, args.warmup)
+    errs_k = errors(pots)
+    fmm.fmm_batch_destroy(batch_k)
+    del plans_k
     # plain FP64 form, one solve per launch sequence, same systems and parameters
     t0 = time.perf_counter()
-    for x, q, c in zip(xs, qs, cfgs):
+    for x, q, c in zip(xs, qs, cfgs_c):
         pl = fmm.fmm_plan(x.double(), c.levels, c.p, c.theta, prec=fmm.FMM_PREC_FP64)
         fmm.fmm_eval(pl, q.double())
         fmm.fmm_destroy(pl)
@@ -502,16 +537,23 @@ def bench_batch(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "batch", "systems": int(len(ns)), "points": total,
                    "n_range": [int(ns.min()), int(ns.max())], "kinds": "uniform/plummer alternating",
-                   "step": "one graph launch evaluating every system",
+                   "p": int(pc), "step": "one graph launch: one kernel per stage over every system",
                    "l2": "flushed between steps (512 MB write)"},
         "plan_all_s": round(t_plan, 3),
         "plan_plus_eval_mpts": round(total / (t_plan + t_eval * 1e-3) / 1e6, 4),
+        "per_class_p": {"value": round(total / (t_k * 1e-3) / 1e6, 4), "unit": "Mpoints/s",
+                        "ms": round(t_k, 3), "kernels_per_graph_launch": info_k["kernels"],
+                        "max_rel_l2_phi": max(errs_k)},
         "fp64_one_solve_per_launch": {"value": round(total / t_fp64 / 1e6, 4), "unit": "Mpoints/s",
                                       "s": round(t_fp64, 3)},
-        "tuner": {"s": round(t_tune, 2), "classes": {f"2^{k[0]}/{'uniform' if k[1] == 0 else 'plummer'}":
-                                                     [c.levels, c.p, c.theta] for k, c in table.items()}},
+        "tuner": {"s": round(t_tune, 2), "cost": "evaluation time per system in a batch of copies",
+                  "classes_levels_theta": {f"2^{k[0]}/{'uniform' if k[1] == 0 else 'plummer'}":
+                                           [table_c[k].levels, table_c[k].theta] for k in table_c},
+                  "per_class_levels_p_theta": {f"2^{k[0]}/{'uniform' if k[1] == 0 else 'plummer'}":
+                                               [table[k].levels, table[k].p, table[k].theta] for k in table}},
         "accuracy": {"max_rel_l2_phi": max(errs), "systems_checked": len(errs)},
-        "gpu_launches": int(launches), "kernels_per_graph_launch": int(graph_kernels),
+        "gpu_launches": int(info["kernels"] * args.steps), "kernels_per_graph_launch": info["kernels"],
+        "batched_stages": info["fused"],
         "clocks": clk.summary(),
     }
     print(json.dumps(out), flush=True)
@@ -807,6 +849,25 @@ def profile_solve(args):
     print(json.dumps({"workload": args.workload, "n": int(x.shape[0]), "checksum": float(pot.double().sum())}))
 
 
+def profile_batch(args):
+    """The batched workload built and evaluated once (one graph launch), then
+    exit: the command the batch's ncu launch list is taken from."""
+    import torch
+    import paper_2002_04894_gb300 as fmm
+    from paper_2002_04894_gb300 import serve
+    fmm.load()
+    ns, xs, qs, _, table_c, _, _ = batch_workload(args.systems, 0)
+    cfgs = [table_c[(int(np.log2(n)), i % 2)] for i, n in enumerate(ns)]
+    plans = serve.build_plans(xs, cfgs, prec=fmm.FMM_PREC_MIXED, workers=8)
+    pots = [torch.empty(int(n), dtype=torch.float32, device="cuda") for n in ns]
+    flds = [torch.empty((int(n), 3), dtype=torch.float32, device="cuda") for n in ns]
+    batch = fmm.fmm_batch_create(plans, qs, pots, flds)
+    fmm.fmm_batch_launch(batch)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": "batch", "systems": len(ns), "kernels": fmm.fmm_batch_info(batch)["kernels"],
+                      "checksum": float(sum(p.double().sum() for p in pots))}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -833,7 +894,7 @@ def main():
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.profile_solve:
-        profile_solve(args)
+        (profile_batch if args.workload == "batch" else profile_solve)(args)
         return
     if args.impl == "reference":
         bench_reference(args, rank, world)

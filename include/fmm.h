@@ -53,7 +53,8 @@ enum fmm_status {
     FMM_ENOMEM = -2,      /* the allocator returned NULL */
     FMM_ENONFINITE = -3,  /* a point coordinate is NaN or infinite */
     FMM_ECAPACITY = -4,   /* an interaction list exceeds 2^31 - 1 entries */
-    FMM_ETIMEDOUT = -5,   /* a bounded device wait gave up (reserved for persistent kernels) */
+    FMM_ETIMEDOUT = -5,   /* a bounded device wait gave up (one-launch downward pass,
+                             tensor-core M2L); reported by fmm_eval_check */
     FMM_ECUDA = -6,       /* a CUDA runtime call failed; fmm_last_cuda_error() has the code */
     FMM_EINTERNAL = -7    /* a device-side consistency check of the tree build failed (the
                              partition of a box did not give the sizes the split rule
@@ -336,20 +337,30 @@ int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, int levels, 
  * fmm_batch_create -- record the evaluation (fmm_eval) of nplans plans into
  * one CUDA graph. Plan i reads charges[i] and writes potentials[i] and
  * fields[i] (NULL entry: no field); all of these must be DEVICE pointers and
- * stay valid for the life of the batch. The evaluations are spread over
- * nstreams (1..64; 0 = 16) forked branches of the graph, so that independent
- * systems of different sizes run concurrently on the device. `stream` is the
- * stream used for the capture (a private one is made if it is NULL). The plans
- * must not be evaluated elsewhere while the batch runs, and must outlive it.
- * Errors: FMM_EINVAL, FMM_ECUDA.
+ * stay valid for the life of the batch. When every plan is mixed-precision
+ * (FMM_PREC_MIXED) on binary levels with the single-precision M2L, and all
+ * share the order p and the data type, the graph holds nine kernels that
+ * each run one stage for every system at once (charges in / zeroing, P2M,
+ * M2M, M2L, L2L, L2P, near field for 64- and 128-target tiles, partial-sum
+ * combine); the systems' near-field work units are merged, heaviest first,
+ * when the batch is made. Otherwise the plans' own evaluations are spread
+ * over nstreams (1..64; 0 = 16) forked branches of the graph. `stream` is
+ * the stream used for the set-up and the capture (a private one is made if
+ * it is NULL). The plans must not be evaluated elsewhere while the batch
+ * runs, and must outlive it. A wait of the batched downward pass that runs
+ * out is reported by fmm_eval_check on that system's plan (FMM_ETIMEDOUT).
+ * Errors: FMM_EINVAL, FMM_ENOMEM, FMM_ECUDA.
  * fmm_batch_launch -- run the recorded evaluations on `stream` (asynchronous).
- * fmm_batch_destroy -- release the graph and its streams (NULL: no-op).
+ * fmm_batch_info -- the kernel launches one fmm_batch_launch makes, and
+ * whether the batched stages (1) or per-plan branches (0) were recorded.
+ * fmm_batch_destroy -- release the graph, its streams and tables (NULL: no-op).
  */
 typedef struct fmm_batch_s *fmm_batch_t;
 int fmm_batch_create(const fmm_plan_t *plans, int nplans, const void *const *charges,
                      void *const *potentials, void *const *fields, int nstreams, void *stream,
                      fmm_batch_t *out);
 int fmm_batch_launch(fmm_batch_t batch, void *stream);
+int fmm_batch_info(fmm_batch_t batch, int64_t *kernels, int *fused);
 void fmm_batch_destroy(fmm_batch_t batch);
 
 /*
@@ -425,6 +436,18 @@ int fmm_measure_peak(int kind, int64_t iters, void *stream, double *ops_per_s, d
  * already built are not affected.
  */
 int64_t fmm_set_list_capacity(int64_t entries);
+
+/*
+ * fmm_set_wait_limit -- the bound of the device-side waits of the one-launch
+ * downward pass (a box waits for its parent's expansion): `sleeps` waits of
+ * ~0.1 us each before the wait gives up and the evaluation reports
+ * FMM_ETIMEDOUT through fmm_eval_check (default and any value <= 0: 2^24,
+ * ~2 s). `withhold` > 0 names a box (heap index) whose completion is never
+ * signalled, so that its children's waits run out: a test of the timeout
+ * path that needs no device fault (<= 0: none). Process-wide; returns the
+ * previous limit.
+ */
+int64_t fmm_set_wait_limit(int64_t sleeps, int64_t withhold);
 
 /* fmm_strerror -- static text for a status code. */
 const char *fmm_strerror(int status);

@@ -66,11 +66,11 @@ _LIB = None
 EXPORTS = ("fmm_plan", "fmm_eval", "fmm_destroy", "fmm_direct", "fmm_plan_stats",
            "fmm_plan_tree", "fmm_plan_list", "fmm_eval_expansions", "fmm_strerror",
            "fmm_last_cuda_error", "fmm_stage_times", "fmm_kernel_launches",
-           "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy",
+           "fmm_orb_order_noalloc", "fmm_batch_create", "fmm_batch_launch", "fmm_batch_destroy", "fmm_batch_info",
            "fmm_eval_check", "fmm_pool_trim", "fmm_set_list_capacity", "fmm_measure_peak",
            "fmm_theta_test", "fmm_eval_upward", "fmm_plan_multipoles", "fmm_plan_add_locals",
            "fmm_m2l_external", "fmm_plan_leaf_points", "fmm_p2p_external", "fmm_eval_downward",
-           "fmm_translate")
+           "fmm_translate", "fmm_set_wait_limit")
 FMM_NOALLOC_MAX_POINTS, FMM_NOALLOC_MAX_LEVELS = 4096, 12
 
 
@@ -130,6 +130,8 @@ def load(build: bool = True) -> C.CDLL:
     lib.fmm_batch_launch.restype = i32
     lib.fmm_batch_destroy.argtypes = [vp]
     lib.fmm_batch_destroy.restype = None
+    lib.fmm_batch_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(i32)]
+    lib.fmm_batch_info.restype = i32
     for name, args in (("fmm_theta_test", [C.c_double, i64, vp, vp, vp, vp, vp, vp]),
                        ("fmm_eval_upward", [vp, vp, vp]),
                        ("fmm_plan_multipoles", [vp, i32, i64, vp, vp, vp]),
@@ -141,6 +143,8 @@ def load(build: bool = True) -> C.CDLL:
                        ("fmm_translate", [i32, i32, i64, vp, vp, vp, vp, vp])):
         getattr(lib, name).argtypes = args
         getattr(lib, name).restype = i32
+    lib.fmm_set_wait_limit.argtypes = [i64, i64]
+    lib.fmm_set_wait_limit.restype = i64
     lib.fmm_measure_peak.argtypes = [i32, i64, vp, vp, vp]
     lib.fmm_measure_peak.restype = i32
     lib.fmm_set_list_capacity.argtypes = [i64]
@@ -402,6 +406,12 @@ def fmm_measure_peak(kind: str, iters: int = 1 << 16, stream=None):
     return v.value, ms.value
 
 
+def fmm_set_wait_limit(sleeps: int, withhold: int = -1) -> int:
+    """Bound of the downward pass's device waits (sleeps of ~0.1 us; <= 0:
+    default) and, for tests, a box whose completion is never signalled."""
+    return int(load().fmm_set_wait_limit(int(sleeps), int(withhold)))
+
+
 def fmm_set_list_capacity(entries: int) -> int:
     """Largest candidate-pair count per connectivity level (tests lower it to
     reach FMM_ECAPACITY); returns the previous value. 0 restores the default."""
@@ -464,6 +474,13 @@ def fmm_batch_create(plans, charges, potentials, fields=None, nstreams: int = 16
 
 def fmm_batch_launch(batch: Batch, stream=None) -> None:
     _check(load().fmm_batch_launch(batch.handle, _stream(stream)), "fmm_batch_launch")
+
+
+def fmm_batch_info(batch: Batch) -> dict:
+    """{'kernels': kernel launches per fmm_batch_launch, 'fused': batched stages (True) or per-plan branches}"""
+    k, f = C.c_int64(), C.c_int32()
+    _check(load().fmm_batch_info(batch.handle, C.byref(k), C.byref(f)), "fmm_batch_info")
+    return {"kernels": int(k.value), "fused": bool(f.value)}
 
 
 def fmm_batch_destroy(batch: Batch) -> None:

@@ -151,6 +151,9 @@ struct fmm_batch_s {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
     cudaStream_t own = nullptr;
+    fmm::BatchRun run;  // batched stages (one launch per stage over all systems)
+    bool fused = false;
+    int64_t kernels = 0;  // kernel nodes of the graph
 };
 
 namespace {
@@ -480,6 +483,7 @@ void fmm_batch_destroy(fmm_batch_t b) {
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     if (b->own) cudaStreamDestroy(b->own);
+    fmm::batch_release(b->run);
     cudaGetLastError();
     delete b;
 }
@@ -494,54 +498,84 @@ int fmm_batch_create(const fmm_plan_t *plans, int nplans, const void *const *cha
         if (!plans[i] || !is_device_ptr(charges[i]) || !is_device_ptr(potentials[i])) return FMM_EINVAL;
         if (fields && fields[i] && !is_device_ptr(fields[i])) return FMM_EINVAL;
     }
-    const int K = std::min(nstreams ? nstreams : 16, nplans);
     fmm_batch_s *b = new (std::nothrow) fmm_batch_s();
     if (!b) return FMM_ENOMEM;
     cudaError_t e = cudaSuccess;
     cudaStream_t s0 = (cudaStream_t)stream;
     if (!s0) e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), s0 = b->own;
-    for (int k = 0; k < K && e == cudaSuccess; k++) {
-        cudaStream_t s;
-        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-        if (e == cudaSuccess) b->streams.push_back(s);
-    }
-    for (int k = 0; k <= K && e == cudaSuccess; k++) {
-        cudaEvent_t ev;
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) b->events.push_back(ev);
-    }
-    if (e != cudaSuccess) {
-        fmm_batch_destroy(b);
-        return cuda_status(e);
-    }
-    e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaEventRecord(b->events[K], s0);  // fork
-        for (int k = 0; k < K; k++) cudaStreamWaitEvent(b->streams[k], b->events[K], 0);
-        for (int i = 0; i < nplans && e == cudaSuccess; i++) {
-            Plan &P = plans[i]->P;
-            const cudaStream_t keep = P.stream;
-            const bool prof = P.profile;
-            P.stream = b->streams[i % K];
-            P.profile = false;
-            e = fmm::eval_expansions(P, charges[i], P.dtype);
-            if (e == cudaSuccess) e = fmm::eval_p2p(P, potentials[i], fields ? fields[i] : nullptr, P.dtype);
-            P.stream = keep;
-            P.profile = prof;
+    std::vector<const Plan *> pl(nplans);
+    for (int i = 0; i < nplans; i++) pl[i] = &plans[i]->P;
+    if (e == cudaSuccess && fmm::batch_eligible(pl.data(), nplans)) {
+        // every system in one launch per stage
+        e = fmm::batch_setup(pl.data(), nplans, charges, potentials, fields, b->run, s0);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = fmm::batch_enqueue(b->run, s0);
+            cudaError_t e2 = cudaStreamEndCapture(s0, &b->graph);
+            if (e == cudaSuccess) e = e2;
         }
-        for (int k = 0; k < K; k++) {  // join
-            cudaEventRecord(b->events[k], b->streams[k]);
-            cudaStreamWaitEvent(s0, b->events[k], 0);
+        b->fused = true;
+    } else if (e == cudaSuccess) {
+        // per-plan evaluations on forked branches of the graph
+        const int K = std::min(nstreams ? nstreams : 16, nplans);
+        for (int k = 0; k < K && e == cudaSuccess; k++) {
+            cudaStream_t s;
+            e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e == cudaSuccess) b->streams.push_back(s);
         }
-        cudaError_t e2 = cudaStreamEndCapture(s0, &b->graph);
-        if (e == cudaSuccess) e = e2;
+        for (int k = 0; k <= K && e == cudaSuccess; k++) {
+            cudaEvent_t ev;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->events.push_back(ev);
+        }
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaEventRecord(b->events[K], s0);  // fork
+            for (int k = 0; k < K; k++) cudaStreamWaitEvent(b->streams[k], b->events[K], 0);
+            for (int i = 0; i < nplans && e == cudaSuccess; i++) {
+                Plan &P = plans[i]->P;
+                const cudaStream_t keep = P.stream;
+                const bool prof = P.profile;
+                P.stream = b->streams[i % K];
+                P.profile = false;
+                P.full_upward = P.ext_active = false;
+                e = fmm::eval_expansions(P, charges[i], P.dtype);
+                if (e == cudaSuccess) e = fmm::eval_p2p(P, potentials[i], fields ? fields[i] : nullptr, P.dtype);
+                P.stream = keep;
+                P.profile = prof;
+            }
+            for (int k = 0; k < K; k++) {  // join
+                cudaEventRecord(b->events[k], b->streams[k]);
+                cudaStreamWaitEvent(s0, b->events[k], 0);
+            }
+            cudaError_t e2 = cudaStreamEndCapture(s0, &b->graph);
+            if (e == cudaSuccess) e = e2;
+        }
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(b->graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+        for (size_t i = 0; i < nn && e == cudaSuccess; i++) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[i], &t);
+            if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) b->kernels++;
+        }
+    }
     if (e != cudaSuccess) {
         fmm_batch_destroy(b);
         return cuda_status(e);
     }
     *out = b;
+    return FMM_OK;
+}
+
+int fmm_batch_info(fmm_batch_t b, int64_t *kernels, int *fused) {
+    if (!b) return FMM_EINVAL;
+    if (kernels) *kernels = b->kernels;
+    if (fused) *fused = b->fused ? 1 : 0;
     return FMM_OK;
 }
 

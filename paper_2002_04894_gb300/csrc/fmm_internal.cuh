@@ -32,6 +32,53 @@ struct Arena {
     size_t left = 0, hint = 0;
 };
 
+// weak pairs of every level, concatenated (levels lmin..lmax); passed by value
+struct PairTable {
+    const int32_t *tgt[FMM_MAX_LEVELS + 1];
+    const int32_t *src[FMM_MAX_LEVELS + 1];
+    long long off[FMM_MAX_LEVELS + 2];
+    int lmin, lmax;
+};
+
+// One system of a batched evaluation as the batched stage kernels read it
+// (an array of these lives on the device): the plan's arrays, its sizes,
+// its first level with weak pairs, its caller's charges and outputs.
+// warps (one child box each) per block of the M2M/L2L kernels
+constexpr int kWarpChildMax = 8;
+
+struct BatchSys {
+    int B, lw, dtype, p;
+    int64_t n, nbox, nleaf, npairs;
+    const int32_t *perm, *begin, *count, *ssrc, *poff;
+    const double *centre, *radius;
+    const float *hl;
+    float *qf, *far_phi, *far_E;
+    const float4 *lgeo;
+    double2 *M, *L, *Lh;
+    float2 *Mf;
+    unsigned *arrive;
+    int *done, *err;
+    const void *charges;
+    void *pot, *field;
+    double4 *partial;
+    const int4 *units;             // near-field work units, heaviest bucket first
+    const int32_t *upart, *ubstart;
+    PairTable pt;
+};
+
+// Block b of a batched launch belongs to system s with off[s] <= b < off[s+1].
+__device__ __forceinline__ int batch_sys_of(const int32_t *__restrict__ off, int nsys, int64_t b) {
+    int lo = 0, hi = nsys;  // off[lo] <= b < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= b)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 // A given root cell (FMM_FLAG_ROOT_CELL), passed to the root kernel by value.
 struct RootCell {
     double lo[3] = {0.0, 0.0, 0.0}, hi[3] = {0.0, 0.0, 0.0};
@@ -88,9 +135,13 @@ struct Plan {
     int64_t p2p_nparts = 0;
     double4 *p2p_partial = nullptr;
     int p2p_tile = kP2PTile;  // targets per work unit (kP2PTile or kP2PTileSmall)
+    int32_t *p2p_bstart = nullptr;  // first unit of each of the 256 weight buckets; [256] = units
     bool capacity_exceeded = false;
     // M2L rotation tables (D = d(pi/2) quadrants, axial coefficients, F_nm)
     double *m2l_tab = nullptr;
+    unsigned *m2m_arrive = nullptr;         // one-launch upward pass: arrivals per parent
+    int *l2l_done = nullptr;                // one-launch downward pass: box finished
+    unsigned long long *l2l_next = nullptr; // one-launch downward pass: next box to take
     int m2l_ntab = 0, m2l_threads = 0;
     size_t m2l_smem = 0;
     // mixed precision: leaf offsets hi|lo (6n floats), float charges and far
@@ -212,6 +263,55 @@ cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype);
 cudaError_t eval_downward(Plan &P);
 cudaError_t add_external_locals(Plan &P);
 cudaError_t add_external_near(Plan &P);
+// batched stages: every system of a batch (same order, mixed form, binary
+// levels) in one launch per stage; `off` holds per-system block (or chunk)
+// offsets, off[nsys] = the total
+cudaError_t batch_p2m(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int pmax, cudaStream_t st);
+cudaError_t batch_m2m_up(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int p, const double *tab,
+                         cudaStream_t st);
+cudaError_t batch_m2l(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, int p, const void *tab,
+                      cudaStream_t st);
+cudaError_t batch_l2l_down(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, int p,
+                           const double *tab, unsigned long long *next, cudaStream_t st);
+cudaError_t batch_l2p(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int pmax, cudaStream_t st);
+cudaError_t batch_p2p(const BatchSys *S, const int4 *units, const int32_t *usys, const int32_t *upart, int64_t n,
+                      int tile, int dtype, cudaStream_t st);
+cudaError_t batch_combine(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int dtype,
+                          cudaStream_t st);
+cudaError_t batch_smem_limits(int p);
+
+// a batch's device tables (batch.cu): descriptors, per-stage block offsets
+// (the order-dependent stages per group of systems of one order), the merged
+// near-field units, the L2L queue counters; one allocation
+constexpr int kBatchMaxGroups = 8;
+struct BatchGroup {
+    int p = 0;
+    int32_t *off[3] = {};    // M2M blocks, M2L chunks, L2L chunks (other orders: none)
+    int64_t blocks[3] = {};
+    const double *tab = nullptr;
+    const void *ftab = nullptr;
+};
+struct BatchRun {
+    void *mem = nullptr;
+    int nsys = 0, pmax = 0, dtype = 0, ngroups = 0;
+    BatchSys *S = nullptr;
+    int32_t *off[4] = {};    // prepare, leaves (P2M, L2P), combine, unit merge
+    int64_t blocks[4] = {};
+    BatchGroup grp[kBatchMaxGroups];
+    int4 *units = nullptr;
+    int32_t *upart = nullptr, *usys = nullptr;
+    int64_t nunits[2] = {0, 0};  // tile 64, tile 128
+    unsigned long long *next = nullptr;  // one L2L queue counter per group
+};
+bool batch_eligible(const Plan *const *plans, int n);
+cudaError_t batch_setup(const Plan *const *plans, int n, const void *const *charges, void *const *pot,
+                        void *const *field, BatchRun &R, cudaStream_t st);
+cudaError_t batch_enqueue(const BatchRun &R, cudaStream_t st);
+void batch_release(BatchRun &R);
+int first_weak_level_of(const Plan &P);
+PairTable pair_table(const Plan &P);
+int64_t total_weak(const Plan &P);
+
 // FP64 M2L from multipoles outside the plan into L_ext: n pairs (target box
 // `tgt[i]` of `level`, source i with multipole M[i] about centre[i])
 cudaError_t m2l_external(Plan &P, int level, int64_t n, const int32_t *tgt, const double2 *M,
@@ -219,6 +319,8 @@ cudaError_t m2l_external(Plan &P, int level, int64_t n, const int32_t *tgt, cons
 cudaError_t m2l_all(Plan &P);
 void m2m_level(Plan &P, int level);
 void l2l_level(Plan &P, int level);
+void m2m_up(Plan &P, int stop);
+void l2l_down(Plan &P, int lw);
 bool m2l_f32_supported(int p);
 // Raises a kernel's dynamic shared-memory limit to the device's opt-in
 // maximum (never lowers it): plans of different orders share the kernels,

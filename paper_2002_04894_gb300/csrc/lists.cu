@@ -368,6 +368,13 @@ k_units_scatter(const int32_t *total, const uint8_t *bucket, const int4 *units, 
     }
 }
 
+// first sorted unit of each weight bucket (bstart[256] = the unit count)
+__global__ void k_bucket_starts(const int32_t *boff, int nblocks, const int32_t *total, int32_t *bstart) {
+    const int b = threadIdx.x;
+    bstart[b] = boff[(int64_t)b * nblocks];
+    if (b == 0) bstart[256] = *total;
+}
+
 }  // namespace
 
 namespace {
@@ -531,7 +538,8 @@ cudaError_t lists_build(Plan &P) {
     P.p2p_units = (int4 *)palloc(P, (size_t)std::max<int64_t>(nunits, 1) * sizeof(int4));
     P.p2p_upart = (int32_t *)palloc(P, (size_t)std::max<int64_t>(nunits, 1) * 4);
     P.p2p_partial = P.p2p_nparts ? (double4 *)palloc(P, (size_t)P.p2p_nparts * sizeof(double4)) : nullptr;
-    if (!units || !upart || !bucket || !bh || !boff || !P.p2p_units || !P.p2p_upart ||
+    P.p2p_bstart = (int32_t *)palloc(P, 257 * 4);
+    if (!units || !upart || !bucket || !bh || !boff || !P.p2p_units || !P.p2p_upart || !P.p2p_bstart ||
         (P.p2p_nparts && !P.p2p_partial))
         return cudaErrorMemoryAllocation;
     P.p2p_nunits_dev = uoff + nl;
@@ -543,7 +551,8 @@ cudaError_t lists_build(Plan &P) {
     if (e != cudaSuccess) return e;
     FMM_LAUNCH(k_units_scatter, (unsigned)nblk, kUnitBlock, 0, st, P.p2p_nunits_dev, bucket, units, upart, nblk,
                boff, P.p2p_units, P.p2p_upart);
-    return e != cudaSuccess ? e : cudaGetLastError();
+    FMM_LAUNCH(k_bucket_starts, 1, 256, 0, st, boff, nblk, P.p2p_nunits_dev, P.p2p_bstart);
+    return cudaGetLastError();
 }
 
 }  // namespace fmm

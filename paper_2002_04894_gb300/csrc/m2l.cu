@@ -210,13 +210,58 @@ __global__ void k_m2l_rot_f64(PairTable PT, int p, const double *__restrict__ ce
 // spread over a warp keeps each lane's serial chain to a few dozen
 // operations (the small levels near the root finish in microseconds), and
 // blocks of 1 to 8 warps spread even a small level over all SMs.
-constexpr int kWarpChildMax = 8;
-
 __device__ __forceinline__ int degree_of(int c) {
     int n = (int)((sqrtf(8.f * (float)c + 1.f) - 1.f) * 0.5f);
     while (tri(n + 1, 0) <= c) n++;
     while (n > 0 && tri(n, 0) > c) n--;
     return n;
+}
+
+// One warp per box: lane n <= p forms r^-n (a single division), and each
+// coefficient takes its degree's factor from that lane.
+__device__ __forceinline__ double inv_radius_pow(const double *__restrict__ radius, int64_t g, int p, int lane) {
+    double pw = 1.0;
+    if (lane <= p) {
+        const double r = radius[g] > 0.0 ? radius[g] : 1.0;
+        double b = 1.0 / r;
+        for (int e = lane; e; e >>= 1) {
+            if (e & 1) pw *= b;
+            b *= b;
+        }
+    }
+    return pw;
+}
+
+// Box g's coefficients times r^-n, by one warp: Mhat = M / r^n into Mf
+// (float, read through L2: completed by other warps of the launch) or
+// L = Lhat / r^n into L.
+__device__ __forceinline__ void warp_scale_multipole(const double *__restrict__ radius, int64_t g, int p,
+                                                     const double2 *M, float2 *Mf) {
+    const int nc = ncoef(p), lane = threadIdx.x & 31;
+    const double pw = inv_radius_pow(radius, g, p, lane);
+    for (int c0 = 0; c0 < nc; c0 += 32) {  // warp-uniform trip count around the shuffle
+        const int c = c0 + lane;
+        const double sc = __shfl_sync(0xffffffffu, pw, degree_of(min(c, nc - 1)));
+        if (c < nc) {
+            const double2 m = __ldcg(M + g * nc + c);
+            Mf[g * mf_stride(p) + c] = make_float2((float)(m.x * sc), (float)(m.y * sc));
+        }
+    }
+}
+
+__device__ __forceinline__ void warp_unscale_local(const double *__restrict__ radius, int64_t g, int p,
+                                                   const double2 *__restrict__ Lh, double2 *L) {
+    const int nc = ncoef(p), lane = threadIdx.x & 31;
+    const double pw = inv_radius_pow(radius, g, p, lane);
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int c = c0 + lane;
+        const double sc = __shfl_sync(0xffffffffu, pw, degree_of(min(c, nc - 1)));
+        if (c < nc) {
+            const double2 h = Lh[g * nc + c];
+            L[g * nc + c] = make_double2(h.x * sc, h.y * sc);
+        }
+    }
+    __syncwarp();
 }
 
 // double2 slots of one warp's slice: A, B (nc each), powers of e^{ia} and
@@ -257,20 +302,23 @@ struct WarpChild {
     int nc, lane;
 };
 
-// Tables into shared memory; the warp's child, its parent at `step` levels
-// up, and the powers of the child-to-parent offset. Returns false for warps
-// past the end of the level (they take no further part: no block barrier
-// follows).
-__device__ __forceinline__ bool warp_child_setup(int level, int step, int p, const double *__restrict__ centre,
-                                                 const double *__restrict__ gtab, double2 *sw, WarpChild &W) {
-    const int nc = ncoef(p), nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Tables into shared memory (every thread of the block; one barrier).
+__device__ __forceinline__ double *stage_child_tables(int p, const double *__restrict__ gtab, double2 *sw) {
+    const int nc = ncoef(p), nw = blockDim.x >> 5;
     const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
     double *tab = (double *)(sw + nw * warp_slice(p));
     for (int i = threadIdx.x; i < nD; i += blockDim.x) tab[i] = gtab[i];
     for (int i = threadIdx.x; i < 2 * nc + p + 2; i += blockDim.x) tab[nD + i] = gtab[2 * nD + i];
     __syncthreads();
-    const int64_t j = blockIdx.x * (int64_t)nw + w;
-    if (j >= ((int64_t)1 << level)) return false;
+    return tab;
+}
+
+// The warp's child gc, its parent gp, and the powers of the child-to-parent
+// offset, in the warp's slice of shared memory (warp-synchronous only).
+__device__ __forceinline__ void warp_child_init(int64_t gc, int64_t gp, int p, const double *__restrict__ centre,
+                                                const double *tab, double2 *sw, WarpChild &W) {
+    const int nc = ncoef(p), w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
     W.A = sw + w * warp_slice(p);
     W.B = W.A + nc;
     W.pa = W.B + nc;
@@ -279,12 +327,12 @@ __device__ __forceinline__ bool warp_child_setup(int level, int step, int p, con
     W.Dt = tab;
     W.Ft = tab + nD;
     W.iFt = W.Ft + nc;
-    W.gc = ((int64_t)1 << level) - 1 + j;
-    W.gp = ((W.gc + 1) >> step) - 1;
+    W.gc = gc;
+    W.gp = gp;
     W.nc = nc;
     W.lane = lane;
+    __syncwarp();
     if (lane < 3) {
-        const int64_t gc = W.gc, gp = W.gp;
         const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
                      dz = centre[3 * gc + 2] - centre[3 * gp + 2];
         const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
@@ -312,15 +360,26 @@ __device__ __forceinline__ bool warp_child_setup(int level, int step, int p, con
         }
     }
     __syncwarp();
+}
+
+// Tables into shared memory; the warp's child of `level` (block-strided),
+// its parent at `step` levels up. Returns false for warps past the end of
+// the level (they take no further part: no block barrier follows).
+__device__ __forceinline__ bool warp_child_setup(int level, int step, int p, const double *__restrict__ centre,
+                                                 const double *__restrict__ gtab, double2 *sw, WarpChild &W) {
+    const double *tab = stage_child_tables(p, gtab, sw);
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    const int64_t j = blockIdx.x * (int64_t)nw + w;
+    if (j >= ((int64_t)1 << level)) return false;
+    const int64_t gc = ((int64_t)1 << level) - 1 + j;
+    warp_child_init(gc, ((gc + 1) >> step) - 1, p, centre, tab, sw, W);
     return true;
 }
 
-__global__ void __launch_bounds__(kWarpChildMax * 32)
-k_m2m_warp(int level, int step, int p, const double *__restrict__ centre, double2 *M,
-           const double *__restrict__ gtab) {
-    extern __shared__ double2 sw[];
-    WarpChild W;
-    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
+// M2M of the warp's child into its parent (atomic adds). The child's
+// multipole is read through L2: in the one-launch upward pass another warp
+// completed it.
+__device__ __forceinline__ void m2m_body(const WarpChild &W, double2 *M) {
     const int nc = W.nc, lane = W.lane;
     double2 *A = W.A, *B = W.B;
     const double2 *pa = W.pa, *pb = W.pb;
@@ -328,7 +387,7 @@ k_m2m_warp(int level, int step, int p, const double *__restrict__ centre, double
     // forward rotation: u = F M (-i e^{ia})^m, doubled for m > 0
     for (int c = lane; c < nc; c += 32) {
         const int m = c - tri(degree_of(c), 0);
-        A[c] = cscale(cmul(M[W.gc * nc + c], mul_ipow(4 - (m & 3), pa[m])), Ft[c] * (m ? 2.0 : 1.0));
+        A[c] = cscale(cmul(__ldcg(M + W.gc * nc + c), mul_ipow(4 - (m & 3), pa[m])), Ft[c] * (m ? 2.0 : 1.0));
     }
     __syncwarp();
     fold_all<false>(W.Dt, nc, A, lane,
@@ -358,22 +417,21 @@ k_m2m_warp(int level, int step, int p, const double *__restrict__ centre, double
         atomicAdd(&Mp[c].x, t.x);
         atomicAdd(&Mp[c].y, t.y);
     });
+    __syncwarp();
 }
 
-__global__ void __launch_bounds__(kWarpChildMax * 32)
-k_l2l_warp(int level, int step, int p, const double *__restrict__ centre, double2 *L,
-           const double *__restrict__ gtab) {
-    extern __shared__ double2 sw[];
-    WarpChild W;
-    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
-    const int nc = W.nc, lane = W.lane, pmax = p;
+// L2L of the warp's parent into its child (added to the child's local
+// expansion). The parent's expansion is read through L2: in the one-launch
+// downward pass another warp completed it.
+__device__ __forceinline__ void l2l_body(const WarpChild &W, double2 *L, int pmax) {
+    const int nc = W.nc, lane = W.lane;
     double2 *A = W.A, *B = W.B;
     const double2 *pa = W.pa, *pb = W.pb;
     const double *f = W.f, *Ft = W.Ft, *iFt = W.iFt;
     // forward rotation of the parent's local expansion: Lt = L / F, i^l e^{-ila}, doubled for l > 0
     for (int c = lane; c < nc; c += 32) {
         const int l = c - tri(degree_of(c), 0);
-        A[c] = cscale(cmul(mul_ipow(l, L[W.gp * nc + c]), cconj(pa[l])), (l ? 2.0 : 1.0) * iFt[c]);
+        A[c] = cscale(cmul(mul_ipow(l, __ldcg(L + W.gp * nc + c)), cconj(pa[l])), (l ? 2.0 : 1.0) * iFt[c]);
     }
     __syncwarp();
     fold_all<false>(W.Dt, nc, A, lane,
@@ -402,6 +460,166 @@ k_l2l_warp(int level, int step, int p, const double *__restrict__ centre, double
     fold_all<true>(W.Dt, nc, A, lane, [&](int c, int l, double2 r) {
         Lc[c] = cadd(Lc[c], cscale(cmul(mul_ipow(4 - (l & 3), r), pa[l]), Ft[c]));
     });
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_m2m_warp(int level, int step, int p, const double *__restrict__ centre, double2 *M,
+           const double *__restrict__ gtab) {
+    extern __shared__ double2 sw[];
+    WarpChild W;
+    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
+    m2m_body(W, M);
+}
+
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_l2l_warp(int level, int step, int p, const double *__restrict__ centre, double2 *L,
+           const double *__restrict__ gtab) {
+    extern __shared__ double2 sw[];
+    WarpChild W;
+    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
+    l2l_body(W, L, p);
+}
+
+// Leaf j's walk up: translate into the parent; the warp that delivers a
+// parent's second child (an arrival counter per parent) carries on with that
+// parent, whose multipole is then complete, so no warp ever waits.
+// Translations stop at level `stop` (no multipole above it is read). With
+// `Mf`, each box the walk completes (its leaf, every parent it carries on,
+// down to level `stop`) is also scaled into Mf for the single-precision M2L.
+__device__ __forceinline__ void m2m_walk(int B, int stop, int64_t j, int p, const double *__restrict__ centre,
+                                         const double *__restrict__ radius, double2 *M, float2 *Mf,
+                                         const double *tab, double2 *sw, unsigned *arrive) {
+    const int lane = threadIdx.x & 31;
+    WarpChild W;
+    int64_t gc = ((int64_t)1 << B) - 1 + j;
+    for (int l = B;; l--) {
+        if (Mf) warp_scale_multipole(radius, gc, p, M, Mf);
+        if (l <= stop) break;
+        const int64_t gp = (gc - 1) >> 1;
+        warp_child_init(gc, gp, p, centre, tab, sw, W);
+        m2m_body(W, M);
+        __threadfence();
+        unsigned old = 0;
+        if (lane == 0) old = atomicAdd(&arrive[gp], 1u);
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old == 0) break;  // the sibling is still on its way: it carries the parent on
+        __threadfence();
+        gc = gp;
+    }
+}
+
+// The whole upward pass (binary levels) in one launch, one warp per leaf.
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_m2m_up(int B, int stop, int p, const double *__restrict__ centre, double2 *M, const double *__restrict__ gtab,
+         unsigned *arrive) {
+    extern __shared__ double2 sw[];
+    const double *tab = stage_child_tables(p, gtab, sw);
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    const int64_t nleaf = (int64_t)1 << B;
+    for (int64_t j = blockIdx.x * (int64_t)nw + w; j < nleaf; j += (int64_t)gridDim.x * nw)
+        m2m_walk(B, stop, j, p, centre, nullptr, M, nullptr, tab, sw, arrive);
+}
+
+// batched: blocks of kWarpChildMax leaves of one system each; every box the
+// walks complete is scaled for the single-precision M2L on the way
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_b_m2m_up(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys, int p,
+           const double *__restrict__ gtab) {
+    extern __shared__ double2 sw[];
+    const double *tab = stage_child_tables(p, gtab, sw);
+    const int s = batch_sys_of(off, nsys, blockIdx.x);
+    const BatchSys &y = S[s];
+    const int64_t j = (blockIdx.x - off[s]) * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j < y.nleaf) m2m_walk(y.B, min(y.lw, y.B), j, p, y.centre, y.radius, y.M, y.Mf, tab, sw, y.arrive);
+}
+
+// The whole downward pass (binary levels) in one launch: warps take boxes in
+// chunks of kL2LChunk from one counter in heap order (level by level), so a
+// box's parent was taken earlier by a running warp; a box whose parent holds
+// a local expansion (parent level >= lw) waits for the parent's flag, then
+// adds the parent's L2L to its own expansion and raises its flag. Each wait
+// is bounded (wait_limit sleeps of ~0.1 us): a wait that runs out sets bit
+// 16 of err[1] (FMM_ETIMEDOUT, results invalid) and the box goes on.
+// `withhold` (>= 0: tests only) is a box whose flag is never raised. With
+// `Lh`, a box first takes its own M2L result L = Lhat / r^n (the
+// single-precision M2L's output), then its parent's L2L.
+constexpr int kL2LChunk = 8;
+__device__ __forceinline__ void l2l_chunk(int lw, int p, const double *__restrict__ centre,
+                                          const double *__restrict__ radius, const double2 *__restrict__ Lh,
+                                          double2 *L, const double *tab, double2 *sw, int *done, int *err, int64_t g0,
+                                          int64_t g1, long long wait_limit, long long withhold) {
+    const int lane = threadIdx.x & 31;
+    WarpChild W;
+    for (int64_t g = g0; g < g1; g++) {
+        const int l = 63 - __clzll((unsigned long long)(g + 1));
+        const int64_t gp = (g - 1) >> 1;
+        if (Lh) warp_unscale_local(radius, g, p, Lh, L);
+        if (l - 1 >= lw) {
+            if (gp > 0) {  // the root's expansion is complete before the launch
+                int ok = 1;
+                if (lane == 0) {
+                    long long it = 0;
+                    while (__ldcg(done + gp) == 0) {
+                        if (++it > wait_limit) {
+                            ok = 0;
+                            atomicOr(err + 1, 16);
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                (void)ok;  // a box whose wait ran out goes on: the error word says the results are invalid
+                __threadfence();  // the parent's expansion after its flag
+            }
+            warp_child_init(g, gp, p, centre, tab, sw, W);
+            l2l_body(W, L, p);
+            __threadfence();
+        }
+        if (lane == 0 && g != withhold) atomicExch(done + g, 1);
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_l2l_down(int B, int lw, int p, const double *__restrict__ centre, double2 *L, const double *__restrict__ gtab,
+           int *done, unsigned long long *next, int *err, long long wait_limit, long long withhold) {
+    extern __shared__ double2 sw[];
+    const double *tab = stage_child_tables(p, gtab, sw);
+    const int lane = threadIdx.x & 31;
+    const int64_t nbox = ((int64_t)2 << B) - 1;
+    for (;;) {
+        unsigned long long c0 = 0;
+        if (lane == 0) c0 = atomicAdd(next, (unsigned long long)kL2LChunk);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if ((int64_t)c0 + 1 >= nbox) break;
+        l2l_chunk(lw, p, centre, nullptr, nullptr, L, tab, sw, done, err, (int64_t)c0 + 1,
+                  std::min<int64_t>((int64_t)c0 + 1 + kL2LChunk, nbox), wait_limit, withhold);
+    }
+}
+
+// batched: chunk c of the queue is chunk c - off[s] of system s (chunks of
+// kL2LChunk boxes from box 0, never across systems), so a box's parent is
+// always earlier in the queue; every box first takes its unscaled M2L result
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_b_l2l_down(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys, int p,
+             const double *__restrict__ gtab, unsigned long long *next, long long wait_limit, long long withhold) {
+    extern __shared__ double2 sw[];
+    const double *tab = stage_child_tables(p, gtab, sw);
+    const int lane = threadIdx.x & 31;
+    const int64_t total = off[nsys];
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(next, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((int64_t)c >= total) break;
+        const int s = batch_sys_of(off, nsys, (int64_t)c);
+        const BatchSys &y = S[s];
+        const int64_t g0 = ((int64_t)c - off[s]) * kL2LChunk;
+        l2l_chunk(y.lw, p, y.centre, y.radius, y.Lh, y.L, tab, sw, y.done, y.err, g0,
+                  std::min<int64_t>(g0 + kL2LChunk, y.nbox), wait_limit, withhold);
+    }
 }
 
 }  // namespace
@@ -499,7 +717,10 @@ cudaError_t m2l_setup(Plan &P) {
     const std::vector<double> &t = m2l_tables_cached(P.p);
     P.m2l_ntab = (int)t.size();
     P.m2l_tab = (double *)palloc(P, t.size() * 8);
-    if (!P.m2l_tab) return cudaErrorMemoryAllocation;
+    P.m2m_arrive = (unsigned *)palloc(P, (size_t)P.nbox * 4);
+    P.l2l_done = (int *)palloc(P, (size_t)P.nbox * 4);
+    P.l2l_next = (unsigned long long *)palloc(P, 8);
+    if (!P.m2l_tab || !P.m2m_arrive || !P.l2l_done || !P.l2l_next) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMemcpyAsync(P.m2l_tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, P.stream);
     if (e != cudaSuccess) return e;
     // stream-ordered copy from pageable memory completes before return
@@ -515,6 +736,10 @@ cudaError_t m2l_setup(Plan &P) {
         e = allow_max_smem((const void *)k_l2l_warp, grp_max);
     if (e == cudaSuccess)
         e = allow_max_smem((const void *)k_m2m_warp, grp_max);
+    if (e == cudaSuccess)
+        e = allow_max_smem((const void *)k_m2m_up, grp_max);
+    if (e == cudaSuccess)
+        e = allow_max_smem((const void *)k_l2l_down, grp_max);
     return e;
 }
 
@@ -556,6 +781,37 @@ cudaError_t m2l_external(Plan &P, int level, int64_t n, const int32_t *tgt, cons
     FMM_LAUNCH(k_m2l_rot_f64, (unsigned)((n + P.m2l_threads - 1) / P.m2l_threads), P.m2l_threads, P.m2l_smem,
                P.stream, PT, P.p, P.centre, (const double2 *)nullptr, P.L_ext, P.m2l_tab, P.m2l_ntab, csrc, Msrc);
     return cudaGetLastError();
+}
+
+// Device-wide bounded waits of the one-launch downward pass: sleeps of
+// ~0.1 us before the wait gives up, and a box whose flag is never raised
+// (tests only; -1 = none). Set by fmm_set_wait_limit.
+std::atomic<long long> g_wait_limit{1LL << 24};
+std::atomic<long long> g_withhold{-1};
+
+// the upward pass of binary levels in one launch, translations up to level `stop`
+void m2m_up(Plan &P, int stop) {
+    const int64_t nleaf = P.nleaf;
+    cudaMemsetAsync(P.M, 0, (size_t)(nleaf - 1) * P.nc * sizeof(double2), P.stream);
+    if (stop >= P.B) return;
+    cudaMemsetAsync(P.m2m_arrive, 0, (size_t)P.nbox * 4, P.stream);
+    const int w = kWarpChildMax;
+    const unsigned grid = (unsigned)std::min<int64_t>((nleaf + w - 1) / w, (int64_t)sm_count() * 16);
+    FMM_LAUNCH(k_m2m_up, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, stop, P.p, P.centre, P.M,
+               P.m2l_tab, P.m2m_arrive);
+}
+
+// the downward pass of binary levels in one launch; boxes whose parent level
+// is below lw receive nothing
+void l2l_down(Plan &P, int lw) {
+    if (P.B == 0) return;
+    cudaMemsetAsync(P.l2l_done, 0, (size_t)P.nbox * 4, P.stream);
+    cudaMemsetAsync(P.l2l_next, 0, 8, P.stream);
+    const int w = kWarpChildMax;
+    const int64_t items = (P.nbox + kL2LChunk - 1) / kL2LChunk;
+    const unsigned grid = (unsigned)std::min<int64_t>((items + w - 1) / w, (int64_t)sm_count() * 8);
+    FMM_LAUNCH(k_l2l_down, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, lw, P.p, P.centre, P.L,
+               P.m2l_tab, P.l2l_done, P.l2l_next, P.d_err, g_wait_limit.load(), g_withhold.load());
 }
 
 // FP64 M2L over all levels in one launch; accumulates into L (zeroed first)
@@ -1193,19 +1449,44 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
     }
 }
 
-// One warp per box: lane n <= p forms r^-n (a single division), and each
-// coefficient takes its degree's factor from that lane.
-__device__ __forceinline__ double inv_radius_pow(const double *__restrict__ radius, int64_t g, int p, int lane) {
-    double pw = 1.0;
-    if (lane <= p) {
-        const double r = radius[g] > 0.0 ? radius[g] : 1.0;
-        double b = 1.0 / r;
-        for (int e = lane; e; e >>= 1) {
-            if (e & 1) pw *= b;
-            b *= b;
-        }
+// batched: the 128-pair chunks of every system of the same order in one launch
+template <int P>
+__global__ void __launch_bounds__(kF32Threads, 3)
+k_b_m2l_rot_f32(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys,
+                const float4 *__restrict__ gtab) {
+    using SP = VSplit<P>;
+    extern __shared__ float2 smf[];  // [NS][threads], the per-warp regions, the tables
+    __shared__ uint32_t s_tmem, s_tphase;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float4 *tab = (float4 *)((char *)smf + SP::TAB);
+    for (int i = tid; i < pair_tab_len(P); i += kF32Threads) tab[i] = gtab[i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tmem)),
+                     "r"(SP::COLS));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tphase)),
+                     "r"(SP::PHC));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    return pw;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = s_tmem, tphase = s_tphase;
+    // chunk c of the batch is chunk c - off[s] of system s (128 pairs each)
+    const int64_t nchunks = off[nsys];
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int s = batch_sys_of(off, nsys, c);
+        const BatchSys &y = S[s];
+        m2l_chunk<P>(y.pt, y.centre, y.radius, y.Mf, y.Lh, tab, (c - off[s]) * kF32Threads + tid, y.npairs, smf,
+                     tbase, tphase);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SP::COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tphase), "r"(SP::PHC));
+    }
 }
 
 // Mhat = M / r^n in float, every box (levels >= 1)
@@ -1325,7 +1606,15 @@ const std::vector<float4> &f32_pair_tables_cached(int p) {
 
 template <int P>
 cudaError_t attr_f32() {
-    return allow_max_smem((const void *)k_m2l_rot_f32<P>, VSplit<P>::SMEM);
+    cudaError_t e = allow_max_smem((const void *)k_m2l_rot_f32<P>, VSplit<P>::SMEM);
+    return e == cudaSuccess ? allow_max_smem((const void *)k_b_m2l_rot_f32<P>, VSplit<P>::SMEM) : e;
+}
+
+template <int P>
+void launch_b_f32(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, const void *tab,
+                  cudaStream_t st) {
+    FMM_LAUNCH(k_b_m2l_rot_f32<P>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(nchunks, (int64_t)sm_count() * 3)),
+               kF32Threads, VSplit<P>::SMEM, st, S, off, nsys, (const float4 *)tab);
 }
 
 template <int P>
@@ -1402,4 +1691,52 @@ cudaError_t m2l_f32_all(Plan &P) {
     return cudaGetLastError();
 }
 
+// ---- batched stages (every system of a batch in one launch per stage)
+cudaError_t batch_m2m_up(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int p, const double *tab,
+                         cudaStream_t st) {
+    if (blocks == 0) return cudaGetLastError();
+    FMM_LAUNCH(k_b_m2m_up, (unsigned)blocks, 32 * kWarpChildMax, warp_child_smem(p, kWarpChildMax), st, S, off, nsys,
+               p, tab);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_m2l(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, int p, const void *tab,
+                      cudaStream_t st) {
+    if (nchunks == 0) return cudaGetLastError();
+    switch (p) {
+        case 4: launch_b_f32<4>(S, off, nsys, nchunks, tab, st); break;
+        case 6: launch_b_f32<6>(S, off, nsys, nchunks, tab, st); break;
+        case 8: launch_b_f32<8>(S, off, nsys, nchunks, tab, st); break;
+        case 10: launch_b_f32<10>(S, off, nsys, nchunks, tab, st); break;
+        case 12: launch_b_f32<12>(S, off, nsys, nchunks, tab, st); break;
+        case 14: launch_b_f32<14>(S, off, nsys, nchunks, tab, st); break;
+        case 16: launch_b_f32<16>(S, off, nsys, nchunks, tab, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_l2l_down(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, int p,
+                           const double *tab, unsigned long long *next, cudaStream_t st) {
+    if (nchunks == 0) return cudaGetLastError();
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((nchunks + kWarpChildMax - 1) / kWarpChildMax, (int64_t)sm_count() * 8));
+    FMM_LAUNCH(k_b_l2l_down, grid, 32 * kWarpChildMax, warp_child_smem(p, kWarpChildMax), st, S, off, nsys, p, tab,
+               next, g_wait_limit.load(), g_withhold.load());
+    return cudaGetLastError();
+}
+
+cudaError_t batch_smem_limits(int p) {
+    const size_t need = warp_child_smem(p, kWarpChildMax);
+    cudaError_t e = allow_max_smem((const void *)k_b_m2m_up, need);
+    return e == cudaSuccess ? allow_max_smem((const void *)k_b_l2l_down, need) : e;
+}
+
 }  // namespace fmm
+
+extern "C" int64_t fmm_set_wait_limit(int64_t sleeps, int64_t withhold) {
+    const long long prev = fmm::g_wait_limit.load();
+    fmm::g_wait_limit.store(sleeps > 0 ? sleeps : (1LL << 24));
+    fmm::g_withhold.store(withhold > 0 ? withhold : -1);
+    return (int64_t)prev;
+}

@@ -7,14 +7,6 @@
 
 namespace fmm {
 
-// weak pairs of every level, concatenated (levels lmin..lmax); passed by value
-struct PairTable {
-    const int32_t *tgt[FMM_MAX_LEVELS + 1];
-    const int32_t *src[FMM_MAX_LEVELS + 1];
-    long long off[FMM_MAX_LEVELS + 2];
-    int lmin, lmax;
-};
-
 __device__ __forceinline__ void pair_of(const PairTable &PT, int64_t g, int64_t &gt, int64_t &gs) {
     int l = PT.lmin;
     while (l < PT.lmax && g >= PT.off[l + 1]) l++;

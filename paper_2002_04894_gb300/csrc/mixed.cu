@@ -78,13 +78,13 @@ __global__ void k_gather_qf(const T *__restrict__ qin, const int32_t *__restrict
 // a 64-term tree. The leaf's multipole is stored unscaled in double
 // (M_n^m = r^n Mhat_n^m).
 constexpr int kP2MSlots = 4;
-__global__ void __launch_bounds__(32)
-k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__restrict__ q,
-          const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
-          const double *__restrict__ radius, double2 *__restrict__ M) {
+__device__ __forceinline__ void p2m_f32_body(int B, int p, int64_t n, const float *__restrict__ hl,
+                                             const float *__restrict__ q, const int32_t *__restrict__ begin,
+                                             const int32_t *__restrict__ count, const double *__restrict__ radius,
+                                             double2 *__restrict__ M, int64_t leaf) {
     extern __shared__ float2 accf[];  // [2][nc]
     const int nc = ncoef(p);
-    const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
+    const int64_t g = ((int64_t)1 << B) - 1 + leaf;
     const int b = begin[g], cnt = count[g];
     const int lane = threadIdx.x;
     const double rs = box_scale(radius[g]);
@@ -167,15 +167,30 @@ k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__
     }
 }
 
+__global__ void __launch_bounds__(32)
+k_p2m_f32(int B, int p, int64_t n, const float *__restrict__ hl, const float *__restrict__ q,
+          const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+          const double *__restrict__ radius, double2 *__restrict__ M) {
+    p2m_f32_body(B, p, n, hl, q, begin, count, radius, M, blockIdx.x);
+}
+
+// batched: one block per leaf of every system (block offsets per system)
+__global__ void __launch_bounds__(32)
+k_b_p2m_f32(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys) {
+    const int s = batch_sys_of(off, nsys, blockIdx.x);
+    const BatchSys &y = S[s];
+    p2m_f32_body(y.B, y.p, y.n, y.hl, y.qf, y.begin, y.count, y.radius, y.M, blockIdx.x - off[s]);
+}
+
 // L2P on scaled offsets: Lhat_k^l = r^k L_k^l; phi = sum Lhat conj(Y(a/r));
 // E = -grad phi = (Re G1, Im G1, -G0) / r with the degree-1 shifted terms.
-__global__ void __launch_bounds__(kThreads)
-k_l2p_f32(int B, int p, int64_t n, const float *__restrict__ hl, const int32_t *__restrict__ begin,
-          const int32_t *__restrict__ count, const double *__restrict__ radius,
-          const double2 *__restrict__ L, float *__restrict__ far_phi, float *__restrict__ far_E) {
+__device__ __forceinline__ void l2p_f32_body(int B, int p, int64_t n, const float *__restrict__ hl,
+                                             const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                                             const double *__restrict__ radius, const double2 *__restrict__ L,
+                                             float *__restrict__ far_phi, float *__restrict__ far_E, int64_t leaf) {
     extern __shared__ float2 Ls[];
     const int nc = ncoef(p);
-    const int64_t g = ((int64_t)1 << B) - 1 + blockIdx.x;
+    const int64_t g = ((int64_t)1 << B) - 1 + leaf;
     const int b = begin[g], cnt = count[g];
     const double rs = box_scale(radius[g]);
     for (int c = threadIdx.x; c < nc; c += kThreads) {
@@ -239,6 +254,20 @@ k_l2p_f32(int B, int p, int64_t n, const float *__restrict__ hl, const int32_t *
         far_E[n + b + i] = g1.y * rinv;
         far_E[2 * n + b + i] = -g0 * rinv;
     }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_l2p_f32(int B, int p, int64_t n, const float *__restrict__ hl, const int32_t *__restrict__ begin,
+          const int32_t *__restrict__ count, const double *__restrict__ radius,
+          const double2 *__restrict__ L, float *__restrict__ far_phi, float *__restrict__ far_E) {
+    l2p_f32_body(B, p, n, hl, begin, count, radius, L, far_phi, far_E, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_b_l2p_f32(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys) {
+    const int s = batch_sys_of(off, nsys, blockIdx.x);
+    const BatchSys &y = S[s];
+    l2p_f32_body(y.B, y.p, y.n, y.hl, y.begin, y.count, y.radius, y.L, y.far_phi, y.far_E, blockIdx.x - off[s]);
 }
 
 __device__ __forceinline__ void kahan(float &s, float &c, float v) {
@@ -357,14 +386,13 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
 // summed in plain float over runs of 64 (full runs with a fixed trip count)
 // and the runs compensated (Kahan).
 template <typename OutT, int T>
-__global__ void __launch_bounds__(T)
-k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
-          const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
-          const float4 *__restrict__ geo, const int32_t *__restrict__ ssrc, const int4 *__restrict__ units,
-          const int32_t *__restrict__ upart, const int32_t *__restrict__ nunits,
-          const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
-          const float *__restrict__ far_E, double4 *__restrict__ partial, OutT *__restrict__ pot,
-          OutT *__restrict__ field) {
+__device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__restrict__ hl,
+                                             const float *__restrict__ qf, const int32_t *__restrict__ begin,
+                                             const int32_t *__restrict__ count, const float4 *__restrict__ geo,
+                                             const int32_t *__restrict__ ssrc, const int4 unit, const int part,
+                                             const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
+                                             const float *__restrict__ far_E, double4 *__restrict__ partial,
+                                             OutT *__restrict__ pot, OutT *__restrict__ field) {
     constexpr int kP2PThreads = T, kSrcTile = T;
     __shared__ float4 sA[kSrcTile / 2], sB[kSrcTile / 2];  // hi parts and charges, per source pair
     __shared__ float4 sC[kSrcTile / 2], sD[kSrcTile / 2];  // lo parts (near leaves)
@@ -374,9 +402,6 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
     static_assert(T == kP2PTile || T == kP2PTileSmall, "one target per thread");
     static_assert(kRun <= kSrcTile, "a run fits in a staged tile");
     const int64_t off = ((int64_t)1 << B) - 1;
-    if ((int)blockIdx.x >= *nunits) return;  // launched for an upper bound on the units
-    const int4 unit = units[blockIdx.x];
-    const int part = upart[blockIdx.x];
     const int t = unit.x;
     const int64_t gt = off + t;
     const int bt = begin[gt], nt = count[gt];
@@ -502,6 +527,31 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
     }
 }
 
+template <typename OutT, int T>
+__global__ void __launch_bounds__(T)
+k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
+          const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+          const float4 *__restrict__ geo, const int32_t *__restrict__ ssrc, const int4 *__restrict__ units,
+          const int32_t *__restrict__ upart, const int32_t *__restrict__ nunits,
+          const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
+          const float *__restrict__ far_E, double4 *__restrict__ partial, OutT *__restrict__ pot,
+          OutT *__restrict__ field) {
+    if ((int)blockIdx.x >= *nunits) return;  // launched for an upper bound on the units
+    p2p_f32_body<OutT, T>(B, n, hl, qf, begin, count, geo, ssrc, units[blockIdx.x], upart[blockIdx.x], perm,
+                          far_phi, far_E, partial, pot, field);
+}
+
+// batched: the work units of every system in one list, heaviest first, each
+// with its system
+template <typename OutT, int T>
+__global__ void __launch_bounds__(T)
+k_b_p2p_f32(const BatchSys *__restrict__ S, const int4 *__restrict__ units, const int32_t *__restrict__ usys,
+            const int32_t *__restrict__ upart) {
+    const BatchSys &y = S[usys[blockIdx.x]];
+    p2p_f32_body<OutT, T>(y.B, y.n, y.hl, y.qf, y.begin, y.count, y.lgeo, y.ssrc, units[blockIdx.x],
+                          upart[blockIdx.x], y.perm, y.far_phi, y.far_E, y.partial, (OutT *)y.pot, (OutT *)y.field);
+}
+
 }  // namespace
 
 cudaError_t mixed_setup(Plan &P) {
@@ -557,6 +607,37 @@ cudaError_t mixed_p2p(Plan &P, void *pot, void *field, int dtype) {
     else
         launch_p2p_f32<kP2PTile>(P, pot, field, dtype);
     return p2p_combine(P, pot, field, dtype);
+}
+
+// ---- batched stages
+// (pmax: the largest order of the batch, for the shared-memory size)
+cudaError_t batch_p2m(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int pmax, cudaStream_t st) {
+    if (blocks == 0) return cudaGetLastError();
+    FMM_LAUNCH(k_b_p2m_f32, (unsigned)blocks, 32, sizeof(float2) * ncoef(pmax) * 2, st, S, off, nsys);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_l2p(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int pmax, cudaStream_t st) {
+    if (blocks == 0) return cudaGetLastError();
+    FMM_LAUNCH(k_b_l2p_f32, (unsigned)blocks, kThreads, sizeof(float2) * ncoef(pmax), st, S, off, nsys);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_p2p(const BatchSys *S, const int4 *units, const int32_t *usys, const int32_t *upart, int64_t n,
+                      int tile, int dtype, cudaStream_t st) {
+    if (n == 0) return cudaGetLastError();
+    if (tile == kP2PTileSmall) {
+        if (dtype == FMM_F64)
+            FMM_LAUNCH((k_b_p2p_f32<double, kP2PTileSmall>), (unsigned)n, kP2PTileSmall, 0, st, S, units, usys, upart);
+        else
+            FMM_LAUNCH((k_b_p2p_f32<float, kP2PTileSmall>), (unsigned)n, kP2PTileSmall, 0, st, S, units, usys, upart);
+    } else {
+        if (dtype == FMM_F64)
+            FMM_LAUNCH((k_b_p2p_f32<double, kP2PTile>), (unsigned)n, kP2PTile, 0, st, S, units, usys, upart);
+        else
+            FMM_LAUNCH((k_b_p2p_f32<float, kP2PTile>), (unsigned)n, kP2PTile, 0, st, S, units, usys, upart);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace fmm

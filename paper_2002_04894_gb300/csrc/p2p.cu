@@ -179,6 +179,37 @@ k_p2p_combine(int B, int64_t npts, const int32_t *__restrict__ begin, const int3
     }
 }
 
+// batched: one block per leaf of every system that has partial slots
+template <typename OutT>
+__global__ void __launch_bounds__(128)
+k_b_p2p_combine(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys) {
+    const int s = batch_sys_of(off, nsys, blockIdx.x);
+    const BatchSys &y = S[s];
+    const int64_t t = blockIdx.x - off[s], nl = y.nleaf;
+    const int p0 = y.poff[t], np = y.poff[t + 1] - p0;
+    if (np == 0) return;
+    const int nt = y.count[nl - 1 + t], bt = y.begin[nl - 1 + t];
+    const int k = np / nt;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        double4 a = y.partial[p0 + i];
+        for (int j = 1; j < k; j++) {
+            const double4 v = y.partial[p0 + j * nt + i];
+            a.x += v.x;
+            a.y += v.y;
+            a.z += v.z;
+            a.w += v.w;
+        }
+        const int64_t g = bt + i;
+        const int64_t o = y.perm[g];
+        ((OutT *)y.pot)[o] = (OutT)((double)y.far_phi[g] + a.x);
+        if (y.field) {
+            ((OutT *)y.field)[3 * o] = (OutT)((double)y.far_E[g] + a.y);
+            ((OutT *)y.field)[3 * o + 1] = (OutT)((double)y.far_E[y.n + g] + a.z);
+            ((OutT *)y.field)[3 * o + 2] = (OutT)((double)y.far_E[2 * y.n + g] + a.w);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t eval_p2p(Plan &P, void *pot, void *field, int dtype) {
@@ -231,6 +262,16 @@ cudaError_t direct_run(const void *points, const void *charges, int64_t n, int d
     else
         FMM_LAUNCH(k_direct<float>, (unsigned)nt, 256, 0, s, (const float *)points, (const float *)charges, n,
                                                      targets, (float *)pot, (float *)field);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_combine(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int dtype,
+                          cudaStream_t st) {
+    if (blocks == 0) return cudaGetLastError();
+    if (dtype == FMM_F64)
+        FMM_LAUNCH(k_b_p2p_combine<double>, (unsigned)blocks, 128, 0, st, S, off, nsys);
+    else
+        FMM_LAUNCH(k_b_p2p_combine<float>, (unsigned)blocks, 128, 0, st, S, off, nsys);
     return cudaGetLastError();
 }
 

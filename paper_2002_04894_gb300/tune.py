@@ -16,7 +16,12 @@ C theta^(p+1) / (1 - theta)^2 (Sec. 3.1). The tuner uses all three:
 The search logic (`descend`) is independent of the GPU: it takes any cost
 function, so it can be exercised on the CPU. `tune` supplies the GPU cost:
 one plan + evaluation timed with CUDA events, and the error against the FP64
-direct sum on sampled targets.
+direct sum on sampled targets. For systems that are evaluated many at a time
+(`batch` > 0) the cost is instead the evaluation time per system of a batch
+of copies of the system in one launch per stage: alone, a small system's
+solve is dominated by per-launch latency, which pushes the search towards
+few levels and heavy near fields; in a batch that latency is shared, and the
+arithmetic is what counts.
 """
 from __future__ import annotations
 
@@ -75,14 +80,22 @@ def descend(cost, start: int, lo: int, hi: int, step: int = 1):
     return x, best, memo
 
 
+def batch_copies(n: int, points: int = 1_000_000, cap: int = 128) -> int:
+    """Copies of an n-point system that make a batch of about `points`."""
+    return max(1, min(cap, points // max(n, 1)))
+
+
 def tune(points, charges, tol: float = 1e-6, leaf_range=(32, 256), thetas=(0.4, 0.5, 0.6),
-         ps=(6, 8, 10, 12, 14, 16), prec=None, targets: int = 300, seed: int = 0) -> TuneResult:
+         ps=(6, 8, 10, 12, 14, 16), prec=None, targets: int = 300, seed: int = 0, batch: int = 0) -> TuneResult:
     """Search (levels, theta, p) for the fastest solve meeting `tol` (relative
-    L2 potential error against the FP64 direct sum on sampled targets)."""
+    L2 potential error against the FP64 direct sum on sampled targets).
+    batch > 0: the cost is the evaluation time per system in a batch of
+    `batch` copies (one launch per stage)."""
     import numpy as np
     import torch
 
-    from . import FMM_PREC_MIXED, fmm_destroy, fmm_direct, fmm_eval, fmm_plan
+    from . import (FMM_PREC_MIXED, fmm_batch_create, fmm_batch_destroy, fmm_batch_launch, fmm_destroy,
+                   fmm_direct, fmm_eval, fmm_plan)
     from . import inputs as _inputs
 
     prec = FMM_PREC_MIXED if prec is None else prec
@@ -93,7 +106,30 @@ def tune(points, charges, tol: float = 1e-6, leaf_range=(32, 256), thetas=(0.4, 
     ref = fmm_direct(xd, qd, tgt)[0].double().cpu().numpy()
     trials = []
 
+    def run_batch(cfg: Config):
+        from .serve import build_plans
+        plans = build_plans([xd] * batch, [cfg] * batch, prec=prec)
+        pots = [torch.empty(n, dtype=qd.dtype, device=qd.device) for _ in range(batch)]
+        b = fmm_batch_create(plans, [qd] * batch, pots)
+        times = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fmm_batch_launch(b)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / batch)
+        fmm_batch_destroy(b)
+        for pl in plans:
+            fmm_destroy(pl)
+        got = pots[0].double().cpu().numpy()[tgt.cpu().numpy()]
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        trials.append((cfg, min(times), err))
+        return min(times), err
+
     def run(cfg: Config):
+        if batch > 0:
+            return run_batch(cfg)
         times = []
         for _ in range(2):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -36,6 +36,13 @@ def test_batch_graph_equals_individual_evals(gpu_lib, prec):
         pots.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
         flds.append(torch.zeros((n, 3), dtype=torch.float64, device="cuda"))
     batch = fmm.fmm_batch_create(plans, qs, pots, flds, nstreams=4)
+    info = fmm.fmm_batch_info(batch)
+    # mixed precision, one order: every system in one launch per stage
+    assert info["fused"] == (prec == 1)
+    if prec == 1:
+        assert info["kernels"] <= 9
+    else:
+        assert info["kernels"] >= len(SYSTEMS)
     for rep in range(2):                                   # replay: same graph, same buffers
         for p_ in pots:
             p_.zero_()
@@ -49,6 +56,84 @@ def test_batch_graph_equals_individual_evals(gpu_lib, prec):
     fmm.fmm_batch_launch(batch)
     torch.cuda.synchronize()
     assert rel(pots[1].cpu().numpy(), -2.0 * alone[1][0]) <= TOL[prec]
+    fmm.fmm_batch_destroy(batch)
+
+
+# (kind, n, levels, tight, p): leaves of ~6 to ~25000 points (both near-field
+# tile sizes), a single leaf, strong lists long enough to be cut into
+# segments, six orders (the order-dependent stages run once per order)
+HETERO = [("uniform", 64, 0, False, 8), ("plummer", 5000, 10, False, 12), ("gmm", 300000, 13, True, 10),
+          ("uniform", 20000, 5, False, 6), ("helix", 9000, 8, True, 14), ("shell", 2500, 9, False, 16),
+          ("plummer", 70000, 9, False, 10), ("uniform", 200000, 3, False, 4)]
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_batched_stages_equal_individual_evals(gpu_lib, dt):
+    fmm = gpu_lib
+    tt = torch.float64 if dt == np.float64 else torch.float32
+    plans, qs, pots, flds, alone = [], [], [], [], []
+    tiles, parts = set(), 0
+    for i, (kind, n, B, tight, p) in enumerate(HETERO):
+        x = torch.from_numpy(inputs.points(kind, n, seed=20 + i).astype(dt)).cuda()
+        q = torch.from_numpy(inputs.charges_uniform(n, seed=20 + i).astype(dt)).cuda()
+        plan = fmm.fmm_plan(x, B, p, 0.5, prec=1, tight=tight)
+        st = fmm.fmm_plan_stats(plan)
+        parts += st["p2p_partial_slots"]
+        tiles.add(n <= 64 * (1 << B))
+        a, b = fmm.fmm_eval(plan, q)
+        alone.append((a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)))
+        plans.append(plan)
+        qs.append(q)
+        pots.append(torch.zeros(n, dtype=tt, device="cuda"))
+        flds.append(torch.zeros((n, 3), dtype=tt, device="cuda") if i % 3 != 2 else None)
+    assert parts > 0 and tiles == {True, False}  # the cases the batched kernels branch on
+    batch = fmm.fmm_batch_create(plans, qs, pots, flds)
+    info = fmm.fmm_batch_info(batch)
+    orders = len({h[4] for h in HETERO})
+    assert info["fused"] and info["kernels"] <= 6 + 3 * orders
+    tol = 1e-6 if dt == np.float64 else 1e-5
+    for rep in range(2):
+        for p_ in pots:
+            p_.zero_()
+        fmm.fmm_batch_launch(batch)
+        torch.cuda.synchronize()
+        for i, ((a, b), p_, f_) in enumerate(zip(alone, pots, flds)):
+            assert rel(p_.cpu().numpy().astype(np.float64), a) <= tol, (i, rep)
+            if f_ is not None:
+                assert rel(f_.cpu().numpy().astype(np.float64), b) <= tol, (i, rep)
+    for plan in plans:
+        fmm.fmm_eval_check(plan)
+    fmm.fmm_batch_destroy(batch)
+
+
+def test_batched_downward_wait_that_runs_out_reports_etimedout(gpu_lib):
+    """The batched downward pass waits (bounded) on each parent as the
+    single-plan pass does: a withheld box (test hook, in force when the batch
+    is made) makes its children's waits run out, and fmm_eval_check reports
+    FMM_ETIMEDOUT on every plan deep enough to hold that box."""
+    fmm = gpu_lib
+    plans, qs, pots = [], [], []
+    for i, (n, B) in enumerate([(20000, 8), (3000, 4), (9000, 8)]):
+        x = torch.from_numpy(inputs.points("uniform", n, seed=40 + i)).cuda()
+        qs.append(torch.from_numpy(inputs.charges_uniform(n, seed=40 + i)).cuda())
+        plans.append(fmm.fmm_plan(x, B, 6, 0.5, prec=1))
+        pots.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
+    withheld = (1 << 7) - 1            # first box of level 7
+    fmm.fmm_set_wait_limit(2000, withheld)
+    try:
+        batch = fmm.fmm_batch_create(plans, qs, pots)
+    finally:
+        fmm.fmm_set_wait_limit(0, -1)
+    assert fmm.fmm_batch_info(batch)["fused"]
+    fmm.fmm_batch_launch(batch)
+    torch.cuda.synchronize()
+    for plan, deep in zip(plans, [True, False, True]):
+        if deep:
+            with pytest.raises(fmm.FmmError) as e:
+                fmm.fmm_eval_check(plan)
+            assert e.value.status == -5
+        else:
+            fmm.fmm_eval_check(plan)
     fmm.fmm_batch_destroy(batch)
 
 
@@ -86,10 +171,11 @@ def test_server_tight_budget_serialises_but_completes(gpu_lib):
     assert len(res) == 5 and adm.peak <= need + 1
 
 
-def test_tuner_meets_target(gpu_lib):
+@pytest.mark.parametrize("batch", [0, 8])
+def test_tuner_meets_target(gpu_lib, batch):
     x = torch.from_numpy(inputs.points("plummer", 60000, 3)).cuda()
     q = torch.from_numpy(inputs.charges_uniform(60000, 3)).cuda()
-    r = tune.tune(x, q, tol=1e-5, ps=(6, 8, 10, 12))
+    r = tune.tune(x, q, tol=1e-5, ps=(6, 8, 10, 12), batch=batch)
     assert r.error <= 1e-5
     assert 32 <= 60000 / 2 ** r.config.levels <= 256
     assert r.config.theta in (0.4, 0.5, 0.6)

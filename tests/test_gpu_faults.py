@@ -107,3 +107,31 @@ def test_nonfinite_point_is_reported_and_nothing_leaks(gpu_lib):
     a = CountingAllocator(fmm)
     st, h = _plan(fmm, torch.from_numpy(xn).cuda(), a)
     assert st == -3 and not h.value and a.balance == 0
+
+
+def test_downward_wait_that_runs_out_reports_etimedout(gpu_lib):
+    """The one-launch downward pass waits (bounded) for each parent's local
+    expansion. A box whose completion is withheld (test hook) makes its
+    children's waits run out: the evaluation ends, and fmm_eval_check
+    reports FMM_ETIMEDOUT. With the limit restored a new plan evaluates as
+    before."""
+    fmm = gpu_lib
+    x = torch.from_numpy(inputs.points("uniform", 20000, 4)).cuda()
+    q = torch.from_numpy(inputs.charges_uniform(20000, 4)).cuda()
+    B = 8
+    good, _ = fmm.fmm_eval(fmm.fmm_plan(x, B, 6, 0.5), q)
+    plan = fmm.fmm_plan(x, B, 6, 0.5)
+    withheld = (1 << (B - 1)) - 1          # first box of the level above the leaves
+    prev = fmm.fmm_set_wait_limit(2000, withheld)
+    try:
+        fmm.fmm_eval(plan, q)
+        with pytest.raises(fmm.FmmError) as e:
+            fmm.fmm_eval_check(plan)
+        assert e.value.status == -5        # FMM_ETIMEDOUT
+    finally:
+        fmm.fmm_set_wait_limit(0, -1)
+    assert prev > 0
+    plan2 = fmm.fmm_plan(x, B, 6, 0.5)
+    again, _ = fmm.fmm_eval(plan2, q)
+    fmm.fmm_eval_check(plan2)
+    assert (torch.linalg.norm(again - good) / torch.linalg.norm(good)).item() <= 1e-13
