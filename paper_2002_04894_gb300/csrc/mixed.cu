@@ -410,6 +410,9 @@ __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__re
     const int tid = threadIdx.x;
     const int i = unit.y + tid;
     const bool active = i < nt;
+    // a warp with no target of the unit stages sources and keeps the barriers
+    // but skips the products (the warps past a small leaf's last target)
+    const bool busy = __any_sync(0xffffffffu, active);  // warp-uniform
     float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
     if (active) {
         xh = hl[bt + i], yh = hl[n + bt + i], zh = hl[2 * n + bt + i];
@@ -481,7 +484,7 @@ __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__re
                 }
                 __syncthreads();
                 const int mcount = min(kSrcTile, ns - sb);
-                for (int j0 = 0; j0 < mcount; j0 += kRun) {
+                for (int j0 = 0; j0 < (busy ? mcount : 0); j0 += kRun) {
                     const int npair = (min(kRun, mcount - j0) + 1) >> 1;
                     const int p0 = j0 >> 1;
                     float2 a[4];

@@ -48,6 +48,10 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
         const int tb = unit.y;
         const int i = tb + threadIdx.x;
         const bool active = i < nt;
+        // a warp with no target of the unit stages sources and keeps the
+        // barriers, but skips the products (small leaves: the warps past the
+        // leaf's last target cost no arithmetic)
+        const bool busy = __any_sync(0xffffffffu, active);  // warp-uniform
         const double xi = active ? x[bt + i] : 0.0;
         const double yi = active ? y[bt + i] : 0.0;
         const double zi = active ? z[bt + i] : 0.0;
@@ -60,7 +64,7 @@ k_p2p_f64(int B, int64_t npts, const double *__restrict__ x, const double *__res
                 tile[threadIdx.x] = j < ns ? Src{x[bs + j], y[bs + j], z[bs + j], q[bs + j]} : Src{0.0, 0.0, 0.0, 0.0};
                 __syncthreads();
                 const int mcount = min(kP2PThreads, ns - sb);
-                for (int jj = 0; jj < mcount; jj++) {
+                for (int jj = 0; jj < (busy ? mcount : 0); jj++) {
                     const Src s = tile[jj];
                     const double dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
                     const double r2 = dx * dx + dy * dy + dz * dz;
