@@ -96,7 +96,7 @@ bool batch_eligible(const Plan *const *plans, int n) {
     int groups = 0;
     for (int i = 0; i < n; i++) {
         const Plan &P = *plans[i];
-        if (P.prec != FMM_PREC_MIXED || P.step != 1 || !P.Mf || P.m2l_tc || !P.f32_tab) return false;
+        if (P.prec != FMM_PREC_MIXED || P.step != 1 || !P.Mf || P.m2l_tc || !P.f32_tab || !P.box_geo) return false;
         if (P.dtype != A.dtype || P.device != A.device) return false;
         if (!seen[P.p]) seen[P.p] = true, groups++;
     }
@@ -170,6 +170,7 @@ cudaError_t batch_setup(const Plan *const *plans, int n, const void *const *char
         y.units = P.p2p_units;
         y.upart = P.p2p_upart;
         y.ubstart = P.p2p_bstart;
+        y.box_geo = P.box_geo;
         y.pt = pair_table(P);
         cnt[kOffPrep][i] =
             std::max<int64_t>(1, (std::max<int64_t>(P.n, P.nbox * P.nc) + kPrepItems - 1) / kPrepItems);
@@ -182,6 +183,7 @@ cudaError_t batch_setup(const Plan *const *plans, int n, const void *const *char
         gcnt[g][kGrpL2L][i] = (P.nbox + 7) / 8;
         if (!R.grp[g].tab) {
             R.grp[g].tab = P.m2l_tab;
+            R.grp[g].tab_df = P.m2l_tab_df;
             R.grp[g].ftab = P.f32_tab;
         }
     }
@@ -286,7 +288,7 @@ cudaError_t batch_enqueue(const BatchRun &R, cudaStream_t st) {
     if (e == cudaSuccess) e = batch_p2m(R.S, R.off[kOffLeaf], n, R.blocks[kOffLeaf], R.pmax, st);
     for (int g = 0; g < R.ngroups && e == cudaSuccess; g++) {
         const BatchGroup &G = R.grp[g];
-        e = batch_m2m_up(R.S, G.off[kGrpM2M], n, G.blocks[kGrpM2M], G.p, G.tab, st);
+        e = batch_m2m_up(R.S, G.off[kGrpM2M], n, G.blocks[kGrpM2M], G.p, G.tab_df, st);
     }
     for (int g = 0; g < R.ngroups && e == cudaSuccess; g++) {
         const BatchGroup &G = R.grp[g];
@@ -294,7 +296,7 @@ cudaError_t batch_enqueue(const BatchRun &R, cudaStream_t st) {
     }
     for (int g = 0; g < R.ngroups && e == cudaSuccess; g++) {
         const BatchGroup &G = R.grp[g];
-        e = batch_l2l_down(R.S, G.off[kGrpL2L], n, G.blocks[kGrpL2L], G.p, G.tab, R.next + g, st);
+        e = batch_l2l_down(R.S, G.off[kGrpL2L], n, G.blocks[kGrpL2L], G.p, G.tab, G.tab_df, R.next + g, st);
     }
     if (e == cudaSuccess) e = batch_l2p(R.S, R.off[kOffLeaf], n, R.blocks[kOffLeaf], R.pmax, st);
     if (e == cudaSuccess) e = batch_p2p(R.S, R.units, R.usys, R.upart, R.nunits[0], kP2PTileSmall, R.dtype, st);

@@ -61,6 +61,7 @@ struct BatchSys {
     const void *charges;
     void *pot, *field;
     double4 *partial;
+    const void *box_geo;           // per box: geometry of the translation to / from its parent
     const int4 *units;             // near-field work units, heaviest bucket first
     const int32_t *upart, *ubstart;
     PairTable pt;
@@ -139,6 +140,10 @@ struct Plan {
     bool capacity_exceeded = false;
     // M2L rotation tables (D = d(pi/2) quadrants, axial coefficients, F_nm)
     double *m2l_tab = nullptr;
+    // mixed form: the same tables as double-float pairs (hi, lo floats), and
+    // per box the geometry of its translation from / to its parent
+    float2 *m2l_tab_df = nullptr;
+    void *box_geo = nullptr;
     unsigned *m2m_arrive = nullptr;         // one-launch upward pass: arrivals per parent
     int *l2l_done = nullptr;                // one-launch downward pass: box finished
     unsigned long long *l2l_next = nullptr; // one-launch downward pass: next box to take
@@ -267,12 +272,12 @@ cudaError_t add_external_near(Plan &P);
 // levels) in one launch per stage; `off` holds per-system block (or chunk)
 // offsets, off[nsys] = the total
 cudaError_t batch_p2m(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int pmax, cudaStream_t st);
-cudaError_t batch_m2m_up(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int p, const double *tab,
-                         cudaStream_t st);
+cudaError_t batch_m2m_up(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int p,
+                         const float2 *tab_df, cudaStream_t st);
 cudaError_t batch_m2l(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, int p, const void *tab,
                       cudaStream_t st);
 cudaError_t batch_l2l_down(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, int p,
-                           const double *tab, unsigned long long *next, cudaStream_t st);
+                           const double *tab, const float2 *tab_df, unsigned long long *next, cudaStream_t st);
 cudaError_t batch_l2p(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int pmax, cudaStream_t st);
 cudaError_t batch_p2p(const BatchSys *S, const int4 *units, const int32_t *usys, const int32_t *upart, int64_t n,
                       int tile, int dtype, cudaStream_t st);
@@ -289,6 +294,7 @@ struct BatchGroup {
     int32_t *off[3] = {};    // M2M blocks, M2L chunks, L2L chunks (other orders: none)
     int64_t blocks[3] = {};
     const double *tab = nullptr;
+    const float2 *tab_df = nullptr;
     const void *ftab = nullptr;
 };
 struct BatchRun {

@@ -315,29 +315,18 @@ __device__ __forceinline__ double *stage_child_tables(int p, const double *__res
 
 // The warp's child gc, its parent gp, and the powers of the child-to-parent
 // offset, in the warp's slice of shared memory (warp-synchronous only).
-__device__ __forceinline__ void warp_child_init(int64_t gc, int64_t gp, int p, const double *__restrict__ centre,
-                                                const double *tab, double2 *sw, WarpChild &W) {
-    const int nc = ncoef(p), w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
-    W.A = sw + w * warp_slice(p);
-    W.B = W.A + nc;
-    W.pa = W.B + nc;
-    W.pb = W.pa + p + 1;
-    W.f = (double *)(W.pb + p + 1);
-    W.Dt = tab;
-    W.Ft = tab + nD;
-    W.iFt = W.Ft + nc;
-    W.gc = gc;
-    W.gp = gp;
-    W.nc = nc;
-    W.lane = lane;
+// the child-to-parent offset's powers e^{ia}, e^{ib} and rho^k/k! (lanes
+// 0..2) into the warp's slice
+__device__ __forceinline__ void warp_child_geometry(WarpChild &W, int p, const double *__restrict__ centre) {
+    const int64_t gc = W.gc, gp = W.gp;
+    const int lane = W.lane;
     __syncwarp();
     if (lane < 3) {
         const double dx = centre[3 * gc] - centre[3 * gp], dy = centre[3 * gc + 1] - centre[3 * gp + 1],
                      dz = centre[3 * gc + 2] - centre[3 * gp + 2];
         const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
         if (lane == 2) {
-            const double *ik = W.iFt + nc;
+            const double *ik = W.iFt + W.nc;
             double t = 1.0;
             for (int k = 0; k <= p; k++) {
                 W.f[k] = t;
@@ -362,18 +351,25 @@ __device__ __forceinline__ void warp_child_init(int64_t gc, int64_t gp, int p, c
     __syncwarp();
 }
 
-// Tables into shared memory; the warp's child of `level` (block-strided),
-// its parent at `step` levels up. Returns false for warps past the end of
-// the level (they take no further part: no block barrier follows).
-__device__ __forceinline__ bool warp_child_setup(int level, int step, int p, const double *__restrict__ centre,
-                                                 const double *__restrict__ gtab, double2 *sw, WarpChild &W) {
-    const double *tab = stage_child_tables(p, gtab, sw);
-    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-    const int64_t j = blockIdx.x * (int64_t)nw + w;
-    if (j >= ((int64_t)1 << level)) return false;
-    const int64_t gc = ((int64_t)1 << level) - 1 + j;
-    warp_child_init(gc, ((gc + 1) >> step) - 1, p, centre, tab, sw, W);
-    return true;
+// The warp's child gc, its parent gp, and the powers of the child-to-parent
+// offset, in the warp's slice of shared memory (warp-synchronous only).
+__device__ __forceinline__ void warp_child_init(int64_t gc, int64_t gp, int p, const double *__restrict__ centre,
+                                                const double *tab, double2 *sw, WarpChild &W) {
+    const int nc = ncoef(p), w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    W.A = sw + w * warp_slice(p);
+    W.B = W.A + nc;
+    W.pa = W.B + nc;
+    W.pb = W.pa + p + 1;
+    W.f = (double *)(W.pb + p + 1);
+    W.Dt = tab;
+    W.Ft = tab + nD;
+    W.iFt = W.Ft + nc;
+    W.gc = gc;
+    W.gp = gp;
+    W.nc = nc;
+    W.lane = lane;
+    warp_child_geometry(W, p, centre);
 }
 
 // M2M of the warp's child into its parent (atomic adds). The child's
@@ -463,22 +459,417 @@ __device__ __forceinline__ void l2l_body(const WarpChild &W, double2 *L, int pma
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kWarpChildMax * 32)
-k_m2m_warp(int level, int step, int p, const double *__restrict__ centre, double2 *M,
-           const double *__restrict__ gtab) {
-    extern __shared__ double2 sw[];
-    WarpChild W;
-    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
-    m2m_body(W, M);
+// ---------------------------------------------------------------------------
+// Double-float translations (mixed form). GB300's FP64 pipe retires ~1.7
+// multiply-adds per clock per SM against 128 on the FP32 pipe, so M2M and
+// L2L in double precision cost as much as all the single-precision stages
+// together. The mixed form runs them in double-float arithmetic instead: a
+// value is an unevaluated sum hi + lo of two floats (Dekker's and Knuth's
+// error-free transformations: TwoSum, and TwoProd through the fused
+// multiply-add), about 44 significant bits, every operation an explicitly
+// rounded intrinsic so that the compiler neither contracts nor reorders it.
+// Float's exponent range would not hold a deep box's high-degree
+// multipole (M_n ~ q r^n), so the coefficients are scaled while translated
+// by s = 2^e, the power of two within a factor 2 below the parent's radius
+// (exact in double): M2M reads M_n / s^n and writes s^n times its result,
+// L2L reads L_n s^n and writes s^-n times its result, and the axial factors
+// become (rho / s)^k / k!: every value stays O(1). Rotations act within a
+// degree and commute with the scaling. The stored expansions stay double.
+// ---------------------------------------------------------------------------
+struct DF {
+    float h, l;
+};
+struct CDF {
+    DF x, y;
+};
+__device__ __forceinline__ DF df_of(double d) {
+    const float h = __double2float_rn(d);
+    return {h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double df_val(DF a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.h, -a.l}; }
+// s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+// renormalise (|a| >= |b|, or a + b rounds to a)
+__device__ __forceinline__ DF df_fast(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// a b: the product's rounding error from the fused multiply-add, plus the cross terms
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_fast(p, e);
+}
+// a b + c
+__device__ __forceinline__ DF df_fma(DF a, DF b, DF c) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const DF s = df_two_sum(p, c.h);
+    return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(e, c.l)));
+}
+__device__ __forceinline__ CDF cdf_of(double2 v) { return {df_of(v.x), df_of(v.y)}; }
+__device__ __forceinline__ double2 cdf_val(CDF a) { return make_double2(df_val(a.x), df_val(a.y)); }
+__device__ __forceinline__ CDF cdf_conj(CDF a) { return {a.x, df_neg(a.y)}; }
+__device__ __forceinline__ CDF cdf_mul(CDF a, CDF b) {
+    return {df_fma(a.x, b.x, df_neg(df_mul(a.y, b.y))), df_fma(a.x, b.y, df_mul(a.y, b.x))};
+}
+__device__ __forceinline__ CDF cdf_scale(CDF a, DF s) { return {df_mul(a.x, s), df_mul(a.y, s)}; }
+// exact doubling
+__device__ __forceinline__ CDF cdf_twice(CDF a) {
+    return {{2.f * a.x.h, 2.f * a.x.l}, {2.f * a.y.h, 2.f * a.y.l}};
+}
+__device__ __forceinline__ CDF cdf_ipow(int m, CDF v) {  // i^m v
+    switch (m & 3) {
+        case 0: return v;
+        case 1: return {df_neg(v.y), v.x};
+        case 2: return {df_neg(v.x), df_neg(v.y)};
+        default: return {v.y, df_neg(v.x)};
+    }
 }
 
+// Geometry of box g's translation to / from its parent, formed once per
+// plan in double (k_box_geo) and kept as double-float pairs: the unit
+// complex numbers e^{ia} (azimuth) and e^{ib} (polar angle of the offset),
+// and q = rho / s for the scale s = 2^e, the power of two with
+// s <= r_p < 2 s (r_p the parent's radius): scaling by powers of two is exact
+// and needs no power of r_p in float, whose range r_p^12 of a deep box
+// would leave.
+struct alignas(16) BoxGeo {
+    CDF za, zb;
+    DF q;
+    int e;     // s = 2^e
+    int skip;  // an empty box outside its parent's box (rho > 2 r_p): nothing to translate
+};
+
+// 2^k as a double, for |k| <= 1022
+__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+// 1/k! as double-float pairs, built at compile time
+struct IFact {
+    DF v[FMM_MAX_P + 2];
+};
+constexpr IFact make_ifact() {
+    IFact t{};
+    double f = 1.0;
+    for (int k = 0; k <= FMM_MAX_P + 1; k++) {
+        if (k > 1) f /= (double)k;
+        const float h = (float)f;
+        t.v[k] = DF{h, (float)(f - (double)h)};
+    }
+    return t;
+}
+__constant__ IFact c_ifact = make_ifact();
+
+__device__ __forceinline__ DF df_pow(DF x, int k) {
+    DF r = {1.f, 0.f};
+    while (k) {
+        if (k & 1) r = df_mul(r, x);
+        k >>= 1;
+        if (k) x = df_mul(x, x);
+    }
+    return r;
+}
+__device__ __forceinline__ CDF cdf_pow(CDF z, int k) {
+    CDF r = {{1.f, 0.f}, {0.f, 0.f}};
+    while (k) {
+        if (k & 1) r = cdf_mul(r, z);
+        k >>= 1;
+        if (k) z = cdf_mul(z, z);
+    }
+    return r;
+}
+
+// one thread per box (box 0 has no parent)
+__global__ void k_box_geo(int64_t nbox, int step, const double *__restrict__ centre,
+                          const double *__restrict__ radius, BoxGeo *__restrict__ geo) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nbox; g += (int64_t)gridDim.x * blockDim.x) {
+        BoxGeo o{};
+        if (g == 0) {
+            o.skip = 1;
+            geo[g] = o;
+            continue;
+        }
+        const int64_t gp = ((g + 1) >> step) - 1;
+        const double dx = centre[3 * g] - centre[3 * gp], dy = centre[3 * g + 1] - centre[3 * gp + 1],
+                     dz = centre[3 * g + 2] - centre[3 * gp + 2];
+        const double rxy = sqrt(dx * dx + dy * dy), rho = sqrt(dx * dx + dy * dy + dz * dz);
+        const double rp = radius[gp] > 0.0 ? radius[gp] : 1.0;
+        // s = 2^e <= r_p < 2^(e+1); |e| <= 48 keeps s^n within double range for n <= 20
+        const int e = max(-48, min(48, ilogb(rp)));
+        o.za = rxy > 0.0 ? cdf_of(make_double2(dx / rxy, dy / rxy)) : cdf_of(make_double2(1.0, 0.0));
+        o.zb = rho > 0.0 ? cdf_of(make_double2(dz / rho, rxy / rho)) : cdf_of(make_double2(1.0, 0.0));
+        o.q = df_of(rho * pow2i(-e));
+        o.e = e;
+        o.skip = rho > 2.0 * rp;
+        geo[g] = o;
+    }
+}
+
+struct WarpChildDF {
+    CDF *A, *B, *pa, *pb;
+    DF *f;  // (rho / s)^k / k!
+    const DF *Dt, *Ft, *iFt;
+    int64_t gc, gp;
+    int nc, lane, e;  // s = 2^e
+    bool skip;
+};
+
+// The double-float tables into shared memory (plain copies; same offsets as the double tables)
+__device__ __forceinline__ const DF *stage_child_tables_df(int p, const float2 *__restrict__ gtab, double2 *sw) {
+    const int nc = ncoef(p), nw = blockDim.x >> 5;
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    float2 *tab = (float2 *)(sw + nw * warp_slice(p));
+    for (int i = threadIdx.x; i < nD; i += blockDim.x) tab[i] = gtab[i];
+    for (int i = threadIdx.x; i < 2 * nc + p + 2; i += blockDim.x) tab[nD + i] = gtab[2 * nD + i];
+    __syncthreads();
+    return (const DF *)tab;
+}
+
+// the warp's child: the powers of its geometry, lanes over the degrees, all
+// in double-float on the FP32 pipe
+__device__ __forceinline__ void warp_child_init_df(int64_t gc, int64_t gp, int p, const BoxGeo *__restrict__ geo,
+                                                   const DF *tab, double2 *sw, WarpChildDF &W) {
+    const int nc = ncoef(p), w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+    double2 *base = sw + w * warp_slice(p);
+    W.A = (CDF *)base;
+    W.B = W.A + nc;
+    W.pa = W.B + nc;
+    W.pb = W.pa + p + 1;
+    W.f = (DF *)(W.pb + p + 1);
+    W.Dt = tab;
+    W.Ft = tab + nD;
+    W.iFt = W.Ft + nc;
+    W.gc = gc;
+    W.gp = gp;
+    W.nc = nc;
+    W.lane = lane;
+    const BoxGeo o = geo[gc];
+    W.skip = o.skip != 0;
+    W.e = o.e;
+    __syncwarp();
+    for (int k = lane; k <= p; k += 32) {
+        W.pa[k] = cdf_pow(o.za, k);
+        W.pb[k] = cdf_pow(o.zb, k);
+        W.f[k] = df_mul(df_pow(o.q, k), c_ifact.v[k]);
+    }
+    __syncwarp();
+}
+
+// out_k = fold(D^n) of in, in double-float (as fold_all)
+template <bool kTranspose, typename Post>
+__device__ __forceinline__ void fold_all_df(const DF *__restrict__ Dt, int nc, const CDF *in, int lane, Post post) {
+    for (int c = lane; c < nc; c += 32) {
+        const int n = degree_of(c), b = tri(n, 0), k = c - b, par = (n + k) & 1;
+        const DF *Dn = Dt + n * (n + 1) * (2 * n + 1) / 6;
+        DF ev = {0.f, 0.f}, od = {0.f, 0.f};  // sums over even and odd m
+        int m = 0;
+        for (; m + 1 <= n; m += 2) {
+            const CDF v0 = in[b + m], v1 = in[b + m + 1];
+            ev = df_fma(kTranspose ? Dn[m * (n + 1) + k] : Dn[k * (n + 1) + m], par ? v0.y : v0.x, ev);
+            od = df_fma(kTranspose ? Dn[(m + 1) * (n + 1) + k] : Dn[k * (n + 1) + m + 1], par ? v1.x : v1.y, od);
+        }
+        if (m == n) {
+            const CDF v0 = in[b + m];
+            ev = df_fma(kTranspose ? Dn[m * (n + 1) + k] : Dn[k * (n + 1) + m], par ? v0.y : v0.x, ev);
+        }
+        post(c, k, par ? CDF{od, ev} : CDF{ev, od});
+    }
+}
+
+// m2m_body in double-float on scaled coefficients
+__device__ __forceinline__ void m2m_body_df(const WarpChildDF &W, double2 *M) {
+    const int nc = W.nc, lane = W.lane;
+    CDF *A = W.A, *B = W.B;
+    const CDF *pa = W.pa, *pb = W.pb;
+    const DF *f = W.f, *Ft = W.Ft, *iFt = W.iFt;
+    for (int c = lane; c < nc; c += 32) {
+        const int n = degree_of(c), m = c - tri(n, 0);
+        const double sc = pow2i(-W.e * n);  // M_n / s^n, exact
+        const double2 v = __ldcg(M + W.gc * nc + c);
+        const CDF u = cdf_mul(cdf_of(make_double2(v.x * sc, v.y * sc)), cdf_ipow(4 - (m & 3), pa[m]));
+        A[c] = m ? cdf_twice(cdf_scale(u, Ft[c])) : cdf_scale(u, Ft[c]);
+    }
+    __syncwarp();
+    fold_all_df<false>(W.Dt, nc, A, lane, [&](int c, int k, CDF r) {
+        const CDF t = cdf_mul(r, pb[k]);
+        B[c] = k ? cdf_twice(t) : t;
+    });
+    __syncwarp();
+    fold_all_df<true>(W.Dt, nc, B, lane, [&](int c, int m, CDF r) { A[c] = cdf_scale(cdf_ipow(m, r), iFt[c]); });
+    __syncwarp();
+    for (int c = lane; c < nc; c += 32) {
+        const int n = degree_of(c), m = c - tri(n, 0);
+        DF re = {0.f, 0.f}, im = {0.f, 0.f};
+        for (int k = 0; k <= n - m; k++) {
+            const CDF t = A[tri(n - k, m)];
+            re = df_fma(f[k], t.x, re);
+            im = df_fma(f[k], t.y, im);
+        }
+        const CDF u = cdf_scale(cdf_ipow(4 - (m & 3), CDF{re, im}), Ft[c]);
+        B[c] = m ? cdf_twice(u) : u;
+    }
+    __syncwarp();
+    fold_all_df<false>(W.Dt, nc, B, lane, [&](int c, int k, CDF r) {
+        const CDF t = cdf_mul(r, cdf_conj(pb[k]));
+        A[c] = k ? cdf_twice(t) : t;
+    });
+    __syncwarp();
+    double2 *Mp = M + W.gp * nc;
+    fold_all_df<true>(W.Dt, nc, A, lane, [&](int c, int m, CDF r) {
+        const double2 t = cdf_val(cdf_scale(cdf_mul(cdf_ipow(m, r), cdf_conj(pa[m])), iFt[c]));
+        const double sc = pow2i(W.e * degree_of(c));  // times s^n, exact
+        atomicAdd(&Mp[c].x, t.x * sc);
+        atomicAdd(&Mp[c].y, t.y * sc);
+    });
+    __syncwarp();
+}
+
+// l2l_body in double-float on scaled coefficients
+__device__ __forceinline__ void l2l_body_df(const WarpChildDF &W, double2 *L, int pmax) {
+    const int nc = W.nc, lane = W.lane;
+    CDF *A = W.A, *B = W.B;
+    const CDF *pa = W.pa, *pb = W.pb;
+    const DF *f = W.f, *Ft = W.Ft, *iFt = W.iFt;
+    for (int c = lane; c < nc; c += 32) {
+        const int n = degree_of(c), l = c - tri(n, 0);
+        const double sc = pow2i(W.e * n);  // L_n s^n, exact
+        const double2 w = __ldcg(L + W.gp * nc + c);
+        const CDF v = cdf_of(make_double2(w.x * sc, w.y * sc));
+        const CDF u = cdf_scale(cdf_mul(cdf_ipow(l, v), cdf_conj(pa[l])), iFt[c]);
+        A[c] = l ? cdf_twice(u) : u;
+    }
+    __syncwarp();
+    fold_all_df<false>(W.Dt, nc, A, lane, [&](int c, int k, CDF r) {
+        const CDF t = cdf_mul(r, cdf_conj(pb[k]));
+        B[c] = k ? cdf_twice(t) : t;
+    });
+    __syncwarp();
+    fold_all_df<true>(W.Dt, nc, B, lane,
+                      [&](int c, int m, CDF r) { A[c] = cdf_scale(cdf_ipow(4 - (m & 3), r), Ft[c]); });
+    __syncwarp();
+    for (int c = lane; c < nc; c += 32) {
+        const int j = degree_of(c), i = c - tri(j, 0);
+        DF re = {0.f, 0.f}, im = {0.f, 0.f};
+        for (int k = j; k <= pmax; k++) {
+            const CDF t = A[tri(k, i)];
+            re = df_fma(f[k - j], t.x, re);
+            im = df_fma(f[k - j], t.y, im);
+        }
+        const CDF u = cdf_scale(cdf_ipow(i, CDF{re, im}), iFt[c]);
+        B[c] = i ? cdf_twice(u) : u;
+    }
+    __syncwarp();
+    fold_all_df<false>(W.Dt, nc, B, lane, [&](int c, int k, CDF r) {
+        const CDF t = cdf_mul(r, pb[k]);
+        A[c] = k ? cdf_twice(t) : t;
+    });
+    __syncwarp();
+    double2 *Lc = L + W.gc * nc;
+    fold_all_df<true>(W.Dt, nc, A, lane, [&](int c, int l, CDF r) {
+        const double2 t = cdf_val(cdf_scale(cdf_mul(cdf_ipow(4 - (l & 3), r), pa[l]), Ft[c]));
+        const double sc = pow2i(-W.e * degree_of(c));  // times s^-n, exact
+        Lc[c] = cadd(Lc[c], make_double2(t.x * sc, t.y * sc));
+    });
+    __syncwarp();
+}
+
+// What the translation kernels read besides the expansions.
+struct TrIn {
+    const double *centre, *radius;
+    const BoxGeo *geo;      // double-float translations
+    const double *tab;      // tables in double (global memory)
+    const float2 *tab_df;   // the same as double-float pairs
+};
+
+// One translation of child gc with parent gp, in double (FP64 form) or in
+// double-float (DFT: mixed form); `tab` from stage_tables<DFT>.
+template <bool DFT>
+__device__ __forceinline__ const void *stage_tables(int p, const TrIn &a, double2 *sw) {
+    if constexpr (DFT)
+        return stage_child_tables_df(p, a.tab_df, sw);
+    else
+        return stage_child_tables(p, a.tab, sw);
+}
+template <bool DFT>
+__device__ __forceinline__ void m2m_one(int64_t gc, int64_t gp, int p, const TrIn &a, double2 *M, const void *tab,
+                                        double2 *sw) {
+    if constexpr (DFT) {
+        WarpChildDF W;
+        warp_child_init_df(gc, gp, p, a.geo, (const DF *)tab, sw, W);
+        if (!W.skip) m2m_body_df(W, M);  // skipped: an empty child, whose multipole is zero
+    } else {
+        WarpChild W;
+        warp_child_init(gc, gp, p, a.centre, (const double *)tab, sw, W);
+        m2m_body(W, M);
+    }
+}
+template <bool DFT>
+__device__ __forceinline__ void l2l_one(int64_t gc, int64_t gp, int p, const TrIn &a, double2 *L, const void *tab,
+                                        double2 *sw) {
+    if constexpr (DFT) {
+        WarpChildDF W;
+        warp_child_init_df(gc, gp, p, a.geo, (const DF *)tab, sw, W);
+        if (!W.skip) {
+            l2l_body_df(W, L, p);
+        } else {
+            // an empty box outside its parent's (tight) box: its expansion
+            // reaches no point, and translated that far it would leave the
+            // float range; formed in double with the tables from global memory
+            const int nD = (p + 1) * (p + 2) * (2 * p + 3) / 6;
+            WarpChild V;
+            V.A = (double2 *)W.A;
+            V.B = (double2 *)W.B;
+            V.pa = (double2 *)W.pa;
+            V.pb = (double2 *)W.pb;
+            V.f = (double *)W.f;
+            V.Dt = a.tab;
+            V.Ft = a.tab + 2 * nD;
+            V.iFt = V.Ft + W.nc;
+            V.gc = gc;
+            V.gp = gp;
+            V.nc = W.nc;
+            V.lane = W.lane;
+            warp_child_geometry(V, p, a.centre);
+            l2l_body(V, L, p);
+        }
+    } else {
+        WarpChild W;
+        warp_child_init(gc, gp, p, a.centre, (const double *)tab, sw, W);
+        l2l_body(W, L, p);
+    }
+}
+
+template <bool DFT>
 __global__ void __launch_bounds__(kWarpChildMax * 32)
-k_l2l_warp(int level, int step, int p, const double *__restrict__ centre, double2 *L,
-           const double *__restrict__ gtab) {
+k_m2m_warp(int level, int step, int p, TrIn a, double2 *M) {
     extern __shared__ double2 sw[];
-    WarpChild W;
-    if (!warp_child_setup(level, step, p, centre, gtab, sw, W)) return;
-    l2l_body(W, L, p);
+    const void *tab = stage_tables<DFT>(p, a, sw);
+    const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= ((int64_t)1 << level)) return;  // no block barrier follows
+    const int64_t gc = ((int64_t)1 << level) - 1 + j;
+    m2m_one<DFT>(gc, ((gc + 1) >> step) - 1, p, a, M, tab, sw);
+}
+
+template <bool DFT>
+__global__ void __launch_bounds__(kWarpChildMax * 32)
+k_l2l_warp(int level, int step, int p, TrIn a, double2 *L) {
+    extern __shared__ double2 sw[];
+    const void *tab = stage_tables<DFT>(p, a, sw);
+    const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= ((int64_t)1 << level)) return;
+    const int64_t gc = ((int64_t)1 << level) - 1 + j;
+    l2l_one<DFT>(gc, ((gc + 1) >> step) - 1, p, a, L, tab, sw);
 }
 
 // Leaf j's walk up: translate into the parent; the warp that delivers a
@@ -487,18 +878,16 @@ k_l2l_warp(int level, int step, int p, const double *__restrict__ centre, double
 // Translations stop at level `stop` (no multipole above it is read). With
 // `Mf`, each box the walk completes (its leaf, every parent it carries on,
 // down to level `stop`) is also scaled into Mf for the single-precision M2L.
-__device__ __forceinline__ void m2m_walk(int B, int stop, int64_t j, int p, const double *__restrict__ centre,
-                                         const double *__restrict__ radius, double2 *M, float2 *Mf,
-                                         const double *tab, double2 *sw, unsigned *arrive) {
+template <bool DFT>
+__device__ __forceinline__ void m2m_walk(int B, int stop, int64_t j, int p, const TrIn &a, double2 *M, float2 *Mf,
+                                         const void *tab, double2 *sw, unsigned *arrive) {
     const int lane = threadIdx.x & 31;
-    WarpChild W;
     int64_t gc = ((int64_t)1 << B) - 1 + j;
     for (int l = B;; l--) {
-        if (Mf) warp_scale_multipole(radius, gc, p, M, Mf);
+        if (Mf) warp_scale_multipole(a.radius, gc, p, M, Mf);
         if (l <= stop) break;
         const int64_t gp = (gc - 1) >> 1;
-        warp_child_init(gc, gp, p, centre, tab, sw, W);
-        m2m_body(W, M);
+        m2m_one<DFT>(gc, gp, p, a, M, tab, sw);
         __threadfence();
         unsigned old = 0;
         if (lane == 0) old = atomicAdd(&arrive[gp], 1u);
@@ -510,28 +899,29 @@ __device__ __forceinline__ void m2m_walk(int B, int stop, int64_t j, int p, cons
 }
 
 // The whole upward pass (binary levels) in one launch, one warp per leaf.
+template <bool DFT>
 __global__ void __launch_bounds__(kWarpChildMax * 32)
-k_m2m_up(int B, int stop, int p, const double *__restrict__ centre, double2 *M, const double *__restrict__ gtab,
-         unsigned *arrive) {
+k_m2m_up(int B, int stop, int p, TrIn a, double2 *M, unsigned *arrive) {
     extern __shared__ double2 sw[];
-    const double *tab = stage_child_tables(p, gtab, sw);
+    const void *tab = stage_tables<DFT>(p, a, sw);
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
     const int64_t nleaf = (int64_t)1 << B;
     for (int64_t j = blockIdx.x * (int64_t)nw + w; j < nleaf; j += (int64_t)gridDim.x * nw)
-        m2m_walk(B, stop, j, p, centre, nullptr, M, nullptr, tab, sw, arrive);
+        m2m_walk<DFT>(B, stop, j, p, a, M, nullptr, tab, sw, arrive);
 }
 
 // batched: blocks of kWarpChildMax leaves of one system each; every box the
 // walks complete is scaled for the single-precision M2L on the way
 __global__ void __launch_bounds__(kWarpChildMax * 32)
 k_b_m2m_up(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys, int p,
-           const double *__restrict__ gtab) {
+           const float2 *__restrict__ tab_df) {
     extern __shared__ double2 sw[];
-    const double *tab = stage_child_tables(p, gtab, sw);
+    const DF *tab = stage_child_tables_df(p, tab_df, sw);
     const int s = batch_sys_of(off, nsys, blockIdx.x);
     const BatchSys &y = S[s];
+    const TrIn a{y.centre, y.radius, (const BoxGeo *)y.box_geo, nullptr, tab_df};
     const int64_t j = (blockIdx.x - off[s]) * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j < y.nleaf) m2m_walk(y.B, min(y.lw, y.B), j, p, y.centre, y.radius, y.M, y.Mf, tab, sw, y.arrive);
+    if (j < y.nleaf) m2m_walk<true>(y.B, min(y.lw, y.B), j, p, a, y.M, y.Mf, tab, sw, y.arrive);
 }
 
 // The whole downward pass (binary levels) in one launch: warps take boxes in
@@ -545,16 +935,15 @@ k_b_m2m_up(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int 
 // `Lh`, a box first takes its own M2L result L = Lhat / r^n (the
 // single-precision M2L's output), then its parent's L2L.
 constexpr int kL2LChunk = 8;
-__device__ __forceinline__ void l2l_chunk(int lw, int p, const double *__restrict__ centre,
-                                          const double *__restrict__ radius, const double2 *__restrict__ Lh,
-                                          double2 *L, const double *tab, double2 *sw, int *done, int *err, int64_t g0,
-                                          int64_t g1, long long wait_limit, long long withhold) {
+template <bool DFT>
+__device__ __forceinline__ void l2l_chunk(int lw, int p, const TrIn &a, const double2 *__restrict__ Lh, double2 *L,
+                                          const void *tab, double2 *sw, int *done, int *err, int64_t g0, int64_t g1,
+                                          long long wait_limit, long long withhold) {
     const int lane = threadIdx.x & 31;
-    WarpChild W;
     for (int64_t g = g0; g < g1; g++) {
         const int l = 63 - __clzll((unsigned long long)(g + 1));
         const int64_t gp = (g - 1) >> 1;
-        if (Lh) warp_unscale_local(radius, g, p, Lh, L);
+        if (Lh) warp_unscale_local(a.radius, g, p, Lh, L);
         if (l - 1 >= lw) {
             if (gp > 0) {  // the root's expansion is complete before the launch
                 int ok = 1;
@@ -573,8 +962,7 @@ __device__ __forceinline__ void l2l_chunk(int lw, int p, const double *__restric
                 (void)ok;  // a box whose wait ran out goes on: the error word says the results are invalid
                 __threadfence();  // the parent's expansion after its flag
             }
-            warp_child_init(g, gp, p, centre, tab, sw, W);
-            l2l_body(W, L, p);
+            l2l_one<DFT>(g, gp, p, a, L, tab, sw);
             __threadfence();
         }
         if (lane == 0 && g != withhold) atomicExch(done + g, 1);
@@ -582,11 +970,12 @@ __device__ __forceinline__ void l2l_chunk(int lw, int p, const double *__restric
     }
 }
 
+template <bool DFT>
 __global__ void __launch_bounds__(kWarpChildMax * 32)
-k_l2l_down(int B, int lw, int p, const double *__restrict__ centre, double2 *L, const double *__restrict__ gtab,
-           int *done, unsigned long long *next, int *err, long long wait_limit, long long withhold) {
+k_l2l_down(int B, int lw, int p, TrIn a, double2 *L, int *done, unsigned long long *next, int *err,
+           long long wait_limit, long long withhold) {
     extern __shared__ double2 sw[];
-    const double *tab = stage_child_tables(p, gtab, sw);
+    const void *tab = stage_tables<DFT>(p, a, sw);
     const int lane = threadIdx.x & 31;
     const int64_t nbox = ((int64_t)2 << B) - 1;
     for (;;) {
@@ -594,8 +983,8 @@ k_l2l_down(int B, int lw, int p, const double *__restrict__ centre, double2 *L, 
         if (lane == 0) c0 = atomicAdd(next, (unsigned long long)kL2LChunk);
         c0 = __shfl_sync(0xffffffffu, c0, 0);
         if ((int64_t)c0 + 1 >= nbox) break;
-        l2l_chunk(lw, p, centre, nullptr, nullptr, L, tab, sw, done, err, (int64_t)c0 + 1,
-                  std::min<int64_t>((int64_t)c0 + 1 + kL2LChunk, nbox), wait_limit, withhold);
+        l2l_chunk<DFT>(lw, p, a, nullptr, L, tab, sw, done, err, (int64_t)c0 + 1,
+                       std::min<int64_t>((int64_t)c0 + 1 + kL2LChunk, nbox), wait_limit, withhold);
     }
 }
 
@@ -604,9 +993,10 @@ k_l2l_down(int B, int lw, int p, const double *__restrict__ centre, double2 *L, 
 // always earlier in the queue; every box first takes its unscaled M2L result
 __global__ void __launch_bounds__(kWarpChildMax * 32)
 k_b_l2l_down(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int nsys, int p,
-             const double *__restrict__ gtab, unsigned long long *next, long long wait_limit, long long withhold) {
+             const double *__restrict__ gtab, const float2 *__restrict__ tab_df, unsigned long long *next,
+             long long wait_limit, long long withhold) {
     extern __shared__ double2 sw[];
-    const double *tab = stage_child_tables(p, gtab, sw);
+    const DF *tab = stage_child_tables_df(p, tab_df, sw);
     const int lane = threadIdx.x & 31;
     const int64_t total = off[nsys];
     for (;;) {
@@ -616,9 +1006,10 @@ k_b_l2l_down(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, in
         if ((int64_t)c >= total) break;
         const int s = batch_sys_of(off, nsys, (int64_t)c);
         const BatchSys &y = S[s];
+        const TrIn a{y.centre, y.radius, (const BoxGeo *)y.box_geo, gtab, tab_df};
         const int64_t g0 = ((int64_t)c - off[s]) * kL2LChunk;
-        l2l_chunk(y.lw, p, y.centre, y.radius, y.Lh, y.L, tab, sw, y.done, y.err, g0,
-                  std::min<int64_t>(g0 + kL2LChunk, y.nbox), wait_limit, withhold);
+        l2l_chunk<true>(y.lw, p, a, y.Lh, y.L, tab, sw, y.done, y.err, g0,
+                        std::min<int64_t>(g0 + kL2LChunk, y.nbox), wait_limit, withhold);
     }
 }
 
@@ -724,6 +1115,22 @@ cudaError_t m2l_setup(Plan &P) {
     cudaError_t e = cudaMemcpyAsync(P.m2l_tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, P.stream);
     if (e != cudaSuccess) return e;
     // stream-ordered copy from pageable memory completes before return
+    if (P.prec == FMM_PREC_MIXED) {
+        // double-float translations: the tables as (hi, lo) float pairs, and
+        // the geometry of every box's translation to / from its parent
+        std::vector<float2> tdf(t.size());
+        for (size_t i = 0; i < t.size(); i++) {
+            const float h = (float)t[i];
+            tdf[i] = make_float2(h, (float)(t[i] - (double)h));
+        }
+        P.m2l_tab_df = (float2 *)palloc(P, tdf.size() * sizeof(float2));
+        P.box_geo = palloc(P, (size_t)P.nbox * sizeof(BoxGeo));
+        if (!P.m2l_tab_df || !P.box_geo) return cudaErrorMemoryAllocation;
+        e = cudaMemcpyAsync(P.m2l_tab_df, tdf.data(), tdf.size() * sizeof(float2), cudaMemcpyHostToDevice, P.stream);
+        if (e != cudaSuccess) return e;
+        FMM_LAUNCH(k_box_geo, (unsigned)std::min<int64_t>((P.nbox + 255) / 256, (int64_t)sm_count() * 8), 256, 0,
+                   P.stream, P.nbox, P.step, P.centre, P.radius, (BoxGeo *)P.box_geo);
+    }
     const int nc = P.nc;
     int threads = 64;
     auto smem = [&](int T) { return (size_t)T * (nc + 2 * (P.p + 1)) * 16 + t.size() * 8; };
@@ -732,15 +1139,19 @@ cudaError_t m2l_setup(Plan &P) {
     P.m2l_smem = smem(threads);
     e = allow_max_smem((const void *)k_m2l_rot_f64, P.m2l_smem);
     const size_t grp_max = (size_t)kWarpChildMax * warp_slice(P.p) * 16 + (size_t)warp_tabs(P.p) * 8;
-    if (e == cudaSuccess)
-        e = allow_max_smem((const void *)k_l2l_warp, grp_max);
-    if (e == cudaSuccess)
-        e = allow_max_smem((const void *)k_m2m_warp, grp_max);
-    if (e == cudaSuccess)
-        e = allow_max_smem((const void *)k_m2m_up, grp_max);
-    if (e == cudaSuccess)
-        e = allow_max_smem((const void *)k_l2l_down, grp_max);
+    const void *kernels[] = {(const void *)k_l2l_warp<false>, (const void *)k_m2m_warp<false>,
+                             (const void *)k_m2m_up<false>,   (const void *)k_l2l_down<false>,
+                             (const void *)k_l2l_warp<true>,  (const void *)k_m2m_warp<true>,
+                             (const void *)k_m2m_up<true>,    (const void *)k_l2l_down<true>};
+    for (const void *k : kernels)
+        if (e == cudaSuccess) e = allow_max_smem(k, grp_max);
     return e;
+}
+
+// M2M and L2L of the mixed form run in double-float arithmetic
+static bool df_translations(const Plan &P) { return P.prec == FMM_PREC_MIXED && P.box_geo; }
+static TrIn tr_in(const Plan &P) {
+    return TrIn{P.centre, P.radius, (const BoxGeo *)P.box_geo, P.m2l_tab, P.m2l_tab_df};
 }
 
 // Warps (children) per block for a level of nch children: 8, or fewer so
@@ -758,16 +1169,24 @@ void m2m_level(Plan &P, int l) {
     const int64_t np = (int64_t)1 << (l - P.step), nch = (int64_t)1 << l;
     cudaMemsetAsync(P.M + (np - 1) * P.nc, 0, (size_t)np * P.nc * sizeof(double2), P.stream);
     const int w = warps_per_block(nch);
-    FMM_LAUNCH(k_m2m_warp, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l, P.step,
-               P.p, P.centre, P.M, P.m2l_tab);
+    if (df_translations(P))
+        FMM_LAUNCH(k_m2m_warp<true>, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l,
+                   P.step, P.p, tr_in(P), P.M);
+    else
+        FMM_LAUNCH(k_m2m_warp<false>, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l,
+                   P.step, P.p, tr_in(P), P.M);
 }
 
 // level l from its ancestors at level l-step
 void l2l_level(Plan &P, int l) {
     const int64_t nch = (int64_t)1 << l;
     const int w = warps_per_block(nch);
-    FMM_LAUNCH(k_l2l_warp, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l, P.step,
-               P.p, P.centre, P.L, P.m2l_tab);
+    if (df_translations(P))
+        FMM_LAUNCH(k_l2l_warp<true>, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l,
+                   P.step, P.p, tr_in(P), P.L);
+    else
+        FMM_LAUNCH(k_l2l_warp<false>, (unsigned)((nch + w - 1) / w), 32 * w, warp_child_smem(P.p, w), P.stream, l,
+                   P.step, P.p, tr_in(P), P.L);
 }
 
 cudaError_t m2l_external(Plan &P, int level, int64_t n, const int32_t *tgt, const double2 *Msrc,
@@ -797,8 +1216,12 @@ void m2m_up(Plan &P, int stop) {
     cudaMemsetAsync(P.m2m_arrive, 0, (size_t)P.nbox * 4, P.stream);
     const int w = kWarpChildMax;
     const unsigned grid = (unsigned)std::min<int64_t>((nleaf + w - 1) / w, (int64_t)sm_count() * 16);
-    FMM_LAUNCH(k_m2m_up, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, stop, P.p, P.centre, P.M,
-               P.m2l_tab, P.m2m_arrive);
+    if (df_translations(P))
+        FMM_LAUNCH(k_m2m_up<true>, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, stop, P.p, tr_in(P), P.M,
+                   P.m2m_arrive);
+    else
+        FMM_LAUNCH(k_m2m_up<false>, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, stop, P.p, tr_in(P), P.M,
+                   P.m2m_arrive);
 }
 
 // the downward pass of binary levels in one launch; boxes whose parent level
@@ -810,8 +1233,12 @@ void l2l_down(Plan &P, int lw) {
     const int w = kWarpChildMax;
     const int64_t items = (P.nbox + kL2LChunk - 1) / kL2LChunk;
     const unsigned grid = (unsigned)std::min<int64_t>((items + w - 1) / w, (int64_t)sm_count() * 8);
-    FMM_LAUNCH(k_l2l_down, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, lw, P.p, P.centre, P.L,
-               P.m2l_tab, P.l2l_done, P.l2l_next, P.d_err, g_wait_limit.load(), g_withhold.load());
+    if (df_translations(P))
+        FMM_LAUNCH(k_l2l_down<true>, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, lw, P.p, tr_in(P), P.L,
+                   P.l2l_done, P.l2l_next, P.d_err, g_wait_limit.load(), g_withhold.load());
+    else
+        FMM_LAUNCH(k_l2l_down<false>, grid, 32 * w, warp_child_smem(P.p, w), P.stream, P.B, lw, P.p, tr_in(P), P.L,
+                   P.l2l_done, P.l2l_next, P.d_err, g_wait_limit.load(), g_withhold.load());
 }
 
 // FP64 M2L over all levels in one launch; accumulates into L (zeroed first)
@@ -1692,8 +2119,8 @@ cudaError_t m2l_f32_all(Plan &P) {
 }
 
 // ---- batched stages (every system of a batch in one launch per stage)
-cudaError_t batch_m2m_up(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int p, const double *tab,
-                         cudaStream_t st) {
+cudaError_t batch_m2m_up(const BatchSys *S, const int32_t *off, int nsys, int64_t blocks, int p,
+                         const float2 *tab, cudaStream_t st) {
     if (blocks == 0) return cudaGetLastError();
     FMM_LAUNCH(k_b_m2m_up, (unsigned)blocks, 32 * kWarpChildMax, warp_child_smem(p, kWarpChildMax), st, S, off, nsys,
                p, tab);
@@ -1717,12 +2144,12 @@ cudaError_t batch_m2l(const BatchSys *S, const int32_t *off, int nsys, int64_t n
 }
 
 cudaError_t batch_l2l_down(const BatchSys *S, const int32_t *off, int nsys, int64_t nchunks, int p,
-                           const double *tab, unsigned long long *next, cudaStream_t st) {
+                           const double *tab, const float2 *tab_df, unsigned long long *next, cudaStream_t st) {
     if (nchunks == 0) return cudaGetLastError();
     const unsigned grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((nchunks + kWarpChildMax - 1) / kWarpChildMax, (int64_t)sm_count() * 8));
     FMM_LAUNCH(k_b_l2l_down, grid, 32 * kWarpChildMax, warp_child_smem(p, kWarpChildMax), st, S, off, nsys, p, tab,
-               next, g_wait_limit.load(), g_withhold.load());
+               tab_df, next, g_wait_limit.load(), g_withhold.load());
     return cudaGetLastError();
 }
 
