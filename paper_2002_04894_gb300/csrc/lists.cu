@@ -264,6 +264,8 @@ __device__ __forceinline__ int unit_bucket(unsigned long long w) {
     return 255 - min(255, 4 * lg + frac);
 }
 
+constexpr int kUnitPre = 8;
+
 // One warp per leaf: cuts the leaf's strong list into k segments of about
 // nsrc / k sources each and emits its units (leaf, first target, segment
 // begin, segment end) with their partial-sum slot (-1 when the leaf is not
@@ -300,28 +302,42 @@ __global__ void k_units_gen(int B, int tile, long long smax, const int32_t *coun
         }
         int j = 0, e_lo = l0;
         long long c_lo = 0, run = 0;  // cumulative sources before the chunk
-        for (int base = l0; base < l1 && j < k - 1; base += 32) {
-            const int e = base + lane;
-            long long c = e < l1 ? (long long)count[off + ssrc[e]] : 0;
+        // chunks of 32 entries; the source counts of kUnitPre chunks are
+        // fetched together (two dependent loads each), so that a long list
+        // waits on memory once per kUnitPre chunks
+        for (int base0 = l0; base0 < l1 && j < k - 1; base0 += 32 * kUnitPre) {
+            long long cn[kUnitPre];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {  // inclusive scan over the chunk
-                const long long y = __shfl_up_sync(0xffffffffu, c, o);
-                if (lane >= o) c += y;
+            for (int u = 0; u < kUnitPre; u++) {
+                const int e = base0 + 32 * u + lane;
+                cn[u] = e < l1 ? (long long)count[off + ssrc[e]] : 0;
             }
-            const long long total = __shfl_sync(0xffffffffu, c, 31);
-            while (j < k - 1) {
-                const long long goal = (long long)(((unsigned long long)ns * (unsigned long long)(j + 1)) / k);
-                const unsigned hit = __ballot_sync(0xffffffffu, e < l1 && run + c >= goal);
-                if (!hit) break;
-                const int f = __ffs(hit) - 1;
-                const int e_hi = base + f + 1;
-                const long long c_hi = run + __shfl_sync(0xffffffffu, c, f);
-                emit(j, e_lo, e_hi, c_hi - c_lo);
-                e_lo = e_hi;
-                c_lo = c_hi;
-                j++;
+#pragma unroll
+            for (int u = 0; u < kUnitPre; u++) {
+                const int base = base0 + 32 * u;
+                if (base >= l1 || j >= k - 1) break;  // warp-uniform
+                const int e = base + lane;
+                long long c = cn[u];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {  // inclusive scan over the chunk
+                    const long long y = __shfl_up_sync(0xffffffffu, c, o);
+                    if (lane >= o) c += y;
+                }
+                const long long total = __shfl_sync(0xffffffffu, c, 31);
+                while (j < k - 1) {
+                    const long long goal = (long long)(((unsigned long long)ns * (unsigned long long)(j + 1)) / k);
+                    const unsigned hit = __ballot_sync(0xffffffffu, e < l1 && run + c >= goal);
+                    if (!hit) break;
+                    const int f = __ffs(hit) - 1;
+                    const int e_hi = base + f + 1;
+                    const long long c_hi = run + __shfl_sync(0xffffffffu, c, f);
+                    emit(j, e_lo, e_hi, c_hi - c_lo);
+                    e_lo = e_hi;
+                    c_lo = c_hi;
+                    j++;
+                }
+                run += total;
             }
-            run += total;
         }
         for (; j < k; j++) {  // the last segment (and any left empty) end at the list's end
             emit(j, e_lo, l1, ns - c_lo);
