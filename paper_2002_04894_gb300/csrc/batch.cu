@@ -96,7 +96,7 @@ bool batch_eligible(const Plan *const *plans, int n) {
     int groups = 0;
     for (int i = 0; i < n; i++) {
         const Plan &P = *plans[i];
-        if (P.prec != FMM_PREC_MIXED || P.step != 1 || !P.Mf || P.m2l_tc || !P.f32_tab || !P.box_geo) return false;
+        if (P.prec != FMM_PREC_MIXED || P.step != 1 || !P.Mf || P.m2l_tc || !P.f32_tab || !P.box_geo || !P.box_cf) return false;
         if (P.dtype != A.dtype || P.device != A.device) return false;
         if (!seen[P.p]) seen[P.p] = true, groups++;
     }
@@ -171,6 +171,7 @@ cudaError_t batch_setup(const Plan *const *plans, int n, const void *const *char
         y.upart = P.p2p_upart;
         y.ubstart = P.p2p_bstart;
         y.box_geo = P.box_geo;
+        y.box_cf = P.box_cf;
         y.pt = pair_table(P);
         cnt[kOffPrep][i] =
             std::max<int64_t>(1, (std::max<int64_t>(P.n, P.nbox * P.nc) + kPrepItems - 1) / kPrepItems);

@@ -62,6 +62,7 @@ struct BatchSys {
     void *pot, *field;
     double4 *partial;
     const void *box_geo;           // per box: geometry of the translation to / from its parent
+    const float4 *box_cf;          // per box: centre hi (xyz) + radius, centre lo
     const int4 *units;             // near-field work units, heaviest bucket first
     const int32_t *upart, *ubstart;
     PairTable pt;
@@ -144,6 +145,9 @@ struct Plan {
     // per box the geometry of its translation from / to its parent
     float2 *m2l_tab_df = nullptr;
     void *box_geo = nullptr;
+    // single-precision M2L: per box its centre split hi + lo in float and its
+    // radius (hi.w), so a pair's offset needs no double arithmetic
+    float4 *box_cf = nullptr;
     unsigned *m2m_arrive = nullptr;         // one-launch upward pass: arrivals per parent
     int *l2l_done = nullptr;                // one-launch downward pass: box finished
     unsigned long long *l2l_next = nullptr; // one-launch downward pass: next box to take

@@ -1780,10 +1780,26 @@ struct VSplit {
     static constexpr size_t SMEM = TAB + (size_t)pair_tab_len(P) * 16;
 };
 
+// per box: centre split hi + lo in float, radius (1 for a zero radius)
+__global__ void k_box_cf(int64_t nbox, const double *__restrict__ centre, const double *__restrict__ radius,
+                         float4 *__restrict__ cf) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nbox; g += (int64_t)gridDim.x * blockDim.x) {
+        float h[3], l[3];
+        for (int d = 0; d < 3; d++) {
+            const double c = centre[3 * g + d];
+            h[d] = (float)c;
+            l[d] = (float)(c - (double)h[d]);
+        }
+        const double r = radius[g];
+        cf[2 * g] = make_float4(h[0], h[1], h[2], r > 0.0 ? (float)r : 1.f);
+        cf[2 * g + 1] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+
 // one chunk of 128 pairs (pair g for this thread; lanes past the end carry zeros)
 template <int P>
-__device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__restrict__ centre,
-                                          const double *__restrict__ radius, const float2 *__restrict__ Mf,
+__device__ __forceinline__ void m2l_chunk(const PairTable &PT, const float4 *__restrict__ cf,
+                                          const float2 *__restrict__ Mf,
                                           double2 *__restrict__ Lh, const float4 *tab, int64_t g, int64_t npairs,
                                           float2 *smf, uint32_t tbase, uint32_t tphase) {
     using SP = VSplit<P>;
@@ -1794,13 +1810,15 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
     float dx = 1.f, dy = 0.f, dz = 0.f, rs = 1.f, rt = 1.f;
     if (valid) {
         pair_of(PT, g, gt, gs);
-        // centre offsets in double, everything after in float
-        dx = (float)(centre[3 * gt] - centre[3 * gs]);
-        dy = (float)(centre[3 * gt + 1] - centre[3 * gs + 1]);
-        dz = (float)(centre[3 * gt + 2] - centre[3 * gs + 2]);
-        const double rsd = radius[gs], rtd = radius[gt];
-        rs = rsd > 0.0 ? (float)rsd : 1.f;
-        rt = rtd > 0.0 ? (float)rtd : 1.f;
+        // the centre offset from the split centres: the hi difference and its
+        // rounding error (TwoSum), plus the lo difference, rounded once: the
+        // double difference rounded to float, without double arithmetic
+        const float4 th = cf[2 * gt], tl = cf[2 * gt + 1], sh = cf[2 * gs], sl = cf[2 * gs + 1];
+        dx = offset_f(th.x, sh.x, tl.x, sl.x);
+        dy = offset_f(th.y, sh.y, tl.y, sl.y);
+        dz = offset_f(th.z, sh.z, tl.z, sl.z);
+        rs = sh.w;
+        rt = th.w;
     }
     bool same[5], head;
     seg_setup(gt, same, head);
@@ -1844,8 +1862,8 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const double *__r
 // pairs; accumulates r_t^k L_k into Lh
 template <int P>
 __global__ void __launch_bounds__(kF32Threads, 3)
-k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__restrict__ radius,
-              const float2 *__restrict__ Mf, double2 *__restrict__ Lh, const float4 *__restrict__ gtab) {
+k_m2l_rot_f32(PairTable PT, const float4 *__restrict__ cf, const float2 *__restrict__ Mf,
+              double2 *__restrict__ Lh, const float4 *__restrict__ gtab) {
     using SP = VSplit<P>;
     extern __shared__ float2 smf[];  // [NS][threads], the per-warp regions, the tables
     __shared__ uint32_t s_tmem, s_tphase;
@@ -1867,7 +1885,7 @@ k_m2l_rot_f32(PairTable PT, const double *__restrict__ centre, const double *__r
     const uint32_t tbase = s_tmem, tphase = s_tphase;
     const int64_t npairs = PT.off[PT.lmax + 1];
     for (int64_t g0 = blockIdx.x * (int64_t)kF32Threads; g0 < npairs; g0 += (int64_t)gridDim.x * kF32Threads)
-        m2l_chunk<P>(PT, centre, radius, Mf, Lh, tab, g0 + tid, npairs, smf, tbase, tphase);
+        m2l_chunk<P>(PT, cf, Mf, Lh, tab, g0 + tid, npairs, smf, tbase, tphase);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -1905,7 +1923,7 @@ k_b_m2l_rot_f32(const BatchSys *__restrict__ S, const int32_t *__restrict__ off,
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int s = batch_sys_of(off, nsys, c);
         const BatchSys &y = S[s];
-        m2l_chunk<P>(y.pt, y.centre, y.radius, y.Mf, y.Lh, tab, (c - off[s]) * kF32Threads + tid, y.npairs, smf,
+        m2l_chunk<P>(y.pt, y.box_cf, y.Mf, y.Lh, tab, (c - off[s]) * kF32Threads + tid, y.npairs, smf,
                      tbase, tphase);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -2047,7 +2065,7 @@ void launch_b_f32(const BatchSys *S, const int32_t *off, int nsys, int64_t nchun
 template <int P>
 cudaError_t launch_f32(Plan &Pl, int64_t tot) {
     const int64_t chunks = (tot + kF32Threads - 1) / kF32Threads;
-    FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)std::min<int64_t>(chunks, (int64_t)sm_count() * 3), kF32Threads, VSplit<P>::SMEM, Pl.stream, pair_table(Pl), Pl.centre, Pl.radius, Pl.Mf, Pl.Lh,
+    FMM_LAUNCH(k_m2l_rot_f32<P>, (unsigned)std::min<int64_t>(chunks, (int64_t)sm_count() * 3), kF32Threads, VSplit<P>::SMEM, Pl.stream, pair_table(Pl), Pl.box_cf, Pl.Mf, Pl.Lh,
                (const float4 *)Pl.f32_tab);
     return cudaGetLastError();
 }
@@ -2066,7 +2084,10 @@ cudaError_t m2l_f32_setup(Plan &P) {
     if (!tc && !m2l_f32_supported(P.p)) return cudaSuccess;  // FP64 M2L
     P.Mf = (float2 *)palloc(P, (size_t)P.nbox * mf_stride(P.p) * sizeof(float2));
     P.Lh = (double2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(double2));
-    if (!P.Mf || !P.Lh) return cudaErrorMemoryAllocation;
+    P.box_cf = (float4 *)palloc(P, (size_t)P.nbox * 2 * sizeof(float4));
+    if (!P.Mf || !P.Lh || !P.box_cf) return cudaErrorMemoryAllocation;
+    FMM_LAUNCH(k_box_cf, (unsigned)std::min<int64_t>((P.nbox + 255) / 256, (int64_t)sm_count() * 8), 256, 0,
+               P.stream, P.nbox, P.centre, P.radius, P.box_cf);
     if (tc) {
         P.m2l_tc = true;
         return m2l_tc_setup(P);

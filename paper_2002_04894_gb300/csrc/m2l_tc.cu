@@ -316,8 +316,8 @@ __device__ __forceinline__ void reduce_out(int n, const float (&vr)[16], const f
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_m2l_tc(PairTable PT, int p, int64_t ntiles, const double *__restrict__ centre,
-         const double *__restrict__ radius, const float2 *__restrict__ Mf, double2 *__restrict__ Lh,
+k_m2l_tc(PairTable PT, int p, int64_t ntiles, const float4 *__restrict__ cf, const float2 *__restrict__ Mf,
+         double2 *__restrict__ Lh,
          const uint4 *__restrict__ gtab, int *err) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ uint32_t s_tmem;
@@ -367,12 +367,13 @@ k_m2l_tc(PairTable PT, int p, int64_t ntiles, const double *__restrict__ centre,
         float dx = 1.f, dy = 0.f, dz = 0.f, rs = 1.f, rt = 1.f;
         if (valid) {
             pair_of(PT, g, gt, gs);
-            dx = (float)(centre[3 * gt] - centre[3 * gs]);
-            dy = (float)(centre[3 * gt + 1] - centre[3 * gs + 1]);
-            dz = (float)(centre[3 * gt + 2] - centre[3 * gs + 2]);
-            const double rsd = radius[gs], rtd = radius[gt];
-            rs = rsd > 0.0 ? (float)rsd : 1.f;
-            rt = rtd > 0.0 ? (float)rtd : 1.f;
+            // the offset from the split float centres, as the CUDA-core kernel forms it
+            const float4 th = cf[2 * gt], tl = cf[2 * gt + 1], sh = cf[2 * gs], sl = cf[2 * gs + 1];
+            dx = offset_f(th.x, sh.x, tl.x, sl.x);
+            dy = offset_f(th.y, sh.y, tl.y, sl.y);
+            dz = offset_f(th.z, sh.z, tl.z, sl.z);
+            rs = sh.w;
+            rt = th.w;
         }
         bool same[5], head;
         seg_setup(gt, same, head);
@@ -651,8 +652,8 @@ cudaError_t m2l_tc_launch(Plan &P) {
     if (tot == 0) return cudaSuccess;
     const int64_t ntiles = (tot + kTeam - 1) / kTeam;
     const int grid = (int)std::min<int64_t>(P.tc_ctas, (ntiles + 1) / 2);
-    FMM_LAUNCH(k_m2l_tc, grid, kTcThreads, smem_bytes(P.p), P.stream, pair_table(P), P.p, ntiles, P.centre,
-               P.radius, P.Mf, P.Lh, (const uint4 *)P.tc_tab, P.d_err + 1);
+    FMM_LAUNCH(k_m2l_tc, grid, kTcThreads, smem_bytes(P.p), P.stream, pair_table(P), P.p, ntiles, P.box_cf, P.Mf,
+               P.Lh, (const uint4 *)P.tc_tab, P.d_err + 1);
     return cudaGetLastError();
 }
 
