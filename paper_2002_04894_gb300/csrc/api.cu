@@ -505,17 +505,26 @@ int fmm_batch_create(const fmm_plan_t *plans, int nplans, const void *const *cha
     if (!s0) e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), s0 = b->own;
     std::vector<const Plan *> pl(nplans);
     for (int i = 0; i < nplans; i++) pl[i] = &plans[i]->P;
+    bool fused = false;
     if (e == cudaSuccess && fmm::batch_eligible(pl.data(), nplans)) {
-        // every system in one launch per stage
+        // every system in one launch per stage; a batch whose block counts
+        // overflow the int32 offset tables takes the per-plan graph instead
         e = fmm::batch_setup(pl.data(), nplans, charges, potentials, fields, b->run, s0);
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            e = fmm::batch_enqueue(b->run, s0);
-            cudaError_t e2 = cudaStreamEndCapture(s0, &b->graph);
-            if (e == cudaSuccess) e = e2;
+        if (e == cudaErrorInvalidValue) {
+            cudaGetLastError();
+            e = cudaSuccess;
+        } else {
+            fused = true;
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                e = fmm::batch_enqueue(b->run, s0);
+                cudaError_t e2 = cudaStreamEndCapture(s0, &b->graph);
+                if (e == cudaSuccess) e = e2;
+            }
+            b->fused = true;
         }
-        b->fused = true;
-    } else if (e == cudaSuccess) {
+    }
+    if (e == cudaSuccess && !fused) {
         // per-plan evaluations on forked branches of the graph
         const int K = std::min(nstreams ? nstreams : 16, nplans);
         for (int k = 0; k < K && e == cudaSuccess; k++) {

@@ -530,8 +530,17 @@ __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__re
     }
 }
 
+// resident blocks asked of the register allocator (0: no constraint). The
+// batched kernel holds the system's pointers in registers, and unconstrained
+// spills in its loop: at <= 80 registers (6 blocks of 128, 12 of 64) it does
+// not (512 systems: 53.6 -> 58.9 Mpoints/s). The single-plan kernel runs best
+// unconstrained (64 registers for 128-target tiles, 72 for 64: with 80 the
+// 2M-point near field took 17.5 instead of 17.0 ms).
+template <int T>
+constexpr int p2p_min_blocks(bool batched) { return batched ? (T == kP2PTile ? 6 : 12) : 0; }
+
 template <typename OutT, int T>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, p2p_min_blocks<T>(false))
 k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restrict__ qf,
           const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
           const float4 *__restrict__ geo, const int32_t *__restrict__ ssrc, const int4 *__restrict__ units,
@@ -547,7 +556,7 @@ k_p2p_f32(int B, int64_t n, const float *__restrict__ hl, const float *__restric
 // batched: the work units of every system in one list, heaviest first, each
 // with its system
 template <typename OutT, int T>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, p2p_min_blocks<T>(true))
 k_b_p2p_f32(const BatchSys *__restrict__ S, const int4 *__restrict__ units, const int32_t *__restrict__ usys,
             const int32_t *__restrict__ upart) {
     const BatchSys &y = S[usys[blockIdx.x]];
