@@ -80,9 +80,9 @@ def m2l_flops_per_pair(p):
 # workload, valid only while the kernel's source is the one that was captured
 # (checked by hash; otherwise null).
 MEASURED_TRAFFIC = {
-    ("gmm8m_l17_p12", "k_p2p_f32"): {"bytes": 7879.7e6 + 537.0e6,
+    ("gmm8m_l17_p12", "k_p2p_f32"): {"bytes": 7900.3e6 + 539.6e6,
                                      "source": "paper_2002_04894_gb300/csrc/mixed.cu",
-                                     "sha256_16": "bdf8d2bf19cbabc2"},
+                                     "sha256_16": "aa5df43c33bf9447"},
 }
 
 
