@@ -68,6 +68,15 @@ struct BatchSys {
     PairTable pt;
 };
 
+// (ah + al) - (bh + bl) in float from the split values: TwoSum of the hi
+// parts, then the error and the lo parts
+__device__ __forceinline__ float offset_f(float ah, float bh, float al, float bl) {
+    const float d = __fsub_rn(ah, bh);
+    const float bb = __fsub_rn(d, ah);
+    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(d, bb)), __fsub_rn(-bh, bb));
+    return __fadd_rn(d, __fadd_rn(e, __fsub_rn(al, bl)));
+}
+
 // Block b of a batched launch belongs to system s with off[s] <= b < off[s+1].
 __device__ __forceinline__ int batch_sys_of(const int32_t *__restrict__ off, int nsys, int64_t b) {
     int lo = 0, hi = nsys;  // off[lo] <= b < off[hi]
@@ -145,8 +154,9 @@ struct Plan {
     // per box the geometry of its translation from / to its parent
     float2 *m2l_tab_df = nullptr;
     void *box_geo = nullptr;
-    // single-precision M2L: per box its centre split hi + lo in float and its
-    // radius (hi.w), so a pair's offset needs no double arithmetic
+    // per box its centre split hi + lo in float and its radius (hi.w): the
+    // theta-test's pre-test and the single-precision M2L form offsets from
+    // them without double arithmetic
     float4 *box_cf = nullptr;
     unsigned *m2m_arrive = nullptr;         // one-launch upward pass: arrivals per parent
     int *l2l_done = nullptr;                // one-launch downward pass: box finished
@@ -319,6 +329,8 @@ cudaError_t batch_setup(const Plan *const *plans, int n, const void *const *char
 cudaError_t batch_enqueue(const BatchRun &R, cudaStream_t st);
 void batch_release(BatchRun &R);
 int first_weak_level_of(const Plan &P);
+// P.box_cf from the final box geometry (the list build makes it)
+void box_centres_f(Plan &P);
 PairTable pair_table(const Plan &P);
 int64_t total_weak(const Plan &P);
 

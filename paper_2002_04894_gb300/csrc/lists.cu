@@ -69,10 +69,30 @@ __device__ __forceinline__ bool theta_weak(double theta, const double *ca, doubl
 // i.e. grouped by target C T + a and, inside a target, by ascending source
 // (the parent's sources are ascending). A scan of the weak flags then places
 // every weak and strong pair directly in its sorted CSR slot.
+// The pre-test of theta_weak from the boxes' split float centres and float
+// radii (no double arithmetic: GB300's FP64 pipe is narrow); 1 weak, 0
+// strong, -1 undecided (near the boundary, or out of the comfortable float
+// range): the double-precision test then decides.
+__device__ __forceinline__ int theta_pretest(float ft, const float4 &ah, const float4 &al, const float4 &bh,
+                                             const float4 &bl) {
+    const float fx = offset_f(ah.x, bh.x, al.x, bl.x);
+    const float fy = offset_f(ah.y, bh.y, al.y, bl.y);
+    const float fz = offset_f(ah.z, bh.z, al.z, bl.z);
+    const float R = fmaxf(ah.w, bh.w), r = fminf(ah.w, bh.w);
+    const float fs = fx * fx + fy * fy + fz * fz;
+    const float fl = R + ft * r;
+    const float fa = fl * fl, fb = ft * ft * fs;
+    if (fs > 1e-30f && fs < 1e30f && fa > 1e-30f && fa < 1e30f && fb > 1e-30f && fb < 1e30f) {
+        if (fa < fb * (1.0f - 1e-4f)) return 1;
+        if (fa > fb * (1.0f + 1e-4f)) return 0;
+    }
+    return -1;
+}
+
 __global__ void k_cand(int level, int step, int64_t npar, double theta, const int32_t *__restrict__ pptr,
                        const int32_t *__restrict__ psrc, const int32_t *__restrict__ prow,
                        const double *__restrict__ centre, const double *__restrict__ radius,
-                       int32_t *__restrict__ flag, int32_t *__restrict__ csrc,
+                       const float4 *__restrict__ cf, int32_t *__restrict__ flag, int32_t *__restrict__ csrc,
                        int32_t *__restrict__ ctgt) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= npar) return;
@@ -87,7 +107,10 @@ __global__ void k_cand(int level, int step, int64_t npar, double theta, const in
         for (int b = 0; b < C; b++) {
             const int32_t s = C * S + b;
             const int64_t gs = off + s;
-            flag[base + b] = theta_weak(theta, centre + 3 * gt, radius[gt], centre + 3 * gs, radius[gs]);
+            int w = theta > 0.0 ? theta_pretest((float)theta, cf[2 * gt], cf[2 * gt + 1], cf[2 * gs], cf[2 * gs + 1])
+                                : 0;
+            if (w < 0) w = theta_weak(theta, centre + 3 * gt, radius[gt], centre + 3 * gs, radius[gs]) ? 1 : 0;
+            flag[base + b] = w;
             csrc[base + b] = s;
             ctgt[base + b] = t;
         }
@@ -441,6 +464,11 @@ std::atomic<long long> g_list_capacity{0x7fffffffLL};
 
 cudaError_t lists_build(Plan &P) {
     cudaStream_t st = P.stream;
+    // every box's centre split hi + lo in float and its radius, for the
+    // theta-test's single-precision pre-test (and the single-precision M2L)
+    P.box_cf = (float4 *)palloc(P, (size_t)P.nbox * 2 * sizeof(float4));
+    if (!P.box_cf) return cudaErrorMemoryAllocation;
+    box_centres_f(P);
     // level 0: the root is strongly connected to itself
     P.wptr[0] = (int32_t *)palloc(P, 8);
     P.sptr[0] = (int32_t *)palloc(P, 8);
@@ -489,7 +517,7 @@ cudaError_t lists_build(Plan &P) {
         P.sptr[l] = (int32_t *)palloc(P, (nt + 1) * 4);
         if (!flag || !wpos || !csrc || !ctgt || !P.wptr[l] || !P.sptr[l]) return cudaErrorMemoryAllocation;
         FMM_LAUNCH(k_cand, (unsigned)((npar + 127) / 128), 128, 0, st, l, step, npar, P.theta, P.sptr[lp],
-                   P.ssrc[lp], srow_prev, P.centre, P.radius, flag, csrc, ctgt);
+                   P.ssrc[lp], srow_prev, P.centre, P.radius, P.box_cf, flag, csrc, ctgt);
         e = scan_exclusive(P, flag, wpos, ncand);
         if (e != cudaSuccess) return e;
         FMM_LAUNCH(k_cand_ptrs, (unsigned)((nt + 1 + 255) / 256), 256, 0, st, l, step, P.sptr[lp], wpos,

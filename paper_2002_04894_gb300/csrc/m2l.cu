@@ -1780,22 +1780,6 @@ struct VSplit {
     static constexpr size_t SMEM = TAB + (size_t)pair_tab_len(P) * 16;
 };
 
-// per box: centre split hi + lo in float, radius (1 for a zero radius)
-__global__ void k_box_cf(int64_t nbox, const double *__restrict__ centre, const double *__restrict__ radius,
-                         float4 *__restrict__ cf) {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nbox; g += (int64_t)gridDim.x * blockDim.x) {
-        float h[3], l[3];
-        for (int d = 0; d < 3; d++) {
-            const double c = centre[3 * g + d];
-            h[d] = (float)c;
-            l[d] = (float)(c - (double)h[d]);
-        }
-        const double r = radius[g];
-        cf[2 * g] = make_float4(h[0], h[1], h[2], r > 0.0 ? (float)r : 1.f);
-        cf[2 * g + 1] = make_float4(l[0], l[1], l[2], 0.f);
-    }
-}
-
 // one chunk of 128 pairs (pair g for this thread; lanes past the end carry zeros)
 template <int P>
 __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const float4 *__restrict__ cf,
@@ -1817,8 +1801,8 @@ __device__ __forceinline__ void m2l_chunk(const PairTable &PT, const float4 *__r
         dx = offset_f(th.x, sh.x, tl.x, sl.x);
         dy = offset_f(th.y, sh.y, tl.y, sl.y);
         dz = offset_f(th.z, sh.z, tl.z, sl.z);
-        rs = sh.w;
-        rt = th.w;
+        rs = sh.w > 0.f ? sh.w : 1.f;
+        rt = th.w > 0.f ? th.w : 1.f;
     }
     bool same[5], head;
     seg_setup(gt, same, head);
@@ -2084,10 +2068,7 @@ cudaError_t m2l_f32_setup(Plan &P) {
     if (!tc && !m2l_f32_supported(P.p)) return cudaSuccess;  // FP64 M2L
     P.Mf = (float2 *)palloc(P, (size_t)P.nbox * mf_stride(P.p) * sizeof(float2));
     P.Lh = (double2 *)palloc(P, (size_t)P.nbox * P.nc * sizeof(double2));
-    P.box_cf = (float4 *)palloc(P, (size_t)P.nbox * 2 * sizeof(float4));
     if (!P.Mf || !P.Lh || !P.box_cf) return cudaErrorMemoryAllocation;
-    FMM_LAUNCH(k_box_cf, (unsigned)std::min<int64_t>((P.nbox + 255) / 256, (int64_t)sm_count() * 8), 256, 0,
-               P.stream, P.nbox, P.centre, P.radius, P.box_cf);
     if (tc) {
         P.m2l_tc = true;
         return m2l_tc_setup(P);

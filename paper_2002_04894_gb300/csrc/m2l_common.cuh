@@ -45,13 +45,4 @@ int64_t total_weak(const Plan &P);
 long double factl(int n);
 long double wigner_half_pi(int n, int k, int m);  // d^n_{km}(pi/2)
 
-// (ah + al) - (bh + bl) in float from the split values: TwoSum of the hi
-// parts, then the error and the lo parts
-__device__ __forceinline__ float offset_f(float ah, float bh, float al, float bl) {
-    const float d = __fsub_rn(ah, bh);
-    const float bb = __fsub_rn(d, ah);
-    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(d, bb)), __fsub_rn(-bh, bb));
-    return __fadd_rn(d, __fadd_rn(e, __fsub_rn(al, bl)));
-}
-
 }  // namespace fmm

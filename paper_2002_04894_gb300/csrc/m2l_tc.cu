@@ -372,8 +372,8 @@ k_m2l_tc(PairTable PT, int p, int64_t ntiles, const float4 *__restrict__ cf, con
             dx = offset_f(th.x, sh.x, tl.x, sl.x);
             dy = offset_f(th.y, sh.y, tl.y, sl.y);
             dz = offset_f(th.z, sh.z, tl.z, sl.z);
-            rs = sh.w;
-            rt = th.w;
+            rs = sh.w > 0.f ? sh.w : 1.f;
+            rt = th.w > 0.f ? th.w : 1.f;
         }
         bool same[5], head;
         seg_setup(gt, same, head);

@@ -1021,6 +1021,28 @@ cudaError_t noalloc_scratch(unsigned char **out) {
 
 }  // namespace
 
+namespace {
+// per box: centre split hi + lo in float (hi.xyz, lo.xyz) and its radius (hi.w)
+__global__ void k_box_cf(int64_t nbox, const double *__restrict__ centre, const double *__restrict__ radius,
+                         float4 *__restrict__ cf) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nbox; g += (int64_t)gridDim.x * blockDim.x) {
+        float h[3], l[3];
+        for (int d = 0; d < 3; d++) {
+            const double c = centre[3 * g + d];
+            h[d] = (float)c;
+            l[d] = (float)(c - (double)h[d]);
+        }
+        cf[2 * g] = make_float4(h[0], h[1], h[2], (float)radius[g]);
+        cf[2 * g + 1] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+}  // namespace
+
+void box_centres_f(Plan &P) {
+    FMM_LAUNCH(k_box_cf, (unsigned)std::min<int64_t>((P.nbox + 255) / 256, (int64_t)sm_count() * 8), 256, 0,
+               P.stream, P.nbox, P.centre, P.radius, P.box_cf);
+}
+
 }  // namespace fmm
 
 extern "C" int fmm_orb_order_noalloc(const void *points, int64_t n, int dtype, int levels,
