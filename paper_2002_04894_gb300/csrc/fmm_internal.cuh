@@ -77,6 +77,9 @@ __device__ __forceinline__ float offset_f(float ah, float bh, float al, float bl
     return __fadd_rn(d, __fadd_rn(e, __fsub_rn(al, bl)));
 }
 
+// 2^k as a double, for |k| <= 1022 (exact; integer operations only)
+__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
 // Block b of a batched launch belongs to system s with off[s] <= b < off[s+1].
 __device__ __forceinline__ int batch_sys_of(const int32_t *__restrict__ off, int nsys, int64_t b) {
     int lo = 0, hi = nsys;  // off[lo] <= b < off[hi]

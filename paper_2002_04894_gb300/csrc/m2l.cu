@@ -551,8 +551,7 @@ struct alignas(16) BoxGeo {
     int skip;  // an empty box outside its parent's box (rho > 2 r_p): nothing to translate
 };
 
-// 2^k as a double, for |k| <= 1022
-__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
 
 // 1/k! as double-float pairs, built at compile time
 struct IFact {

@@ -10,10 +10,11 @@
 // close pairs keep full relative precision. Per-target sums are plain float
 // over runs of 64 sources and Kahan-compensated across runs (the rounding of
 // a 64-term sum stays near the float unit roundoff while the compensation
-// costs a fraction of an instruction per pair). The expansions are evaluated
-// on scaled offsets a / r (r the
-// box radius, so |a / r| <= 1) and with scaled coefficients M_n / r^n and
-// L_n r^n, which keeps every float value O(1) whatever the box size.
+// costs a fraction of an instruction per pair). P2M and L2P evaluate on
+// scaled offsets a / s (s = 2^e within a factor 2 below the leaf's radius, so
+// |a / s| < 2) with scaled coefficients M_n / s^n and L_n s^n; the M2L reads
+// M_n / r^n and forms r^k L_k (r the box radius). Every float value stays
+// O(1) whatever the box size.
 
 #include <algorithm>
 
@@ -42,7 +43,10 @@ __device__ __forceinline__ float2 fcmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ double box_scale(double r) { return r > 0.0 ? r : 1.0; }
+// The leaf's scale s = 2^e with s <= r < 2 s (r its radius; 1 for r = 0):
+// offsets are taken over s (|x / s| < 2 in the box), and the coefficients
+// scale by s^n, a power of two formed exactly without a power loop in double
+__device__ __forceinline__ int box_scale_exp(double r) { return r > 0.0 ? max(-48, min(48, ilogb(r))) : 0; }
 
 // offsets from the leaf centre, split hi/lo
 __global__ void k_leaf_offsets(int B, int64_t n, const double *__restrict__ x,
@@ -71,12 +75,13 @@ __global__ void k_gather_qf(const T *__restrict__ qin, const int32_t *__restrict
         q[i] = (float)qin[perm[i]];
 }
 
-// P2M on scaled offsets, one warp per leaf: each lane carries kP2MSlots
+// P2M on scaled offsets a / s (s = 2^e, the power of two within a factor
+// 2 below the leaf's radius), one warp per leaf: each lane carries kP2MSlots
 // points, and two warp sums per coefficient (slots 0-1 and 2-3, 64 points
 // each) cover a batch of 128; the two sums stay apart in float in shared
 // memory and are combined in double, so each float sum is no deeper than
 // a 64-term tree. The leaf's multipole is stored unscaled in double
-// (M_n^m = r^n Mhat_n^m).
+// (M_n^m = s^n Mhat_n^m, s^n exact).
 constexpr int kP2MSlots = 4;
 __device__ __forceinline__ void p2m_f32_body(int B, int p, int64_t n, const float *__restrict__ hl,
                                              const float *__restrict__ q, const int32_t *__restrict__ begin,
@@ -87,8 +92,8 @@ __device__ __forceinline__ void p2m_f32_body(int B, int p, int64_t n, const floa
     const int64_t g = ((int64_t)1 << B) - 1 + leaf;
     const int b = begin[g], cnt = count[g];
     const int lane = threadIdx.x;
-    const double rs = box_scale(radius[g]);
-    const float rinv = (float)(1.0 / rs);
+    const int es = box_scale_exp(radius[g]);
+    const float rinv = (float)pow2i(-es);
     for (int c = lane; c < 2 * nc; c += 32) accf[c] = make_float2(0.f, 0.f);
     __syncwarp();
     for (int base = 0; base < cnt; base += 32 * kP2MSlots) {
@@ -160,8 +165,7 @@ __device__ __forceinline__ void p2m_f32_body(int B, int p, int64_t n, const floa
     for (int c = lane; c < nc; c += 32) {
         int nn = 0;
         while (tri(nn + 1, 0) <= c) nn++;
-        double s = 1.0;
-        for (int j = 0; j < nn; j++) s *= rs;
+        const double s = pow2i(es * nn);
         M[g * nc + c] = make_double2(((double)accf[c].x + (double)accf[nc + c].x) * s,
                                      ((double)accf[c].y + (double)accf[nc + c].y) * s);
     }
@@ -182,8 +186,9 @@ k_b_p2m_f32(const BatchSys *__restrict__ S, const int32_t *__restrict__ off, int
     p2m_f32_body(y.B, y.p, y.n, y.hl, y.qf, y.begin, y.count, y.radius, y.M, blockIdx.x - off[s]);
 }
 
-// L2P on scaled offsets: Lhat_k^l = r^k L_k^l; phi = sum Lhat conj(Y(a/r));
-// E = -grad phi = (Re G1, Im G1, -G0) / r with the degree-1 shifted terms.
+// L2P on scaled offsets: Lhat_k^l = s^k L_k^l (s = 2^e near the leaf's
+// radius, s^k exact); phi = sum Lhat conj(Y(a/s)); E = -grad phi =
+// (Re G1, Im G1, -G0) / s with the degree-1 shifted terms.
 __device__ __forceinline__ void l2p_f32_body(int B, int p, int64_t n, const float *__restrict__ hl,
                                              const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
                                              const double *__restrict__ radius, const double2 *__restrict__ L,
@@ -192,17 +197,16 @@ __device__ __forceinline__ void l2p_f32_body(int B, int p, int64_t n, const floa
     const int nc = ncoef(p);
     const int64_t g = ((int64_t)1 << B) - 1 + leaf;
     const int b = begin[g], cnt = count[g];
-    const double rs = box_scale(radius[g]);
+    const int es = box_scale_exp(radius[g]);
     for (int c = threadIdx.x; c < nc; c += kThreads) {
         int nn = 0;
         while (tri(nn + 1, 0) <= c) nn++;
-        double s = 1.0;
-        for (int j = 0; j < nn; j++) s *= rs;
+        const double s = pow2i(es * nn);
         const double2 v = L[g * nc + c];
         Ls[c] = make_float2((float)(v.x * s), (float)(v.y * s));
     }
     __syncthreads();
-    const float rinv = (float)(1.0 / rs);
+    const float rinv = (float)pow2i(-es);
     for (int i = threadIdx.x; i < cnt; i += kThreads) {
         const float sx = (hl[b + i] + hl[3 * n + b + i]) * rinv;
         const float sy = (hl[n + b + i] + hl[4 * n + b + i]) * rinv;
