@@ -106,6 +106,35 @@ def test_batched_stages_equal_individual_evals(gpu_lib, dt):
     fmm.fmm_batch_destroy(batch)
 
 
+@pytest.mark.parametrize("sizes", [[(1, 0)], [(2, 1), (1, 0), (5000, 7)], [(40000, 9)]])
+def test_batched_stages_small_and_single_systems(gpu_lib, sizes):
+    """Batches of one system, and systems of one or two points (a single leaf,
+    no weak pairs, no M2M or L2L), equal the same evaluations alone."""
+    fmm = gpu_lib
+    plans, qs, pots, flds, alone = [], [], [], [], []
+    for i, (n, B) in enumerate(sizes):
+        x = torch.from_numpy(inputs.points("plummer", n, seed=60 + i)).cuda()
+        q = torch.from_numpy(inputs.charges_uniform(n, seed=60 + i)).cuda()
+        plan = fmm.fmm_plan(x, B, 8, 0.5, prec=1)
+        a, b = fmm.fmm_eval(plan, q)
+        alone.append((a.cpu().numpy(), b.cpu().numpy()))
+        plans.append(plan)
+        qs.append(q)
+        pots.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
+        flds.append(torch.zeros((n, 3), dtype=torch.float64, device="cuda"))
+    batch = fmm.fmm_batch_create(plans, qs, pots, flds)
+    assert fmm.fmm_batch_info(batch)["fused"]
+    fmm.fmm_batch_launch(batch)
+    torch.cuda.synchronize()
+    for (a, b), p_, f_ in zip(alone, pots, flds):
+        if np.linalg.norm(a) == 0:
+            assert np.array_equal(p_.cpu().numpy(), a)
+        else:
+            assert rel(p_.cpu().numpy(), a) <= 1e-6
+            assert rel(f_.cpu().numpy(), b) <= 1e-6
+    fmm.fmm_batch_destroy(batch)
+
+
 def test_batched_downward_wait_that_runs_out_reports_etimedout(gpu_lib):
     """The batched downward pass waits (bounded) on each parent as the
     single-plan pass does: a withheld box (test hook, in force when the batch
