@@ -1612,7 +1612,7 @@ __device__ __noinline__ void seg_add(float sx, float sy, unsigned same_mask, boo
 
 // Column sums of a warp's transpose buffer (2 (N+1) columns: Re of orders
 // 0..N, then Im) into the target's coefficients c0..c0+N.
-__device__ __noinline__ void col_add(const float *red, int N, double2 *dst) {
+__device__ __forceinline__ void col_add(const float *red, int N, double2 *dst) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     for (int col = lane; col < 2 * (N + 1); col += 32) {
