@@ -859,29 +859,32 @@ __global__ void k_tight_boxes(int B, const double *__restrict__ x, const double 
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double *src[3] = {x, y, z};
+    // min and max on the order-preserving integer keys of the coordinates
+    // (exact, and equal to fmin / fmax here: no NaN, -0 canonicalised to +0),
+    // off the narrow FP64 pipe
     for (int64_t j = warp; j < nl; j += nwarps) {
         int64_t g = nl - 1 + j;
         const int b = begin[g], n = count[g];
-        double lo[3], hi[3];
+        uint64_t lo[3], hi[3];
         for (int a = 0; a < 3; a++) {
-            double l = __longlong_as_double(0x7ff0000000000000LL), h = -l;  // +inf, -inf
+            uint64_t l = 0xfff0000000000000ull, h = 0x000fffffffffffffull;  // dkey(+inf), dkey(-inf)
             for (int i = lane; i < n; i += 32) {
-                const double v = src[a][b + i];
-                l = fmin(l, v);
-                h = fmax(h, v);
+                const uint64_t v = dkey(src[a][b + i]);
+                l = min(l, v);
+                h = max(h, v);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
-                h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+                l = min(l, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)l, o));
+                h = max(h, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)h, o));
             }
             lo[a] = l;
             hi[a] = h;
         }
         if (lane == 0) {
             for (int a = 0; a < 3; a++) {
-                tlo[3 * g + a] = lo[a];
-                thi[3 * g + a] = hi[a];
+                tlo[3 * g + a] = dkey_inv(lo[a]);
+                thi[3 * g + a] = dkey_inv(hi[a]);
             }
             while (g > 0) {
                 __threadfence();
@@ -890,8 +893,8 @@ __global__ void k_tight_boxes(int B, const double *__restrict__ x, const double 
                 __threadfence();
                 const int64_t c0 = 2 * par + 1, c1 = c0 + 1;
                 for (int a = 0; a < 3; a++) {
-                    tlo[3 * par + a] = fmin(__ldcg(tlo + 3 * c0 + a), __ldcg(tlo + 3 * c1 + a));
-                    thi[3 * par + a] = fmax(__ldcg(thi + 3 * c0 + a), __ldcg(thi + 3 * c1 + a));
+                    tlo[3 * par + a] = dkey_inv(min(dkey(__ldcg(tlo + 3 * c0 + a)), dkey(__ldcg(tlo + 3 * c1 + a))));
+                    thi[3 * par + a] = dkey_inv(max(dkey(__ldcg(thi + 3 * c0 + a)), dkey(__ldcg(thi + 3 * c1 + a))));
                 }
                 g = par;
             }
