@@ -309,7 +309,7 @@ __global__ void k_leaf_geo(int B, const double *__restrict__ lo, const double *_
     geo[3 * j + 2] = make_float4(e[0], e[1], e[2], 0.f);
 }
 
-constexpr int kLeafChunk = 256;
+constexpr int kLeafChunk = 128;
 constexpr float kFarGap = 0.1f;   // far: cell gap >= kFarGap (r_t + r_s)
 constexpr float kPadFar = 1.0e18f;  // padding source: zero charge, far away
 constexpr int kRun = 64;  // sources summed in float before the compensated add
@@ -372,6 +372,38 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
     a[3] = fma2(qr3, dz, a[3]);
 }
 
+// exclusive prefix of v[0..len) in place (len <= kLeafChunk), the total at
+// v[len]; block-wide (T threads), synchronised on return
+template <int T>
+__device__ __forceinline__ void block_excl_scan(int *v, int len, int *wsum) {
+    constexpr int kPer = (kLeafChunk + T - 1) / T;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k0 = tid * kPer;
+    int loc[kPer], own = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; i++) {
+        loc[i] = k0 + i < len ? v[k0 + i] : 0;
+        own += loc[i];
+    }
+    int inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int run = inc - own;
+    for (int i = 0; i < w; i++) run += wsum[i];
+#pragma unroll
+    for (int i = 0; i < kPer; i++) {
+        if (k0 + i < len) v[k0 + i] = run;
+        run += loc[i];
+    }
+    if (tid == T - 1) v[len] = run;  // entries past len count zero
+    __syncthreads();
+}
+
 // Near field in float. One CTA per work unit (a tile of up to T = 128 or 64
 // targets of one leaf, by the plan's mean leaf size; heaviest units first),
 // T sources staged per pass, one target point per thread, two
@@ -386,9 +418,13 @@ __device__ __forceinline__ void near_pair2(float2 X, float2 Y, float2 Z, float2 
 // g >= 0.5 (r_t + r_s), known to ~20u): a single float per coordinate
 // suffices, and no two points can coincide. Near leaves (touching or nearly
 // touching cells, ~4% of the pairs on a Plummer sphere) keep the split hi/lo
-// offsets, whose difference is exact for close pairs. Per target the sources are
-// summed in plain float over runs of 64 (full runs with a fixed trip count)
-// and the runs compensated (Kahan).
+// offsets, whose difference is exact for close pairs. The far source leaves
+// of a chunk of the strong list are staged as one stream (a block scan of
+// their counts places each source), 4T sources per pass across leaf
+// boundaries, so that the pair loop mostly runs full runs and the barriers
+// and staging are shared by several leaves; the near leaves form a second
+// stream, 2T per pass. Per target the sources are summed in plain float over runs of 64
+// (full runs with a fixed trip count) and the runs compensated (Kahan).
 template <typename OutT, int T>
 __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__restrict__ hl,
                                              const float *__restrict__ qf, const int32_t *__restrict__ begin,
@@ -397,14 +433,17 @@ __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__re
                                              const int32_t *__restrict__ perm, const float *__restrict__ far_phi,
                                              const float *__restrict__ far_E, double4 *__restrict__ partial,
                                              OutT *__restrict__ pot, OutT *__restrict__ field) {
-    constexpr int kP2PThreads = T, kSrcTile = T;
-    __shared__ float4 sA[kSrcTile / 2], sB[kSrcTile / 2];  // hi parts and charges, per source pair
-    __shared__ float4 sC[kSrcTile / 2], sD[kSrcTile / 2];  // lo parts (near leaves)
+    constexpr int kP2PThreads = T, kFarCap = 4 * T, kNearCap = 2 * T;
+    __shared__ float4 sA[kFarCap / 2], sB[kFarCap / 2];    // hi parts and charges, per source pair
+    __shared__ float4 sC[kNearCap / 2], sD[kNearCap / 2];  // lo parts (near leaves)
     __shared__ float4 dh[kLeafChunk];   // per source leaf: centre offset hi, near flag
     __shared__ float4 dl[kLeafChunk];   // centre offset lo
     __shared__ int2 rng[kLeafChunk];    // begin, count
+    __shared__ int fpre[kLeafChunk + 1];  // far leaves' counts (near: 0), then their exclusive prefix
+    __shared__ int npre[kLeafChunk + 1];  // the same for the near leaves
+    __shared__ int wsum[T / 32];
     static_assert(T == kP2PTile || T == kP2PTileSmall, "one target per thread");
-    static_assert(kRun <= kSrcTile, "a run fits in a staged tile");
+    static_assert(kRun <= kNearCap && kNearCap <= kFarCap, "a run fits in a staged pass");
     const int64_t off = ((int64_t)1 << B) - 1;
     const int t = unit.x;
     const int64_t gt = off + t;
@@ -428,8 +467,26 @@ __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__re
 #pragma unroll
     for (int j = 0; j < 4; j++) sum[j] = comp[j] = 0.f;
     float *fA = (float *)sA, *fB = (float *)sB, *fC = (float *)sC, *fD = (float *)sD;
-    // slot of this thread's staged source: pair tid/2, component tid&1
-    const int sp = (tid >> 1) * 4 + (tid & 1);
+    // runs of 64 staged sources (m of them from pair slot 0) against this
+    // thread's target, each run compensated into the sums
+    auto far_runs = [&](int m) {
+        for (int j0 = 0; j0 < (busy ? m : 0); j0 += kRun) {
+            const int npair = (min(kRun, m - j0) + 1) >> 1;
+            const int p0 = j0 >> 1;
+            float2 a[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) a[c] = make_float2(0.f, 0.f);
+            if (npair == kRun / 2) {
+#pragma unroll 8
+                for (int pp = 0; pp < kRun / 2; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
+            } else {
+#pragma unroll 4
+                for (int pp = 0; pp < npair; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) kahan(sum[c], comp[c], a[c].x + a[c].y);
+        }
+    };
     for (int cb = e0; cb < e1; cb += kLeafChunk) {
         const int clen = min(kLeafChunk, e1 - cb);
         __syncthreads();
@@ -445,77 +502,95 @@ __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__re
             const float gz = fmaxf(0.f, fabsf(dzh) - (tc_e.z + se.z));
             const float lim = kFarGap * (tc_h.w + sh.w);
             const bool far = gx * gx + gy * gy + gz * gz >= lim * lim && lim > 0.f;
+            const int ns = count[off + s];
             dh[k] = make_float4(dxh, dyh, dzh, far ? 1.f : 0.f);
             dl[k] = make_float4(e_x + (sl.x - tc_l.x), e_y + (sl.y - tc_l.y), e_z + (sl.z - tc_l.z), 0.f);
-            rng[k] = make_int2(begin[off + s], count[off + s]);
+            rng[k] = make_int2(begin[off + s], ns);
+            fpre[k] = far ? ns : 0;
+            npre[k] = far ? 0 : ns;
         }
         __syncthreads();
-        for (int k = 0; k < clen; k++) {
-            const float4 d = dh[k];
-            const float4 dlo = dl[k];
-            const int bs = rng[k].x, ns = rng[k].y;
-            const bool far = d.w != 0.f;
-            for (int sb = 0; sb < ns; sb += kSrcTile) {
-                __syncthreads();
-                const int j = sb + tid;
+        block_excl_scan<T>(fpre, clen, wsum);
+        block_excl_scan<T>(npre, clen, wsum);
+        // far leaves: their sources as one stream, far source f of the chunk
+        // in leaf kc with fpre[kc] <= f < fpre[kc + 1] (each thread's cursor
+        // only moves forward)
+        const int nfar = fpre[clen];
+        int kc = 0;
+        for (int base = 0; base < nfar; base += kFarCap) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < kFarCap / kP2PThreads; r++) {
+                const int slot = r * kP2PThreads + tid, f = base + slot;
+                float sx = kPadFar, sy = kPadFar, sz = kPadFar, q = 0.f;
+                if (f < nfar) {
+                    while (fpre[kc + 1] <= f) kc++;
+                    const int bs = rng[kc].x + (f - fpre[kc]);
+                    const float4 d = dh[kc], dlo = dl[kc];
+                    sx = (hl[bs] + d.x) + (hl[3 * n + bs] + dlo.x);
+                    sy = (hl[n + bs] + d.y) + (hl[4 * n + bs] + dlo.y);
+                    sz = (hl[2 * n + bs] + d.z) + (hl[5 * n + bs] + dlo.z);
+                    q = qf[bs];
+                }
+                const int sq = (slot >> 1) * 4 + (slot & 1);
+                fA[sq] = -sx;
+                fA[sq + 2] = -sy;
+                fB[sq] = -sz;
+                fB[sq + 2] = q;
+            }
+            __syncthreads();
+            far_runs(min(kFarCap, nfar - base));
+        }
+        // near leaves: the second stream, with split hi/lo offsets
+        const int nnear = npre[clen];
+        kc = 0;
+        for (int base = 0; base < nnear; base += kNearCap) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < kNearCap / kP2PThreads; r++) {
+                const int slot = r * kP2PThreads + tid, f = base + slot;
                 float sx = kPadFar, sy = kPadFar, sz = kPadFar, q = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-                if (j < ns) {
-                    const float ahx = hl[bs + j], ahy = hl[n + bs + j], ahz = hl[2 * n + bs + j];
-                    const float alx = hl[3 * n + bs + j], aly = hl[4 * n + bs + j], alz = hl[5 * n + bs + j];
-                    q = qf[bs + j];
-                    if (far) {
-                        sx = (ahx + d.x) + (alx + dlo.x);
-                        sy = (ahy + d.y) + (aly + dlo.y);
-                        sz = (ahz + d.z) + (alz + dlo.z);
-                    } else {
-                        float ex, ey, ez;
-                        sx = two_sum(ahx, d.x, ex);
-                        sy = two_sum(ahy, d.y, ey);
-                        sz = two_sum(ahz, d.z, ez);
-                        ux = ex + (alx + dlo.x);
-                        uy = ey + (aly + dlo.y);
-                        uz = ez + (alz + dlo.z);
-                    }
+                if (f < nnear) {
+                    while (npre[kc + 1] <= f) kc++;
+                    const int bs = rng[kc].x + (f - npre[kc]);
+                    const float4 d = dh[kc], dlo = dl[kc];
+                    float ex, ey, ez;
+                    sx = two_sum(hl[bs], d.x, ex);
+                    sy = two_sum(hl[n + bs], d.y, ey);
+                    sz = two_sum(hl[2 * n + bs], d.z, ez);
+                    ux = ex + (hl[3 * n + bs] + dlo.x);
+                    uy = ey + (hl[4 * n + bs] + dlo.y);
+                    uz = ez + (hl[5 * n + bs] + dlo.z);
+                    q = qf[bs];
                 }
-                fA[sp] = -sx;
-                fA[sp + 2] = -sy;
-                fB[sp] = -sz;
-                fB[sp + 2] = q;
-                if (!far) {
-                    fC[sp] = -ux;
-                    fC[sp + 2] = -uy;
-                    fD[sp] = -uz;
-                }
-                __syncthreads();
-                const int mcount = min(kSrcTile, ns - sb);
-                for (int j0 = 0; j0 < (busy ? mcount : 0); j0 += kRun) {
-                    const int npair = (min(kRun, mcount - j0) + 1) >> 1;
-                    const int p0 = j0 >> 1;
-                    float2 a[4];
+                const int sq = (slot >> 1) * 4 + (slot & 1);
+                fA[sq] = -sx;
+                fA[sq + 2] = -sy;
+                fB[sq] = -sz;
+                fB[sq + 2] = q;
+                fC[sq] = -ux;
+                fC[sq + 2] = -uy;
+                fD[sq] = -uz;
+            }
+            __syncthreads();
+            const int m = min(kNearCap, nnear - base);
+            for (int j0 = 0; j0 < (busy ? m : 0); j0 += kRun) {
+                const int npair = (min(kRun, m - j0) + 1) >> 1;
+                const int p0 = j0 >> 1;
+                float2 a[4];
 #pragma unroll
-                    for (int c = 0; c < 4; c++) a[c] = make_float2(0.f, 0.f);
-                    if (far) {
-                        if (npair == kRun / 2) {
+                for (int c = 0; c < 4; c++) a[c] = make_float2(0.f, 0.f);
+                if (npair == kRun / 2) {
 #pragma unroll 8
-                            for (int pp = 0; pp < kRun / 2; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
-                        } else {
+                    for (int pp = 0; pp < kRun / 2; pp++)
+                        near_pair2(X, Y, Z, XL, YL, ZL, sA[p0 + pp], sB[p0 + pp], sC[p0 + pp], sD[p0 + pp], a);
+                } else {
 #pragma unroll 4
-                            for (int pp = 0; pp < npair; pp++) far_pair2(X, Y, Z, sA[p0 + pp], sB[p0 + pp], a);
-                        }
-                    } else {
-                        if (npair == kRun / 2) {
-#pragma unroll 8
-                            for (int pp = 0; pp < kRun / 2; pp++)
-                                near_pair2(X, Y, Z, XL, YL, ZL, sA[p0 + pp], sB[p0 + pp], sC[p0 + pp], sD[p0 + pp], a);
-                        } else {
-#pragma unroll 4
-                            for (int pp = 0; pp < npair; pp++)
-                                near_pair2(X, Y, Z, XL, YL, ZL, sA[p0 + pp], sB[p0 + pp], sC[p0 + pp], sD[p0 + pp], a);
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 4; c++) kahan(sum[c], comp[c], a[c].x + a[c].y);
+                    for (int pp = 0; pp < npair; pp++)
+                        near_pair2(X, Y, Z, XL, YL, ZL, sA[p0 + pp], sB[p0 + pp], sC[p0 + pp], sD[p0 + pp], a);
                 }
+#pragma unroll
+                for (int c = 0; c < 4; c++) kahan(sum[c], comp[c], a[c].x + a[c].y);
             }
         }
     }
