@@ -569,7 +569,10 @@ def bench_batch(args, rank, world, local):
 def bench_serve(args, rank, world, local):
     """Serving: a Poisson stream of requests (200/s), N log-uniform in
     [1e3, 1e6], uniform / Plummer / Gaussian-mixture points (1/3 each),
-    target error 1e-5 (p = args.serve_p, theta = 0.5, ~100 points per leaf,
+    target error 1e-5 (theta = 0.5, ~100 points per leaf, p by size: 8 below
+    100,000 points, 10 from there on -- at p = 8 the error of the larger
+    Plummer requests reached 2.2e-5, at p = 10 every size and kind stays below
+    5e-6; --serve-p fixes one order for all,
     mixed form), admitted under a device-memory budget by the continuous-batching
     server: throughput and p50/p99 latency at the offered rate, then the same
     requests all queued at once (the server's capacity). A share of the
@@ -602,11 +605,12 @@ def bench_serve(args, rank, world, local):
             x, q = x[o:o + n], q[o:o + n]
             geom = ("req", i) if args.repeat_frac > 0 else None
             sets.append((x, n, geom))
-        reqs.append(serve.Request(i, x, q, arrival=float(arr[i]), p=args.serve_p, theta=0.5,
+        order = args.serve_p or (8 if n < 100_000 else 10)
+        reqs.append(serve.Request(i, x, q, arrival=float(arr[i]), p=order, theta=0.5,
                                   prec=fmm.FMM_PREC_MIXED, geom=geom))
     cache = int(args.cache_gb * (1 << 30)) if args.repeat_frac > 0 else 0
     srv = serve.FmmServer(budget=int(args.budget_gb * (1 << 30)), workers=args.workers, cache_bytes=cache)
-    warm = [serve.Request(-1 - j, reqs[j].points, reqs[j].charges, 0.0, p=args.serve_p) for j in range(4)]
+    warm = [serve.Request(-1 - j, reqs[j].points, reqs[j].charges, 0.0, p=reqs[j].p) for j in range(4)]
     srv.run(warm, realtime=False)
     pts = sum(len(r.charges) for r in reqs)
     launches0 = fmm.fmm_kernel_launches()
@@ -656,7 +660,7 @@ def bench_serve(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serve", "requests": args.requests, "rate_per_s": args.rate,
                    "n_range": [1000, 1000000], "budget_gb": args.budget_gb, "workers": args.workers,
-                   "p": args.serve_p, "theta": 0.5, "leaf": 100, "repeat_frac": args.repeat_frac,
+                   "p": args.serve_p or "8 below 100,000 points, else 10", "theta": 0.5, "leaf": 100, "repeat_frac": args.repeat_frac,
                    "resident_cache_gb": cache / (1 << 30)},
         "latency_ms": lat, "requests_per_s": round(args.requests / makespan, 2),
         "points": int(pts), "resident_hits": hits_rt,
@@ -897,7 +901,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve mode: device memory budget")
     ap.add_argument("--workers", type=int, default=8, help="serve mode: concurrent solves")
-    ap.add_argument("--serve-p", type=int, default=8, help="serve mode: expansion order (target 1e-5)")
+    ap.add_argument("--serve-p", type=int, default=0,
+                    help="serve mode: one expansion order for every request (0: by size, 8 below 1e5 points, else 10)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.profile_solve:

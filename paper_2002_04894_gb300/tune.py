@@ -53,6 +53,13 @@ def p_from_bound(tol: float, theta: float, allowed=(6, 8, 10, 12, 14, 16)) -> in
     return allowed[-1]
 
 
+def pick(trials, tol: float):
+    """The fastest (config, ms, error) trial whose error meets `tol`; when
+    none does, the most accurate one."""
+    ok = [t for t in trials if t[2] <= tol]
+    return min(ok, key=lambda t: t[1]) if ok else min(trials, key=lambda t: t[2])
+
+
 def levels_for_leaf(n: int, leaf: float) -> int:
     return max(0, int(round(math.log2(max(n, 1) / leaf))))
 
@@ -153,14 +160,12 @@ def tune(points, charges, tol: float = 1e-6, leaf_range=(32, 256), thetas=(0.4, 
     ti, _, _ = descend(lambda i: run(Config(lev, p, thetas[i]))[0], list(thetas).index(0.5)
                        if 0.5 in thetas else 0, 0, len(thetas) - 1)
     theta = thetas[ti]
-    best = None
     for pp in ps:  # smallest p meeting the target at (lev, theta)
-        ms, err = run(Config(lev, pp, theta))
-        if err <= tol:
-            best = TuneResult(Config(lev, pp, theta), ms, err)
+        if run(Config(lev, pp, theta))[1] <= tol:
             break
-    if best is None:
-        cfg, ms, err = min(trials, key=lambda t: t[2])
-        best = TuneResult(cfg, ms, err)
+    # the levels and theta were searched by time alone (a faster theta may
+    # miss the target at every allowed p): the fastest trial that meets it
+    cfg, ms, err = pick(trials, tol)
+    best = TuneResult(cfg, ms, err)
     best.trials = trials
     return best

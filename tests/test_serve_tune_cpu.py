@@ -89,6 +89,15 @@ def test_p_from_bound_meets_the_a_priori_bound(tol, theta):
     assert theta ** p / (1 - theta) ** 2 > tol        # and is the smallest such p
 
 
+def test_pick_takes_the_fastest_trial_meeting_the_target():
+    C = tune.Config
+    trials = [(C(11, 12, 0.5), 5.19, 3.5e-7), (C(12, 12, 0.5), 5.29, 4.0e-7), (C(10, 12, 0.5), 6.24, 2.3e-7),
+              (C(11, 12, 0.6), 3.52, 1.1e-5)]
+    assert tune.pick(trials, 5e-7)[0] == C(11, 12, 0.5)     # not the most accurate, not the fastest overall
+    assert tune.pick(trials, 1e-7)[0] == C(10, 12, 0.5)     # none meets it: the most accurate
+    assert tune.pick(trials, 1e-4)[0] == C(11, 12, 0.6)
+
+
 def test_levels_for_leaf():
     assert tune.levels_for_leaf(2_000_000, 122) == 14
     assert 2 ** tune.levels_for_leaf(100_000, 100) == pytest.approx(1000, rel=0.5)
