@@ -315,8 +315,7 @@ int64_t fmm_kernel_launches(void);
  * `stream`, then copies the build's 4-byte status word to the host and
  * synchronises `stream`, so perm is complete when it returns FMM_OK.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins. Every call shares the one array and
+ * (cudaGetSymbolAddress) with that device current. Every call shares the one array and
  * re-initialises what must start cleared, so calls that overlap on the GPU
  * (other streams, other host threads) race and corrupt each other's results:
  * serialise them.

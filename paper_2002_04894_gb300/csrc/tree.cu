@@ -948,8 +948,8 @@ cudaError_t tight_geometry(Plan &P) {
 // ---------------------------------------------------------------------------
 // Allocation-free ORB leaf order for small point sets (fmm_orb_order_noalloc).
 //
-// For callers that cannot allocate device memory (stream capture, host
-// applications that own all device memory, real-time loops): the small-regime
+// For callers that cannot allocate device memory (host applications that
+// own all device memory, loops that cannot wait on an allocator): the small-regime
 // split kernels above run with every scratch buffer carved out of one static
 // device array. Up to FMM_NOALLOC_MAX_POINTS points every level is in the
 // one-CTA regime, so no chunk counters or histograms are needed.

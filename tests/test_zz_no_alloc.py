@@ -1,8 +1,7 @@
 """The allocation-free entry point, fmm_orb_order_noalloc, against fmm_plan.
 
-Some callers cannot allocate device memory: code running while a stream is
-captured into a CUDA graph, plug-ins whose host application owns all device
-memory, real-time loops. For them the library offers the balanced tree's leaf
+Some callers cannot allocate device memory: plug-ins whose host application
+owns all device memory, real-time loops. For them the library offers the balanced tree's leaf
 order for up to 4096 points with all scratch in a static device array. These
 tests call it through the C ABI twice in a row and compare each result, bit
 for bit, with the permutation that fmm_plan + fmm_plan_tree report for the
