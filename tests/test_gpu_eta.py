@@ -135,4 +135,4 @@ def test_mixed_eta_accuracy(gpu_lib, eta):
     # bounds: twice the values measured on a GB300, rounded up
     parity.check(f"eta_mixed_vs_direct/{eta}", "l2_phi", parity.rel_l2(got, ref), 4e-7)
     parity.check(f"eta_mixed_vs_direct/{eta}", "point_phi", parity.pointwise_phi(got, ref),
-                 {0.0: 8e-6, 0.5: 4e-6}[eta])
+                 {0.0: 8e-6, 0.5: 7e-6}[eta])

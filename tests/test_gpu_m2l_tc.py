@@ -22,13 +22,13 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = {"l2_phi": 1e-5, "l2_field": 1e-5, "point_phi": 1e-2, "point_field": 1e-2, "box_L": 1e-2}
 MEASURED = {
-    "tc/gmm/9000/9/10/0.6": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 9e-07, "box_L": 0.0002},
-    "tc/plummer/12000/8/12/0.5": {"l2_phi": 5e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 1e-06, "box_L": 5e-05},
-    "tc/plummer/6000/9/5/0.5": {"l2_phi": 4e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 1e-06, "box_L": 7e-06},
-    "tc/shell/4000/9/11/0.5": {"l2_phi": 3e-07, "l2_field": 2e-07, "point_phi": 7e-06, "point_field": 8e-07, "box_L": 6e-05},
-    "tc/uniform/2000/8/1/0.4": {"l2_phi": 4e-07, "l2_field": 9e-08, "point_phi": 2e-05, "point_field": 5e-07, "box_L": 7e-06},
-    "tc/uniform/20000/8/8/0.5": {"l2_phi": 4e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 3e-06, "box_L": 2e-05},
-    "tc/uniform/700/5/12/0.7": {"l2_phi": 2e-07, "l2_field": 2e-07, "point_phi": 4e-06, "point_field": 8e-07, "box_L": 2e-05},
+    "tc/gmm/9000/9/10/0.6": {"l2_phi": 5e-07, "l2_field": 4e-07, "point_phi": 3e-05, "point_field": 2e-06, "box_L": 0.0001},
+    "tc/plummer/12000/8/12/0.5": {"l2_phi": 5e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 2e-06, "box_L": 5e-05},
+    "tc/plummer/6000/9/5/0.5": {"l2_phi": 5e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 2e-06, "box_L": 6e-06},
+    "tc/shell/4000/9/11/0.5": {"l2_phi": 4e-07, "l2_field": 3e-07, "point_phi": 8e-06, "point_field": 2e-06, "box_L": 6e-05},
+    "tc/uniform/2000/8/1/0.4": {"l2_phi": 5e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 8e-07, "box_L": 7e-06},
+    "tc/uniform/20000/8/8/0.5": {"l2_phi": 4e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 2e-06, "box_L": 2e-05},
+    "tc/uniform/700/5/12/0.7": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 8e-06, "point_field": 2e-06, "box_L": 2e-05},
 }
 # p -> bounds of the tensor-core vs CUDA-core comparison (2 x measured, rounded up)
 VS_SIMT = {4: (4e-6, 1e-5), 6: (2e-5, 2e-5), 8: (3e-5, 2e-6), 10: (9e-5, 2e-5), 12: (3e-4, 2e-5)}

@@ -24,17 +24,17 @@ DEFAULT = {"l2_phi": 1e-5, "l2_field": 1e-5, "point_phi": 1e-2, "point_field": 1
            "box_M": 1e-2, "box_L": 1e-2}
 # case id -> {measure: 2 x the value measured on a GB300, rounded up}
 MEASURED = {
-    "mixed/gmm/30000/8/12/0.5/float32/pm1": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 2e-06, "box_M": 9e-06, "box_L": 0.0002},
-    "mixed/gmm/6000/8/6/0.5/float64/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 9e-06, "point_field": 2e-06, "box_M": 3e-05, "box_L": 3e-05},
-    "mixed/gmm/9000/9/12/0.5/float32/uniform": {"l2_phi": 2e-07, "l2_field": 2e-07, "point_phi": 6e-06, "point_field": 1e-06, "box_M": 2e-05, "box_L": 0.0003},
-    "mixed/plummer/12000/8/10/0.5/float64/uniform": {"l2_phi": 2e-07, "l2_field": 4e-07, "point_phi": 3e-06, "point_field": 5e-07, "box_M": 4e-06, "box_L": 2e-05},
-    "mixed/plummer/3000/6/7/0.5/float64/uniform": {"l2_phi": 1e-07, "l2_field": 2e-07, "point_phi": 2e-06, "point_field": 2e-06, "box_M": 3e-06, "box_L": 1e-15},
-    "mixed/plummer/4000/7/16/0.6/float64/uniform": {"l2_phi": 2e-07, "l2_field": 2e-07, "point_phi": 2e-06, "point_field": 2e-06, "box_M": 2e-06, "box_L": 0.0003},
-    "mixed/plummer/8000/8/4/0.5/float64/uniform": {"l2_phi": 2e-07, "l2_field": 3e-07, "point_phi": 2e-06, "point_field": 2e-06, "box_M": 4e-06, "box_L": 4e-06},
-    "mixed/uniform/1000/5/6/0.0/float32/uniform": {"l2_phi": 4e-07, "l2_field": 3e-07, "point_phi": 7e-06, "point_field": 6e-07, "box_M": 2e-06, "box_L": 1e-15},
-    "mixed/uniform/20000/8/8/0.5/float64/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 8e-06, "point_field": 2e-06, "box_M": 2e-06, "box_L": 2e-05},
-    "mixed/uniform/300/10/4/0.5/float64/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 4e-06, "point_field": 9e-07, "box_M": 8e-07, "box_L": 5e-06},
-    "mixed/uniform/5000/7/14/0.6/float64/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 8e-06, "point_field": 2e-06, "box_M": 2e-06, "box_L": 4e-05},
+    "mixed/gmm/30000/8/12/0.5/float32/pm1": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 2e-05, "point_field": 3e-06, "box_M": 2e-05, "box_L": 9e-05},
+    "mixed/gmm/6000/8/6/0.5/float64/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 1e-05, "point_field": 2e-06, "box_M": 3e-05, "box_L": 3e-05},
+    "mixed/gmm/9000/9/12/0.5/float32/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 1e-05, "point_field": 2e-06, "box_M": 2e-05, "box_L": 8e-05},
+    "mixed/plummer/12000/8/10/0.5/float64/uniform": {"l2_phi": 2e-07, "l2_field": 4e-07, "point_phi": 5e-06, "point_field": 6e-07, "box_M": 4e-06, "box_L": 2e-05},
+    "mixed/plummer/3000/6/7/0.5/float64/uniform": {"l2_phi": 1e-07, "l2_field": 3e-07, "point_phi": 5e-07, "point_field": 2e-06, "box_M": 5e-06, "box_L": 1e-15},
+    "mixed/plummer/4000/7/16/0.6/float64/uniform": {"l2_phi": 2e-07, "l2_field": 3e-07, "point_phi": 9e-07, "point_field": 2e-06, "box_M": 2e-06, "box_L": 0.0003},
+    "mixed/plummer/8000/8/4/0.5/float64/uniform": {"l2_phi": 2e-07, "l2_field": 3e-07, "point_phi": 2e-06, "point_field": 2e-06, "box_M": 6e-06, "box_L": 3e-06},
+    "mixed/uniform/1000/5/6/0.0/float32/uniform": {"l2_phi": 5e-07, "l2_field": 2e-07, "point_phi": 2e-05, "point_field": 2e-06, "box_M": 2e-06, "box_L": 1e-15},
+    "mixed/uniform/20000/8/8/0.5/float64/uniform": {"l2_phi": 3e-07, "l2_field": 4e-07, "point_phi": 8e-06, "point_field": 2e-06, "box_M": 2e-06, "box_L": 2e-05},
+    "mixed/uniform/300/10/4/0.5/float64/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 3e-06, "point_field": 9e-07, "box_M": 8e-07, "box_L": 5e-06},
+    "mixed/uniform/5000/7/14/0.6/float64/uniform": {"l2_phi": 3e-07, "l2_field": 3e-07, "point_phi": 9e-06, "point_field": 2e-06, "box_M": 2e-06, "box_L": 3e-05},
 }
 
 
@@ -114,7 +114,7 @@ def test_mixed_vs_direct_accuracy(gpu_lib):
     # bounds: twice the values measured on a GB300, rounded up
     parity.check("mixed_vs_direct", "l2_phi", parity.rel_l2(pot.cpu().numpy()[t], op), 2e-7)
     parity.check("mixed_vs_direct", "l2_field", parity.rel_l2(fld.cpu().numpy()[t], oE), 3e-7)
-    parity.check("mixed_vs_direct", "point_phi", parity.pointwise_phi(pot.cpu().numpy()[t], op), 6e-7)
+    parity.check("mixed_vs_direct", "point_phi", parity.pointwise_phi(pot.cpu().numpy()[t], op), 9e-7)
 
 
 def test_plans_of_different_orders_coexist(gpu_lib):
