@@ -406,8 +406,8 @@ __device__ __forceinline__ void block_excl_scan(int *v, int len, int *wsum) {
 
 // Near field in float. One CTA per work unit (a tile of up to T = 128 or 64
 // targets of one leaf, by the plan's mean leaf size; heaviest units first),
-// T sources staged per pass, one target point per thread, two
-// sources per step in packed float2 arithmetic (FFMA2/FADD2/FMUL2). For
+// one target point per thread, two sources per step in packed float2
+// arithmetic (FFMA2/FADD2/FMUL2). For
 // every source leaf the offset between the two leaf centres is formed once,
 // error-free (float TwoSum on the centres' hi/lo parts), together with a
 // near/far flag: far when the gap g between the two cells is at least
@@ -423,8 +423,9 @@ __device__ __forceinline__ void block_excl_scan(int *v, int len, int *wsum) {
 // their counts places each source), 4T sources per pass across leaf
 // boundaries, so that the pair loop mostly runs full runs and the barriers
 // and staging are shared by several leaves; the near leaves form a second
-// stream, 2T per pass. Per target the sources are summed in plain float over runs of 64
-// (full runs with a fixed trip count) and the runs compensated (Kahan).
+// stream, 2T per pass. Per target the sources are summed in plain float over
+// runs of 64 (full runs with a fixed trip count) and the runs compensated
+// (Kahan).
 template <typename OutT, int T>
 __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__restrict__ hl,
                                              const float *__restrict__ qf, const int32_t *__restrict__ begin,
