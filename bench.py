@@ -87,7 +87,7 @@ MEASURED_TRAFFIC = {
                                      "source": "paper_2002_04894_gb300/csrc/mixed.cu",
                                      "region": ("constexpr int kLeafChunk",
                                                 "// batched: the work units of every system in one list"),
-                                     "sha256_16": "4a71475bfd2f84d7"},
+                                     "sha256_16": "883172ae9597ab61"},
 }
 
 

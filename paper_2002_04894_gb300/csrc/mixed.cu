@@ -611,13 +611,14 @@ __device__ __forceinline__ void p2p_f32_body(int B, int64_t n, const float *__re
 }
 
 // resident blocks asked of the register allocator (0: no constraint). The
-// batched kernel holds the system's pointers in registers, and unconstrained
-// spills in its loop: at <= 80 registers (6 blocks of 128, 12 of 64) it does
-// not (512 systems: 53.6 -> 58.9 Mpoints/s). The single-plan kernel runs best
-// unconstrained (64 registers for 128-target tiles, 72 for 64: with 80 the
-// 2M-point near field took 17.5 instead of 17.0 ms).
+// batched kernel holds the system's pointers in registers; unconstrained it
+// takes 126 registers. At 64 registers for 128-target tiles (8 blocks) and 80
+// for 64-target tiles (12 blocks) the 512-system batch ran in 319.0 ms, against
+// 324.8 ms at 80 registers for both (328 ms at 72). The single-plan kernel runs
+// best unconstrained (64 registers for 128-target tiles, 64 for 64: with 72 the
+// 8M-point near field took 55.4 instead of 53.3 ms).
 template <int T>
-constexpr int p2p_min_blocks(bool batched) { return batched ? (T == kP2PTile ? 6 : 12) : 0; }
+constexpr int p2p_min_blocks(bool batched) { return batched ? (T == kP2PTile ? 8 : 12) : 0; }
 
 template <typename OutT, int T>
 __global__ void __launch_bounds__(T, p2p_min_blocks<T>(false))
