@@ -1276,8 +1276,6 @@ cudaError_t m2l_all(Plan &P) {
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kPMax = FMM_MAX_P;
-__constant__ float c_F[(kPMax + 1) * (kPMax + 2) / 2];
 
 // Packed coefficient-pair tables of order P (float4 = two pairs), built per
 // plan and staged in shared memory. A fold table has, per degree n and
@@ -1953,27 +1951,6 @@ __global__ void k_unscale_locals(int64_t nbox, int p, const double *__restrict__
     }
 }
 
-bool g_ctab_ready[64] = {};
-std::atomic<int> g_ctab_lock{0};
-
-cudaError_t f32_tables_ready() {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    while (g_ctab_lock.exchange(1, std::memory_order_acquire)) {
-    }
-    if (!g_ctab_ready[dev]) {
-        std::vector<float> F;
-        for (int n = 0; n <= kPMax; n++)
-            for (int m = 0; m <= n; m++) F.push_back((float)sqrtl(factl(n + m) * factl(n - m)));
-        e = cudaMemcpyToSymbol(c_F, F.data(), F.size() * 4);
-        if (e == cudaSuccess) g_ctab_ready[dev] = true;
-    }
-    g_ctab_lock.store(0, std::memory_order_release);
-    return e;
-}
-
 long double norm_F(int n, int m) { return sqrtl(factl(n + m) * factl(n - m)); }
 
 // entry (k, m) of fold table `tab` (Df, DTf, Db, DTb) of degree n, zero past m = n
@@ -2072,13 +2049,11 @@ cudaError_t m2l_f32_setup(Plan &P) {
         P.m2l_tc = true;
         return m2l_tc_setup(P);
     }
-    cudaError_t e = f32_tables_ready();
-    if (e != cudaSuccess) return e;
     const std::vector<float4> &pt = f32_pair_tables_cached(P.p);
     P.f32_tab = palloc(P, pt.size() * sizeof(float4));
     if (!P.f32_tab) return cudaErrorMemoryAllocation;
     // stream-ordered copy from pageable memory completes before return
-    e = cudaMemcpyAsync(P.f32_tab, pt.data(), pt.size() * sizeof(float4), cudaMemcpyHostToDevice, P.stream);
+    cudaError_t e = cudaMemcpyAsync(P.f32_tab, pt.data(), pt.size() * sizeof(float4), cudaMemcpyHostToDevice, P.stream);
     if (e != cudaSuccess) return e;
     switch (P.p) {
         case 4: return attr_f32<4>();
