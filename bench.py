@@ -60,6 +60,8 @@ WORKLOADS = {
     "plummer2m_l14_p10_fp64": ("plummer", 2_000_000, 14, 10, 0.5, "f64", "uniform", "fp64", False),
     # the small uniform configuration (8 levels: ~78 points per leaf)
     "uniform20k_l8_p8": ("uniform", 20_000, 8, 8, 0.5, "f64", "uniform", "fp64", False),
+    # the comparison of the two single-precision M2L kernels (with and without --tc-m2l)
+    "plummer400k_l12_p12": ("plummer", 400_000, 12, 12, 0.5, "f64", "uniform", "mixed", False),
 }
 DEFAULT = "gmm8m_l17_p12"
 METRIC = "Mpoints/s per FMM solve (plan+eval) at rel err <= 1e-6 vs FP64 direct"
@@ -269,7 +271,7 @@ def bench_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
 
     def solve():
-        plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True, tight=tight)
+        plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True, tight=tight, tc_m2l=args.tc_m2l)
         fmm.fmm_eval(plan, qd, pot, fld)
         return plan
 
@@ -292,7 +294,7 @@ def bench_ours(args, rank, world, local):
             flush.zero_()
             e0, e1, e2 = ev[k]
             e0.record(stream)
-            plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True, tight=tight)
+            plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, profile=True, tight=tight, tc_m2l=args.tc_m2l)
             e1.record(stream)
             fmm.fmm_eval(plan, qd, pot, fld)
             e2.record(stream)
@@ -324,11 +326,11 @@ def bench_ours(args, rank, world, local):
     poth = torch.empty(n, dtype=qh.dtype).pin_memory()
     fldh = torch.empty((n, 3), dtype=qh.dtype).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
-    fmm.fmm_destroy(fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None, tight=tight))
+    fmm.fmm_destroy(fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None, tight=tight, tc_m2l=args.tc_m2l))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        plan = fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None, tight=tight)
+        plan = fmm.fmm_plan(xh, levels, p, theta, prec=prec, allocator=None, tight=tight, tc_m2l=args.tc_m2l)
         fmm.fmm_eval(plan, qh, poth, fldh)
         fmm.fmm_destroy(plan)
     torch.cuda.synchronize()
@@ -381,6 +383,7 @@ def bench_ours(args, rank, world, local):
                    "positions": WORKLOADS[args.workload][5], "charges": WORKLOADS[args.workload][6],
                    "box_geometry": "tight (points' bounding box)" if tight else "cell",
                    "l2": "flushed between steps (512 MB write)",
+                   "m2l": "tensor cores" if args.tc_m2l else "CUDA cores",
                    "parallelism": f"replicas x{world}"},
         "eval_only": {"value": round(replica_throughput(n, world, t_eval), 4), "unit": "Mpoints/s",
                       "ms": round(t_eval, 3)},
@@ -398,7 +401,8 @@ def bench_ours(args, rank, world, local):
                                        else "DFMA FP64 pipe")),
                      "flops_basis": f"{FLOPS_PER_INTERACTION} flop per pair x exact pair count",
                      "time_basis": "stage CUDA events on the plan's stream, mean over the timed steps"},
-        "roofline_m2l": {"kernel": "k_m2l_rot_f32" if prec == fmm.FMM_PREC_MIXED else "k_m2l_rot_f64",
+        "roofline_m2l": {"kernel": ("k_m2l_tc" if args.tc_m2l else "k_m2l_rot_f32") if prec == fmm.FMM_PREC_MIXED
+                         else "k_m2l_rot_f64",
                          "bound": "alu", "achieved": round(m2l_achieved, 4), "peak": round(peak_tflops, 3),
                          "unit": "TFLOP/s", "frac": round(m2l_achieved / peak_tflops, 4),
                          "flops_basis": f"{m2l_flops_per_pair(p)} flop per weak pair (12 sum (n+1)^2, "
@@ -854,7 +858,7 @@ def profile_solve(args):
     x, q, levels, p, theta = make_inputs(args.workload, seed=0)
     prec = fmm.FMM_PREC_MIXED if (args.prec or WORKLOADS[args.workload][7]) == "mixed" else fmm.FMM_PREC_FP64
     xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
-    plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, tight=WORKLOADS[args.workload][8])
+    plan = fmm.fmm_plan(xd, levels, p, theta, prec=prec, tight=WORKLOADS[args.workload][8], tc_m2l=args.tc_m2l)
     pot, _ = fmm.fmm_eval(plan, qd)
     torch.cuda.synchronize()
     print(json.dumps({"workload": args.workload, "n": int(x.shape[0]), "checksum": float(pot.double().sum())}))
@@ -890,6 +894,8 @@ def main():
                     help="steps of the plain FP64 form timed as the comparator (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-m2l", action="store_true",
+                    help="mixed form: the tensor-core M2L (tcgen05) instead of the default CUDA-core kernel")
     ap.add_argument("--profile-solve", action="store_true",
                     help="run one solve of the workload and nothing else (for ncu launch lists and captures)")
     ap.add_argument("--systems", type=int, default=512, help="batch mode: number of systems")
